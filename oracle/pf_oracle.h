@@ -1,0 +1,119 @@
+/*
+ * pf_oracle.h -- CPU oracle of the LMM PF-SMC sampler (Algorithm 1 of
+ * Arnold, Calvetti, Somersalo, "Vectorized and Parallel Particle Filter SMC
+ * Parameter Estimation for Stiff ODEs").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, FP64 restatement of the
+ * method that the CUDA library is checked against.  Only the test-suite, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it.  It shares
+ * no code, header, table or constant generator with the CUDA library.
+ *
+ * Every function cites the section, step or equation of the paper it follows,
+ * or names the reading taken where the paper is silent (the readings are
+ * listed in the repository's design notes).
+ *
+ * Parity pins: every function here is pinned by a CPU test against a closed
+ * form, an invariant, a published known-answer vector or brute force; none is
+ * "parity unpinned".
+ */
+#ifndef PF_ORACLE_H
+#define PF_ORACLE_H
+#include <stdint.h>
+
+#define OR_DMAX 64
+#define OR_PMAX 8
+#define OR_MMAX 16
+#define OR_SMAX 4096
+
+/* problem ids */
+enum { OR_LINEAR2 = 1, OR_ROBERTSON = 2, OR_BRUSSELATOR = 3 };
+/* random-stream purposes (counter word 2, low byte) */
+enum { OR_RNG_INIT = 1, OR_RNG_THETA = 2, OR_RNG_INNOV = 3, OR_RNG_RESAMPLE = 4 };
+enum { OR_UNIFORM = 0, OR_LOGUNIFORM = 1 };          /* prior kinds          */
+enum { OR_SPACING_UNIFORM = 0, OR_SPACING_GEOMETRIC = 1 };
+enum { OR_HIST_CARRY = 0, OR_HIST_RESTART = 1 };
+enum { OR_TRANSFORM_LOG = 0, OR_TRANSFORM_IDENTITY = 1 };
+enum { OR_NOISE_ADDITIVE = 0, OR_NOISE_RELATIVE = 1 };
+enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_DEGENERATE = 5 };
+
+typedef struct {
+  int ode, d, p, m;
+  int64_t N;
+  int lmm;          /* 1 = BDF1 only, 2 = BDF2 (BDF1 on cold starts)        */
+  int newton_iters; /* fixed Newton count K                                 */
+  int spacing;      /* OR_SPACING_*                                          */
+  double dt;        /* uniform substep length                               */
+  int substeps;     /* geometric: substeps per interval                     */
+  double q0;        /* geometric: ratio used on an interval starting at t=0 */
+  int history;      /* OR_HIST_*                                             */
+  int transform;    /* OR_TRANSFORM_*                                        */
+  int obs_idx[OR_MMAX];
+  int noise;        /* OR_NOISE_*                                            */
+  double sigma[OR_MMAX];
+  double a;         /* Liu-West shrinkage factor, 0<a<1 (Step 2)            */
+  double kappa;     /* scale of the innovation covariance                   */
+  uint64_t seed;
+  uint32_t stream;  /* filter id, fourth counter word                       */
+  int prior_kind[OR_PMAX];
+  double prior_lo[OR_PMAX], prior_hi[OR_PMAX];
+  double x0[OR_DMAX];
+  double t0;        /* time of the initial state                            */
+} or_config;
+
+/* One substep of the LMM on the shared grid. */
+typedef struct {
+  int kind;         /* 1 = BDF1 (cold start), 2 = BDF2                      */
+  double h;         /* step length                                          */
+  double gamma;     /* x_{n+1} - rho1 x_n - rho2 x_{n-1} = gamma f(x_{n+1})  */
+  double rho1, rho2;
+  double pi0, pi1, pi2; /* predictor: x_p = pi0 x_n + pi1 x_{n-1} + pi2 x_{n-2} */
+  double mu;        /* local error = mu (x_{n+1} - x_p)                      */
+} or_substep;
+
+typedef struct or_filter or_filter;
+
+/* --- building blocks (each pinned on its own) --------------------------- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double or_uniform(uint64_t seed, uint32_t stream, int purpose, uint32_t n, uint32_t epoch, int k);
+double or_normal(uint64_t seed, uint32_t stream, int purpose, uint32_t n, uint32_t epoch, int k);
+void or_ode_f(int ode, const double* theta, const double* x, double* f);
+void or_ode_jac(int ode, const double* theta, const double* x, double* J);
+int or_ode_dims(int ode, int* d, int* p);
+int or_lu_solve(int n, const double* A, const double* b, double* x);
+int or_bdf_coefficients(int kind, double h0, double h1, double h2, or_substep* out);
+int or_build_substeps(const or_config* cfg, double t_prev, double t_next, int depth,
+                      double hprev1, double hprev2, or_substep* tab, int max_steps,
+                      int* depth_out);
+int or_propagate(int ode, int K, const double* theta, const or_substep* tab, int S,
+                 double* x, double* h1, double* h2, double* E);
+double or_loglik(const or_config* cfg, const double* y, const double* x);
+void or_resample_systematic(int64_t N, const double* c, double u, int32_t* idx);
+void or_cholesky_psd(int p, const double* C, double* L);
+void or_liu_west_shrink(int p, double a, const double* phi, const double* phibar, double* out);
+
+/* --- the filter (Algorithm 1) -------------------------------------------- */
+or_filter* or_create(const or_config* cfg);
+void or_destroy(or_filter* f);
+int or_init(or_filter* f);                                   /* Step 1      */
+int or_epoch(or_filter* f, double t_next, const double* y);  /* Steps 2-6   */
+/* stage entry points for parity injection */
+int or_epoch_substeps(or_filter* f, double t_next, or_substep* tab, int max_steps);
+int or_stage1(or_filter* f, const or_substep* tab, int S, const double* y);
+int or_cumulative(or_filter* f);
+double or_resample_u(const or_filter* f);
+int or_stage2(or_filter* f, const or_substep* tab, int S, const double* y, const int32_t* idx);
+int or_commit(or_filter* f, double t_next);
+/* state access, arrays are particle-major: x[n*d + i], phi[n*p + i] */
+void or_get_state(const or_filter* f, double* x, double* h1, double* h2, double* phi,
+                  double* lw);
+void or_set_state(or_filter* f, const double* x, const double* h1, const double* h2,
+                  const double* phi, const double* lw);
+void or_get_moments(const or_filter* f, double* phibar, double* C, double* xbar, double* ess);
+void or_set_moments(or_filter* f, const double* phibar, const double* C);
+void or_get_work(const or_filter* f, double* ll1, double* lg, double* c, int32_t* idx);
+void or_get_history(const or_filter* f, int* epoch, int* depth, double* t_prev,
+                    double* hprev1, double* hprev2);
+void or_set_history(or_filter* f, int epoch, int depth, double t_prev, double hprev1,
+                    double hprev2);
+int or_threads(void);
+#endif

@@ -1,0 +1,253 @@
+"""Seeded synthetic workloads for the LMM PF-SMC sampler.
+
+This module only describes problems and makes data: observation times, noisy
+observations of a reference trajectory, priors, the initial state and the
+sampler's settings.  It holds none of the sampler's arithmetic: the reference
+trajectory comes from a closed form (the linear system) or from SciPy's Radau
+integrator at tight tolerances (Robertson, Brusselator), and the observation
+noise from NumPy's seeded generator.  Both the CUDA library and the CPU oracle
+consume these inputs.
+
+Problems (the paper's own test systems, Sec. 2.1 and Sec. 4, lack constants or
+need a different solver, so three textbook stiff systems stand in, sized like
+the paper's workloads -- thousands to ~10^5 particles, 30-50 observations):
+
+* ``linear2``      x' = A x, A = [[-th1, th2], [0, -th2]], th* = (1, 1000),
+                   x1 observed with sigma = 0.01 at t = 0.1 k, k = 1..50,
+                   BDF2 with 20 uniform substeps per interval.
+* ``robertson``    Robertson kinetics, th* = (0.04, 3e7, 1e4), y1 and y3
+                   observed with 1% relative noise at 40 log-spaced times on
+                   [1e-4, 1e4], 50 geometric substeps per interval.
+* ``brusselator``  1D Brusselator on 32 interior points (d = 64),
+                   th* = (A, B, alpha) = (1, 3, 0.02), u observed at 8 points
+                   with sigma = 0.02 at t = k/3, k = 1..30, 20 uniform substeps.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+LINEAR2, ROBERTSON, BRUSSELATOR = 1, 2, 3
+UNIFORM, LOGUNIFORM = 0, 1
+SPACING_UNIFORM, SPACING_GEOMETRIC = 0, 1
+HIST_CARRY, HIST_RESTART = 0, 1
+TRANSFORM_LOG, TRANSFORM_IDENTITY = 0, 1
+NOISE_ADDITIVE, NOISE_RELATIVE = 0, 1
+
+# Fixed Newton count per problem (no early exit, so every particle costs the
+# same).  Each is the smallest K whose result agrees with the fully converged
+# Newton solution to 1e-12 relative along the reference trajectory and on the
+# particles of a filter run; the test-suite re-checks the reference trajectory.
+NEWTON_ITERS = {LINEAR2: 1, ROBERTSON: 2, BRUSSELATOR: 3}
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    ode: int
+    d: int
+    p: int
+    N: int
+    lmm: int
+    newton_iters: int
+    spacing: int
+    dt: float
+    substeps: int
+    q0: float
+    history: int
+    transform: int
+    obs_idx: list
+    noise: int
+    sigma: list
+    a: float
+    kappa: float
+    seed: int
+    stream: int
+    prior_kind: list
+    prior_lo: list
+    prior_hi: list
+    x0: np.ndarray
+    t0: float
+    theta_true: np.ndarray
+    t_obs: np.ndarray          # (T,)
+    y_obs: np.ndarray          # (T, m)
+    x_true: np.ndarray         # (T, d) reference states at t_obs
+
+    @property
+    def m(self) -> int:
+        return len(self.obs_idx)
+
+    @property
+    def T(self) -> int:
+        return len(self.t_obs)
+
+    def substeps_per_interval(self, k: int) -> int:
+        """Substep count of observation interval k (0-based)."""
+        if self.spacing == SPACING_GEOMETRIC:
+            return self.substeps
+        t0 = self.t0 if k == 0 else self.t_obs[k - 1]
+        return int(round((self.t_obs[k] - t0) / self.dt))
+
+    def particle_steps(self, k: int) -> int:
+        """particle-LMM-steps of epoch k: two propagations (Steps 2 and 4) of
+        every particle over the interval's substeps."""
+        return 2 * self.substeps_per_interval(k) * self.N
+
+    def with_(self, **kw) -> "Workload":
+        return dataclasses.replace(self, **kw)
+
+
+def _noise(rng, x_obs, sigma, relative):
+    eps = rng.standard_normal(x_obs.shape)
+    if relative:
+        return x_obs * (1.0 + np.asarray(sigma)[None, :] * eps)
+    return x_obs + np.asarray(sigma)[None, :] * eps
+
+
+# ---------------------------------------------------------------- linear2
+def linear2_exact(theta, x0, t):
+    """Closed-form solution of x' = A x, A = [[-th1, th2], [0, -th2]]."""
+    th1, th2 = float(theta[0]), float(theta[1])
+    t = np.asarray(t, dtype=np.float64)
+    x2 = x0[1] * np.exp(-th2 * t)
+    x1 = x0[0] * np.exp(-th1 * t) + th2 * x0[1] * (np.exp(-th2 * t) - np.exp(-th1 * t)) / (th1 - th2)
+    return np.stack([x1, x2], axis=-1)
+
+
+def linear2(N: int = 2000, T: int = 50, seed: int = 0) -> Workload:
+    theta = np.array([1.0, 1000.0])
+    x0 = np.array([1.0, 1.0])
+    t_obs = 0.1 * np.arange(1, T + 1)
+    x_true = linear2_exact(theta, x0, t_obs)
+    obs_idx, sigma = [0], [0.01]
+    rng = np.random.default_rng([seed, 0xDA7A, LINEAR2])
+    y = _noise(rng, x_true[:, obs_idx], sigma, False)
+    return Workload(
+        name="linear2", ode=LINEAR2, d=2, p=2, N=N, lmm=2, newton_iters=NEWTON_ITERS[LINEAR2],
+        spacing=SPACING_UNIFORM, dt=0.005, substeps=20, q0=0.0,
+        history=HIST_CARRY, transform=TRANSFORM_LOG, obs_idx=obs_idx,
+        noise=NOISE_ADDITIVE, sigma=sigma, a=0.98, kappa=1.0, seed=seed, stream=0,
+        prior_kind=[LOGUNIFORM, LOGUNIFORM], prior_lo=[0.1, 100.0], prior_hi=[10.0, 1e4],
+        x0=x0, t0=0.0, theta_true=theta, t_obs=t_obs, y_obs=y, x_true=x_true)
+
+
+# -------------------------------------------------------------- robertson
+def robertson_rhs(theta):
+    k1, k2, k3 = theta
+
+    def f(t, y):
+        return np.array([-k1 * y[0] + k3 * y[1] * y[2],
+                         k1 * y[0] - k3 * y[1] * y[2] - k2 * y[1] ** 2,
+                         k2 * y[1] ** 2])
+
+    def jac(t, y):
+        return np.array([[-k1, k3 * y[2], k3 * y[1]],
+                         [k1, -k3 * y[2] - 2 * k2 * y[1], -k3 * y[1]],
+                         [0.0, 2 * k2 * y[1], 0.0]])
+    return f, jac
+
+
+def robertson_times(T: int = 40):
+    k = np.arange(1, T + 1)
+    return 10.0 ** (-4.0 + 8.0 * (k - 1) / 39.0)
+
+
+def robertson(N: int = 131072, T: int = 40, seed: int = 0) -> Workload:
+    from scipy.integrate import solve_ivp
+    theta = np.array([0.04, 3e7, 1e4])
+    x0 = np.array([1.0, 0.0, 0.0])
+    t_all = robertson_times(40)
+    f, jac = robertson_rhs(theta)
+    sol = solve_ivp(f, (0.0, t_all[-1]), x0, method="Radau", t_eval=t_all, rtol=1e-11,
+                    atol=1e-18, jac=jac)
+    x_true = sol.y.T[:T]
+    t_obs = t_all[:T]
+    obs_idx, sigma = [0, 2], [0.01, 0.01]
+    rng = np.random.default_rng([seed, 0xDA7A, ROBERTSON])
+    y = _noise(rng, x_true[:, obs_idx], sigma, True)
+    S = 50
+    q0 = 10.0 ** (8.0 / (39.0 * S))   # the same ratio as the later intervals
+    return Workload(
+        name="robertson", ode=ROBERTSON, d=3, p=3, N=N, lmm=2, newton_iters=NEWTON_ITERS[ROBERTSON],
+        spacing=SPACING_GEOMETRIC, dt=0.0, substeps=S, q0=q0,
+        history=HIST_CARRY, transform=TRANSFORM_LOG, obs_idx=obs_idx,
+        noise=NOISE_RELATIVE, sigma=sigma, a=0.98, kappa=1.0, seed=seed, stream=0,
+        prior_kind=[LOGUNIFORM] * 3, prior_lo=list(theta / 10.0), prior_hi=list(theta * 10.0),
+        x0=x0, t0=0.0, theta_true=theta, t_obs=t_obs, y_obs=y, x_true=x_true)
+
+
+# ------------------------------------------------------------ brusselator
+BR_POINTS = 32
+
+
+def brusselator_rhs(theta):
+    A, B, alpha = theta
+    D = alpha * 33.0 ** 2
+
+    def f(t, x):
+        u, v = x[0::2], x[1::2]
+        up = np.concatenate([[1.0], u, [1.0]])
+        vp = np.concatenate([[3.0], v, [3.0]])
+        du = A + u * u * v - (B + 1) * u + D * (up[:-2] - 2 * u + up[2:])
+        dv = B * u - u * u * v + D * (vp[:-2] - 2 * v + vp[2:])
+        out = np.empty_like(x)
+        out[0::2], out[1::2] = du, dv
+        return out
+
+    def jac(t, x):
+        u, v = x[0::2], x[1::2]
+        n = 2 * BR_POINTS
+        J = np.zeros((n, n))
+        for i in range(BR_POINTS):
+            a, b = 2 * i, 2 * i + 1
+            J[a, a] = 2 * u[i] * v[i] - (B + 1) - 2 * D
+            J[a, b] = u[i] ** 2
+            J[b, a] = B - 2 * u[i] * v[i]
+            J[b, b] = -u[i] ** 2 - 2 * D
+            if i > 0:
+                J[a, a - 2] = D
+                J[b, b - 2] = D
+            if i < BR_POINTS - 1:
+                J[a, a + 2] = D
+                J[b, b + 2] = D
+        return J
+    return f, jac
+
+
+def brusselator_x0():
+    xi = np.arange(1, BR_POINTS + 1) / 33.0
+    x0 = np.empty(2 * BR_POINTS)
+    x0[0::2] = 1.0 + np.sin(2 * math.pi * xi)
+    x0[1::2] = 3.0
+    return x0
+
+
+def brusselator(N: int = 65536, T: int = 30, seed: int = 0) -> Workload:
+    from scipy.integrate import solve_ivp
+    theta = np.array([1.0, 3.0, 0.02])
+    x0 = brusselator_x0()
+    t_obs = np.arange(1, T + 1) / 3.0
+    f, jac = brusselator_rhs(theta)
+    sol = solve_ivp(f, (0.0, t_obs[-1]), x0, method="Radau", t_eval=t_obs, rtol=1e-11,
+                    atol=1e-12, jac=jac)
+    x_true = sol.y.T
+    obs_idx = [2 * i for i in range(2, 32, 4)]
+    sigma = [0.02] * len(obs_idx)
+    rng = np.random.default_rng([seed, 0xDA7A, BRUSSELATOR])
+    y = _noise(rng, x_true[:, obs_idx], sigma, False)
+    return Workload(
+        name="brusselator", ode=BRUSSELATOR, d=64, p=3, N=N, lmm=2, newton_iters=NEWTON_ITERS[BRUSSELATOR],
+        spacing=SPACING_UNIFORM, dt=1.0 / 60.0, substeps=20, q0=0.0,
+        history=HIST_CARRY, transform=TRANSFORM_LOG, obs_idx=obs_idx,
+        noise=NOISE_ADDITIVE, sigma=sigma, a=0.98, kappa=1.0, seed=seed, stream=0,
+        prior_kind=[UNIFORM] * 3, prior_lo=list(0.5 * theta), prior_hi=list(1.5 * theta),
+        x0=x0, t0=0.0, theta_true=theta, t_obs=t_obs, y_obs=y, x_true=x_true)
+
+
+BY_NAME = {"linear2": linear2, "robertson": robertson, "brusselator": brusselator}
+
+
+def get(name: str, **kw) -> Workload:
+    return BY_NAME[name](**kw)
