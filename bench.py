@@ -1,0 +1,361 @@
+"""Benchmark of the GB300 LMM PF-SMC sampler (particle-LMM-steps/s).
+
+One step = one epoch of Algorithm 1 (Steps 2-6: shrink, propagate, first-stage
+weights, systematic resampling, proliferation, repropagation with the
+local-error innovation, reweighting, moments) over the Robertson workload:
+N = 131072 particles, d = 3, p = 3, 50 geometric BDF2 substeps per interval,
+K = 2 Newton iterations, FP64.  One particle-LMM-step is one implicit substep
+(with its Newton iterations) of one particle; an epoch is 2 * S * N of them.
+
+value     device-resident inputs (the whole observation series uploaded once),
+          CUDA-event time of each step on the filter's stream, L2 flushed
+          (256 MiB write) before every step, summed over K steps.
+e2e       the same metric through the C ABI with host buffers: pf_assimilate
+          (host y_k, parameter upload) + pf_estimates (host read-back), wall
+          time per step.
+roofline  the dominant kernel (stage 2) against the FP64 ALU peak.
+cpu_baseline / --impl reference: the CPU oracle on the host cores.
+
+Multi-GPU (torchrun): independent replicas (one filter per rank, different
+seeds); value = all ranks' particle-steps / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-LMM-steps/s"
+UNIT = "particle-steps/s"
+# FP64 ALU peak of one GB300: 2 FP64 FMA lanes per clock per SM (the
+# sustained peak ncu reports for sm__sass_thread_inst_executed_op_dfma_pred_on
+# on this part) x 152 SMs x 2070 MHz maximum SM clock x 2 flops per FMA
+# = 1.259 TFLOP/s, the nominal GB300 FP64 rate.
+FP64_PEAK_TFLOPS = 2.0 * 152 * 2.070e9 * 2 / 1e12
+
+# Algorithmic FP64 flops (FMA = 2) of one BDF2 substep of one particle in the
+# stage-2 kernel: predictor 5d, history combination 3d, Milne estimate 4d,
+# per-substep constants, and K Newton iterations.
+STAGE2_FLOPS_PER_SUBSTEP = {
+    "robertson": lambda K: 15 + 9 + 12 + 8 + 42 * K,
+    "linear2": lambda K: 10 + 6 + 8 + 20 + 14 * K,
+}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1
+    import torch.distributed as dist
+    backend = "nccl" if os.environ.get("PF_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+    dist.init_process_group(backend)
+    return dist, dist.get_rank(), dist.get_world_size()
+
+
+def reduce_times(dist, total_ms, steps_done, device=None):
+    """Max of the per-rank times and sum of the per-rank particle-steps."""
+    if dist is None:
+        return total_ms, steps_done
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    s = torch.tensor([float(steps_done)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(s.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(w, seconds=12.0, max_epochs=None, N=None):
+    """The oracle as it stands on the host cores: epochs of the same workload
+    until `seconds` of work; returns (steps/s, cores, sample text)."""
+    import oracle
+    oracle.build()
+    o = oracle.Filter(w, N=N)
+    o.init()
+    n = o.N
+    steps, spent, k = 0, 0.0, 0
+    limit = max_epochs or w.T
+    while k < limit and (spent < seconds or k < 2):
+        t0 = time.perf_counter()
+        rc = o.epoch(w.t_obs[k], w.y_obs[k])
+        spent += time.perf_counter() - t0
+        if rc != oracle.OK:
+            break
+        steps += 2 * w.substeps_per_interval(k) * n
+        k += 1
+    return steps / spent, oracle.threads(), f"first {k} epochs of the workload at N={n} ({spent:.1f} s)"
+
+
+def run_reference(args, w):
+    dist, rank, world = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    n_ref = min(w.N, args.ref_particles)
+    o = oracle.Filter(w, N=n_ref)
+    o.init()
+    k = 0
+    for _ in range(args.warmup):
+        o.epoch(w.t_obs[k], w.y_obs[k])
+        k += 1
+    total, steps = 0.0, 0
+    for _ in range(args.steps):
+        if k >= w.T:
+            o.init()
+            k = 0
+        t0 = time.perf_counter()
+        rc = o.epoch(w.t_obs[k], w.y_obs[k])
+        total += time.perf_counter() - t0
+        if rc != oracle.OK:
+            raise RuntimeError(f"oracle epoch failed: {rc}")
+        steps += 2 * w.substeps_per_interval(k) * n_ref
+        k += 1
+    value = steps / total
+    sample = f"one epoch per step at N={n_ref} of the N={w.N} workload"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(w):
+    return {"workload": f"{w.name}: N={w.N} d={w.d} p={w.p} m={w.m} S={w.substeps} "
+                        f"{'geometric' if w.spacing else 'uniform'} substeps, T={w.T}, BDF2, "
+                        f"K={w.newton_iters} Newton, FP64",
+            "N": w.N, "substeps": w.substeps_per_interval(1), "newton_iters": w.newton_iters,
+            "epochs_per_step": 1, "l2": "flushed before every step (256 MiB write)",
+            "parallelism": "replicas"}
+
+
+def run_ours(args, w):
+    import torch
+    dist, rank, world = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_1411_1702_gb300 import build as B
+    B.build()
+    from paper_1411_1702_gb300 import pf
+    # a dedicated stream: the library's kernels, the L2 flush and the timing
+    # events are all ordered on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    if args.profile:
+        return run_profile(args, w, pf, stream)
+    g = pf.Filter.from_workload(w, stream=stream.cuda_stream, seed=w.seed + rank, filter_id=rank,
+                                timing=True)
+    g.pf_load_observations(w.t_obs, w.y_obs)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    k = 0
+
+    def next_epoch():
+        nonlocal k
+        if k >= w.T:
+            g.pf_reset()
+            k = 0
+        g.pf_run(k, k + 1)
+        k += 1
+        return k - 1
+
+    for _ in range(args.warmup):
+        next_epoch()
+    g.pf_synchronize()
+    g.pf_kernel_times()  # drop the warm-up timings
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    steps_done = 0
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for s in range(args.steps):
+            if k >= w.T:
+                g.pf_reset()
+                k = 0
+            flush.zero_()
+            starts[s].record(stream)
+            kk = next_epoch()
+            ends[s].record(stream)
+            steps_done += w.particle_steps(kk)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    g.pf_synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    ktimes = g.pf_kernel_times()
+    total_max, steps_all = reduce_times(dist, total_ms, steps_done, device="cuda")
+    value = steps_all / (total_max * 1e-3)
+
+    # e2e through the C ABI with host buffers
+    e2e_steps = min(args.steps, args.e2e_steps)
+    g.pf_reset()
+    ke, wall, e2e_done = 0, 0.0, 0
+    st0 = g.pf_stats()
+    for _ in range(e2e_steps):
+        if ke >= w.T:
+            g.pf_reset()
+            ke = 0
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.pf_assimilate(w.t_obs[ke], w.y_obs[ke])
+        g.pf_estimates()
+        wall += time.perf_counter() - t0
+        e2e_done += w.particle_steps(ke)
+        ke += 1
+    st1 = g.pf_stats()
+    wall_max, e2e_all = reduce_times(dist, wall * 1e3, e2e_done, device="cuda")
+    e2e_value = e2e_all / (wall_max * 1e-3)
+    # only the data of the steps themselves (the resets in between are not steps)
+    h2d = (st1["h2d_bytes"] - st0["h2d_bytes"]) / e2e_steps
+    d2h = (st1["d2h_bytes"] - st0["d2h_bytes"]) / e2e_steps
+
+    if rank != 0:
+        g.close()
+        return 0
+    # roofline of the dominant kernel: stage 2 (repropagation)
+    ms2, n2 = ktimes["stage2"]
+    S = w.substeps_per_interval(1)
+    flops = STAGE2_FLOPS_PER_SUBSTEP[w.name](w.newton_iters) * S * w.N
+    achieved = flops / (ms2 / n2 * 1e-3) / 1e12 if n2 else None
+    shares = {name: round(ms / max(1e-12, sum(v[0] for v in ktimes.values())), 4)
+              for name, (ms, _) in ktimes.items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(w), "clocks": clocks.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(round(h2d)),
+                "d2h_bytes_per_step": int(round(d2h))},
+        "gpu_launches": 6 * args.steps,
+        "roofline": {"bound": "alu", "kernel": "k_stage2<Robertson>", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                     "traffic": None,
+                     "peak_source": "2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (nominal GB300 FP64)"},
+        "kernel_share": shares,
+        "kernel_ms_per_step": {k2: v[0] / max(1, v[1]) for k2, v in ktimes.items()},
+    }
+    if not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(w, seconds=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    g.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_profile(args, w, pf, stream):
+    """Plain launcher for profilers: Step 1, then warmup + steps epochs of the
+    loaded series on one stream, no timing, no CPU work.  Launch order: k_init,
+    k_moments, then per epoch k_stage1, k_scan_tile, k_scan_add, k_resample,
+    k_stage2, k_moments."""
+    g = pf.Filter.from_workload(w, stream=stream.cuda_stream)
+    g.pf_load_observations(w.t_obs, w.y_obs)
+    n = min(args.warmup + args.steps, w.T)
+    for k in range(n):
+        g.pf_run(k, k + 1)
+    g.pf_synchronize()
+    g.close()
+    print(json.dumps({"profile_run": w.name, "N": w.N, "epochs": n}), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="robertson", choices=["robertson", "linear2"])
+    ap.add_argument("--e2e-steps", type=int, default=80)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-particles", type=int, default=16384)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only launch the epochs (for ncu); prints no measurement")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    from paper_1411_1702_gb300 import workloads as W
+    w = W.get(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,229 @@
+/*
+ * pf.h -- C ABI of the GB300 (sm_103a) LMM PF-SMC sampler.
+ *
+ * The library runs the per-observation epoch of Algorithm 1 ("LMM PF-SMC
+ * Sampler") of Arnold, Calvetti, Somersalo, "Vectorized and Parallel Particle
+ * Filter SMC Parameter Estimation for Stiff ODEs": a Liu-West auxiliary
+ * particle filter over (x, theta) whose particles are propagated by an implicit
+ * linear multistep method (BDF2, BDF1 on cold starts) with a full Newton solve
+ * per particle and per substep, and whose innovation variance comes from the
+ * LMM's local error estimate (Step 4b).  All arithmetic is FP64 and runs in
+ * hand-written CUDA kernels; nothing falls back to the CPU.
+ *
+ * Conventions
+ *  - Every entry point returns a pf_status.  No C++ exception crosses the ABI.
+ *  - Host pointers are owned by the caller and only read or written during the
+ *    call; the library copies what it keeps.  Device memory of a filter is
+ *    owned by the filter (allocated in pf_create, freed in pf_destroy).
+ *  - One filter must not be used from two host threads at once.
+ *  - Epochs are transactional: a failed epoch (degenerate weights, CUDA error)
+ *    leaves the committed ensemble, moments and history unchanged.
+ *  - Indices are 0-based.  Matrices are row-major.  Host ensemble arrays are
+ *    particle-major: x[n*d + i], phi[n*p + i].
+ *  - Parameters live in a working space phi: phi = log(theta) with
+ *    PF_TRANSFORM_LOG (default), phi = theta with PF_TRANSFORM_IDENTITY.
+ *    Means and covariances are reported in phi space.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pf_filter pf_filter; /* opaque, library-owned */
+
+typedef enum {
+  PF_OK = 0,
+  PF_ERR_INVALID_ARG = 1, /* argument out of range or inconsistent          */
+  PF_ERR_OOM = 2,         /* device or pinned-host allocation failed        */
+  PF_ERR_BUDGET = 3,      /* request exceeds a stated size limit            */
+  PF_ERR_CUDA = 4,        /* a CUDA runtime call failed                     */
+  PF_ERR_DEGENERATE = 5,  /* every weight of the epoch is zero or not finite */
+  PF_ERR_NUMERIC = 6,     /* a non-finite moment                            */
+  PF_ERR_TIMEOUT = 7,     /* reserved: a bounded device wait gave up        */
+  PF_ERR_STATE = 8        /* call out of order (e.g. no observation loaded) */
+} pf_status;
+
+/* Test problems x' = f(x; theta) (the paper's Sec. 2.1 and 4 systems lack
+ * constants; these stiff systems stand in for them):
+ *  PF_ODE_LINEAR2        d=2, p=2: x' = A x, A = [[-th1, th2], [0, -th2]].
+ *  PF_ODE_ROBERTSON      d=3, p=3: Robertson kinetics, theta = (k1, k2, k3).
+ *  PF_ODE_BRUSSELATOR1D  d=64, p=3: 1D Brusselator on 32 interior points,
+ *                        Dirichlet u=1, v=3, theta = (A, B, alpha), state
+ *                        interleaved (u_0, v_0, u_1, v_1, ...). */
+typedef enum { PF_ODE_LINEAR2 = 1, PF_ODE_ROBERTSON = 2, PF_ODE_BRUSSELATOR1D = 3 } pf_ode;
+
+/* Implicit LMM of Psi (Sec. 2.1): BDF1 = backward Euler; BDF2 = variable-step
+ * BDF2, with BDF1 on the first two substeps after a cold start. */
+typedef enum { PF_LMM_BDF1 = 1, PF_LMM_BDF2 = 2 } pf_lmm;
+
+enum { PF_PRIOR_UNIFORM = 0, PF_PRIOR_LOGUNIFORM = 1 };
+enum { PF_SPACING_UNIFORM = 0, PF_SPACING_GEOMETRIC = 1 };
+enum { PF_HISTORY_CARRY = 0, PF_HISTORY_RESTART = 1 };
+enum { PF_TRANSFORM_LOG = 0, PF_TRANSFORM_IDENTITY = 1 };
+enum { PF_NOISE_ADDITIVE = 0, PF_NOISE_RELATIVE = 1 };
+
+/* Size limits of this build. */
+#define PF_MAX_OBS 16         /* m                                    */
+#define PF_MAX_SUBSTEPS 640   /* substeps per observation interval    */
+#define PF_MAX_PARTICLES (1LL << 30)
+
+/* Prior pi_0(x_0, theta) of Step 1: x_0 is known (a point mass at x0), and
+ * theta_i is uniform or log-uniform on [lo_i, hi_i], independently. */
+typedef struct {
+  int p;              /* number of parameters, must match the ODE        */
+  const int* kind;    /* p entries, PF_PRIOR_*                           */
+  const double* lo;   /* p entries, 0 < lo <= hi for log-uniform         */
+  const double* hi;   /* p entries                                       */
+  int d;              /* state dimension, must match the ODE             */
+  const double* x0;   /* d entries: the initial state                    */
+  double t0;          /* its time                                        */
+} pf_prior;
+
+/* Sampler settings.  Zero-initialise, then set what you need. */
+typedef struct {
+  double a;           /* Liu-West shrinkage, 0 < a <= 1 (Step 2)          */
+  int newton_iters;   /* fixed Newton count K >= 1 per substep            */
+  int spacing;        /* PF_SPACING_*                                     */
+  int substeps;       /* geometric spacing: substeps per interval         */
+  double q0;          /* geometric spacing: step ratio on an interval that
+                         starts at t = 0 (> 1)                           */
+  int history;        /* PF_HISTORY_CARRY: LMM history carried across
+                         observations (translated by the innovation);
+                         PF_HISTORY_RESTART: cold start every interval    */
+  int transform;      /* PF_TRANSFORM_*                                   */
+  int m;              /* observed components per epoch, 0 < m <= 16      */
+  const int* obs_idx; /* m state indices                                  */
+  int noise;          /* PF_NOISE_ADDITIVE: sd sigma_i; PF_NOISE_RELATIVE:
+                         sd sigma_i * |y_i| (floored at 1e-300)          */
+  const double* sigma;/* m entries                                       */
+  double kappa;       /* Gamma = kappa * diag(sum of squared local errors) */
+  uint64_t seed;      /* Philox4x32-10 key                                */
+  uint32_t filter_id; /* fourth Philox counter word                       */
+  void* stream;       /* cudaStream_t to run on; NULL = a stream the filter
+                         creates and owns                                  */
+  int timing;         /* nonzero: record CUDA events around every kernel of
+                         every epoch (read them with pf_kernel_times)      */
+} pf_options;
+
+/* Create a filter and run Step 1 of Algorithm 1 (prior draws, w = 1/N,
+ * weighted mean and covariance).  dt is the uniform substep length (the
+ * interval length must be an integer multiple of it to 1e-9 relative); it is
+ * ignored with geometric spacing.  Allocates about
+ * 8 * N * (2 * (3d + p + 1) + 4) bytes of device memory.  Errors:
+ * INVALID_ARG (dimensions do not match the ODE, N < 1 or > PF_MAX_PARTICLES,
+ * bad prior or options), OOM, CUDA.  *out is NULL on error. */
+pf_status pf_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
+                    const pf_prior* prior, const pf_options* opt, pf_filter** out);
+
+/* Assimilate one observation y_k (m host doubles) at time t_k > the previous
+ * observation time: Steps 2-6 of Algorithm 1 (shrink, propagate, first-stage
+ * weights, systematic resampling, proliferation, repropagation with the
+ * local-error innovation, reweighting, moments).  Synchronous: returns after
+ * the epoch is committed.  Errors: INVALID_ARG (non-finite y, bad t_k, substep
+ * count out of range), DEGENERATE (all first- or second-stage weights zero;
+ * nothing committed), CUDA. */
+pf_status pf_assimilate(pf_filter* f, double t_k, const double* y_k);
+
+/* Weighted estimates of the committed ensemble (Step 6): theta_bar (p, in phi
+ * space), C (p*p, phi space, weights summing to one, no Bessel factor) and the
+ * weighted mean state x_bar (d).  Any pointer may be NULL.  Synchronous. */
+pf_status pf_estimates(const pf_filter* f, double* theta_bar, double* C, double* x_bar);
+
+typedef struct {
+  int64_t epochs;        /* committed epochs                               */
+  double ess;            /* 1 / sum w^2 of the committed weights           */
+  double log_weight_sum; /* log sum of the unnormalised Step-5 weights     */
+  int64_t unique_parents;/* distinct indices of the last resampling        */
+  int64_t nonfinite;     /* particles given zero weight in the last epoch  */
+  double theta_mean[8];  /* weighted mean of theta (model space)           */
+  double last_epoch_ms;  /* device time of the last synchronous epoch      */
+  int64_t h2d_bytes;     /* host-to-device bytes copied since creation     */
+  int64_t d2h_bytes;     /* device-to-host bytes copied since creation     */
+} pf_stats_t;
+pf_status pf_stats(const pf_filter* f, pf_stats_t* out);
+
+/* Per-kernel device time of the epochs run since the last call (requires
+ * pf_options.timing).  Slot k of ms[] and launches[] (n entries, n >= 6):
+ * 0 stage 1 (shrink, propagate, first-stage weights), 1 scan tiles, 2 scan
+ * offsets, 3 systematic resampling, 4 stage 2 (proliferate, repropagate,
+ * innovation, reweight), 5 moments and commit.  Waits for the filter's stream,
+ * then resets the accumulators.  Errors: INVALID_ARG (n < 6), STATE (timing
+ * off), CUDA. */
+#define PF_KERNEL_SLOTS 6
+pf_status pf_kernel_times(pf_filter* f, double* ms, int64_t* launches, int n);
+
+/* Text of the last error on this filter (or on this thread when f is NULL).
+ * The pointer stays valid until the next call on the same filter/thread. */
+const char* pf_last_error(const pf_filter* f);
+
+/* Free the filter's device and host memory.  NULL is a no-op. */
+void pf_destroy(pf_filter* f);
+
+/* ---- device-resident observation series ---------------------------------
+ * Upload T observations (times t[T], data y[T*m], row k = observation k) and
+ * precompute every interval's substep table, so that pf_run can advance the
+ * filter without any host-to-device traffic.  The series continues from the
+ * filter's current time.  Errors: INVALID_ARG, OOM, CUDA. */
+pf_status pf_load_observations(pf_filter* f, int T, const double* t, const double* y);
+
+/* Enqueue epochs k0..k1-1 of the loaded series on the filter's stream and
+ * return without waiting.  Epoch k0 must be the next unassimilated one.  A
+ * failing epoch stops the rest (they become no-ops on the device).  Errors:
+ * STATE (no series, or k0 out of order), INVALID_ARG, CUDA. */
+pf_status pf_run(pf_filter* f, int k0, int k1);
+
+/* Wait for enqueued work.  Returns the status of the first failed epoch (the
+ * filter then rolls back to the last committed epoch), else PF_OK. */
+pf_status pf_synchronize(pf_filter* f);
+
+/* Redo Step 1 into the existing buffers (no allocation); the loaded series
+ * restarts at observation 0. */
+pf_status pf_reset(pf_filter* f);
+
+/* ---- checkpoint and inspection ------------------------------------------
+ * Copy the committed ensemble to or from host memory: x, h1, h2 (N*d each:
+ * x_n and the two previous LMM substep states), phi (N*p) and the normalised
+ * log weights logw (N).  Any pointer may be NULL (not copied).  Setting the
+ * ensemble does not recompute the moments; use pf_set_moments. */
+pf_status pf_get_ensemble(const pf_filter* f, double* x, double* h1, double* h2, double* phi,
+                          double* logw);
+pf_status pf_set_ensemble(pf_filter* f, const double* x, const double* h1, const double* h2,
+                          const double* phi, const double* logw);
+pf_status pf_set_moments(pf_filter* f, const double* phibar, const double* C);
+
+/* Work arrays of the last epoch (N each): first-stage log-likelihoods, log
+ * fitness weights, cumulative fitness weights c_k and resampled indices. */
+pf_status pf_get_work(const pf_filter* f, double* loglik1, double* log_g, double* cumulative,
+                      int32_t* idx);
+
+/* LMM history bookkeeping: committed epoch count, history depth (0-2 stored
+ * past points), time of the last observation and the last two step lengths. */
+pf_status pf_get_history(const pf_filter* f, int64_t* epochs, int* depth, double* t_prev,
+                         double* hprev1, double* hprev2);
+pf_status pf_set_history(pf_filter* f, int64_t epochs, int depth, double t_prev, double hprev1,
+                         double hprev2);
+
+/* ---- host-only helper (no GPU needed) -----------------------------------
+ * Substep table of one interval (t_prev, t_next] for the given history state,
+ * as the filter builds it.  Per substep i, row i of coef (9 doubles):
+ * kind, h, gamma, rho1, rho2, pi0, pi1, pi2, mu, with
+ * x_{n+1} - rho1 x_n - rho2 x_{n-1} = gamma f(x_{n+1}),
+ * predictor pi0 x_n + pi1 x_{n-1} + pi2 x_{n-2}, Milne factor mu.
+ * Returns the substep count S (> 0) or -1; *depth_out gets the history depth
+ * after the interval.  lmm, spacing, dt, substeps, q0 as in pf_create. */
+int pf_substep_table(int lmm, int spacing, double dt, int substeps, double q0, double t_prev,
+                     double t_next, int depth, double hprev1, double hprev2, double* coef,
+                     int max_steps, int* depth_out);
+
+/* Library version string. */
+const char* pf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

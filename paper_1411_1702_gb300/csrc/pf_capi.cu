@@ -1,0 +1,691 @@
+// pf_capi.cu -- the C ABI of include/pf.h: argument checks, device memory,
+// the host side of each epoch (substep table, parameter upload, launch,
+// commit check) and the checkpoint/inspection calls.  All of the method's
+// arithmetic on particles runs in the kernels of pf_kernels.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pf_kernels.h"
+
+using namespace pfg;
+
+namespace {
+
+struct HistoryState {
+  int64_t epochs;
+  int depth;
+  double t_prev, hprev1, hprev2;
+};
+
+thread_local std::string g_thread_error;
+
+}  // namespace
+
+struct pf_filter {
+  // configuration
+  int ode, d, p, m, lmm, K, spacing, substeps, history, transform, noise;
+  double dt, q0, a, kappa;
+  uint64_t seed;
+  uint32_t filter_id;
+  int64_t N;
+  int obs[kMMax];
+  double sigma[kMMax];
+  int prior_kind[kPMax];
+  double prior_lo[kPMax], prior_hi[kPMax];
+  double x0[kDMax];
+  double t0;
+  // CUDA resources
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* dmem = nullptr;
+  size_t dbytes = 0;
+  FilterDev fd{};
+  EpochParams* ep_dev = nullptr;    // online parameter slot
+  EpochParams* ep_host = nullptr;   // pinned staging
+  Ctrl* ctrl_host = nullptr;        // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // committed history (host view)
+  HistoryState hist{};
+  // device-resident observation series
+  EpochParams* series_dev = nullptr;
+  int series_T = 0;
+  int series_next = 0;
+  std::vector<int> series_S;
+  std::vector<HistoryState> series_after;  // history after epoch k of the series
+  HistoryState series_start{};
+  // per-kernel timing (pf_options.timing)
+  bool timing = false;
+  std::vector<cudaEvent_t*> mark_free;     // sets of kEpochKernels + 1 events
+  std::vector<cudaEvent_t*> mark_pending;  // recorded, not yet read
+  double kernel_ms[kEpochKernels] = {0};
+  int64_t kernel_launches[kEpochKernels] = {0};
+  // bookkeeping
+  double last_ms = 0.0;
+  int64_t h2d_bytes = 0, d2h_bytes = 0;
+  std::string err;
+};
+
+// A set of timing events for one epoch, or NULL when timing is off.
+static cudaEvent_t* take_marks(pf_filter* f) {
+  if (!f->timing) return nullptr;
+  if (!f->mark_free.empty()) {
+    cudaEvent_t* m = f->mark_free.back();
+    f->mark_free.pop_back();
+    f->mark_pending.push_back(m);
+    return m;
+  }
+  cudaEvent_t* m = new cudaEvent_t[kEpochKernels + 1];
+  for (int i = 0; i <= kEpochKernels; ++i) {
+    if (cudaEventCreate(&m[i]) != cudaSuccess) {
+      for (int j = 0; j < i; ++j) cudaEventDestroy(m[j]);
+      delete[] m;
+      return nullptr;
+    }
+  }
+  f->mark_pending.push_back(m);
+  return m;
+}
+
+static void free_marks(pf_filter* f) {
+  for (auto* v : {&f->mark_free, &f->mark_pending}) {
+    for (cudaEvent_t* m : *v) {
+      for (int i = 0; i <= kEpochKernels; ++i) cudaEventDestroy(m[i]);
+      delete[] m;
+    }
+    v->clear();
+  }
+}
+
+static pf_status fail(pf_filter* f, pf_status st, const std::string& msg) {
+  if (f) f->err = msg;
+  else g_thread_error = msg;
+  return st;
+}
+
+static pf_status cuda_fail(pf_filter* f, cudaError_t e, const char* what) {
+  std::string msg = std::string("CUDA error in ") + what + ": " + cudaGetErrorName(e) + " (" +
+                    cudaGetErrorString(e) + ")";
+  return fail(f, PF_ERR_CUDA, msg);
+}
+
+#define PF_CUDA(f, call)                                  \
+  do {                                                    \
+    cudaError_t e__ = (call);                             \
+    if (e__ != cudaSuccess) return cuda_fail(f, e__, #call); \
+  } while (0)
+
+static bool ode_dims(int ode, int* d, int* p) {
+  switch (ode) {
+    case PF_ODE_LINEAR2: *d = 2; *p = 2; return true;
+    case PF_ODE_ROBERTSON: *d = 3; *p = 3; return true;
+    case PF_ODE_BRUSSELATOR1D: *d = 64; *p = 3; return true;
+  }
+  return false;
+}
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Carve the filter's single device allocation.
+static size_t layout(pf_filter* f, char* base) {
+  const int64_t N = f->N;
+  const int d = f->d, p = f->p;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* ptr = base ? base + off : nullptr;
+    off = align_up(off + bytes);
+    return ptr;
+  };
+  for (int b = 0; b < 2; ++b) {
+    f->fd.ens[b].x = (double*)take(sizeof(double) * N * d);
+    f->fd.ens[b].h1 = (double*)take(sizeof(double) * N * d);
+    f->fd.ens[b].h2 = (double*)take(sizeof(double) * N * d);
+    f->fd.ens[b].phi = (double*)take(sizeof(double) * N * p);
+    f->fd.ens[b].lw = (double*)take(sizeof(double) * N);
+  }
+  f->fd.ll1 = (double*)take(sizeof(double) * N);
+  f->fd.lg = (double*)take(sizeof(double) * N);
+  f->fd.c = (double*)take(sizeof(double) * N);
+  f->fd.idx = (int32_t*)take(sizeof(int32_t) * N);
+  f->fd.blk = (double*)take(sizeof(double) * max_grid_blocks(N));
+  f->fd.boff = (double*)take(sizeof(double) * scan_tiles(N));
+  f->fd.pmax = (double*)take(sizeof(double) * scan_tiles(N));
+  f->fd.part = (double*)take(sizeof(double) * kMomentBlocks * f->fd.nrec);
+  f->fd.ticket = (unsigned*)take(sizeof(unsigned) * 8);
+  f->fd.ctrl = (Ctrl*)take(sizeof(Ctrl));
+  f->ep_dev = (EpochParams*)take(sizeof(EpochParams));
+  return off;
+}
+
+static double prior_center_phi(const pf_filter* f, int i) {
+  const double lo = f->prior_lo[i], hi = f->prior_hi[i];
+  if (f->prior_kind[i] == PF_PRIOR_LOGUNIFORM) {
+    const double c = 0.5 * (std::log(lo) + std::log(hi));
+    return f->transform == PF_TRANSFORM_LOG ? c : std::exp(c);
+  }
+  const double c = 0.5 * (lo + hi);
+  return f->transform == PF_TRANSFORM_LOG ? std::log(c) : c;
+}
+
+// Ordered copy on the filter's stream, waited for (host buffers may be pageable).
+static cudaError_t copy_sync(pf_filter* f, void* dst, const void* src, size_t bytes,
+                             cudaMemcpyKind kind) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, f->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(f->stream);
+}
+
+static pf_status read_ctrl(pf_filter* f) {
+  PF_CUDA(f, cudaMemcpyAsync(f->ctrl_host, f->fd.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, f->stream));
+  PF_CUDA(f, cudaStreamSynchronize(f->stream));
+  f->d2h_bytes += sizeof(Ctrl);
+  return PF_OK;
+}
+
+// Step 1 into the existing buffers.
+static pf_status do_init(pf_filter* f) {
+  Ctrl* h = f->ctrl_host;
+  std::memset(h, 0, sizeof(Ctrl));
+  h->cur = 0;
+  h->status = PF_OK;
+  for (int i = 0; i < f->p; ++i) h->phibar[i] = prior_center_phi(f, i);
+  h->lw_max = 0.0;
+  PF_CUDA(f, cudaMemcpyAsync(f->fd.ctrl, h, sizeof(Ctrl), cudaMemcpyHostToDevice, f->stream));
+  PF_CUDA(f, cudaMemsetAsync(f->fd.ticket, 0, sizeof(unsigned) * 8, f->stream));
+  PF_CUDA(f, launch_init(f->ode, f->fd, f->stream));
+  pf_status st = read_ctrl(f);
+  if (st != PF_OK) return st;
+  if (f->ctrl_host->status != PF_OK)
+    return fail(f, (pf_status)f->ctrl_host->status, "initial moments are not finite");
+  f->hist = HistoryState{0, 0, f->t0, 0.0, 0.0};
+  return PF_OK;
+}
+
+// Parameter block of one epoch from the history state h.
+static int fill_epoch(const pf_filter* f, const HistoryState& h, double t_k, const double* y,
+                      EpochParams* ep, int* depth_out) {
+  const int depth = (f->history == PF_HISTORY_RESTART) ? 0 : h.depth;
+  const int S = build_substeps(f->lmm, f->spacing, f->dt, f->substeps, f->q0, h.t_prev, t_k, depth,
+                               h.hprev1, h.hprev2, ep->sc, kSMax, depth_out);
+  if (S < 1) return -1;
+  ep->t = t_k;
+  ep->S = S;
+  ep->epoch = (uint32_t)h.epochs;
+  ep->pad = 0;
+  for (int i = 0; i < kMMax; ++i) {
+    ep->y[i] = 0.0;
+    ep->inv_sigma[i] = 0.0;
+  }
+  for (int i = 0; i < f->m; ++i) {
+    ep->y[i] = y[i];
+    double sig = f->sigma[i];
+    if (f->noise == PF_NOISE_RELATIVE) sig = f->sigma[i] * std::fmax(std::fabs(y[i]), 1e-300);
+    ep->inv_sigma[i] = 1.0 / sig;
+  }
+  return S;
+}
+
+static HistoryState advance(const pf_filter* f, const HistoryState& h, double t_k,
+                            const EpochParams* ep, int depth_out) {
+  HistoryState n = h;
+  const int S = ep->S;
+  n.epochs = h.epochs + 1;
+  n.depth = depth_out;
+  n.hprev1 = ep->sc[S - 1].h;
+  n.hprev2 = S >= 2 ? ep->sc[S - 2].h : h.hprev1;
+  n.t_prev = t_k;
+  (void)f;
+  return n;
+}
+
+static pf_status clear_device_status(pf_filter* f) {
+  PF_CUDA(f, cudaMemsetAsync(&f->fd.ctrl->status, 0, sizeof(int), f->stream));
+  PF_CUDA(f, cudaMemsetAsync(f->fd.ticket, 0, sizeof(unsigned) * 8, f->stream));
+  PF_CUDA(f, cudaStreamSynchronize(f->stream));
+  return PF_OK;
+}
+
+static const char* status_text(int st) {
+  switch (st) {
+    case PF_ERR_DEGENERATE: return "degenerate epoch: every weight is zero or not finite";
+    case PF_ERR_NUMERIC: return "non-finite weighted moments";
+    case PF_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "epoch failed";
+}
+
+extern "C" {
+
+const char* pf_version(void) { return "paper_1411_1702_gb300 0.1 (sm_103a, FP64)"; }
+
+pf_status pf_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
+                    const pf_prior* prior, const pf_options* opt, pf_filter** out) {
+  if (!out) return fail(nullptr, PF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int dd, pp;
+  if (!ode_dims(ode, &dd, &pp)) return fail(nullptr, PF_ERR_INVALID_ARG, "unknown ODE");
+  if (!ode_supported(ode)) return fail(nullptr, PF_ERR_INVALID_ARG, "ODE not available in this build");
+  if (d != dd || p != pp) return fail(nullptr, PF_ERR_INVALID_ARG, "d or p does not match the ODE");
+  if (N < 1 || N > PF_MAX_PARTICLES) return fail(nullptr, PF_ERR_INVALID_ARG, "N out of range");
+  if (lmm != PF_LMM_BDF1 && lmm != PF_LMM_BDF2) return fail(nullptr, PF_ERR_INVALID_ARG, "unknown LMM");
+  if (!prior || !opt) return fail(nullptr, PF_ERR_INVALID_ARG, "prior or options is NULL");
+  if (prior->p != p || prior->d != d || !prior->kind || !prior->lo || !prior->hi || !prior->x0)
+    return fail(nullptr, PF_ERR_INVALID_ARG, "prior does not match the ODE");
+  for (int i = 0; i < p; ++i) {
+    const double lo = prior->lo[i], hi = prior->hi[i];
+    if (!(std::isfinite(lo) && std::isfinite(hi) && lo <= hi))
+      return fail(nullptr, PF_ERR_INVALID_ARG, "prior bounds must satisfy lo <= hi");
+    if (prior->kind[i] == PF_PRIOR_LOGUNIFORM) {
+      if (!(lo > 0.0)) return fail(nullptr, PF_ERR_INVALID_ARG, "log-uniform prior needs lo > 0");
+    } else if (prior->kind[i] != PF_PRIOR_UNIFORM) {
+      return fail(nullptr, PF_ERR_INVALID_ARG, "unknown prior kind");
+    }
+  }
+  for (int i = 0; i < d; ++i)
+    if (!std::isfinite(prior->x0[i])) return fail(nullptr, PF_ERR_INVALID_ARG, "x0 not finite");
+  if (!(opt->a > 0.0 && opt->a <= 1.0)) return fail(nullptr, PF_ERR_INVALID_ARG, "need 0 < a <= 1");
+  if (opt->newton_iters < 1 || opt->newton_iters > 64)
+    return fail(nullptr, PF_ERR_INVALID_ARG, "newton_iters out of range");
+  if (opt->m < 1 || opt->m > kMMax || !opt->obs_idx || !opt->sigma)
+    return fail(nullptr, PF_ERR_INVALID_ARG, "need 1 <= m <= 16 observed components");
+  for (int i = 0; i < opt->m; ++i) {
+    if (opt->obs_idx[i] < 0 || opt->obs_idx[i] >= d)
+      return fail(nullptr, PF_ERR_INVALID_ARG, "observation index out of range");
+    if (!(opt->sigma[i] > 0.0) || !std::isfinite(opt->sigma[i]))
+      return fail(nullptr, PF_ERR_INVALID_ARG, "sigma must be positive");
+  }
+  if (opt->spacing == PF_SPACING_UNIFORM) {
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, PF_ERR_INVALID_ARG, "dt must be positive");
+  } else if (opt->spacing == PF_SPACING_GEOMETRIC) {
+    if (opt->substeps < 1 || opt->substeps > kSMax)
+      return fail(nullptr, PF_ERR_INVALID_ARG, "substeps out of range");
+  } else {
+    return fail(nullptr, PF_ERR_INVALID_ARG, "unknown spacing");
+  }
+  if (opt->history != PF_HISTORY_CARRY && opt->history != PF_HISTORY_RESTART)
+    return fail(nullptr, PF_ERR_INVALID_ARG, "unknown history mode");
+  if (opt->transform != PF_TRANSFORM_LOG && opt->transform != PF_TRANSFORM_IDENTITY)
+    return fail(nullptr, PF_ERR_INVALID_ARG, "unknown transform");
+  if (opt->noise != PF_NOISE_ADDITIVE && opt->noise != PF_NOISE_RELATIVE)
+    return fail(nullptr, PF_ERR_INVALID_ARG, "unknown noise model");
+  if (!(opt->kappa >= 0.0) || !std::isfinite(opt->kappa))
+    return fail(nullptr, PF_ERR_INVALID_ARG, "kappa must be >= 0");
+
+  pf_filter* f = new (std::nothrow) pf_filter();
+  if (!f) return fail(nullptr, PF_ERR_OOM, "host allocation failed");
+  f->ode = ode; f->d = d; f->p = p; f->m = opt->m; f->lmm = lmm; f->K = opt->newton_iters;
+  f->spacing = opt->spacing; f->substeps = opt->substeps; f->history = opt->history;
+  f->transform = opt->transform; f->noise = opt->noise;
+  f->dt = dt; f->q0 = opt->q0; f->a = opt->a; f->kappa = opt->kappa;
+  f->seed = opt->seed; f->filter_id = opt->filter_id; f->N = N; f->t0 = prior->t0;
+  f->timing = opt->timing != 0;
+  for (int i = 0; i < opt->m; ++i) { f->obs[i] = opt->obs_idx[i]; f->sigma[i] = opt->sigma[i]; }
+  for (int i = 0; i < p; ++i) {
+    f->prior_kind[i] = prior->kind[i]; f->prior_lo[i] = prior->lo[i]; f->prior_hi[i] = prior->hi[i];
+  }
+  for (int i = 0; i < d; ++i) f->x0[i] = prior->x0[i];
+
+  FilterDev& fd = f->fd;
+  fd.N = N; fd.d = d; fd.p = p; fd.m = f->m; fd.K = f->K; fd.transform = f->transform;
+  for (int i = 0; i < kMMax; ++i) fd.obs[i] = i < f->m ? f->obs[i] : 0;
+  fd.a = f->a; fd.s = std::sqrt(1.0 - f->a * f->a); fd.kappa = f->kappa;
+  fd.seed = f->seed; fd.stream_id = f->filter_id;
+  fd.nrec = moment_record_size(ode);
+  for (int i = 0; i < kPMax; ++i) {
+    fd.prior_kind[i] = i < p ? f->prior_kind[i] : 0;
+    fd.prior_lo[i] = i < p ? f->prior_lo[i] : 0.0;
+    fd.prior_hi[i] = i < p ? f->prior_hi[i] : 0.0;
+  }
+  for (int i = 0; i < kDMax; ++i) fd.x0[i] = i < d ? f->x0[i] : 0.0;
+
+  pf_status st = PF_OK;
+  cudaError_t e;
+  if (opt->stream) {
+    f->stream = (cudaStream_t)opt->stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { st = cuda_fail(nullptr, e, "cudaStreamCreateWithFlags"); pf_destroy(f); return st; }
+    f->own_stream = true;
+  }
+  f->dbytes = layout(f, nullptr);
+  e = cudaMalloc(&f->dmem, f->dbytes);
+  if (e != cudaSuccess) {
+    f->dmem = nullptr;
+    g_thread_error = "device allocation of " + std::to_string(f->dbytes) + " bytes failed";
+    pf_destroy(f);
+    return PF_ERR_OOM;
+  }
+  layout(f, (char*)f->dmem);
+  e = cudaMallocHost(&f->ep_host, sizeof(EpochParams));
+  if (e == cudaSuccess) e = cudaMallocHost(&f->ctrl_host, sizeof(Ctrl));
+  if (e == cudaSuccess) e = cudaEventCreate(&f->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&f->ev1);
+  if (e != cudaSuccess) { st = cuda_fail(nullptr, e, "pinned buffers/events"); pf_destroy(f); return st; }
+  st = do_init(f);
+  if (st != PF_OK) {
+    g_thread_error = f->err;
+    pf_destroy(f);
+    return st;
+  }
+  *out = f;
+  return PF_OK;
+}
+
+void pf_destroy(pf_filter* f) {
+  if (!f) return;
+  if (f->stream) cudaStreamSynchronize(f->stream);
+  if (f->series_dev) cudaFree(f->series_dev);
+  if (f->dmem) cudaFree(f->dmem);
+  if (f->ep_host) cudaFreeHost(f->ep_host);
+  if (f->ctrl_host) cudaFreeHost(f->ctrl_host);
+  free_marks(f);
+  if (f->ev0) cudaEventDestroy(f->ev0);
+  if (f->ev1) cudaEventDestroy(f->ev1);
+  if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
+  delete f;
+}
+
+const char* pf_last_error(const pf_filter* f) {
+  return f ? f->err.c_str() : g_thread_error.c_str();
+}
+
+pf_status pf_assimilate(pf_filter* f, double t_k, const double* y_k) {
+  if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
+  if (!y_k) return fail(f, PF_ERR_INVALID_ARG, "y_k is NULL");
+  for (int i = 0; i < f->m; ++i)
+    if (!std::isfinite(y_k[i])) return fail(f, PF_ERR_INVALID_ARG, "observation is not finite");
+  if (!std::isfinite(t_k) || !(t_k > f->hist.t_prev))
+    return fail(f, PF_ERR_INVALID_ARG, "t_k must exceed the previous observation time");
+  int depth_out = 0;
+  const int S = fill_epoch(f, f->hist, t_k, y_k, f->ep_host, &depth_out);
+  if (S < 1) return fail(f, PF_ERR_INVALID_ARG, "substep grid of the interval is invalid");
+  const size_t bytes = kEpochHeaderBytes + sizeof(StepCoef) * (size_t)S;
+  PF_CUDA(f, cudaMemcpyAsync(f->ep_dev, f->ep_host, bytes, cudaMemcpyHostToDevice, f->stream));
+  f->h2d_bytes += (int64_t)bytes;
+  PF_CUDA(f, cudaEventRecord(f->ev0, f->stream));
+  PF_CUDA(f, launch_epoch(f->ode, f->fd, f->ep_dev, S, f->stream, take_marks(f)));
+  PF_CUDA(f, cudaEventRecord(f->ev1, f->stream));
+  pf_status st = read_ctrl(f);
+  if (st != PF_OK) return st;
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, f->ev0, f->ev1) == cudaSuccess) f->last_ms = ms;
+  const int dst = f->ctrl_host->status;
+  if (dst != PF_OK) {
+    pf_status cs = clear_device_status(f);
+    if (cs != PF_OK) return cs;
+    return fail(f, (pf_status)dst, status_text(dst));
+  }
+  f->hist = advance(f, f->hist, t_k, f->ep_host, depth_out);
+  return PF_OK;
+}
+
+pf_status pf_estimates(const pf_filter* cf, double* theta_bar, double* C, double* x_bar) {
+  pf_filter* f = const_cast<pf_filter*>(cf);
+  if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
+  pf_status st = read_ctrl(f);
+  if (st != PF_OK) return st;
+  const Ctrl* h = f->ctrl_host;
+  if (theta_bar) for (int i = 0; i < f->p; ++i) theta_bar[i] = h->phibar[i];
+  if (C)
+    for (int i = 0; i < f->p; ++i)
+      for (int j = 0; j < f->p; ++j) C[i * f->p + j] = h->C[i * kPMax + j];
+  if (x_bar) for (int i = 0; i < f->d; ++i) x_bar[i] = h->xbar[i];
+  return PF_OK;
+}
+
+pf_status pf_stats(const pf_filter* cf, pf_stats_t* out) {
+  pf_filter* f = const_cast<pf_filter*>(cf);
+  if (!f || !out) return fail(f, PF_ERR_INVALID_ARG, "NULL argument");
+  pf_status st = read_ctrl(f);
+  if (st != PF_OK) return st;
+  const Ctrl* h = f->ctrl_host;
+  std::memset(out, 0, sizeof(*out));
+  out->epochs = h->epochs_done;
+  out->ess = h->ess;
+  out->log_weight_sum = h->logW;
+  out->unique_parents = h->n_unique;
+  out->nonfinite = h->n_nonfinite;
+  for (int i = 0; i < f->p && i < 8; ++i) out->theta_mean[i] = h->theta_mean[i];
+  out->last_epoch_ms = f->last_ms;
+  out->h2d_bytes = f->h2d_bytes;
+  out->d2h_bytes = f->d2h_bytes;
+  return PF_OK;
+}
+
+pf_status pf_kernel_times(pf_filter* f, double* ms, int64_t* launches, int n) {
+  if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
+  if (!ms || !launches || n < kEpochKernels) return fail(f, PF_ERR_INVALID_ARG, "need 6 slots");
+  if (!f->timing) return fail(f, PF_ERR_STATE, "timing was not enabled at creation");
+  PF_CUDA(f, cudaStreamSynchronize(f->stream));
+  for (cudaEvent_t* m : f->mark_pending) {
+    for (int i = 0; i < kEpochKernels; ++i) {
+      float t = 0.0f;
+      PF_CUDA(f, cudaEventElapsedTime(&t, m[i], m[i + 1]));
+      f->kernel_ms[i] += t;
+      f->kernel_launches[i] += 1;
+    }
+    f->mark_free.push_back(m);
+  }
+  f->mark_pending.clear();
+  for (int i = 0; i < n; ++i) {
+    ms[i] = i < kEpochKernels ? f->kernel_ms[i] : 0.0;
+    launches[i] = i < kEpochKernels ? f->kernel_launches[i] : 0;
+  }
+  for (int i = 0; i < kEpochKernels; ++i) {
+    f->kernel_ms[i] = 0.0;
+    f->kernel_launches[i] = 0;
+  }
+  return PF_OK;
+}
+
+pf_status pf_load_observations(pf_filter* f, int T, const double* t, const double* y) {
+  if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
+  if (T < 1 || !t || !y) return fail(f, PF_ERR_INVALID_ARG, "need T >= 1 observations");
+  PF_CUDA(f, cudaStreamSynchronize(f->stream));
+  std::vector<EpochParams> host((size_t)T);
+  std::vector<int> S((size_t)T);
+  std::vector<HistoryState> after((size_t)T);
+  HistoryState h = f->hist;
+  for (int k = 0; k < T; ++k) {
+    for (int i = 0; i < f->m; ++i)
+      if (!std::isfinite(y[(size_t)k * f->m + i]))
+        return fail(f, PF_ERR_INVALID_ARG, "observation is not finite");
+    if (!std::isfinite(t[k]) || !(t[k] > h.t_prev))
+      return fail(f, PF_ERR_INVALID_ARG, "observation times must increase");
+    int depth_out = 0;
+    S[k] = fill_epoch(f, h, t[k], y + (size_t)k * f->m, &host[k], &depth_out);
+    if (S[k] < 1) return fail(f, PF_ERR_INVALID_ARG, "substep grid of an interval is invalid");
+    h = advance(f, h, t[k], &host[k], depth_out);
+    after[k] = h;
+  }
+  if (f->series_dev) {
+    cudaFree(f->series_dev);
+    f->series_dev = nullptr;
+    f->series_T = 0;
+  }
+  EpochParams* dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, sizeof(EpochParams) * (size_t)T);
+  if (e != cudaSuccess) return fail(f, PF_ERR_OOM, "device allocation of the series failed");
+  e = copy_sync(f, dev, host.data(), sizeof(EpochParams) * (size_t)T, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    return cuda_fail(f, e, "cudaMemcpy(series)");
+  }
+  f->series_dev = dev;
+  f->series_T = T;
+  f->series_next = 0;
+  f->series_S = S;
+  f->series_after = after;
+  f->series_start = f->hist;
+  return PF_OK;
+}
+
+pf_status pf_run(pf_filter* f, int k0, int k1) {
+  if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
+  if (!f->series_dev) return fail(f, PF_ERR_STATE, "no observation series loaded");
+  if (k0 != f->series_next) return fail(f, PF_ERR_STATE, "epochs must run in order");
+  if (k1 < k0 || k1 > f->series_T) return fail(f, PF_ERR_INVALID_ARG, "epoch range out of bounds");
+  for (int k = k0; k < k1; ++k) {
+    PF_CUDA(f, launch_epoch(f->ode, f->fd, f->series_dev + k, f->series_S[k], f->stream,
+                            take_marks(f)));
+    f->hist = f->series_after[k];
+  }
+  f->series_next = k1;
+  return PF_OK;
+}
+
+pf_status pf_synchronize(pf_filter* f) {
+  if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
+  pf_status st = read_ctrl(f);
+  if (st != PF_OK) return st;
+  const int dst = f->ctrl_host->status;
+  if (dst == PF_OK) return PF_OK;
+  // roll the host view back to the last committed epoch
+  const int64_t done = f->ctrl_host->epochs_done;
+  const int64_t k = done - f->series_start.epochs;  // series index of the failed epoch
+  if (f->series_dev && k >= 0 && k <= f->series_T) {
+    f->hist = (k == 0) ? f->series_start : f->series_after[(size_t)k - 1];
+    f->series_next = (int)k;
+  }
+  pf_status cs = clear_device_status(f);
+  if (cs != PF_OK) return cs;
+  return fail(f, (pf_status)dst, status_text(dst));
+}
+
+pf_status pf_reset(pf_filter* f) {
+  if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
+  PF_CUDA(f, cudaStreamSynchronize(f->stream));
+  pf_status st = do_init(f);
+  if (st != PF_OK) return st;
+  if (f->series_dev) {
+    const HistoryState& s = f->series_start;
+    const bool from_start = s.epochs == 0 && s.depth == 0 && s.t_prev == f->t0;
+    if (from_start) {
+      f->series_next = 0;
+    } else {
+      cudaFree(f->series_dev);
+      f->series_dev = nullptr;
+      f->series_T = 0;
+    }
+  }
+  return PF_OK;
+}
+
+pf_status pf_get_ensemble(const pf_filter* cf, double* x, double* h1, double* h2, double* phi,
+                          double* logw) {
+  pf_filter* f = const_cast<pf_filter*>(cf);
+  if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
+  pf_status st = read_ctrl(f);
+  if (st != PF_OK) return st;
+  const Ensemble& E = f->ctrl_host->cur ? f->fd.ens[1] : f->fd.ens[0];
+  const int64_t N = f->N;
+  std::vector<double> tmp;
+  auto pull = [&](const double* src, int rows, double* dst) -> pf_status {
+    if (!dst) return PF_OK;
+    tmp.resize((size_t)rows * N);
+    PF_CUDA(f, copy_sync(f, tmp.data(), src, sizeof(double) * rows * N, cudaMemcpyDeviceToHost));
+    f->d2h_bytes += (int64_t)(sizeof(double) * rows * N);
+    for (int64_t n = 0; n < N; ++n)
+      for (int i = 0; i < rows; ++i) dst[n * rows + i] = tmp[(size_t)i * N + n];
+    return PF_OK;
+  };
+  if ((st = pull(E.x, f->d, x)) != PF_OK) return st;
+  if ((st = pull(E.h1, f->d, h1)) != PF_OK) return st;
+  if ((st = pull(E.h2, f->d, h2)) != PF_OK) return st;
+  if ((st = pull(E.phi, f->p, phi)) != PF_OK) return st;
+  if (logw) {
+    if ((st = pull(E.lw, 1, logw)) != PF_OK) return st;
+    const double lw0 = f->ctrl_host->logW;
+    for (int64_t n = 0; n < N; ++n) logw[n] = logw[n] - lw0;
+  }
+  return PF_OK;
+}
+
+pf_status pf_set_ensemble(pf_filter* f, const double* x, const double* h1, const double* h2,
+                          const double* phi, const double* logw) {
+  if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
+  pf_status st = read_ctrl(f);
+  if (st != PF_OK) return st;
+  const Ensemble& E = f->ctrl_host->cur ? f->fd.ens[1] : f->fd.ens[0];
+  const int64_t N = f->N;
+  std::vector<double> tmp;
+  auto push = [&](double* dst, int rows, const double* src) -> pf_status {
+    if (!src) return PF_OK;
+    tmp.resize((size_t)rows * N);
+    for (int64_t n = 0; n < N; ++n)
+      for (int i = 0; i < rows; ++i) tmp[(size_t)i * N + n] = src[n * rows + i];
+    PF_CUDA(f, copy_sync(f, dst, tmp.data(), sizeof(double) * rows * N, cudaMemcpyHostToDevice));
+    f->h2d_bytes += (int64_t)(sizeof(double) * rows * N);
+    return PF_OK;
+  };
+  if ((st = push(E.x, f->d, x)) != PF_OK) return st;
+  if ((st = push(E.h1, f->d, h1)) != PF_OK) return st;
+  if ((st = push(E.h2, f->d, h2)) != PF_OK) return st;
+  if ((st = push(E.phi, f->p, phi)) != PF_OK) return st;
+  if (logw) {
+    if ((st = push(E.lw, 1, logw)) != PF_OK) return st;
+    const double zero = 0.0;
+    PF_CUDA(f, copy_sync(f, &f->fd.ctrl->logW, &zero, sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return PF_OK;
+}
+
+pf_status pf_set_moments(pf_filter* f, const double* phibar, const double* C) {
+  if (!f || !phibar || !C) return fail(f, PF_ERR_INVALID_ARG, "NULL argument");
+  pf_status st = read_ctrl(f);
+  if (st != PF_OK) return st;
+  Ctrl* h = f->ctrl_host;
+  for (int i = 0; i < f->p; ++i) h->phibar[i] = phibar[i];
+  for (int i = 0; i < f->p; ++i)
+    for (int j = 0; j < f->p; ++j) h->C[i * kPMax + j] = C[i * f->p + j];
+  PF_CUDA(f, cudaMemcpyAsync(f->fd.ctrl, h, sizeof(Ctrl), cudaMemcpyHostToDevice, f->stream));
+  PF_CUDA(f, launch_set_moments(f->fd, f->stream));
+  PF_CUDA(f, cudaStreamSynchronize(f->stream));
+  return PF_OK;
+}
+
+pf_status pf_get_work(const pf_filter* cf, double* loglik1, double* log_g, double* cumulative,
+                      int32_t* idx) {
+  pf_filter* f = const_cast<pf_filter*>(cf);
+  if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
+  PF_CUDA(f, cudaStreamSynchronize(f->stream));
+  const size_t nb = sizeof(double) * f->N;
+  if (loglik1) PF_CUDA(f, copy_sync(f, loglik1, f->fd.ll1, nb, cudaMemcpyDeviceToHost));
+  if (log_g) PF_CUDA(f, copy_sync(f, log_g, f->fd.lg, nb, cudaMemcpyDeviceToHost));
+  if (cumulative) PF_CUDA(f, copy_sync(f, cumulative, f->fd.c, nb, cudaMemcpyDeviceToHost));
+  if (idx) PF_CUDA(f, copy_sync(f, idx, f->fd.idx, sizeof(int32_t) * f->N, cudaMemcpyDeviceToHost));
+  f->d2h_bytes += (int64_t)((loglik1 ? nb : 0) + (log_g ? nb : 0) + (cumulative ? nb : 0) +
+                            (idx ? sizeof(int32_t) * f->N : 0));
+  return PF_OK;
+}
+
+pf_status pf_get_history(const pf_filter* f, int64_t* epochs, int* depth, double* t_prev,
+                         double* hprev1, double* hprev2) {
+  if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
+  if (epochs) *epochs = f->hist.epochs;
+  if (depth) *depth = f->hist.depth;
+  if (t_prev) *t_prev = f->hist.t_prev;
+  if (hprev1) *hprev1 = f->hist.hprev1;
+  if (hprev2) *hprev2 = f->hist.hprev2;
+  return PF_OK;
+}
+
+pf_status pf_set_history(pf_filter* f, int64_t epochs, int depth, double t_prev, double hprev1,
+                         double hprev2) {
+  if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
+  if (epochs < 0 || depth < 0 || depth > 2 || !std::isfinite(t_prev))
+    return fail(f, PF_ERR_INVALID_ARG, "history out of range");
+  f->hist = HistoryState{epochs, depth, t_prev, hprev1, hprev2};
+  PF_CUDA(f, copy_sync(f, &f->fd.ctrl->epochs_done, &epochs, sizeof(int64_t), cudaMemcpyHostToDevice));
+  if (f->series_dev) {
+    cudaFree(f->series_dev);
+    f->series_dev = nullptr;
+    f->series_T = 0;
+  }
+  return PF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,720 @@
+// pf_kernels.cu -- the per-observation epoch of Algorithm 1 (Arnold, Calvetti,
+// Somersalo) for one filter, as CUDA kernels for sm_103a.
+//
+// One epoch j -> j+1 is six launches on the filter's stream:
+//   k_stage1    Steps 2, 3a: shrink phi, propagate by Psi, first-stage log
+//               weights log g = log w + log pi(y | xbar); the last block takes
+//               the maximum (log-sum-exp shift)
+//   k_scan_tile Step 3a/3b: g = exp(log g - max), tile-local inclusive scan;
+//               the last block scans the tile totals
+//   k_scan_add  cumulative weights c_k = tile offset + tile-local sum
+//   k_resample  Step 3b: systematic resampling, l_i = min{k : c_k > tau_i}
+//   k_stage2    Steps 3c, 4, 5: gather by l, proliferate phi, repropagate with
+//               the Milne local-error sums, innovation, new log weights; the
+//               last block takes the maximum
+//   k_moments   Steps 5-6: normalisation, weighted mean/covariance of phi,
+//               mean state, ESS; the last block commits (flips the ensemble
+//               buffer) unless the epoch is degenerate
+// Every kernel returns at once if an earlier epoch failed (Ctrl::status), so
+// epochs can be enqueued ahead without host round trips.
+#include "pf_common.cuh"
+#include "pf_kernels.h"
+#include "pf_models.cuh"
+
+namespace pfg {
+
+constexpr int kSmallThreads = 128;
+constexpr int kResampleThreads = 256;
+
+__device__ __forceinline__ Ensemble committed(const FilterDev& fd, int cur) {
+  return cur ? fd.ens[1] : fd.ens[0];
+}
+__device__ __forceinline__ Ensemble pending(const FilterDev& fd, int cur) {
+  return cur ? fd.ens[0] : fd.ens[1];
+}
+
+// Gaussian log-likelihood of the observed components, without the constant
+// terms (they cancel in every normalisation of Steps 3a and 5).
+template <int D>
+__device__ __forceinline__ double loglik(const FilterDev& fd, const EpochParams* __restrict__ ep,
+                                         const double (&x)[D]) {
+  double s = 0.0;
+  for (int i = 0; i < fd.m; ++i) {
+    const int o = fd.obs[i];
+    double xo = x[0];
+#pragma unroll
+    for (int j = 1; j < D; ++j) xo = (o == j) ? x[j] : xo;
+    const double z = (ep->y[i] - xo) * ep->inv_sigma[i];
+    s = fma(z, z, s);
+  }
+  return -0.5 * s;
+}
+
+template <int P>
+__device__ __forceinline__ void to_theta(const FilterDev& fd, const double (&ph)[P], double (&th)[P]) {
+#pragma unroll
+  for (int i = 0; i < P; ++i) th[i] = (fd.transform == PF_TRANSFORM_LOG) ? exp(ph[i]) : ph[i];
+}
+
+// Psi of Algorithm 1 for one particle over the S substeps of the interval.
+// (x, h1, h2) = (x_n, x_{n-1}, x_{n-2}).  With ERR the squared Milne local
+// error estimates are summed into E (Step 4b).
+template <class M, bool ERR>
+__device__ __forceinline__ void propagate(const typename M::Th& T, const StepCoef* sc, int S, int K,
+                                          double (&x)[M::D], double (&h1)[M::D],
+                                          double (&h2)[M::D], double (&E)[M::D]) {
+  constexpr int D = M::D;
+  for (int s = 0; s < S; ++s) {
+    const StepCoef& c = sc[s];
+    double xp[D], r[D], y[D];
+    if (c.kind == 2) {
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        xp[i] = fma(c.pi2, h2[i], fma(c.pi1, h1[i], c.pi0 * x[i]));
+        r[i] = fma(c.rho2, h1[i], c.rho1 * x[i]);
+        y[i] = xp[i];
+      }
+    } else {
+      // BDF1 (cold start): r = x_n, Newton from x_n, error predictor x_n + h f(x_n)
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        r[i] = x[i];
+        y[i] = x[i];
+      }
+      if (ERR) {
+        double g[D];
+        M::gf(T, c.h, x, g);
+#pragma unroll
+        for (int i = 0; i < D; ++i) xp[i] = x[i] + g[i];
+      }
+    }
+    M::newton(T, c.gamma, r, y, K);
+    if (ERR) {
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const double e = c.mu * (y[i] - xp[i]);
+        E[i] = fma(e, e, E[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      h2[i] = h1[i];
+      h1[i] = x[i];
+      x[i] = y[i];
+    }
+  }
+}
+
+__device__ __forceinline__ void load_steps(StepCoef* s_sc, const EpochParams* __restrict__ ep, int S) {
+  const double* src = reinterpret_cast<const double*>(ep->sc);
+  double* dst = reinterpret_cast<double*>(s_sc);
+  const int nd = S * (int)(sizeof(StepCoef) / sizeof(double));
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ init
+// Step 1: phi drawn from the prior (uniform or log-uniform per component,
+// Philox purpose INIT, epoch word 0), x = h1 = h2 = x0, unnormalised log
+// weight 0 (w = 1/N after normalisation), into the pending buffer.
+template <int D, int P>
+__global__ void __launch_bounds__(256) k_init(const FilterDev fd) {
+  const Ctrl* ctrl = fd.ctrl;
+  const Ensemble dst = pending(fd, ctrl->cur);
+  const int64_t N = fd.N;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+#pragma unroll
+  for (int b = 0; b < (P + 1) / 2; ++b) {
+    const U4 w = draw_block(fd, kRngInit, (uint32_t)n, 0u, (uint32_t)b);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * b + h;
+      if (i >= P) break;
+      const double u = h == 0 ? uniform53(w.x, w.y) : uniform53(w.z, w.w);
+      double phi;
+      if (fd.prior_kind[i] == PF_PRIOR_LOGUNIFORM) {
+        const double lo = log(fd.prior_lo[i]), hi = log(fd.prior_hi[i]);
+        const double lphi = lo + u * (hi - lo);
+        phi = (fd.transform == PF_TRANSFORM_LOG) ? lphi : exp(lphi);
+      } else {
+        const double th = fd.prior_lo[i] + u * (fd.prior_hi[i] - fd.prior_lo[i]);
+        phi = (fd.transform == PF_TRANSFORM_LOG) ? log(th) : th;
+      }
+      dst.phi[i * N + n] = phi;
+    }
+  }
+  for (int i = 0; i < D; ++i) {
+    dst.x[i * N + n] = fd.x0[i];
+    dst.h1[i * N + n] = fd.x0[i];
+    dst.h2[i * N + n] = fd.x0[i];
+  }
+  dst.lw[n] = 0.0;
+}
+
+// ---------------------------------------------------------------- stage 1
+template <class M>
+__global__ void __launch_bounds__(kSmallThreads) k_stage1(const FilterDev fd,
+                                                          const EpochParams* __restrict__ ep) {
+  constexpr int D = M::D, P = M::P;
+  extern __shared__ double s_dyn[];
+  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  Ctrl* ctrl = fd.ctrl;
+  if (ctrl->status != PF_OK) return;
+  const int S = ep->S;
+  load_steps(s_sc, ep, S);
+  const Ensemble E = committed(fd, ctrl->cur);
+  const int64_t N = fd.N;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double lg = -CUDART_INF;
+  if (n < N) {
+    double ph[P], th[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) ph[i] = fd.a * E.phi[i * N + n] + (1.0 - fd.a) * ctrl->phibar[i];
+    to_theta<P>(fd, ph, th);
+    const typename M::Th T = M::theta(th);
+    double x[D], h1[D], h2[D], Eunused[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      x[i] = E.x[i * N + n];
+      h1[i] = E.h1[i * N + n];
+      h2[i] = E.h2[i * N + n];
+    }
+    propagate<M, false>(T, s_sc, S, fd.K, x, h1, h2, Eunused);
+    const double ll = loglik<D>(fd, ep, x);
+    fd.ll1[n] = ll;
+    lg = (E.lw[n] - ctrl->logW) + ll;
+    if (!finite_bits(lg)) lg = -CUDART_INF;
+    fd.lg[n] = lg;
+  }
+  const double bm = block_max(lg, s_red);
+  if (threadIdx.x == 0) fd.blk[blockIdx.x] = bm;
+  if (elect_last_block(fd.ticket + 0, &s_flag)) {
+    double m = -CUDART_INF;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmax(m, __ldcg(fd.blk + b));
+    m = block_max(m, s_red);
+    if (threadIdx.x == 0) {
+      ctrl->lg_max = m;
+      ctrl->n_unique = 0;
+      ctrl->n_nonfinite = 0;
+      if (!(m > -CUDART_INF)) {
+        ctrl->status = PF_ERR_DEGENERATE;
+        ctrl->failed_epoch = ep->epoch;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------- scan
+// g_k = exp(lg_k - max lg) and its cumulative sums c_k (Step 3a, 3b).  Each
+// thread sums kScanItems consecutive g sequentially, threads are combined by a
+// block scan and tiles by the tile offsets of the last block.  A parallel FP64
+// scan may dip by an ulp where partial sums meet, so two exact prefix-maximum
+// passes (thread level and tile level) make c non-decreasing; the maximum is
+// exact and associative, so c is still a deterministic function of g for a
+// given N.
+struct SumOp {
+  __device__ static double apply(double a, double b) { return a + b; }
+};
+struct MaxOp {
+  __device__ static double apply(double a, double b) { return fmax(a, b); }
+};
+
+// Exclusive block scan with identity 0 (all inputs are >= 0); total gets the
+// inclusive result of the last thread.  s_warp needs 33 doubles.
+template <class Op>
+__device__ __forceinline__ double block_exclusive_scan(double v, double* s_warp, double& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  double incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl = Op::apply(t, incl);
+  }
+  double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+  if (lane == 0) excl = 0.0;
+  __syncthreads();
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const double w = (lane < nw) ? s_warp[lane] : 0.0;
+    double wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi = Op::apply(t, wi);
+    }
+    double we = __shfl_up_sync(0xffffffffu, wi, 1);
+    if (lane == 0) we = 0.0;
+    if (lane < nw) s_warp[lane] = we;
+    if (lane == nw - 1) s_warp[32] = wi;
+  }
+  __syncthreads();
+  total = s_warp[32];
+  return Op::apply(s_warp[wid], excl);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile(const FilterDev fd) {
+  __shared__ double s_warp[33];
+  __shared__ int s_flag;
+  Ctrl* ctrl = fd.ctrl;
+  if (ctrl->status != PF_OK) return;
+  const double M = ctrl->lg_max;
+  const int64_t N = fd.N;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  double v[kScanItems];
+  double run = 0.0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    const int64_t k = base + j;
+    const double g = (k < N) ? exp(fd.lg[k] - M) : 0.0;
+    run += g;
+    v[j] = run;
+  }
+  double total;
+  const double excl = block_exclusive_scan<SumOp>(run, s_warp, total);
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) v[j] = excl + v[j];
+  double tile_last;
+  const double floor_prev = block_exclusive_scan<MaxOp>(v[kScanItems - 1], s_warp, tile_last);
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    const int64_t k = base + j;
+    if (k < N) fd.c[k] = fmax(v[j], floor_prev);
+  }
+  if (threadIdx.x == 0) fd.blk[blockIdx.x] = tile_last;
+  if (elect_last_block(fd.ticket + 1, &s_flag)) {
+    // tile offsets boff_b = sum of earlier tile totals, and the running maximum
+    // pmax_b of the earlier tiles' last values boff_b' + T_b'
+    const int nb = gridDim.x;
+    const int chunk = (nb + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * chunk;
+    double acc = 0.0;
+    for (int b = b0; b < b0 + chunk && b < nb; ++b) acc += __ldcg(fd.blk + b);
+    double grand;
+    double off = block_exclusive_scan<SumOp>(acc, s_warp, grand);
+    double lmax = 0.0;
+    for (int b = b0; b < b0 + chunk && b < nb; ++b) {
+      fd.boff[b] = off;
+      const double T = __ldcg(fd.blk + b);
+      lmax = fmax(lmax, off + T);
+      off += T;
+    }
+    double gmax;
+    double pm = block_exclusive_scan<MaxOp>(lmax, s_warp, gmax);
+    for (int b = b0; b < b0 + chunk && b < nb; ++b) {
+      fd.pmax[b] = pm;
+      pm = fmax(pm, fd.boff[b] + __ldcg(fd.blk + b));
+    }
+    if (threadIdx.x == 0) ctrl->c_total = gmax;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_scan_add(const FilterDev fd) {
+  if (fd.ctrl->status != PF_OK) return;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < fd.N) {
+    const int64_t b = k / kScanTile;
+    fd.c[k] = fmax(fd.boff[b] + fd.c[k], fd.pmax[b]);
+  }
+}
+
+// --------------------------------------------------------------- resample
+// Step 3b read as systematic resampling: tau_i = ((i + u)/N) c_{N-1} with one
+// u per epoch (Philox purpose RESAMPLE, slot 0); l_i = min{k : c_k > tau_i},
+// else the first k with c_k = c_{N-1}.  All values are >= +0, so their IEEE
+// bit patterns order like the numbers and the search compares integers.
+__device__ __forceinline__ int64_t upper_bound_bits(const double* c, int64_t N, long long key) {
+  int64_t lo = 0, hi = N;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__double_as_longlong(__ldg(c + mid)) > key) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int64_t lower_bound_bits(const double* c, int64_t N, long long key) {
+  int64_t lo = 0, hi = N;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__double_as_longlong(__ldg(c + mid)) >= key) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int32_t systematic_index(const double* c, int64_t N, int64_t i, double u,
+                                                    double total) {
+  const double tau = ((double)i + u) / (double)N * total;
+  int64_t k = upper_bound_bits(c, N, __double_as_longlong(tau));
+  if (k == N) k = lower_bound_bits(c, N, __double_as_longlong(total));
+  return (int32_t)k;
+}
+
+__global__ void __launch_bounds__(kResampleThreads) k_resample(const FilterDev fd,
+                                                               const EpochParams* __restrict__ ep) {
+  __shared__ int32_t s_l[kResampleThreads];
+  __shared__ double s_red[32];
+  Ctrl* ctrl = fd.ctrl;
+  if (ctrl->status != PF_OK) return;
+  const int64_t N = fd.N;
+  const U4 w = draw_block(fd, kRngResample, 0u, ep->epoch, 0u);
+  const double u = uniform53(w.x, w.y);
+  const double total = __ldg(fd.c + (N - 1));
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int32_t l = -1;
+  if (i < N) {
+    l = systematic_index(fd.c, N, i, u, total);
+    fd.idx[i] = l;
+  }
+  s_l[threadIdx.x] = l;
+  __syncthreads();
+  int32_t prev;
+  if (threadIdx.x > 0) prev = s_l[threadIdx.x - 1];
+  else prev = (i > 0 && i < N) ? systematic_index(fd.c, N, i - 1, u, total) : -1;
+  const double fresh = (i < N && l != prev) ? 1.0 : 0.0;
+  const double cnt = block_sum(fresh, s_red);
+  if (threadIdx.x == 0 && cnt > 0.0)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&ctrl->n_unique), (unsigned long long)cnt);
+}
+
+// ---------------------------------------------------------------- stage 2
+template <class M>
+__global__ void __launch_bounds__(kSmallThreads) k_stage2(const FilterDev fd,
+                                                          const EpochParams* __restrict__ ep) {
+  constexpr int D = M::D, P = M::P;
+  extern __shared__ double s_dyn[];
+  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  Ctrl* ctrl = fd.ctrl;
+  if (ctrl->status != PF_OK) return;
+  const int S = ep->S;
+  load_steps(s_sc, ep, S);
+  const int cur = ctrl->cur;
+  const Ensemble src = committed(fd, cur);
+  const Ensemble dst = pending(fd, cur);
+  const int64_t N = fd.N;
+  const uint32_t epoch = ep->epoch;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double lwn = -CUDART_INF;
+  double bad = 0.0;
+  if (n < N) {
+    const int64_t l = fd.idx[n];
+    // 4a: phi_{j+1} = (a phi^l + (1 - a) phibar) + s L z
+    double z[P + 1];
+#pragma unroll
+    for (int b = 0; b < (P + 1) / 2; ++b) {
+      const U4 w = draw_block(fd, kRngTheta, (uint32_t)n, epoch, (uint32_t)b);
+      normal_pair(w, z[2 * b], z[2 * b + 1]);
+    }
+    double ph[P], th[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      double lz = 0.0;
+#pragma unroll
+      for (int k = 0; k <= i; ++k) lz = fma(ctrl->L[i * kPMax + k], z[k], lz);
+      const double shr = fd.a * src.phi[i * N + l] + (1.0 - fd.a) * ctrl->phibar[i];
+      ph[i] = fma(fd.s, lz, shr);
+    }
+    to_theta<P>(fd, ph, th);
+    const typename M::Th T = M::theta(th);
+    double x[D], h1[D], h2[D], Eacc[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      x[i] = src.x[i * N + l];
+      h1[i] = src.h1[i * N + l];
+      h2[i] = src.h2[i * N + l];
+      Eacc[i] = 0.0;
+    }
+    // 4b, 4d: repropagate, summing the squared Milne estimates
+    propagate<M, true>(T, s_sc, S, fd.K, x, h1, h2, Eacc);
+    // 4c, 4d: v ~ N(0, kappa diag(E)), added to x and to the stored history
+#pragma unroll
+    for (int b = 0; b < (D + 1) / 2; ++b) {
+      const U4 w = draw_block(fd, kRngInnov, (uint32_t)n, epoch, (uint32_t)b);
+      double z0, z1;
+      normal_pair(w, z0, z1);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = 2 * b + h;
+        if (i < D) {
+          const double v = sqrt(fd.kappa * Eacc[i]) * (h == 0 ? z0 : z1);
+          x[i] += v;
+          h1[i] += v;
+          h2[i] += v;
+        }
+      }
+    }
+    // 5: log w = log pi(y | x_{j+1}) - log pi(y | xbar^l)
+    const double ll2 = loglik<D>(fd, ep, x);
+    lwn = ll2 - fd.ll1[l];
+    if (!finite_bits(lwn)) {
+      lwn = -CUDART_INF;
+      bad = 1.0;
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      dst.x[i * N + n] = x[i];
+      dst.h1[i * N + n] = h1[i];
+      dst.h2[i * N + n] = h2[i];
+    }
+#pragma unroll
+    for (int i = 0; i < P; ++i) dst.phi[i * N + n] = ph[i];
+    dst.lw[n] = lwn;
+  }
+  const double bm = block_max(lwn, s_red);
+  const double nb = block_sum(bad, s_red);
+  if (threadIdx.x == 0) {
+    fd.blk[blockIdx.x] = bm;
+    if (nb > 0.0)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&ctrl->n_nonfinite), (unsigned long long)nb);
+  }
+  if (elect_last_block(fd.ticket + 2, &s_flag)) {
+    double m = -CUDART_INF;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmax(m, __ldcg(fd.blk + b));
+    m = block_max(m, s_red);
+    if (threadIdx.x == 0) {
+      ctrl->lw_max = m;
+      if (!(m > -CUDART_INF)) {
+        ctrl->status = PF_ERR_DEGENERATE;
+        ctrl->failed_epoch = epoch;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- moments
+// Weighted sums of the pending buffer with e_n = exp(lw_n - max lw):
+//   [S0 = sum e, Sw2 = sum e^2, S1 = sum e phi, S2 = sum e (phi - c)(phi - c)^T
+//    (upper triangle, shift c = the committed mean), Sx = sum e x,
+//    St = sum e theta]
+// Zero-weight particles are skipped (their state may be non-finite).  The last
+// block reduces the partial records and commits the epoch.
+template <int D, int P>
+struct MomentLayout {
+  static constexpr int kS0 = 0, kW2 = 1, kS1 = 2, kS2 = 2 + P, kSx = kS2 + P * (P + 1) / 2,
+                       kSt = kSx + D, kN = kSt + P;
+};
+
+// Cholesky factor of a PSD matrix; a non-positive pivot gives a zero column.
+__device__ void cholesky_psd(int p, const double* C, double* L) {
+  for (int i = 0; i < kPMax * kPMax; ++i) L[i] = 0.0;
+  for (int j = 0; j < p; ++j) {
+    double dsum = C[j * kPMax + j];
+    for (int k = 0; k < j; ++k) dsum -= L[j * kPMax + k] * L[j * kPMax + k];
+    if (!(dsum > 0.0)) continue;
+    const double ljj = sqrt(dsum);
+    L[j * kPMax + j] = ljj;
+    for (int i = j + 1; i < p; ++i) {
+      double s = C[i * kPMax + j];
+      for (int k = 0; k < j; ++k) s -= L[i * kPMax + k] * L[j * kPMax + k];
+      L[i * kPMax + j] = s / ljj;
+    }
+  }
+}
+
+template <int D, int P>
+__global__ void __launch_bounds__(kMomentThreads) k_moments(const FilterDev fd, int is_init) {
+  using Lay = MomentLayout<D, P>;
+  constexpr int NV = Lay::kN;
+  __shared__ double s_red[32];
+  __shared__ double s_tot[NV];
+  __shared__ int s_flag;
+  Ctrl* ctrl = fd.ctrl;
+  if (ctrl->status != PF_OK) return;
+  const int cur = ctrl->cur;
+  const Ensemble nw = pending(fd, cur);
+  const int64_t N = fd.N;
+  const double M = ctrl->lw_max;
+  double c[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) c[i] = ctrl->phibar[i];
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    const double lw = nw.lw[n];
+    if (is_neg_inf(lw)) continue;
+    const double e = exp(lw - M);
+    acc[Lay::kS0] += e;
+    acc[Lay::kW2] = fma(e, e, acc[Lay::kW2]);
+    double ph[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      ph[i] = nw.phi[i * N + n];
+      acc[Lay::kS1 + i] = fma(e, ph[i], acc[Lay::kS1 + i]);
+      const double th = (fd.transform == PF_TRANSFORM_LOG) ? exp(ph[i]) : ph[i];
+      acc[Lay::kSt + i] = fma(e, th, acc[Lay::kSt + i]);
+    }
+    int q = Lay::kS2;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      const double di = e * (ph[i] - c[i]);
+#pragma unroll
+      for (int j = i; j < P; ++j) {
+        acc[q] = fma(di, ph[j] - c[j], acc[q]);
+        ++q;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) acc[Lay::kSx + i] = fma(e, nw.x[i * N + n], acc[Lay::kSx + i]);
+  }
+#pragma unroll 1
+  for (int k = 0; k < NV; ++k) {
+    const double t = block_sum(acc[k], s_red);
+    if (threadIdx.x == 0) fd.part[(int64_t)blockIdx.x * fd.nrec + k] = t;
+  }
+  if (!elect_last_block(fd.ticket + 3, &s_flag)) return;
+#pragma unroll 1
+  for (int k = 0; k < NV; ++k) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      t += __ldcg(fd.part + (int64_t)b * fd.nrec + k);
+    t = block_sum(t, s_red);
+    if (threadIdx.x == 0) s_tot[k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double S0 = s_tot[Lay::kS0];
+  double mean[P], C[kPMax * kPMax], L[kPMax * kPMax];
+  for (int i = 0; i < kPMax * kPMax; ++i) C[i] = 0.0;
+  bool ok = S0 > 0.0;
+  for (int i = 0; i < P; ++i) {
+    mean[i] = s_tot[Lay::kS1 + i] / S0;
+    ok = ok && finite_bits(mean[i]);
+  }
+  int q = Lay::kS2;
+  for (int i = 0; i < P; ++i) {
+    for (int j = i; j < P; ++j) {
+      const double v = s_tot[q++] / S0 - (mean[i] - c[i]) * (mean[j] - c[j]);
+      C[i * kPMax + j] = v;
+      C[j * kPMax + i] = v;
+      ok = ok && finite_bits(v);
+    }
+  }
+  if (!ok) {
+    ctrl->status = PF_ERR_NUMERIC;
+    ctrl->failed_epoch = ctrl->epochs_done;
+    return;
+  }
+  cholesky_psd(P, C, L);
+  for (int i = 0; i < P; ++i) {
+    ctrl->phibar[i] = mean[i];
+    ctrl->theta_mean[i] = s_tot[Lay::kSt + i] / S0;
+  }
+  for (int i = 0; i < kPMax * kPMax; ++i) {
+    ctrl->C[i] = C[i];
+    ctrl->L[i] = L[i];
+  }
+  for (int i = 0; i < D; ++i) ctrl->xbar[i] = s_tot[Lay::kSx + i] / S0;
+  ctrl->ess = S0 * S0 / s_tot[Lay::kW2];
+  ctrl->logW = M + log(S0);
+  ctrl->cur = 1 - cur;
+  if (!is_init) ctrl->epochs_done += 1;
+}
+
+// ----------------------------------------------------------------- launch
+template <int D, int P>
+static int moment_nrec() {
+  return MomentLayout<D, P>::kN;
+}
+
+int moment_record_size(int ode) {
+  switch (ode) {
+    case PF_ODE_LINEAR2: return moment_nrec<2, 2>();
+    case PF_ODE_ROBERTSON: return moment_nrec<3, 3>();
+  }
+  return -1;
+}
+
+int max_grid_blocks(int64_t N) {
+  const int64_t a = (N + kSmallThreads - 1) / kSmallThreads;
+  const int64_t b = (N + kScanTile - 1) / kScanTile;
+  const int64_t c = (N + kResampleThreads - 1) / kResampleThreads;
+  int64_t m = a > b ? a : b;
+  m = m > c ? m : c;
+  return (int)(m > kMomentBlocks ? m : kMomentBlocks);
+}
+
+int scan_tiles(int64_t N) { return (int)((N + kScanTile - 1) / kScanTile); }
+
+static int moment_grid(int64_t N) {
+  const int64_t b = (N + kMomentThreads - 1) / kMomentThreads;
+  return (int)(b < kMomentBlocks ? b : kMomentBlocks);
+}
+
+template <class M>
+static cudaError_t launch_init_t(const FilterDev& fd, cudaStream_t st) {
+  const int64_t N = fd.N;
+  k_init<M::D, M::P><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(fd);
+  k_moments<M::D, M::P><<<moment_grid(N), kMomentThreads, 0, st>>>(fd, 1);
+  return cudaGetLastError();
+}
+
+template <class M>
+static cudaError_t launch_epoch_t(const FilterDev& fd, const EpochParams* ep, int S,
+                                  cudaStream_t st, cudaEvent_t* marks) {
+  const int64_t N = fd.N;
+  const size_t smem = (size_t)S * sizeof(StepCoef);
+  const unsigned g_small = (unsigned)((N + kSmallThreads - 1) / kSmallThreads);
+  auto mark = [&](int i) {
+    if (marks) cudaEventRecord(marks[i], st);
+  };
+  mark(0);
+  k_stage1<M><<<g_small, kSmallThreads, smem, st>>>(fd, ep);
+  mark(1);
+  k_scan_tile<<<(unsigned)scan_tiles(N), kScanThreads, 0, st>>>(fd);
+  mark(2);
+  k_scan_add<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(fd);
+  mark(3);
+  k_resample<<<(unsigned)((N + kResampleThreads - 1) / kResampleThreads), kResampleThreads, 0, st>>>(fd, ep);
+  mark(4);
+  k_stage2<M><<<g_small, kSmallThreads, smem, st>>>(fd, ep);
+  mark(5);
+  k_moments<M::D, M::P><<<moment_grid(N), kMomentThreads, 0, st>>>(fd, 0);
+  mark(6);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(int ode, const FilterDev& fd, cudaStream_t st) {
+  switch (ode) {
+    case PF_ODE_LINEAR2: return launch_init_t<Linear2>(fd, st);
+    case PF_ODE_ROBERTSON: return launch_init_t<Robertson>(fd, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_epoch(int ode, const FilterDev& fd, const EpochParams* ep, int S, cudaStream_t st,
+                         cudaEvent_t* marks) {
+  switch (ode) {
+    case PF_ODE_LINEAR2: return launch_epoch_t<Linear2>(fd, ep, S, st, marks);
+    case PF_ODE_ROBERTSON: return launch_epoch_t<Robertson>(fd, ep, S, st, marks);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int kernels_per_epoch(int ode) {
+  (void)ode;
+  return kEpochKernels;
+}
+
+bool ode_supported(int ode) { return ode == PF_ODE_LINEAR2 || ode == PF_ODE_ROBERTSON; }
+
+__global__ void k_set_moments(const FilterDev fd) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double L[kPMax * kPMax];
+  cholesky_psd(fd.p, fd.ctrl->C, L);
+  for (int i = 0; i < kPMax * kPMax; ++i) fd.ctrl->L[i] = L[i];
+}
+
+cudaError_t launch_set_moments(const FilterDev& fd, cudaStream_t st) {
+  k_set_moments<<<1, 32, 0, st>>>(fd);
+  return cudaGetLastError();
+}
+
+}  // namespace pfg

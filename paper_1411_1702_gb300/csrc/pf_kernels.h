@@ -1,0 +1,29 @@
+// pf_kernels.h -- launch interface between the C ABI and the kernels.
+#pragma once
+#include "pf_common.cuh"
+
+namespace pfg {
+
+// Step 1 of Algorithm 1 into the pending buffer, then the moments and commit.
+cudaError_t launch_init(int ode, const FilterDev& fd, cudaStream_t st);
+// One epoch (Steps 2-6) with the parameter block ep (device) of S substeps.
+// If marks is not NULL, marks[i] is recorded before kernel i and marks[6]
+// after the last kernel (kernel order: stage1, scan_tile, scan_add, resample,
+// stage2, moments).
+constexpr int kEpochKernels = 6;
+cudaError_t launch_epoch(int ode, const FilterDev& fd, const EpochParams* ep, int S, cudaStream_t st,
+                         cudaEvent_t* marks = nullptr);
+// Recompute the Cholesky factor after the host set phibar and C.
+cudaError_t launch_set_moments(const FilterDev& fd, cudaStream_t st);
+int moment_record_size(int ode);
+int max_grid_blocks(int64_t N);
+int scan_tiles(int64_t N);
+int kernels_per_epoch(int ode);
+bool ode_supported(int ode);
+
+// Substep table of one observation interval (host code, pf_grid.cu).
+int build_substeps(int lmm, int spacing, double dt, int substeps, double q0, double t_prev,
+                   double t_next, int depth, double hprev1, double hprev2, StepCoef* tab,
+                   int max_steps, int* depth_out);
+
+}  // namespace pfg

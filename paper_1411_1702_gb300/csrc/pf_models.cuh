@@ -1,0 +1,105 @@
+// pf_models.cuh -- the test problems as per-particle device models.
+//
+// Each model solves the implicit substep equation of the LMM (the paper's
+// Sec. 2.1: implicit methods need a Newton-type solve every step)
+//     G(y) = y - r - gamma f(y) = 0,   r = rho1 x_n + rho2 x_{n-1},
+// by K full Newton iterations (I - gamma J(y)) dy = -G(y) with the analytic
+// Jacobian re-evaluated at every iterate.  State, Jacobian and elimination
+// live in registers, one particle per thread.  Each elimination below is exact
+// Gaussian elimination specialised to the sparsity of I - gamma J; its result
+// equals dense partial-pivoting elimination up to rounding.
+#pragma once
+#include "pf_common.cuh"
+
+namespace pfg {
+
+// x' = A x, A = [[-th1, th2], [0, -th2]].
+struct Linear2 {
+  static constexpr int D = 2, P = 2, ODE = PF_ODE_LINEAR2;
+  struct Th {
+    double t1, t2;
+  };
+  __device__ __forceinline__ static Th theta(const double* t) { return Th{t[0], t[1]}; }
+
+  // gamma f(x)
+  __device__ __forceinline__ static void gf(const Th& T, double g, const double* x, double* out) {
+    out[0] = g * fma(-T.t1, x[0], T.t2 * x[1]);
+    out[1] = -g * T.t2 * x[1];
+  }
+
+  // I - gamma A = [[1 + g t1, -g t2], [0, 1 + g t2]] is constant: its two
+  // pivots are inverted once per substep (J does not depend on y).
+  __device__ __forceinline__ static void newton(const Th& T, double g, const double* r, double* y,
+                                                int K) {
+    const double gt1 = g * T.t1, gt2 = g * T.t2;
+    // two refinement steps: with K = 1 no later iteration absorbs the
+    // reciprocal's error
+    const double i1 = rcp_nr2(1.0 + gt1), i2 = rcp_nr2(1.0 + gt2);
+    for (int it = 0; it < K; ++it) {
+      const double G0 = fma(-gt2, y[1], fma(gt1, y[0], y[0] - r[0]));
+      const double G1 = fma(gt2, y[1], y[1] - r[1]);
+      const double d1 = -G1 * i2;
+      const double d0 = fma(gt2, d1, -G0) * i1;
+      y[0] += d0;
+      y[1] += d1;
+    }
+  }
+};
+
+// Robertson: y1' = -k1 y1 + k3 y2 y3, y2' = k1 y1 - k3 y2 y3 - k2 y2^2,
+// y3' = k2 y2^2.  With q = g k3 y2, p = g k3 y3, w = 2 g k2 y2,
+//   M = I - gamma J = [[m11, -p, -q], [-g k1, 1 + p + w, q], [0, -w, 1]],
+// m11 = 1 + g k1 >= 1 is the same for every Newton iteration of a substep, so
+// it is the elimination pivot of column 1 (no row swap is ever needed):
+// with im = 1/m11 and l = g k1 im = 1 - im, row 2 + l row 1 and row 3
+// (d3 = w d2 - G3) give
+//   (1 + w + im (p + q w)) d2 = -(G2 + l G1) + im q G3,
+//   d1 = im (q d3 + p d2 - G1).
+// Each correction is formed from quantities on its own scale (y2 and y3 can be
+// 1e-9 of y1), and G1 enters y2's equation only through l, as in the exact
+// inverse.
+struct Robertson {
+  static constexpr int D = 3, P = 3, ODE = PF_ODE_ROBERTSON;
+  struct Th {
+    double k1, k2, k3;
+  };
+  __device__ __forceinline__ static Th theta(const double* t) { return Th{t[0], t[1], t[2]}; }
+
+  __device__ __forceinline__ static void gf(const Th& T, double g, const double* x, double* out) {
+    const double a = g * T.k1 * x[0];
+    const double b = g * T.k3 * x[1] * x[2];
+    const double c = g * T.k2 * x[1] * x[1];
+    out[0] = b - a;
+    out[1] = (a - b) - c;
+    out[2] = c;
+  }
+
+  __device__ __forceinline__ static void newton(const Th& T, double g, const double* r, double* y,
+                                                int K) {
+    const double gk1 = g * T.k1, gk2 = g * T.k2, gk3 = g * T.k3;
+    const double im = rcp_nr(1.0 + gk1);
+    const double l = gk1 * im;
+    for (int it = 0; it < K; ++it) {
+      const double q = gk3 * y[1];  // g k3 y2
+      const double p = gk3 * y[2];  // g k3 y3
+      const double t = gk2 * y[1];  // g k2 y2
+      const double c = t * y[1];    // g k2 y2^2
+      const double w = t + t;       // 2 g k2 y2
+      const double b = q * y[2];    // g k3 y2 y3
+      // G = y - r - gamma f(y)
+      const double G1 = fma(gk1, y[0], (y[0] - r[0]) - b);
+      const double G2 = fma(-gk1, y[0], ((y[1] - r[1]) + b) + c);
+      const double G3 = (y[2] - r[2]) - c;
+      const double den = fma(im, fma(q, w, p), 1.0 + w);
+      const double num = fma(q * im, G3, -fma(l, G1, G2));
+      const double d2 = num * rcp_nr(den);
+      const double d3 = fma(w, d2, -G3);
+      const double d1 = im * fma(q, d3, fma(p, d2, -G1));
+      y[0] += d1;
+      y[1] += d2;
+      y[2] += d3;
+    }
+  }
+};
+
+}  // namespace pfg

@@ -1,0 +1,260 @@
+"""Thin ctypes binding of the C ABI in include/pf.h (libpf_gb300.so).
+
+Argument marshalling only: every step of the sampler runs in the library's
+CUDA kernels.  Importing this module loads the in-tree library and raises if
+it is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpf_gb300.so")
+
+PF_OK, PF_ERR_INVALID_ARG, PF_ERR_OOM, PF_ERR_BUDGET, PF_ERR_CUDA = 0, 1, 2, 3, 4
+PF_ERR_DEGENERATE, PF_ERR_NUMERIC, PF_ERR_TIMEOUT, PF_ERR_STATE = 5, 6, 7, 8
+PF_ODE_LINEAR2, PF_ODE_ROBERTSON, PF_ODE_BRUSSELATOR1D = 1, 2, 3
+PF_LMM_BDF1, PF_LMM_BDF2 = 1, 2
+MAX_SUBSTEPS = 640
+
+STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_INVALID_ARG", 2: "PF_ERR_OOM", 3: "PF_ERR_BUDGET",
+                4: "PF_ERR_CUDA", 5: "PF_ERR_DEGENERATE", 6: "PF_ERR_NUMERIC",
+                7: "PF_ERR_TIMEOUT", 8: "PF_ERR_STATE"}
+
+# every symbol declared in include/pf.h
+ABI_SYMBOLS = [
+    "pf_create", "pf_assimilate", "pf_estimates", "pf_stats", "pf_last_error", "pf_destroy",
+    "pf_load_observations", "pf_run", "pf_synchronize", "pf_reset", "pf_get_ensemble",
+    "pf_set_ensemble", "pf_set_moments", "pf_get_work", "pf_get_history", "pf_set_history",
+    "pf_substep_table", "pf_version", "pf_kernel_times",
+]
+KERNEL_SLOTS = ["stage1", "scan_tile", "scan_add", "resample", "stage2", "moments"]
+
+
+class PfError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Prior(C.Structure):
+    _fields_ = [("p", C.c_int), ("kind", C.POINTER(C.c_int)), ("lo", C.POINTER(C.c_double)),
+                ("hi", C.POINTER(C.c_double)), ("d", C.c_int), ("x0", C.POINTER(C.c_double)),
+                ("t0", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("a", C.c_double), ("newton_iters", C.c_int), ("spacing", C.c_int),
+                ("substeps", C.c_int), ("q0", C.c_double), ("history", C.c_int),
+                ("transform", C.c_int), ("m", C.c_int), ("obs_idx", C.POINTER(C.c_int)),
+                ("noise", C.c_int), ("sigma", C.POINTER(C.c_double)), ("kappa", C.c_double),
+                ("seed", C.c_uint64), ("filter_id", C.c_uint32), ("stream", C.c_void_p),
+                ("timing", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("epochs", C.c_int64), ("ess", C.c_double), ("log_weight_sum", C.c_double),
+                ("unique_parents", C.c_int64), ("nonfinite", C.c_int64),
+                ("theta_mean", C.c_double * 8), ("last_epoch_ms", C.c_double),
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpf_gb300.so (build it first with paper_1411_1702_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build the CUDA library first "
+                          "(python -m paper_1411_1702_gb300.build)")
+    L = C.CDLL(path)
+    sig = {
+        "pf_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int, C.c_double,
+                                C.POINTER(Prior), C.POINTER(Options), C.POINTER(C.c_void_p)]),
+        "pf_assimilate": (C.c_int, [C.c_void_p, C.c_double, _dp]),
+        "pf_estimates": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
+        "pf_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+        "pf_last_error": (C.c_char_p, [C.c_void_p]),
+        "pf_destroy": (None, [C.c_void_p]),
+        "pf_load_observations": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp]),
+        "pf_run": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+        "pf_synchronize": (C.c_int, [C.c_void_p]),
+        "pf_reset": (C.c_int, [C.c_void_p]),
+        "pf_get_ensemble": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _dp, _dp]),
+        "pf_set_ensemble": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _dp, _dp]),
+        "pf_set_moments": (C.c_int, [C.c_void_p, _dp, _dp]),
+        "pf_get_work": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
+        "pf_get_history": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int), _dp, _dp, _dp]),
+        "pf_set_history": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_double]),
+        "pf_substep_table": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
+                                       C.c_double, C.c_int, C.c_double, C.c_double, _dp, C.c_int,
+                                       C.POINTER(C.c_int)]),
+        "pf_version": (C.c_char_p, []),
+        "pf_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _d(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(st, handle=None):
+    if st != PF_OK:
+        msg = load().pf_last_error(handle)
+        raise PfError(st, msg.decode() if msg else "")
+
+
+def pf_version() -> str:
+    return load().pf_version().decode()
+
+
+def pf_substep_table(lmm, spacing, dt, substeps, q0, t_prev, t_next, depth, hprev1, hprev2):
+    """Host-only: the substep table of one interval, shape (S, 9)."""
+    coef = np.zeros((MAX_SUBSTEPS, 9))
+    dout = C.c_int()
+    S = load().pf_substep_table(lmm, spacing, dt, substeps, q0, t_prev, t_next, depth, hprev1,
+                                hprev2, _d(coef), MAX_SUBSTEPS, C.byref(dout))
+    if S < 1:
+        raise ValueError("invalid interval")
+    return coef[:S].copy(), dout.value
+
+
+class Filter:
+    """One LMM PF-SMC filter on the GPU (Algorithm 1), owned by the library."""
+
+    def __init__(self, ode, d, p, N, lmm, dt, prior_kind, prior_lo, prior_hi, x0, t0, *,
+                 a, newton_iters, spacing, substeps, q0, history, transform, obs_idx, noise,
+                 sigma, kappa, seed, filter_id=0, stream=None, timing=False):
+        L = load()
+        self._keep = []
+        kind = (C.c_int * len(prior_kind))(*[int(k) for k in prior_kind])
+        lo, hi = _f64(prior_lo), _f64(prior_hi)
+        x0a = _f64(x0)
+        obs = (C.c_int * len(obs_idx))(*[int(o) for o in obs_idx])
+        sig = _f64(sigma)
+        self._keep += [kind, lo, hi, x0a, obs, sig]
+        pr = Prior(p, kind, _d(lo), _d(hi), d, _d(x0a), float(t0))
+        op = Options(float(a), int(newton_iters), int(spacing), int(substeps), float(q0),
+                     int(history), int(transform), len(obs_idx), obs, int(noise), _d(sig),
+                     float(kappa), int(seed), int(filter_id), C.c_void_p(stream) if stream else None,
+                     1 if timing else 0)
+        h = C.c_void_p()
+        st = L.pf_create(int(ode), int(d), int(p), int(N), int(lmm), float(dt), C.byref(pr),
+                         C.byref(op), C.byref(h))
+        _check(st, None)
+        self._h = h
+        self.ode, self.d, self.p, self.N, self.m = ode, d, p, N, len(obs_idx)
+
+    @classmethod
+    def from_workload(cls, w, N=None, stream=None, seed=None, filter_id=0, timing=False):
+        return cls(w.ode, w.d, w.p, int(N if N is not None else w.N), w.lmm, w.dt, w.prior_kind,
+                   w.prior_lo, w.prior_hi, w.x0, w.t0, a=w.a, newton_iters=w.newton_iters,
+                   spacing=w.spacing, substeps=w.substeps, q0=w.q0, history=w.history,
+                   transform=w.transform, obs_idx=w.obs_idx, noise=w.noise, sigma=w.sigma,
+                   kappa=w.kappa, seed=w.seed if seed is None else seed, filter_id=filter_id,
+                   stream=stream, timing=timing)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.pf_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- the calls of include/pf.h ---------------------------------------
+    def pf_assimilate(self, t, y):
+        y = _f64(y)
+        _check(load().pf_assimilate(self._h, float(t), _d(y)), self._h)
+
+    def pf_estimates(self):
+        tb, Cm, xb = np.zeros(self.p), np.zeros((self.p, self.p)), np.zeros(self.d)
+        _check(load().pf_estimates(self._h, _d(tb), _d(Cm), _d(xb)), self._h)
+        return tb, Cm, xb
+
+    def pf_stats(self):
+        s = Stats()
+        _check(load().pf_stats(self._h, C.byref(s)), self._h)
+        return dict(epochs=s.epochs, ess=s.ess, log_weight_sum=s.log_weight_sum,
+                    unique_parents=s.unique_parents, nonfinite=s.nonfinite,
+                    theta_mean=np.array(s.theta_mean[:self.p]), last_epoch_ms=s.last_epoch_ms,
+                    h2d_bytes=s.h2d_bytes, d2h_bytes=s.d2h_bytes)
+
+    def pf_kernel_times(self):
+        """Per-kernel device ms and launch counts since the last call."""
+        n = len(KERNEL_SLOTS)
+        ms = np.zeros(n)
+        cnt = (C.c_int64 * n)()
+        _check(load().pf_kernel_times(self._h, _d(ms), cnt, n), self._h)
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_SLOTS)}
+
+    def pf_load_observations(self, t, y):
+        t, y = _f64(t), _f64(y).reshape(len(t), self.m)
+        _check(load().pf_load_observations(self._h, len(t), _d(t), _d(y)), self._h)
+
+    def pf_run(self, k0, k1):
+        _check(load().pf_run(self._h, int(k0), int(k1)), self._h)
+
+    def pf_synchronize(self):
+        _check(load().pf_synchronize(self._h), self._h)
+
+    def pf_reset(self):
+        _check(load().pf_reset(self._h), self._h)
+
+    def pf_get_ensemble(self):
+        N, d, p = self.N, self.d, self.p
+        x, h1, h2 = np.zeros((N, d)), np.zeros((N, d)), np.zeros((N, d))
+        phi, lw = np.zeros((N, p)), np.zeros(N)
+        _check(load().pf_get_ensemble(self._h, _d(x), _d(h1), _d(h2), _d(phi), _d(lw)), self._h)
+        return dict(x=x, h1=h1, h2=h2, phi=phi, lw=lw)
+
+    def pf_set_ensemble(self, x=None, h1=None, h2=None, phi=None, lw=None):
+        a = [None if v is None else _f64(v) for v in (x, h1, h2, phi, lw)]
+        _check(load().pf_set_ensemble(self._h, *[_d(v) for v in a]), self._h)
+
+    def pf_set_moments(self, phibar, Cm):
+        pb, Cm = _f64(phibar), _f64(Cm)
+        _check(load().pf_set_moments(self._h, _d(pb), _d(Cm)), self._h)
+
+    def pf_get_work(self):
+        N = self.N
+        ll1, lg, c = np.zeros(N), np.zeros(N), np.zeros(N)
+        idx = np.zeros(N, dtype=np.int32)
+        _check(load().pf_get_work(self._h, _d(ll1), _d(lg), _d(c), idx.ctypes.data_as(_ip)), self._h)
+        return dict(ll1=ll1, lg=lg, c=c, idx=idx)
+
+    def pf_get_history(self):
+        e, dp = C.c_int64(), C.c_int()
+        t, h1, h2 = C.c_double(), C.c_double(), C.c_double()
+        _check(load().pf_get_history(self._h, C.byref(e), C.byref(dp), C.byref(t), C.byref(h1),
+                                     C.byref(h2)), self._h)
+        return dict(epoch=e.value, depth=dp.value, t_prev=t.value, hprev1=h1.value, hprev2=h2.value)
+
+    def pf_set_history(self, epoch, depth, t_prev, hprev1, hprev2):
+        _check(load().pf_set_history(self._h, int(epoch), int(depth), float(t_prev), float(hprev1),
+                                     float(hprev2)), self._h)

@@ -1,0 +1,121 @@
+"""CPU tests of the C-ABI library: it builds, loads, exports every symbol that
+include/pf.h declares, rejects bad arguments before touching the GPU, and its
+host-side substep grid matches the oracle's (no GPU compute here)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_1702_gb300 import build as B
+from paper_1411_1702_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pf():
+    B.build()
+    from paper_1411_1702_gb300 import pf as _pf
+    _pf.load()
+    return _pf
+
+
+def _declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(pf_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(pf):
+    declared = _declared_functions()
+    assert len(declared) >= 15
+    lib = C.CDLL(pf.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) == set(pf.ABI_SYMBOLS)
+
+
+def test_version(pf):
+    assert "sm_103a" in pf.pf_version()
+
+
+def _create(pf, **over):
+    w = W.robertson(N=8, T=2)
+    args = dict(ode=w.ode, d=w.d, p=w.p, N=8, lmm=w.lmm, dt=w.dt, prior_kind=w.prior_kind,
+                prior_lo=w.prior_lo, prior_hi=w.prior_hi, x0=w.x0, t0=w.t0)
+    kw = dict(a=w.a, newton_iters=w.newton_iters, spacing=w.spacing, substeps=w.substeps, q0=w.q0,
+              history=w.history, transform=w.transform, obs_idx=w.obs_idx, noise=w.noise,
+              sigma=w.sigma, kappa=w.kappa, seed=0)
+    for k, v in over.items():
+        if k in args:
+            args[k] = v
+        else:
+            kw[k] = v
+    return pf.Filter(*args.values(), **kw)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(d=4), dict(p=2), dict(N=0), dict(ode=9), dict(lmm=3), dict(a=0.0), dict(a=1.5),
+    dict(newton_iters=0), dict(obs_idx=[5]), dict(sigma=[0.0, 0.01]), dict(substeps=0),
+    dict(substeps=100000), dict(prior_lo=[-1.0, 1.0, 1.0]), dict(kappa=-1.0), dict(spacing=7),
+])
+def test_invalid_arguments_rejected_before_gpu(pf, bad):
+    with pytest.raises(pf.PfError) as ei:
+        _create(pf, **bad)
+    assert ei.value.status == pf.PF_ERR_INVALID_ARG
+
+
+def _compare_tables(w, t_prev, t_next, depth, h1, h2, pf):
+    cfg = oracle.make_config(w)
+    tab, S, dout = oracle.build_substeps(cfg, t_prev, t_next, depth, h1, h2)
+    coef, gdout = pf.pf_substep_table(w.lmm, w.spacing, w.dt, w.substeps, w.q0, t_prev, t_next,
+                                      depth, h1, h2)
+    assert coef.shape[0] == S and gdout == dout
+    o = oracle.substep_dicts(tab, S)
+    for i in range(S):
+        assert coef[i, 0] == o[i]["kind"]
+        assert coef[i, 1] == o[i]["h"]  # the same grid formula gives the same steps
+        for j, key in enumerate(["gamma", "rho1", "rho2", "pi0", "pi1", "pi2", "mu"], start=2):
+            assert coef[i, j] == pytest.approx(o[i][key], rel=1e-12, abs=1e-15), (i, key)
+    return coef
+
+
+def test_substep_table_matches_oracle(pf):
+    lw = W.linear2(N=4, T=3)
+    _compare_tables(lw, 0.0, 0.1, 0, 0.0, 0.0, pf)
+    _compare_tables(lw, 0.1, 0.2, 2, 0.005, 0.005, pf)
+    _compare_tables(lw, 0.1, 0.2, 2, 0.001, 0.001, pf)        # ratio >= 2: cold start
+    _compare_tables(lw.with_(lmm=1), 0.1, 0.2, 2, 0.005, 0.005, pf)
+    rw = W.robertson(N=4, T=40)
+    t = rw.t_obs
+    _compare_tables(rw, 0.0, t[0], 0, 0.0, 0.0, pf)
+    coef0, _ = pf.pf_substep_table(rw.lmm, rw.spacing, rw.dt, rw.substeps, rw.q0, 0.0, t[0], 0, 0, 0)
+    _compare_tables(rw, t[0], t[1], 2, coef0[-1, 1], coef0[-2, 1], pf)
+    _compare_tables(rw, t[20], t[21], 2, 0.3, 0.29, pf)
+    bw = W.brusselator(N=4, T=3)
+    _compare_tables(bw, 1.0 / 3.0, 2.0 / 3.0, 2, 1.0 / 60.0, 1.0 / 60.0, pf)
+
+
+def test_substep_table_rejects_bad_intervals(pf):
+    with pytest.raises(ValueError):
+        pf.pf_substep_table(2, 0, 0.005, 0, 0.0, 0.1, 0.1013, 2, 0.005, 0.005)
+    with pytest.raises(ValueError):
+        pf.pf_substep_table(2, 0, 0.005, 0, 0.0, 0.2, 0.1, 2, 0.005, 0.005)
+    with pytest.raises(ValueError):
+        pf.pf_substep_table(2, 1, 0.0, 50, 0.0, 0.0, 1e-4, 0, 0.0, 0.0)   # q0 missing
+
+
+def test_substep_coefficients_constant_step(pf):
+    coef, _ = pf.pf_substep_table(2, 0, 0.01, 0, 0.0, 1.0, 1.1, 2, 0.01, 0.01)
+    assert np.allclose(coef[:, 3], 4.0 / 3.0, rtol=1e-12)
+    assert np.allclose(coef[:, 4], -1.0 / 3.0, rtol=1e-12)
+    assert np.allclose(coef[:, 2], 2.0 / 3.0 * 0.01, rtol=1e-9)
+    assert np.allclose(coef[:, 8], -2.0 / 11.0, rtol=1e-9)

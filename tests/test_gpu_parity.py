@@ -1,0 +1,232 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_1702_gb300 import build as B
+from paper_1411_1702_gb300 import workloads as W
+from parity_util import check_epoch, rel_state_err, sync_oracle_from_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf():
+    B.build()
+    oracle.build()
+    from paper_1411_1702_gb300 import pf as _pf
+    _pf.load()
+    return _pf
+
+
+def _pair(pf, w, N=None, **kw):
+    g = pf.Filter.from_workload(w, N=N, **kw)
+    o = oracle.Filter(w, N=N)
+    o.init()
+    return g, o
+
+
+@pytest.mark.parametrize("name,N", [("linear2", 2053), ("robertson", 3001), ("robertson", 129),
+                                    ("linear2", 1)])
+def test_init_matches_oracle(pf, name, N):
+    w = W.get(name, N=N, T=2)
+    g, o = _pair(pf, w, N=N)
+    gs, os_ = g.pf_get_ensemble(), o.state()
+    assert rel_state_err(gs["phi"], os_["phi"]) <= 1e-14
+    assert np.array_equal(gs["x"], os_["x"]) and np.array_equal(gs["h2"], os_["h2"])
+    assert np.allclose(gs["lw"], os_["lw"], rtol=1e-15, atol=0)
+    tb, Cm, xb = g.pf_estimates()
+    om = o.moments()
+    assert np.allclose(tb, om["phibar"], rtol=1e-13, atol=1e-15)
+    assert np.allclose(Cm, om["C"], rtol=1e-10, atol=1e-14)
+    assert np.allclose(xb, om["xbar"], rtol=1e-14)
+
+
+@pytest.mark.parametrize("name,N,T", [("linear2", 2053, 6), ("robertson", 3001, 8),
+                                      ("robertson", 1025, 4)])
+def test_epoch_stage_parity(pf, name, N, T):
+    w = W.get(name, N=N, T=T)
+    g, o = _pair(pf, w, N=N)
+    worst = 0.0
+    for k in range(T):
+        errs = check_epoch(g, o, w.t_obs[k], w.y_obs[k])
+        worst = max(worst, errs["x"])
+    assert worst <= 1e-10
+
+
+def test_full_size_robertson_epochs(pf):
+    """The bench configuration (N = 131072, 50 geometric substeps): full
+    per-particle parity over the first epochs and a late epoch."""
+    w = W.robertson()
+    g, o = _pair(pf, w)
+    for k in range(3):
+        check_epoch(g, o, w.t_obs[k], w.y_obs[k])
+    # jump to a late interval: run on the GPU alone, then compare one epoch
+    for k in range(3, 25):
+        g.pf_assimilate(w.t_obs[k], w.y_obs[k])
+    check_epoch(g, o, w.t_obs[25], w.y_obs[25])
+
+
+def test_independent_runs_agree(pf):
+    """GPU and oracle each run the whole filter on their own (own scan and
+    resampling); with the same seed they follow the same trajectory."""
+    for name, N in [("linear2", 2000), ("robertson", 4096)]:
+        w = W.get(name, N=N)
+        g, o = _pair(pf, w)
+        for k in range(w.T):
+            g.pf_assimilate(w.t_obs[k], w.y_obs[k])
+            assert o.epoch(w.t_obs[k], w.y_obs[k]) == oracle.OK
+            assert np.array_equal(g.pf_get_work()["idx"], o.work()["idx"]), (name, k)
+        tb, Cm, xb = g.pf_estimates()
+        om = o.moments()
+        assert np.allclose(tb, om["phibar"], rtol=1e-9, atol=1e-12)
+        assert np.allclose(Cm, om["C"], rtol=1e-6, atol=1e-14)
+        assert rel_state_err(g.pf_get_ensemble()["x"], o.state()["x"]) <= 1e-8
+
+
+def test_posterior_within_three_mc_standard_errors(pf):
+    """Across seeds, the GPU and oracle posterior means agree within 3 Monte
+    Carlo standard errors."""
+    w0 = W.linear2()
+    R = 6
+    gm, om = [], []
+    for seed in range(R):
+        w = w0.with_(seed=seed)
+        g, o = _pair(pf, w)
+        for k in range(w.T):
+            g.pf_assimilate(w.t_obs[k], w.y_obs[k])
+            assert o.epoch(w.t_obs[k], w.y_obs[k]) == oracle.OK
+        gm.append(g.pf_estimates()[0])
+        om.append(o.moments()["phibar"])
+    gm, om = np.array(gm), np.array(om)
+    se = np.sqrt(gm.var(axis=0, ddof=1) / R + om.var(axis=0, ddof=1) / R) + 1e-15
+    assert np.all(np.abs(gm.mean(axis=0) - om.mean(axis=0)) <= 3 * se)
+
+
+def test_deterministic_reruns(pf):
+    w = W.robertson(N=5000, T=5)
+    runs = []
+    for _ in range(2):
+        g = pf.Filter.from_workload(w)
+        for k in range(w.T):
+            g.pf_assimilate(w.t_obs[k], w.y_obs[k])
+        runs.append(g.pf_get_ensemble())
+        g.close()
+    for key in runs[0]:
+        assert np.array_equal(runs[0][key], runs[1][key])
+
+
+def test_series_path_matches_online_path(pf):
+    w = W.robertson(N=4099, T=12)
+    a = pf.Filter.from_workload(w)
+    for k in range(w.T):
+        a.pf_assimilate(w.t_obs[k], w.y_obs[k])
+    b = pf.Filter.from_workload(w)
+    b.pf_load_observations(w.t_obs, w.y_obs)
+    b.pf_run(0, 5)
+    b.pf_run(5, w.T)
+    b.pf_synchronize()
+    ea, eb = a.pf_get_ensemble(), b.pf_get_ensemble()
+    for key in ea:
+        assert np.array_equal(ea[key], eb[key])
+    assert a.pf_get_history() == b.pf_get_history()
+    # reset restarts the loaded series from observation 0 without reallocation
+    b.pf_reset()
+    b.pf_run(0, w.T)
+    b.pf_synchronize()
+    ec = b.pf_get_ensemble()
+    for key in ea:
+        assert np.array_equal(ea[key], ec[key])
+
+
+def test_single_particle(pf):
+    w = W.linear2(N=1, T=5)
+    g, o = _pair(pf, w, N=1)
+    for k in range(w.T):
+        check_epoch(g, o, w.t_obs[k], w.y_obs[k])
+        assert np.array_equal(g.pf_get_work()["idx"], [0])
+
+
+def test_degenerate_epoch_is_transactional(pf):
+    w = W.linear2(N=300, T=3)
+    g = pf.Filter.from_workload(w)
+    g.pf_assimilate(w.t_obs[0], w.y_obs[0])
+    good = g.pf_get_ensemble()
+    bad = {k: v.copy() for k, v in good.items()}
+    bad["x"][:] = np.nan
+    g.pf_set_ensemble(**bad)
+    h0 = g.pf_get_history()
+    with pytest.raises(pf.PfError) as ei:
+        g.pf_assimilate(w.t_obs[1], w.y_obs[1])
+    assert ei.value.status == pf.PF_ERR_DEGENERATE
+    after = g.pf_get_ensemble()
+    assert np.all(np.isnan(after["x"])) and np.array_equal(after["phi"], good["phi"])
+    assert g.pf_get_history() == h0
+    # recover: restore the state and continue
+    g.pf_set_ensemble(**good)
+    g.pf_assimilate(w.t_obs[1], w.y_obs[1])
+    assert g.pf_stats()["epochs"] == 2
+
+
+def test_invalid_observations_rejected(pf):
+    w = W.linear2(N=64, T=3)
+    g = pf.Filter.from_workload(w)
+    with pytest.raises(pf.PfError) as ei:
+        g.pf_assimilate(w.t_obs[0], [np.nan])
+    assert ei.value.status == pf.PF_ERR_INVALID_ARG
+    with pytest.raises(pf.PfError):
+        g.pf_assimilate(-1.0, w.y_obs[0])
+    with pytest.raises(pf.PfError):
+        g.pf_assimilate(w.t_obs[0] + 0.0013, w.y_obs[0])  # not a whole number of substeps
+    g.pf_assimilate(w.t_obs[0], w.y_obs[0])
+    with pytest.raises(pf.PfError) as ei:
+        g.pf_run(0, 1)
+    assert ei.value.status == pf.PF_ERR_STATE
+
+
+def test_zero_weight_particle_handled(pf):
+    w = W.linear2(N=257, T=2)
+    g, o = _pair(pf, w, N=257)
+    st = g.pf_get_ensemble()
+    st["x"][7] = np.nan
+    g.pf_set_ensemble(**st)
+    errs = check_epoch(g, o, w.t_obs[0], w.y_obs[0])
+    assert 7 not in set(g.pf_get_work()["idx"].tolist())
+    assert np.all(np.isfinite(g.pf_estimates()[0]))
+    assert errs["x"] <= 1e-10
+
+
+def test_deterministic_special_case(pf):
+    """a = 1, kappa = 0, point-mass prior: every particle follows the plain
+    BDF2 solution of the oracle."""
+    w = W.robertson(N=777, T=10)
+    th = w.theta_true
+    w = w.with_(a=1.0, kappa=0.0, prior_lo=list(th), prior_hi=list(th))
+    g = pf.Filter.from_workload(w)
+    cfg = oracle.make_config(w)
+    x = np.array(w.x0, dtype=float)
+    h1, h2 = x.copy(), x.copy()
+    depth, hp1, hp2, t = 0, 0.0, 0.0, 0.0
+    for k in range(w.T):
+        g.pf_assimilate(w.t_obs[k], w.y_obs[k])
+        tab, S, dout = oracle.build_substeps(cfg, t, w.t_obs[k], depth, hp1, hp2)
+        x, h1, h2, _ = oracle.propagate(w.ode, w.newton_iters, th, tab, S, x, h1, h2)
+        hp1, hp2 = tab[S - 1].h, tab[S - 2].h
+        depth, t = dout, w.t_obs[k]
+        _, Cm, xb = g.pf_estimates()
+        assert np.max(np.abs(xb - x)) <= 1e-10 * np.max(np.abs(x))
+        assert np.max(np.abs(Cm)) <= 1e-20
+
+
+def test_restart_history_mode(pf):
+    w = W.robertson(N=1500, T=4).with_(history=W.HIST_RESTART)
+    g, o = _pair(pf, w, N=1500)
+    for k in range(w.T):
+        check_epoch(g, o, w.t_obs[k], w.y_obs[k])
+
+
+def test_bdf1_and_identity_transform(pf):
+    w = W.linear2(N=999, T=4).with_(lmm=1, transform=W.TRANSFORM_IDENTITY)
+    g, o = _pair(pf, w, N=999)
+    for k in range(w.T):
+        check_epoch(g, o, w.t_obs[k], w.y_obs[k])
