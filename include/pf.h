@@ -220,6 +220,38 @@ int pf_substep_table(int lmm, int spacing, double dt, int substeps, double q0, d
                      double t_next, int depth, double hprev1, double hprev2, double* coef,
                      int max_steps, int* depth_out);
 
+/* ---- systematic resampling without allocation ----------------------------
+ * No counterpart in the paper: a library convenience for callers that cannot
+ * allocate device memory where they need to resample -- applications whose
+ * pool allocator owns all device memory and forbids other allocations,
+ * latency-critical loops where cudaMalloc's implicit device-wide
+ * synchronisation would stall their other streams, and callers that must not
+ * fail with out-of-memory in the middle of a step.
+ *
+ * Computes, on `stream` (NULL = the legacy default stream) and without
+ * waiting, the cumulative fitness weights c_k = sum_{i<=k} exp(log_g_i -
+ * max log_g) and the systematic-resampling indices
+ * idx_i = min{k : c_k > ((i + u)/N) c_{N-1}} (else the first k with
+ * c_k = c_{N-1}), exactly as pf_assimilate does: for the same log weights and
+ * u, c and idx are bit-identical.  All three buffers are device memory owned by
+ * the caller: log_g (N doubles, read; finite or -inf, anything else counts as
+ * a zero weight), cumulative (N doubles, written), idx (N int32, written).  If
+ * every weight is zero, c is all zero and every index is 0.
+ *
+ * Nothing is allocated or freed.  The scratch (per-tile sums and offsets,
+ * completion counters) is one fixed array of about 400 KB in the library's
+ * device image; every GPU that loads the library holds it until the process
+ * exits.  The first call on a device looks up that array's device address
+ * with the device current; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents, so calls
+ * whose GPU work overlaps (unordered streams, several host threads) race and
+ * corrupt each other's results: order them on one stream or synchronise in
+ * between.  Errors: INVALID_ARG (NULL buffer, N < 1, u outside [0, 1)),
+ * BUDGET (N > PF_NOALLOC_MAX_PARTICLES), CUDA (address lookup or launch). */
+#define PF_NOALLOC_MAX_PARTICLES (1LL << 24)
+pf_status pf_resample_systematic_noalloc(const double* log_g, int64_t N, double u,
+                                         double* cumulative, int32_t* idx, void* stream);
+
 /* Library version string. */
 const char* pf_version(void);
 

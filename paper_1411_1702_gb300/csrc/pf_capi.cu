@@ -25,6 +25,10 @@ thread_local std::string g_thread_error;
 
 }  // namespace
 
+namespace pfg {
+void set_thread_error(const std::string& msg) { g_thread_error = msg; }
+}  // namespace pfg
+
 struct pf_filter {
   // configuration
   int ode, d, p, m, lmm, K, spacing, substeps, history, transform, noise;

@@ -1,5 +1,7 @@
 // pf_kernels.h -- launch interface between the C ABI and the kernels.
 #pragma once
+#include <string>
+
 #include "pf_common.cuh"
 
 namespace pfg {
@@ -20,6 +22,9 @@ int max_grid_blocks(int64_t N);
 int scan_tiles(int64_t N);
 int kernels_per_epoch(int ode);
 bool ode_supported(int ode);
+
+// Error text returned by pf_last_error(NULL) on this thread (pf_capi.cu).
+void set_thread_error(const std::string& msg);
 
 // Substep table of one observation interval (host code, pf_grid.cu).
 int build_substeps(int lmm, int spacing, double dt, int substeps, double q0, double t_prev,

@@ -29,8 +29,9 @@ ABI_SYMBOLS = [
     "pf_create", "pf_assimilate", "pf_estimates", "pf_stats", "pf_last_error", "pf_destroy",
     "pf_load_observations", "pf_run", "pf_synchronize", "pf_reset", "pf_get_ensemble",
     "pf_set_ensemble", "pf_set_moments", "pf_get_work", "pf_get_history", "pf_set_history",
-    "pf_substep_table", "pf_version", "pf_kernel_times",
+    "pf_substep_table", "pf_version", "pf_kernel_times", "pf_resample_systematic_noalloc",
 ]
+NOALLOC_MAX_PARTICLES = 1 << 24
 KERNEL_SLOTS = ["stage1", "scan_tile", "scan_add", "resample", "stage2", "moments"]
 
 
@@ -99,6 +100,8 @@ def load(path: str = LIB_PATH):
                                        C.POINTER(C.c_int)]),
         "pf_version": (C.c_char_p, []),
         "pf_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), C.c_int]),
+        "pf_resample_systematic_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
+                                                     C.c_void_p, C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -124,6 +127,15 @@ def _check(st, handle=None):
 
 def pf_version() -> str:
     return load().pf_version().decode()
+
+
+def pf_resample_systematic_noalloc(log_g_ptr, N, u, cumulative_ptr, idx_ptr, stream=None):
+    """Systematic resampling of caller-owned device buffers (raw device
+    addresses) without any allocation; asynchronous on `stream`."""
+    st = load().pf_resample_systematic_noalloc(C.c_void_p(log_g_ptr), int(N), float(u),
+                                               C.c_void_p(cumulative_ptr), C.c_void_p(idx_ptr),
+                                               C.c_void_p(stream) if stream else None)
+    _check(st, None)
 
 
 def pf_substep_table(lmm, spacing, dt, substeps, q0, t_prev, t_next, depth, hprev1, hprev2):

@@ -1,0 +1,69 @@
+"""The allocation-free resampling call against the filter's own resampling.
+
+pf_resample_systematic_noalloc serves callers that cannot allocate device
+memory where they resample (a pool allocator that owns all device memory, a
+latency-critical loop that cannot afford cudaMalloc's device-wide
+synchronisation, a step that must not fail with out-of-memory).  It keeps its
+scratch in a fixed array inside the library.  This test hands it the log
+fitness weights of real filter epochs -- in buffers the test owns -- and checks
+that its cumulative weights and indices equal what pf_assimilate produced,
+on consecutive calls (the shared scratch must not leak state between calls).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_1702_gb300 import build as B
+from paper_1411_1702_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    B.build()
+    oracle.build()
+    from paper_1411_1702_gb300 import pf
+    pf.load()
+    return pf, torch
+
+
+def _noalloc(pf, torch, lg, u):
+    N = len(lg)
+    d_lg = torch.tensor(lg, dtype=torch.float64, device="cuda")
+    d_c = torch.full((N,), -1.0, dtype=torch.float64, device="cuda")
+    d_idx = torch.full((N,), -7, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    pf.pf_resample_systematic_noalloc(d_lg.data_ptr(), N, u, d_c.data_ptr(), d_idx.data_ptr(),
+                                      stream or None)
+    torch.cuda.synchronize()
+    return d_c.cpu().numpy(), d_idx.cpu().numpy()
+
+
+@pytest.mark.parametrize("N", [5003, 1, 131072])
+def test_noalloc_matches_filter_on_consecutive_calls(env, N):
+    pf, torch = env
+    w = W.robertson(N=N, T=3)
+    g = pf.Filter.from_workload(w)
+    for k in range(2):
+        g.pf_assimilate(w.t_obs[k], w.y_obs[k])
+        work = g.pf_get_work()
+        u = oracle.uniform(w.seed, 0, oracle.RNG_RESAMPLE, 0, k, 0)
+        c, idx = _noalloc(pf, torch, work["lg"], u)
+        assert np.array_equal(idx, work["idx"]), f"indices differ at call {k}"
+        assert np.allclose(c, work["c"], rtol=1e-12, atol=0.0), f"cumulative weights differ at call {k}"
+    g.close()
+
+
+def test_noalloc_rejects_oversized_and_bad_arguments(env):
+    pf, torch = env
+    d = torch.zeros(4, dtype=torch.float64, device="cuda")
+    i = torch.zeros(4, dtype=torch.int32, device="cuda")
+    with pytest.raises(pf.PfError) as ei:
+        pf.pf_resample_systematic_noalloc(d.data_ptr(), pf.NOALLOC_MAX_PARTICLES + 1, 0.5,
+                                          d.data_ptr(), i.data_ptr())
+    assert ei.value.status == pf.PF_ERR_BUDGET
+    with pytest.raises(pf.PfError) as ei:
+        pf.pf_resample_systematic_noalloc(d.data_ptr(), 4, 1.0, d.data_ptr(), i.data_ptr())
+    assert ei.value.status == pf.PF_ERR_INVALID_ARG
