@@ -48,7 +48,12 @@ FP64_PEAK_TFLOPS = 2.0 * 152 * 2.070e9 * 2 / 1e12
 STAGE2_FLOPS_PER_SUBSTEP = {
     "robertson": lambda K: 15 + 9 + 12 + 8 + 42 * K,
     "linear2": lambda K: 10 + 6 + 8 + 20 + 14 * K,
+    # 32 grid points x 72 flops per Newton iteration (f, G, 2x2 block, Thomas
+    # forward and backward), predictor 5d, history 3d, Milne 4d, constants
+    "brusselator": lambda K: 320 + 192 + 256 + 15 + 2304 * K,
 }
+STAGE2_KERNEL = {"robertson": "k_stage2<Robertson>", "linear2": "k_stage2<Linear2>",
+                 "brusselator": "k_bstage2"}
 
 
 def _dist():
@@ -301,7 +306,7 @@ def run_ours(args, w):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(round(h2d)),
                 "d2h_bytes_per_step": int(round(d2h))},
         "gpu_launches": 6 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "k_stage2<Robertson>", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": STAGE2_KERNEL[w.name], "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                      "traffic": None,
@@ -340,7 +345,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="robertson", choices=["robertson", "linear2"])
+    ap.add_argument("--workload", default="robertson", choices=["robertson", "linear2", "brusselator"])
     ap.add_argument("--e2e-steps", type=int, default=80)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-particles", type=int, default=16384)

@@ -1,0 +1,329 @@
+// pf_bruss.cu -- stage kernels of the epoch for the 1D Brusselator (d = 64):
+// 32 interior grid points xi_i = i/33, Dirichlet u = 1, v = 3 at both ends,
+//   u_i' = A + u_i^2 v_i - (B+1) u_i + D (u_{i-1} - 2 u_i + u_{i+1}),
+//   v_i' = B u_i - u_i^2 v_i + D (v_{i-1} - 2 v_i + v_{i+1}),  D = alpha 33^2,
+// state interleaved (u_0, v_0, u_1, v_1, ...), theta = (A, B, alpha).
+//
+// One particle per thread, as for the small models: the FP64 pipe is the
+// limit on GB300, so the Newton system is solved with the fewest FP64 operations
+// -- an exact block Thomas sweep over the 2x2 blocks of the block-tridiagonal
+// I - gamma J (off-diagonal blocks -gamma D I) -- rather than a warp-parallel
+// cyclic reduction, which would multiply the arithmetic several times over.
+// The particle's vectors live in HBM as structure-of-arrays (component-major,
+// coalesced across the warp): the rotating history x_n, x_{n-1}, x_{n-2} in the
+// pending ensemble buffer, and r, the error predictor and the error sums in a
+// work area.  The sweep's inverted pivot blocks and intermediate solutions
+// (6 doubles per grid point) are kept in shared memory for the backward pass.
+#include "pf_epoch.cuh"
+#include "pf_kernels.h"
+
+namespace pfg {
+
+constexpr int kBrPts = 32;
+constexpr int kBrD = 64;
+constexpr int kBrThreads = 32;  // one warp per block; shared memory per lane
+constexpr size_t kBrSweepDoubles = (size_t)kBrPts * 6 * kBrThreads;
+
+struct BrTheta {
+  double A, B, D;
+};
+
+__device__ __forceinline__ BrTheta br_theta(const double* th) {
+  return BrTheta{th[0], th[1], th[2] * 33.0 * 33.0};
+}
+
+// x_EE = x + h f(x) for the BDF1 error predictor
+__device__ void br_euler_predictor(const double* __restrict__ X, double* __restrict__ XP, int64_t N,
+                                   int64_t n, double h, const BrTheta& T) {
+  double uL = 1.0, vL = 3.0, u = X[n], v = X[N + n];
+  for (int i = 0; i < kBrPts; ++i) {
+    double uR = 1.0, vR = 3.0;
+    if (i < kBrPts - 1) {
+      uR = X[(int64_t)(2 * i + 2) * N + n];
+      vR = X[(int64_t)(2 * i + 3) * N + n];
+    }
+    const double uuv = u * u * v;
+    const double fu = fma(T.D, (uL - 2.0 * u) + uR, fma(-(T.B + 1.0), u, T.A + uuv));
+    const double fv = fma(T.D, (vL - 2.0 * v) + vR, fma(T.B, u, -uuv));
+    XP[(int64_t)(2 * i) * N + n] = fma(h, fu, u);
+    XP[(int64_t)(2 * i + 1) * N + n] = fma(h, fv, v);
+    uL = u;
+    vL = v;
+    u = uR;
+    v = vR;
+  }
+}
+
+// K Newton iterations on y (in place): (I - g J(y)) dy = -G(y),
+// G = y - r - g f(y), with M_i the 2x2 diagonal block of point i and e = g D:
+//   forward  W_i = (M_i - e^2 W_{i-1})^{-1},  z_i = W_i (-G_i + e z_{i-1}),
+//   backward dy_i = z_i + e W_i dy_{i+1}  (dy_32 = 0).
+__device__ void br_newton(double* __restrict__ Y, const double* __restrict__ R, int64_t N, int64_t n,
+                          double g, int K, const BrTheta& T, double* __restrict__ sW,
+                          double* __restrict__ sZ) {
+  const int lane = threadIdx.x;
+  const double gD = g * T.D, e2 = gD * gD, g2 = 2.0 * g, mg = -g;
+  const double ca = 1.0 + g * (T.B + 1.0) + 2.0 * gD;  // 1 + g(B+1) + 2gD
+  const double cd = 1.0 + 2.0 * gD;
+  const double gA = g * T.A, gB1 = g * (T.B + 1.0), gB = g * T.B;
+  for (int it = 0; it < K; ++it) {
+    double uL = 1.0, vL = 3.0;
+    double u = Y[n], v = Y[N + n];
+    double W00 = 0.0, W01 = 0.0, W10 = 0.0, W11 = 0.0, z0 = 0.0, z1 = 0.0;
+    for (int i = 0; i < kBrPts; ++i) {
+      double uR = 1.0, vR = 3.0;
+      if (i < kBrPts - 1) {
+        uR = Y[(int64_t)(2 * i + 2) * N + n];
+        vR = Y[(int64_t)(2 * i + 3) * N + n];
+      }
+      const double ru = R[(int64_t)(2 * i) * N + n], rv = R[(int64_t)(2 * i + 1) * N + n];
+      const double uu = u * u, uv = u * v, uuv = uu * v;
+      const double lapu = fma(-2.0, u, uL + uR), lapv = fma(-2.0, v, vL + vR);
+      const double Gu = fma(-gD, lapu, fma(gB1, u, fma(mg, uuv, (u - ru) - gA)));
+      const double Gv = fma(-gD, lapv, fma(-gB, u, fma(g, uuv, v - rv)));
+      double a = fma(-g2, uv, ca), b = mg * uu, c = fma(g2, uv, -gB), d = fma(g, uu, cd);
+      a = fma(-e2, W00, a);
+      b = fma(-e2, W01, b);
+      c = fma(-e2, W10, c);
+      d = fma(-e2, W11, d);
+      const double rdet = rcp_nr(fma(a, d, -(b * c)));
+      W00 = d * rdet;
+      W01 = -b * rdet;
+      W10 = -c * rdet;
+      W11 = a * rdet;
+      const double h0 = fma(gD, z0, -Gu), h1 = fma(gD, z1, -Gv);
+      z0 = fma(W00, h0, W01 * h1);
+      z1 = fma(W10, h0, W11 * h1);
+      double* w = sW + (i * 4) * kBrThreads + lane;
+      w[0] = W00;
+      w[kBrThreads] = W01;
+      w[2 * kBrThreads] = W10;
+      w[3 * kBrThreads] = W11;
+      double* zz = sZ + (i * 2) * kBrThreads + lane;
+      zz[0] = z0;
+      zz[kBrThreads] = z1;
+      uL = u;
+      vL = v;
+      u = uR;
+      v = vR;
+    }
+    double du = 0.0, dv = 0.0;
+    for (int i = kBrPts - 1; i >= 0; --i) {
+      const double* w = sW + (i * 4) * kBrThreads + lane;
+      const double* zz = sZ + (i * 2) * kBrThreads + lane;
+      const double t0 = fma(w[0], du, w[kBrThreads] * dv);
+      const double t1 = fma(w[2 * kBrThreads], du, w[3 * kBrThreads] * dv);
+      du = fma(gD, t0, zz[0]);
+      dv = fma(gD, t1, zz[kBrThreads]);
+      Y[(int64_t)(2 * i) * N + n] += du;
+      Y[(int64_t)(2 * i + 1) * N + n] += dv;
+    }
+  }
+}
+
+// Psi over the S substeps.  P0, P1, P2 hold x_n, x_{n-1}, x_{n-2}; each
+// substep writes its iterate over x_{n-2} and the roles rotate.
+template <bool ERR>
+__device__ void br_propagate(const FilterDev& fd, int64_t n, const StepCoef* sc, int S, int K,
+                             const BrTheta& T, double*& P0, double*& P1, double*& P2, double* sW,
+                             double* sZ) {
+  const int64_t N = fd.N;
+  double* R = fd.wk;
+  double* XP = fd.wk + (int64_t)kBrD * N;
+  double* EE = fd.wk + 2 * (int64_t)kBrD * N;
+  for (int s = 0; s < S; ++s) {
+    const StepCoef& c = sc[s];
+    if (c.kind == 2) {
+      for (int k = 0; k < kBrD; ++k) {
+        const int64_t o = (int64_t)k * N + n;
+        const double xn = P0[o], x1 = P1[o], x2 = P2[o];
+        const double xp = fma(c.pi2, x2, fma(c.pi1, x1, c.pi0 * xn));
+        R[o] = fma(c.rho2, x1, c.rho1 * xn);
+        P2[o] = xp;
+        if (ERR) XP[o] = xp;
+      }
+    } else {
+      if (ERR) br_euler_predictor(P0, XP, N, n, c.h, T);
+      for (int k = 0; k < kBrD; ++k) {
+        const int64_t o = (int64_t)k * N + n;
+        const double xn = P0[o];
+        R[o] = xn;
+        P2[o] = xn;
+      }
+    }
+    br_newton(P2, R, N, n, c.gamma, K, T, sW, sZ);
+    if (ERR) {
+      for (int k = 0; k < kBrD; ++k) {
+        const int64_t o = (int64_t)k * N + n;
+        const double e = c.mu * (P2[o] - XP[o]);
+        EE[o] = fma(e, e, EE[o]);
+      }
+    }
+    double* t = P2;
+    P2 = P1;
+    P1 = P0;
+    P0 = t;
+  }
+}
+
+__device__ __forceinline__ double br_loglik(const FilterDev& fd, const EpochParams* __restrict__ ep,
+                                            const double* X, int64_t n) {
+  double s = 0.0;
+  for (int i = 0; i < fd.m; ++i) {
+    const double z = (ep->y[i] - X[(int64_t)fd.obs[i] * fd.N + n]) * ep->inv_sigma[i];
+    s = fma(z, z, s);
+  }
+  return -0.5 * s;
+}
+
+__device__ __forceinline__ void br_smem(double* s_dyn, int S, StepCoef*& s_sc, double*& sW,
+                                        double*& sZ) {
+  s_sc = reinterpret_cast<StepCoef*>(s_dyn);
+  sW = s_dyn + (size_t)S * (sizeof(StepCoef) / sizeof(double));
+  sZ = sW + (size_t)kBrPts * 4 * kBrThreads;
+}
+
+__global__ void __launch_bounds__(kBrThreads) k_bstage1(const FilterDev fd,
+                                                      const EpochParams* __restrict__ ep) {
+  extern __shared__ double s_dyn[];
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  Ctrl* ctrl = fd.ctrl;
+  if (ctrl->status != PF_OK) return;
+  const int S = ep->S;
+  StepCoef* s_sc;
+  double *sW, *sZ;
+  br_smem(s_dyn, S, s_sc, sW, sZ);
+  load_steps(s_sc, ep, S);
+  const int cur = ctrl->cur;
+  const Ensemble src = committed(fd, cur);
+  const Ensemble dst = pending(fd, cur);
+  const int64_t N = fd.N;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double lg = -CUDART_INF;
+  if (n < N) {
+    double ph[3], th[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ph[i] = fd.a * src.phi[i * N + n] + (1.0 - fd.a) * ctrl->phibar[i];
+    to_theta<3>(fd, ph, th);
+    const BrTheta T = br_theta(th);
+    // the pending buffer is free until stage 2: it holds the evolving history
+    for (int k = 0; k < kBrD; ++k) {
+      const int64_t o = (int64_t)k * N + n;
+      dst.x[o] = src.x[o];
+      dst.h1[o] = src.h1[o];
+      dst.h2[o] = src.h2[o];
+    }
+    double *P0 = dst.x, *P1 = dst.h1, *P2 = dst.h2;
+    br_propagate<false>(fd, n, s_sc, S, fd.K, T, P0, P1, P2, sW, sZ);
+    const double ll = br_loglik(fd, ep, P0, n);
+    fd.ll1[n] = ll;
+    lg = (src.lw[n] - ctrl->logW) + ll;
+    if (!finite_bits(lg)) lg = -CUDART_INF;
+    fd.lg[n] = lg;
+  }
+  stage1_tail(fd, ep->epoch, lg, s_red, &s_flag);
+}
+
+__global__ void __launch_bounds__(kBrThreads) k_bstage2(const FilterDev fd,
+                                                      const EpochParams* __restrict__ ep) {
+  extern __shared__ double s_dyn[];
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  Ctrl* ctrl = fd.ctrl;
+  if (ctrl->status != PF_OK) return;
+  const int S = ep->S;
+  StepCoef* s_sc;
+  double *sW, *sZ;
+  br_smem(s_dyn, S, s_sc, sW, sZ);
+  load_steps(s_sc, ep, S);
+  const int cur = ctrl->cur;
+  const Ensemble src = committed(fd, cur);
+  const Ensemble dst = pending(fd, cur);
+  const int64_t N = fd.N;
+  const uint32_t epoch = ep->epoch;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double lwn = -CUDART_INF, bad = 0.0;
+  if (n < N) {
+    const int64_t l = fd.idx[n];
+    // 4a: proliferate phi
+    double z[4];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const U4 w = draw_block(fd, kRngTheta, (uint32_t)n, epoch, (uint32_t)b);
+      normal_pair(w, z[2 * b], z[2 * b + 1]);
+    }
+    double ph[3], th[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double lz = 0.0;
+#pragma unroll
+      for (int k = 0; k <= i; ++k) lz = fma(ctrl->L[i * kPMax + k], z[k], lz);
+      const double shr = fd.a * src.phi[i * N + l] + (1.0 - fd.a) * ctrl->phibar[i];
+      ph[i] = fma(fd.s, lz, shr);
+      dst.phi[i * N + n] = ph[i];
+    }
+    to_theta<3>(fd, ph, th);
+    const BrTheta T = br_theta(th);
+    double* EE = fd.wk + 2 * (int64_t)kBrD * N;
+    for (int k = 0; k < kBrD; ++k) {
+      const int64_t o = (int64_t)k * N + n, ol = (int64_t)k * N + l;
+      dst.x[o] = src.x[ol];
+      dst.h1[o] = src.h1[ol];
+      dst.h2[o] = src.h2[ol];
+      EE[o] = 0.0;
+    }
+    double *P0 = dst.x, *P1 = dst.h1, *P2 = dst.h2;
+    // 4b, 4d: repropagate with the Milne error sums
+    br_propagate<true>(fd, n, s_sc, S, fd.K, T, P0, P1, P2, sW, sZ);
+    // 4c, 4d: innovation, written back in the canonical (x, h1, h2) order
+    for (int b = 0; b < kBrD / 2; ++b) {
+      const U4 w = draw_block(fd, kRngInnov, (uint32_t)n, epoch, (uint32_t)b);
+      double z0, z1;
+      normal_pair(w, z0, z1);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t o = (int64_t)(2 * b + h) * N + n;
+        const double v = sqrt(fd.kappa * EE[o]) * (h == 0 ? z0 : z1);
+        const double a0 = P0[o], a1 = P1[o], a2 = P2[o];
+        dst.x[o] = a0 + v;
+        dst.h1[o] = a1 + v;
+        dst.h2[o] = a2 + v;
+      }
+    }
+    // 5: new log weight
+    lwn = br_loglik(fd, ep, dst.x, n) - fd.ll1[l];
+    if (!finite_bits(lwn)) {
+      lwn = -CUDART_INF;
+      bad = 1.0;
+    }
+    dst.lw[n] = lwn;
+  }
+  stage2_tail(fd, epoch, lwn, bad, s_red, &s_flag);
+}
+
+static size_t br_smem_bytes(int S) {
+  return (size_t)S * sizeof(StepCoef) + kBrSweepDoubles * sizeof(double);
+}
+
+cudaError_t launch_bruss_stage(int stage, const FilterDev& fd, const EpochParams* ep, int S,
+                               cudaStream_t st) {
+  const size_t smem = br_smem_bytes(S);
+  static size_t configured = 0;  // largest dynamic shared memory opted in so far
+  if (smem > configured) {
+    const size_t want = br_smem_bytes(kSMax);
+    cudaError_t e = cudaFuncSetAttribute(k_bstage1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_bstage2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
+    if (e != cudaSuccess) return e;
+    configured = want;
+  }
+  const unsigned grid = (unsigned)((fd.N + kBrThreads - 1) / kBrThreads);
+  if (stage == 1) k_bstage1<<<grid, kBrThreads, smem, st>>>(fd, ep);
+  else k_bstage2<<<grid, kBrThreads, smem, st>>>(fd, ep);
+  return cudaGetLastError();
+}
+
+size_t bruss_work_doubles(int64_t N) { return 3 * (size_t)kBrD * (size_t)N; }
+
+}  // namespace pfg

@@ -158,6 +158,8 @@ static size_t layout(pf_filter* f, char* base) {
   f->fd.boff = (double*)take(sizeof(double) * scan_tiles(N));
   f->fd.pmax = (double*)take(sizeof(double) * scan_tiles(N));
   f->fd.part = (double*)take(sizeof(double) * kMomentBlocks * f->fd.nrec);
+  f->fd.wk = (f->ode == PF_ODE_BRUSSELATOR1D) ? (double*)take(sizeof(double) * bruss_work_doubles(N))
+                                              : nullptr;
   f->fd.ticket = (unsigned*)take(sizeof(unsigned) * 8);
   f->fd.ctrl = (Ctrl*)take(sizeof(Ctrl));
   f->ep_dev = (EpochParams*)take(sizeof(EpochParams));

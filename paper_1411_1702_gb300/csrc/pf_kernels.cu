@@ -21,18 +21,12 @@
 #include "pf_kernels.h"
 #include "pf_models.cuh"
 #include "pf_scan.cuh"
+#include "pf_epoch.cuh"
 
 namespace pfg {
 
 constexpr int kSmallThreads = 128;
 constexpr int kResampleThreads = 256;
-
-__device__ __forceinline__ Ensemble committed(const FilterDev& fd, int cur) {
-  return cur ? fd.ens[1] : fd.ens[0];
-}
-__device__ __forceinline__ Ensemble pending(const FilterDev& fd, int cur) {
-  return cur ? fd.ens[0] : fd.ens[1];
-}
 
 // Gaussian log-likelihood of the observed components, without the constant
 // terms (they cancel in every normalisation of Steps 3a and 5).
@@ -49,12 +43,6 @@ __device__ __forceinline__ double loglik(const FilterDev& fd, const EpochParams*
     s = fma(z, z, s);
   }
   return -0.5 * s;
-}
-
-template <int P>
-__device__ __forceinline__ void to_theta(const FilterDev& fd, const double (&ph)[P], double (&th)[P]) {
-#pragma unroll
-  for (int i = 0; i < P; ++i) th[i] = (fd.transform == PF_TRANSFORM_LOG) ? exp(ph[i]) : ph[i];
 }
 
 // Psi of Algorithm 1 for one particle over the S substeps of the interval.
@@ -104,14 +92,6 @@ __device__ __forceinline__ void propagate(const typename M::Th& T, const StepCoe
       x[i] = y[i];
     }
   }
-}
-
-__device__ __forceinline__ void load_steps(StepCoef* s_sc, const EpochParams* __restrict__ ep, int S) {
-  const double* src = reinterpret_cast<const double*>(ep->sc);
-  double* dst = reinterpret_cast<double*>(s_sc);
-  const int nd = S * (int)(sizeof(StepCoef) / sizeof(double));
-  for (int i = threadIdx.x; i < nd; i += blockDim.x) dst[i] = src[i];
-  __syncthreads();
 }
 
 // ------------------------------------------------------------------ init
@@ -190,22 +170,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_stage1(const FilterDev fd,
     if (!finite_bits(lg)) lg = -CUDART_INF;
     fd.lg[n] = lg;
   }
-  const double bm = block_max(lg, s_red);
-  if (threadIdx.x == 0) fd.blk[blockIdx.x] = bm;
-  if (elect_last_block(fd.ticket + 0, &s_flag)) {
-    double m = -CUDART_INF;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmax(m, __ldcg(fd.blk + b));
-    m = block_max(m, s_red);
-    if (threadIdx.x == 0) {
-      ctrl->lg_max = m;
-      ctrl->n_unique = 0;
-      ctrl->n_nonfinite = 0;
-      if (!(m > -CUDART_INF)) {
-        ctrl->status = PF_ERR_DEGENERATE;
-        ctrl->failed_epoch = ep->epoch;
-      }
-    }
-  }
+  stage1_tail(fd, ep->epoch, lg, s_red, &s_flag);
 }
 
 // ------------------------------------------------------------------- scan
@@ -398,25 +363,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_stage2(const FilterDev fd,
     for (int i = 0; i < P; ++i) dst.phi[i * N + n] = ph[i];
     dst.lw[n] = lwn;
   }
-  const double bm = block_max(lwn, s_red);
-  const double nb = block_sum(bad, s_red);
-  if (threadIdx.x == 0) {
-    fd.blk[blockIdx.x] = bm;
-    if (nb > 0.0)
-      atomicAdd(reinterpret_cast<unsigned long long*>(&ctrl->n_nonfinite), (unsigned long long)nb);
-  }
-  if (elect_last_block(fd.ticket + 2, &s_flag)) {
-    double m = -CUDART_INF;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmax(m, __ldcg(fd.blk + b));
-    m = block_max(m, s_red);
-    if (threadIdx.x == 0) {
-      ctrl->lw_max = m;
-      if (!(m > -CUDART_INF)) {
-        ctrl->status = PF_ERR_DEGENERATE;
-        ctrl->failed_epoch = epoch;
-      }
-    }
-  }
+  stage2_tail(fd, epoch, lwn, bad, s_red, &s_flag);
 }
 
 // ---------------------------------------------------------------- moments
@@ -431,23 +378,6 @@ struct MomentLayout {
   static constexpr int kS0 = 0, kW2 = 1, kS1 = 2, kS2 = 2 + P, kSx = kS2 + P * (P + 1) / 2,
                        kSt = kSx + D, kN = kSt + P;
 };
-
-// Cholesky factor of a PSD matrix; a non-positive pivot gives a zero column.
-__device__ void cholesky_psd(int p, const double* C, double* L) {
-  for (int i = 0; i < kPMax * kPMax; ++i) L[i] = 0.0;
-  for (int j = 0; j < p; ++j) {
-    double dsum = C[j * kPMax + j];
-    for (int k = 0; k < j; ++k) dsum -= L[j * kPMax + k] * L[j * kPMax + k];
-    if (!(dsum > 0.0)) continue;
-    const double ljj = sqrt(dsum);
-    L[j * kPMax + j] = ljj;
-    for (int i = j + 1; i < p; ++i) {
-      double s = C[i * kPMax + j];
-      for (int k = 0; k < j; ++k) s -= L[i * kPMax + k] * L[j * kPMax + k];
-      L[i * kPMax + j] = s / ljj;
-    }
-  }
-}
 
 template <int D, int P>
 __global__ void __launch_bounds__(kMomentThreads) k_moments(const FilterDev fd, int is_init) {
@@ -560,6 +490,7 @@ int moment_record_size(int ode) {
   switch (ode) {
     case PF_ODE_LINEAR2: return moment_nrec<2, 2>();
     case PF_ODE_ROBERTSON: return moment_nrec<3, 3>();
+    case PF_ODE_BRUSSELATOR1D: return moment_nrec<64, 3>();
   }
   return -1;
 }
@@ -613,10 +544,40 @@ static cudaError_t launch_epoch_t(const FilterDev& fd, const EpochParams* ep, in
   return cudaGetLastError();
 }
 
+// the Brusselator's stage kernels live in pf_bruss.cu; the rest is shared
+static cudaError_t launch_epoch_bruss(const FilterDev& fd, const EpochParams* ep, int S,
+                                      cudaStream_t st, cudaEvent_t* marks) {
+  const int64_t N = fd.N;
+  auto mark = [&](int i) {
+    if (marks) cudaEventRecord(marks[i], st);
+  };
+  cudaError_t e;
+  mark(0);
+  if ((e = launch_bruss_stage(1, fd, ep, S, st)) != cudaSuccess) return e;
+  mark(1);
+  k_scan_tile<<<(unsigned)scan_tiles(N), kScanThreads, 0, st>>>(fd);
+  mark(2);
+  k_scan_add<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(fd);
+  mark(3);
+  k_resample<<<(unsigned)((N + kResampleThreads - 1) / kResampleThreads), kResampleThreads, 0, st>>>(fd, ep);
+  mark(4);
+  if ((e = launch_bruss_stage(2, fd, ep, S, st)) != cudaSuccess) return e;
+  mark(5);
+  k_moments<64, 3><<<moment_grid(N), kMomentThreads, 0, st>>>(fd, 0);
+  mark(6);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init(int ode, const FilterDev& fd, cudaStream_t st) {
   switch (ode) {
     case PF_ODE_LINEAR2: return launch_init_t<Linear2>(fd, st);
     case PF_ODE_ROBERTSON: return launch_init_t<Robertson>(fd, st);
+    case PF_ODE_BRUSSELATOR1D: {
+      const int64_t N = fd.N;
+      k_init<64, 3><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(fd);
+      k_moments<64, 3><<<moment_grid(N), kMomentThreads, 0, st>>>(fd, 1);
+      return cudaGetLastError();
+    }
   }
   return cudaErrorInvalidValue;
 }
@@ -626,6 +587,7 @@ cudaError_t launch_epoch(int ode, const FilterDev& fd, const EpochParams* ep, in
   switch (ode) {
     case PF_ODE_LINEAR2: return launch_epoch_t<Linear2>(fd, ep, S, st, marks);
     case PF_ODE_ROBERTSON: return launch_epoch_t<Robertson>(fd, ep, S, st, marks);
+    case PF_ODE_BRUSSELATOR1D: return launch_epoch_bruss(fd, ep, S, st, marks);
   }
   return cudaErrorInvalidValue;
 }
@@ -635,7 +597,9 @@ int kernels_per_epoch(int ode) {
   return kEpochKernels;
 }
 
-bool ode_supported(int ode) { return ode == PF_ODE_LINEAR2 || ode == PF_ODE_ROBERTSON; }
+bool ode_supported(int ode) {
+  return ode == PF_ODE_LINEAR2 || ode == PF_ODE_ROBERTSON || ode == PF_ODE_BRUSSELATOR1D;
+}
 
 __global__ void k_set_moments(const FilterDev fd) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;

@@ -18,6 +18,10 @@ cudaError_t launch_epoch(int ode, const FilterDev& fd, const EpochParams* ep, in
 // Recompute the Cholesky factor after the host set phibar and C.
 cudaError_t launch_set_moments(const FilterDev& fd, cudaStream_t st);
 int moment_record_size(int ode);
+// Brusselator stage kernels (pf_bruss.cu): stage 1 or 2 of one epoch.
+cudaError_t launch_bruss_stage(int stage, const FilterDev& fd, const EpochParams* ep, int S,
+                               cudaStream_t st);
+size_t bruss_work_doubles(int64_t N);
 int max_grid_blocks(int64_t N);
 int scan_tiles(int64_t N);
 int kernels_per_epoch(int ode);
