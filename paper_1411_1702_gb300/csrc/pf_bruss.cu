@@ -11,9 +11,12 @@
 // cyclic reduction, which would multiply the arithmetic several times over.
 // The particle's vectors live in HBM as structure-of-arrays (component-major,
 // coalesced across the warp): the rotating history x_n, x_{n-1}, x_{n-2} in the
-// pending ensemble buffer, and r, the error predictor and the error sums in a
-// work area.  The sweep's inverted pivot blocks and intermediate solutions
-// (6 doubles per grid point) are kept in shared memory for the backward pass.
+// pending ensemble buffer, and r, the error predictor, the error sums and the
+// sweep's inverted pivot blocks and intermediate solutions (6 doubles per grid
+// point, read back in reverse by the backward pass) in a work area.  Keeping
+// the sweep out of shared memory lets registers, not shared memory, set the
+// residency, so each SM sub-partition interleaves several particles' sweeps
+// and hides the latency of the block recurrence.
 #include "pf_epoch.cuh"
 #include "pf_kernels.h"
 
@@ -21,8 +24,11 @@ namespace pfg {
 
 constexpr int kBrPts = 32;
 constexpr int kBrD = 64;
-constexpr int kBrThreads = 32;  // one warp per block; shared memory per lane
-constexpr size_t kBrSweepDoubles = (size_t)kBrPts * 6 * kBrThreads;
+constexpr int kBrThreads = 64;
+// work area per particle (doubles, each array component-major over N):
+// r (64), error predictor (64), error sums (64), pivot inverses W (32 x 4),
+// sweep solutions z (32 x 2)
+constexpr int kBrWorkRows = 3 * kBrD + kBrPts * 6;
 
 struct BrTheta {
   double A, B, D;
@@ -59,9 +65,8 @@ __device__ void br_euler_predictor(const double* __restrict__ X, double* __restr
 //   forward  W_i = (M_i - e^2 W_{i-1})^{-1},  z_i = W_i (-G_i + e z_{i-1}),
 //   backward dy_i = z_i + e W_i dy_{i+1}  (dy_32 = 0).
 __device__ void br_newton(double* __restrict__ Y, const double* __restrict__ R, int64_t N, int64_t n,
-                          double g, int K, const BrTheta& T, double* __restrict__ sW,
-                          double* __restrict__ sZ) {
-  const int lane = threadIdx.x;
+                          double g, int K, const BrTheta& T, double* __restrict__ Wg,
+                          double* __restrict__ Zg) {
   const double gD = g * T.D, e2 = gD * gD, g2 = 2.0 * g, mg = -g;
   const double ca = 1.0 + g * (T.B + 1.0) + 2.0 * gD;  // 1 + g(B+1) + 2gD
   const double cd = 1.0 + 2.0 * gD;
@@ -94,14 +99,14 @@ __device__ void br_newton(double* __restrict__ Y, const double* __restrict__ R, 
       const double h0 = fma(gD, z0, -Gu), h1 = fma(gD, z1, -Gv);
       z0 = fma(W00, h0, W01 * h1);
       z1 = fma(W10, h0, W11 * h1);
-      double* w = sW + (i * 4) * kBrThreads + lane;
+      double* w = Wg + (int64_t)(i * 4) * N + n;
       w[0] = W00;
-      w[kBrThreads] = W01;
-      w[2 * kBrThreads] = W10;
-      w[3 * kBrThreads] = W11;
-      double* zz = sZ + (i * 2) * kBrThreads + lane;
+      w[N] = W01;
+      w[2 * N] = W10;
+      w[3 * N] = W11;
+      double* zz = Zg + (int64_t)(i * 2) * N + n;
       zz[0] = z0;
-      zz[kBrThreads] = z1;
+      zz[N] = z1;
       uL = u;
       vL = v;
       u = uR;
@@ -109,12 +114,12 @@ __device__ void br_newton(double* __restrict__ Y, const double* __restrict__ R, 
     }
     double du = 0.0, dv = 0.0;
     for (int i = kBrPts - 1; i >= 0; --i) {
-      const double* w = sW + (i * 4) * kBrThreads + lane;
-      const double* zz = sZ + (i * 2) * kBrThreads + lane;
-      const double t0 = fma(w[0], du, w[kBrThreads] * dv);
-      const double t1 = fma(w[2 * kBrThreads], du, w[3 * kBrThreads] * dv);
+      const double* w = Wg + (int64_t)(i * 4) * N + n;
+      const double* zz = Zg + (int64_t)(i * 2) * N + n;
+      const double t0 = fma(w[0], du, w[N] * dv);
+      const double t1 = fma(w[2 * N], du, w[3 * N] * dv);
       du = fma(gD, t0, zz[0]);
-      dv = fma(gD, t1, zz[kBrThreads]);
+      dv = fma(gD, t1, zz[N]);
       Y[(int64_t)(2 * i) * N + n] += du;
       Y[(int64_t)(2 * i + 1) * N + n] += dv;
     }
@@ -125,12 +130,13 @@ __device__ void br_newton(double* __restrict__ Y, const double* __restrict__ R, 
 // substep writes its iterate over x_{n-2} and the roles rotate.
 template <bool ERR>
 __device__ void br_propagate(const FilterDev& fd, int64_t n, const StepCoef* sc, int S, int K,
-                             const BrTheta& T, double*& P0, double*& P1, double*& P2, double* sW,
-                             double* sZ) {
+                             const BrTheta& T, double*& P0, double*& P1, double*& P2) {
   const int64_t N = fd.N;
   double* R = fd.wk;
   double* XP = fd.wk + (int64_t)kBrD * N;
   double* EE = fd.wk + 2 * (int64_t)kBrD * N;
+  double* Wg = fd.wk + 3 * (int64_t)kBrD * N;
+  double* Zg = Wg + 4 * (int64_t)kBrPts * N;
   for (int s = 0; s < S; ++s) {
     const StepCoef& c = sc[s];
     if (c.kind == 2) {
@@ -151,7 +157,7 @@ __device__ void br_propagate(const FilterDev& fd, int64_t n, const StepCoef* sc,
         P2[o] = xn;
       }
     }
-    br_newton(P2, R, N, n, c.gamma, K, T, sW, sZ);
+    br_newton(P2, R, N, n, c.gamma, K, T, Wg, Zg);
     if (ERR) {
       for (int k = 0; k < kBrD; ++k) {
         const int64_t o = (int64_t)k * N + n;
@@ -176,13 +182,6 @@ __device__ __forceinline__ double br_loglik(const FilterDev& fd, const EpochPara
   return -0.5 * s;
 }
 
-__device__ __forceinline__ void br_smem(double* s_dyn, int S, StepCoef*& s_sc, double*& sW,
-                                        double*& sZ) {
-  s_sc = reinterpret_cast<StepCoef*>(s_dyn);
-  sW = s_dyn + (size_t)S * (sizeof(StepCoef) / sizeof(double));
-  sZ = sW + (size_t)kBrPts * 4 * kBrThreads;
-}
-
 __global__ void __launch_bounds__(kBrThreads) k_bstage1(const FilterDev fd,
                                                       const EpochParams* __restrict__ ep) {
   extern __shared__ double s_dyn[];
@@ -191,9 +190,7 @@ __global__ void __launch_bounds__(kBrThreads) k_bstage1(const FilterDev fd,
   Ctrl* ctrl = fd.ctrl;
   if (ctrl->status != PF_OK) return;
   const int S = ep->S;
-  StepCoef* s_sc;
-  double *sW, *sZ;
-  br_smem(s_dyn, S, s_sc, sW, sZ);
+  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
   load_steps(s_sc, ep, S);
   const int cur = ctrl->cur;
   const Ensemble src = committed(fd, cur);
@@ -215,7 +212,7 @@ __global__ void __launch_bounds__(kBrThreads) k_bstage1(const FilterDev fd,
       dst.h2[o] = src.h2[o];
     }
     double *P0 = dst.x, *P1 = dst.h1, *P2 = dst.h2;
-    br_propagate<false>(fd, n, s_sc, S, fd.K, T, P0, P1, P2, sW, sZ);
+    br_propagate<false>(fd, n, s_sc, S, fd.K, T, P0, P1, P2);
     const double ll = br_loglik(fd, ep, P0, n);
     fd.ll1[n] = ll;
     lg = (src.lw[n] - ctrl->logW) + ll;
@@ -233,9 +230,7 @@ __global__ void __launch_bounds__(kBrThreads) k_bstage2(const FilterDev fd,
   Ctrl* ctrl = fd.ctrl;
   if (ctrl->status != PF_OK) return;
   const int S = ep->S;
-  StepCoef* s_sc;
-  double *sW, *sZ;
-  br_smem(s_dyn, S, s_sc, sW, sZ);
+  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
   load_steps(s_sc, ep, S);
   const int cur = ctrl->cur;
   const Ensemble src = committed(fd, cur);
@@ -275,7 +270,7 @@ __global__ void __launch_bounds__(kBrThreads) k_bstage2(const FilterDev fd,
     }
     double *P0 = dst.x, *P1 = dst.h1, *P2 = dst.h2;
     // 4b, 4d: repropagate with the Milne error sums
-    br_propagate<true>(fd, n, s_sc, S, fd.K, T, P0, P1, P2, sW, sZ);
+    br_propagate<true>(fd, n, s_sc, S, fd.K, T, P0, P1, P2);
     // 4c, 4d: innovation, written back in the canonical (x, h1, h2) order
     for (int b = 0; b < kBrD / 2; ++b) {
       const U4 w = draw_block(fd, kRngInnov, (uint32_t)n, epoch, (uint32_t)b);
@@ -302,28 +297,15 @@ __global__ void __launch_bounds__(kBrThreads) k_bstage2(const FilterDev fd,
   stage2_tail(fd, epoch, lwn, bad, s_red, &s_flag);
 }
 
-static size_t br_smem_bytes(int S) {
-  return (size_t)S * sizeof(StepCoef) + kBrSweepDoubles * sizeof(double);
-}
-
 cudaError_t launch_bruss_stage(int stage, const FilterDev& fd, const EpochParams* ep, int S,
                                cudaStream_t st) {
-  const size_t smem = br_smem_bytes(S);
-  static size_t configured = 0;  // largest dynamic shared memory opted in so far
-  if (smem > configured) {
-    const size_t want = br_smem_bytes(kSMax);
-    cudaError_t e = cudaFuncSetAttribute(k_bstage1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_bstage2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
-    if (e != cudaSuccess) return e;
-    configured = want;
-  }
+  const size_t smem = (size_t)S * sizeof(StepCoef);
   const unsigned grid = (unsigned)((fd.N + kBrThreads - 1) / kBrThreads);
   if (stage == 1) k_bstage1<<<grid, kBrThreads, smem, st>>>(fd, ep);
   else k_bstage2<<<grid, kBrThreads, smem, st>>>(fd, ep);
   return cudaGetLastError();
 }
 
-size_t bruss_work_doubles(int64_t N) { return 3 * (size_t)kBrD * (size_t)N; }
+size_t bruss_work_doubles(int64_t N) { return (size_t)kBrWorkRows * (size_t)N; }
 
 }  // namespace pfg

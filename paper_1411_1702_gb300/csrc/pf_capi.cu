@@ -445,6 +445,7 @@ pf_status pf_estimates(const pf_filter* cf, double* theta_bar, double* C, double
 pf_status pf_stats(const pf_filter* cf, pf_stats_t* out) {
   pf_filter* f = const_cast<pf_filter*>(cf);
   if (!f || !out) return fail(f, PF_ERR_INVALID_ARG, "NULL argument");
+  PF_CUDA(f, launch_theta_mean(f->fd, f->stream));
   pf_status st = read_ctrl(f);
   if (st != PF_OK) return st;
   const Ctrl* h = f->ctrl_host;

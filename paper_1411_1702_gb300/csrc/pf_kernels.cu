@@ -369,21 +369,40 @@ __global__ void __launch_bounds__(kSmallThreads) k_stage2(const FilterDev fd,
 // ---------------------------------------------------------------- moments
 // Weighted sums of the pending buffer with e_n = exp(lw_n - max lw):
 //   [S0 = sum e, Sw2 = sum e^2, S1 = sum e phi, S2 = sum e (phi - c)(phi - c)^T
-//    (upper triangle, shift c = the committed mean), Sx = sum e x,
-//    St = sum e theta]
+//    (upper triangle, shift c = the committed mean), Sx = sum e x]
 // Zero-weight particles are skipped (their state may be non-finite).  The last
 // block reduces the partial records and commits the epoch.
 template <int D, int P>
 struct MomentLayout {
   static constexpr int kS0 = 0, kW2 = 1, kS1 = 2, kS2 = 2 + P, kSx = kS2 + P * (P + 1) / 2,
-                       kSt = kSx + D, kN = kSt + P;
+                       kN = kSx + D;
 };
+
+// Sum each of NV per-thread values over the block with one barrier round:
+// warp shuffles, then one row per warp in shared memory summed by NV threads.
+// out[k] (shared or global) receives the totals; s_part needs 8 * NV doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum_vec(double (&acc)[NV], double* s_part, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) s_part[wid * NV + k] = v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += s_part[w * NV + k];
+    out[k] = t;
+  }
+  __syncthreads();
+}
 
 template <int D, int P>
 __global__ void __launch_bounds__(kMomentThreads) k_moments(const FilterDev fd, int is_init) {
   using Lay = MomentLayout<D, P>;
   constexpr int NV = Lay::kN;
-  __shared__ double s_red[32];
+  __shared__ double s_part[(kMomentThreads / 32) * NV];
   __shared__ double s_tot[NV];
   __shared__ int s_flag;
   Ctrl* ctrl = fd.ctrl;
@@ -410,8 +429,6 @@ __global__ void __launch_bounds__(kMomentThreads) k_moments(const FilterDev fd, 
     for (int i = 0; i < P; ++i) {
       ph[i] = nw.phi[i * N + n];
       acc[Lay::kS1 + i] = fma(e, ph[i], acc[Lay::kS1 + i]);
-      const double th = (fd.transform == PF_TRANSFORM_LOG) ? exp(ph[i]) : ph[i];
-      acc[Lay::kSt + i] = fma(e, th, acc[Lay::kSt + i]);
     }
     int q = Lay::kS2;
 #pragma unroll
@@ -426,21 +443,15 @@ __global__ void __launch_bounds__(kMomentThreads) k_moments(const FilterDev fd, 
 #pragma unroll
     for (int i = 0; i < D; ++i) acc[Lay::kSx + i] = fma(e, nw.x[i * N + n], acc[Lay::kSx + i]);
   }
-#pragma unroll 1
-  for (int k = 0; k < NV; ++k) {
-    const double t = block_sum(acc[k], s_red);
-    if (threadIdx.x == 0) fd.part[(int64_t)blockIdx.x * fd.nrec + k] = t;
-  }
+  block_sum_vec<NV>(acc, s_part, fd.part + (int64_t)blockIdx.x * fd.nrec);
   if (!elect_last_block(fd.ticket + 3, &s_flag)) return;
-#pragma unroll 1
-  for (int k = 0; k < NV; ++k) {
-    double t = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-      t += __ldcg(fd.part + (int64_t)b * fd.nrec + k);
-    t = block_sum(t, s_red);
-    if (threadIdx.x == 0) s_tot[k] = t;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(fd.part + (int64_t)b * fd.nrec + k);
   }
-  __syncthreads();
+  block_sum_vec<NV>(acc, s_part, s_tot);
   if (threadIdx.x != 0) return;
   const double S0 = s_tot[Lay::kS0];
   double mean[P], C[kPMax * kPMax], L[kPMax * kPMax];
@@ -465,10 +476,7 @@ __global__ void __launch_bounds__(kMomentThreads) k_moments(const FilterDev fd, 
     return;
   }
   cholesky_psd(P, C, L);
-  for (int i = 0; i < P; ++i) {
-    ctrl->phibar[i] = mean[i];
-    ctrl->theta_mean[i] = s_tot[Lay::kSt + i] / S0;
-  }
+  for (int i = 0; i < P; ++i) ctrl->phibar[i] = mean[i];
   for (int i = 0; i < kPMax * kPMax; ++i) {
     ctrl->C[i] = C[i];
     ctrl->L[i] = L[i];
@@ -478,6 +486,33 @@ __global__ void __launch_bounds__(kMomentThreads) k_moments(const FilterDev fd, 
   ctrl->logW = M + log(S0);
   ctrl->cur = 1 - cur;
   if (!is_init) ctrl->epochs_done += 1;
+}
+
+// Weighted mean of theta = exp(phi) (or phi) of the committed ensemble, for
+// pf_stats only: w_n = exp(lw_n - logW).  One block, off the epoch path.
+template <int P>
+__global__ void __launch_bounds__(kMomentThreads) k_theta_mean(const FilterDev fd) {
+  __shared__ double s_part[(kMomentThreads / 32) * P];
+  __shared__ double s_tot[P];
+  Ctrl* ctrl = fd.ctrl;
+  const Ensemble E = committed(fd, ctrl->cur);
+  const int64_t N = fd.N;
+  const double lW = ctrl->logW;
+  double acc[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) acc[i] = 0.0;
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+    const double lw = E.lw[n];
+    if (is_neg_inf(lw)) continue;
+    const double w = exp(lw - lW);
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      const double ph = E.phi[i * N + n];
+      acc[i] = fma(w, (fd.transform == PF_TRANSFORM_LOG) ? exp(ph) : ph, acc[i]);
+    }
+  }
+  block_sum_vec<P>(acc, s_part, s_tot);
+  if (threadIdx.x < P) ctrl->theta_mean[threadIdx.x] = s_tot[threadIdx.x];
 }
 
 // ----------------------------------------------------------------- launch
@@ -595,6 +630,12 @@ cudaError_t launch_epoch(int ode, const FilterDev& fd, const EpochParams* ep, in
 int kernels_per_epoch(int ode) {
   (void)ode;
   return kEpochKernels;
+}
+
+cudaError_t launch_theta_mean(const FilterDev& fd, cudaStream_t st) {
+  if (fd.p == 2) k_theta_mean<2><<<1, kMomentThreads, 0, st>>>(fd);
+  else k_theta_mean<3><<<1, kMomentThreads, 0, st>>>(fd);
+  return cudaGetLastError();
 }
 
 bool ode_supported(int ode) {

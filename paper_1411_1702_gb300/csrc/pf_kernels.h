@@ -18,6 +18,8 @@ cudaError_t launch_epoch(int ode, const FilterDev& fd, const EpochParams* ep, in
 // Recompute the Cholesky factor after the host set phibar and C.
 cudaError_t launch_set_moments(const FilterDev& fd, cudaStream_t st);
 int moment_record_size(int ode);
+// Weighted theta-space mean of the committed ensemble into Ctrl::theta_mean.
+cudaError_t launch_theta_mean(const FilterDev& fd, cudaStream_t st);
 // Brusselator stage kernels (pf_bruss.cu): stage 1 or 2 of one epoch.
 cudaError_t launch_bruss_stage(int stage, const FilterDev& fd, const EpochParams* ep, int S,
                                cudaStream_t st);
