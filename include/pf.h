@@ -220,6 +220,43 @@ int pf_substep_table(int lmm, int spacing, double dt, int substeps, double q0, d
                      double t_next, int depth, double hprev1, double hprev2, double* coef,
                      int max_steps, int* depth_out);
 
+/* ---- batches of filters ---------------------------------------------------
+ * A batch advances many independent filters (any mix of ODEs and sizes) by
+ * one epoch each with a handful of tile-scheduled launches -- one per phase
+ * of Algorithm 1's epoch, split by model where the kernels differ -- captured
+ * in a CUDA graph that is reused while the set of active filters stays the
+ * same.  Each filter's results are bit-identical to running it alone: its
+ * reduction trees depend only on its own N.  The batch drives the filters'
+ * own device buffers; while a filter is in a batch, advance it only through
+ * the batch.  A filter belongs to at most one batch at a time. */
+typedef struct pf_batch pf_batch;
+
+typedef struct {
+  int64_t epochs;         /* batched epochs run                            */
+  int64_t graph_captures; /* times the launch graph was (re)captured       */
+  double last_device_ms;  /* device time of the last batched epoch         */
+  int last_active;        /* filters advanced by the last batched epoch    */
+  int last_tiles;         /* thread blocks (tiles) of its launches         */
+} pf_batch_stats_t;
+
+/* Bind n existing filters (distinct, not in another batch) into a batch that
+ * runs on `stream` (NULL = a stream the batch creates and owns).  The
+ * filters' own pending work is waited for.  Errors: INVALID_ARG, OOM, CUDA. */
+pf_status pf_batch_create(pf_filter* const* filters, int n, void* stream, pf_batch** out);
+
+/* One epoch for every filter f with y[f] != NULL (host, m_f doubles) at time
+ * t[f]; filters with y[f] == NULL idle.  Synchronous.  status[f] (n entries)
+ * receives each filter's result (PF_OK, PF_ERR_INVALID_ARG for a bad
+ * observation or time, PF_ERR_DEGENERATE, PF_ERR_NUMERIC); a failed filter
+ * keeps its committed state, the others advance.  Returns PF_OK unless the
+ * batch itself failed (CUDA, NULL arguments). */
+pf_status pf_batch_assimilate(pf_batch* b, const double* t, const double* const* y, int* status);
+
+pf_status pf_batch_stats(const pf_batch* b, pf_batch_stats_t* out);
+const char* pf_batch_last_error(const pf_batch* b);
+/* Release the batch (the filters stay valid and leave the batch). */
+void pf_batch_destroy(pf_batch* b);
+
 /* ---- systematic resampling without allocation ----------------------------
  * No counterpart in the paper: a library convenience for callers that cannot
  * allocate device memory where they need to resample -- applications whose

@@ -182,21 +182,16 @@ __device__ __forceinline__ double br_loglik(const FilterDev& fd, const EpochPara
   return -0.5 * s;
 }
 
-__global__ void __launch_bounds__(kBrThreads) k_bstage1(const FilterDev fd,
-                                                      const EpochParams* __restrict__ ep) {
-  extern __shared__ double s_dyn[];
-  __shared__ double s_red[32];
-  __shared__ int s_flag;
-  Ctrl* ctrl = fd.ctrl;
-  if (ctrl->status != PF_OK) return;
+__device__ __forceinline__ void bstage1_body(const FilterDev& fd, const EpochParams* __restrict__ ep,
+                                             int vb, int vg, const StepCoef* s_sc, double* s_red,
+                                             int* s_flag) {
+  const Ctrl* ctrl = fd.ctrl;
   const int S = ep->S;
-  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
-  load_steps(s_sc, ep, S);
   const int cur = ctrl->cur;
   const Ensemble src = committed(fd, cur);
   const Ensemble dst = pending(fd, cur);
   const int64_t N = fd.N;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = (int64_t)vb * blockDim.x + threadIdx.x;
   double lg = -CUDART_INF;
   if (n < N) {
     double ph[3], th[3];
@@ -219,25 +214,20 @@ __global__ void __launch_bounds__(kBrThreads) k_bstage1(const FilterDev fd,
     if (!finite_bits(lg)) lg = -CUDART_INF;
     fd.lg[n] = lg;
   }
-  stage1_tail(fd, ep->epoch, lg, s_red, &s_flag);
+  stage1_tail(fd, ep->epoch, lg, vb, vg, s_red, s_flag);
 }
 
-__global__ void __launch_bounds__(kBrThreads) k_bstage2(const FilterDev fd,
-                                                      const EpochParams* __restrict__ ep) {
-  extern __shared__ double s_dyn[];
-  __shared__ double s_red[32];
-  __shared__ int s_flag;
-  Ctrl* ctrl = fd.ctrl;
-  if (ctrl->status != PF_OK) return;
+__device__ __forceinline__ void bstage2_body(const FilterDev& fd, const EpochParams* __restrict__ ep,
+                                             int vb, int vg, const StepCoef* s_sc, double* s_red,
+                                             int* s_flag) {
+  const Ctrl* ctrl = fd.ctrl;
   const int S = ep->S;
-  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
-  load_steps(s_sc, ep, S);
   const int cur = ctrl->cur;
   const Ensemble src = committed(fd, cur);
   const Ensemble dst = pending(fd, cur);
   const int64_t N = fd.N;
   const uint32_t epoch = ep->epoch;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = (int64_t)vb * blockDim.x + threadIdx.x;
   double lwn = -CUDART_INF, bad = 0.0;
   if (n < N) {
     const int64_t l = fd.idx[n];
@@ -294,15 +284,57 @@ __global__ void __launch_bounds__(kBrThreads) k_bstage2(const FilterDev fd,
     }
     dst.lw[n] = lwn;
   }
-  stage2_tail(fd, epoch, lwn, bad, s_red, &s_flag);
+  stage2_tail(fd, epoch, lwn, bad, vb, vg, s_red, s_flag);
 }
+
+template <int STAGE>
+__global__ void __launch_bounds__(kBrThreads) k_bstage(const __grid_constant__ FilterDev fd,
+                                                     const EpochParams* __restrict__ ep) {
+  extern __shared__ double s_dyn[];
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  if (fd.ctrl->status != PF_OK) return;
+  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
+  load_steps(s_sc, ep, ep->S);
+  if (STAGE == 1) bstage1_body(fd, ep, blockIdx.x, gridDim.x, s_sc, s_red, &s_flag);
+  else bstage2_body(fd, ep, blockIdx.x, gridDim.x, s_sc, s_red, &s_flag);
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(kBrThreads) k_batch_bstage(const FilterDev* __restrict__ fds,
+                                                           const EpochParams* const* __restrict__ eps,
+                                                           const BatchTile* __restrict__ tiles) {
+  extern __shared__ double s_dyn[];
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  const BatchTile t = tiles[blockIdx.x];
+  const FilterDev& fd = *(fds + t.f);
+  if (fd.ctrl->status != PF_OK) return;
+  const EpochParams* ep = eps[t.f];
+  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
+  load_steps(s_sc, ep, ep->S);
+  const int vg = (int)((fd.N + kBrThreads - 1) / kBrThreads);
+  if (STAGE == 1) bstage1_body(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
+  else bstage2_body(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
+}
+
+int bruss_stage_blocks(int64_t N) { return (int)((N + kBrThreads - 1) / kBrThreads); }
 
 cudaError_t launch_bruss_stage(int stage, const FilterDev& fd, const EpochParams* ep, int S,
                                cudaStream_t st) {
   const size_t smem = (size_t)S * sizeof(StepCoef);
-  const unsigned grid = (unsigned)((fd.N + kBrThreads - 1) / kBrThreads);
-  if (stage == 1) k_bstage1<<<grid, kBrThreads, smem, st>>>(fd, ep);
-  else k_bstage2<<<grid, kBrThreads, smem, st>>>(fd, ep);
+  const unsigned grid = (unsigned)bruss_stage_blocks(fd.N);
+  if (stage == 1) k_bstage<1><<<grid, kBrThreads, smem, st>>>(fd, ep);
+  else k_bstage<2><<<grid, kBrThreads, smem, st>>>(fd, ep);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_bruss_stage(int stage, const FilterDev* fds, const EpochParams* const* eps,
+                                     const BatchTile* tiles, int ntiles, size_t smem,
+                                     cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (stage == 1) k_batch_bstage<1><<<ntiles, kBrThreads, smem, st>>>(fds, eps, tiles);
+  else k_batch_bstage<2><<<ntiles, kBrThreads, smem, st>>>(fds, eps, tiles);
   return cudaGetLastError();
 }
 

@@ -9,69 +9,17 @@
 #include <string>
 #include <vector>
 
-#include "pf_kernels.h"
+#include "pf_filter.h"
 
 using namespace pfg;
 
 namespace {
-
-struct HistoryState {
-  int64_t epochs;
-  int depth;
-  double t_prev, hprev1, hprev2;
-};
-
 thread_local std::string g_thread_error;
-
 }  // namespace
 
 namespace pfg {
 void set_thread_error(const std::string& msg) { g_thread_error = msg; }
 }  // namespace pfg
-
-struct pf_filter {
-  // configuration
-  int ode, d, p, m, lmm, K, spacing, substeps, history, transform, noise;
-  double dt, q0, a, kappa;
-  uint64_t seed;
-  uint32_t filter_id;
-  int64_t N;
-  int obs[kMMax];
-  double sigma[kMMax];
-  int prior_kind[kPMax];
-  double prior_lo[kPMax], prior_hi[kPMax];
-  double x0[kDMax];
-  double t0;
-  // CUDA resources
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  void* dmem = nullptr;
-  size_t dbytes = 0;
-  FilterDev fd{};
-  EpochParams* ep_dev = nullptr;    // online parameter slot
-  EpochParams* ep_host = nullptr;   // pinned staging
-  Ctrl* ctrl_host = nullptr;        // pinned
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  // committed history (host view)
-  HistoryState hist{};
-  // device-resident observation series
-  EpochParams* series_dev = nullptr;
-  int series_T = 0;
-  int series_next = 0;
-  std::vector<int> series_S;
-  std::vector<HistoryState> series_after;  // history after epoch k of the series
-  HistoryState series_start{};
-  // per-kernel timing (pf_options.timing)
-  bool timing = false;
-  std::vector<cudaEvent_t*> mark_free;     // sets of kEpochKernels + 1 events
-  std::vector<cudaEvent_t*> mark_pending;  // recorded, not yet read
-  double kernel_ms[kEpochKernels] = {0};
-  int64_t kernel_launches[kEpochKernels] = {0};
-  // bookkeeping
-  double last_ms = 0.0;
-  int64_t h2d_bytes = 0, d2h_bytes = 0;
-  std::string err;
-};
 
 // A set of timing events for one epoch, or NULL when timing is off.
 static cudaEvent_t* take_marks(pf_filter* f) {
@@ -210,9 +158,10 @@ static pf_status do_init(pf_filter* f) {
   return PF_OK;
 }
 
+namespace pfg {
 // Parameter block of one epoch from the history state h.
-static int fill_epoch(const pf_filter* f, const HistoryState& h, double t_k, const double* y,
-                      EpochParams* ep, int* depth_out) {
+int fill_epoch(const pf_filter* f, const HistoryState& h, double t_k, const double* y,
+               EpochParams* ep, int* depth_out) {
   const int depth = (f->history == PF_HISTORY_RESTART) ? 0 : h.depth;
   const int S = build_substeps(f->lmm, f->spacing, f->dt, f->substeps, f->q0, h.t_prev, t_k, depth,
                                h.hprev1, h.hprev2, ep->sc, kSMax, depth_out);
@@ -234,8 +183,8 @@ static int fill_epoch(const pf_filter* f, const HistoryState& h, double t_k, con
   return S;
 }
 
-static HistoryState advance(const pf_filter* f, const HistoryState& h, double t_k,
-                            const EpochParams* ep, int depth_out) {
+HistoryState advance_history(const HistoryState& h, double t_k, const EpochParams* ep,
+                             int depth_out) {
   HistoryState n = h;
   const int S = ep->S;
   n.epochs = h.epochs + 1;
@@ -243,9 +192,9 @@ static HistoryState advance(const pf_filter* f, const HistoryState& h, double t_
   n.hprev1 = ep->sc[S - 1].h;
   n.hprev2 = S >= 2 ? ep->sc[S - 2].h : h.hprev1;
   n.t_prev = t_k;
-  (void)f;
   return n;
 }
+}  // namespace pfg
 
 static pf_status clear_device_status(pf_filter* f) {
   PF_CUDA(f, cudaMemsetAsync(&f->fd.ctrl->status, 0, sizeof(int), f->stream));
@@ -335,7 +284,7 @@ pf_status pf_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
   for (int i = 0; i < d; ++i) f->x0[i] = prior->x0[i];
 
   FilterDev& fd = f->fd;
-  fd.N = N; fd.d = d; fd.p = p; fd.m = f->m; fd.K = f->K; fd.transform = f->transform;
+  fd.N = N; fd.ode = ode; fd.d = d; fd.p = p; fd.m = f->m; fd.K = f->K; fd.transform = f->transform;
   for (int i = 0; i < kMMax; ++i) fd.obs[i] = i < f->m ? f->obs[i] : 0;
   fd.a = f->a; fd.s = std::sqrt(1.0 - f->a * f->a); fd.kappa = f->kappa;
   fd.seed = f->seed; fd.stream_id = f->filter_id;
@@ -424,7 +373,7 @@ pf_status pf_assimilate(pf_filter* f, double t_k, const double* y_k) {
     if (cs != PF_OK) return cs;
     return fail(f, (pf_status)dst, status_text(dst));
   }
-  f->hist = advance(f, f->hist, t_k, f->ep_host, depth_out);
+  f->hist = advance_history(f->hist, t_k, f->ep_host, depth_out);
   return PF_OK;
 }
 
@@ -505,7 +454,7 @@ pf_status pf_load_observations(pf_filter* f, int T, const double* t, const doubl
     int depth_out = 0;
     S[k] = fill_epoch(f, h, t[k], y + (size_t)k * f->m, &host[k], &depth_out);
     if (S[k] < 1) return fail(f, PF_ERR_INVALID_ARG, "substep grid of an interval is invalid");
-    h = advance(f, h, t[k], &host[k], depth_out);
+    h = advance_history(h, t[k], &host[k], depth_out);
     after[k] = h;
   }
   if (f->series_dev) {

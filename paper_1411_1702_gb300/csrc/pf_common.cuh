@@ -86,6 +86,7 @@ struct Ensemble {
 // Everything a kernel needs about one filter (passed by value).
 struct FilterDev {
   int64_t N;
+  int ode;
   int d, p, m, K;
   int transform;
   int obs[kMMax];
@@ -230,14 +231,16 @@ __device__ __forceinline__ double block_max(double v, double* s) {
   return s[0];
 }
 
-// Last-block election: after every block has written its partial result, the
-// block that increments the ticket last sees all of them.  No waiting.
-__device__ __forceinline__ bool elect_last_block(unsigned* ticket, int* s_flag) {
+// Last-block election among the vg blocks that work on one filter (vg =
+// gridDim.x for a single-filter launch): after every block has written its
+// partial result, the block that increments the ticket last sees all of them.
+// No waiting.
+__device__ __forceinline__ bool elect_last_block(unsigned* ticket, int* s_flag, unsigned vg) {
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned t = atomicAdd(ticket, 1u);
-    *s_flag = (t == gridDim.x - 1) ? 1 : 0;
+    *s_flag = (t == vg - 1) ? 1 : 0;
   }
   __syncthreads();
   if (*s_flag) {

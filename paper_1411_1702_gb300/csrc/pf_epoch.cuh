@@ -43,16 +43,16 @@ __device__ inline void cholesky_psd(int p, const double* C, double* L) {
 }
 
 // End of stage 1 (Step 3a): block maximum of the log fitness weights; the
-// last block stores the global maximum (the log-sum-exp shift) and flags a
-// degenerate epoch.  Every thread of the block must call it.
-__device__ __forceinline__ void stage1_tail(const FilterDev& fd, uint32_t epoch, double lg,
-                                            double* s_red, int* s_flag) {
+// last of the filter's vg blocks stores the global maximum (the log-sum-exp
+// shift) and flags a degenerate epoch.  Every thread of the block must call it.
+__device__ __forceinline__ void stage1_tail(const FilterDev& fd, uint32_t epoch, double lg, int vb,
+                                            int vg, double* s_red, int* s_flag) {
   Ctrl* ctrl = fd.ctrl;
   const double bm = block_max(lg, s_red);
-  if (threadIdx.x == 0) fd.blk[blockIdx.x] = bm;
-  if (elect_last_block(fd.ticket + 0, s_flag)) {
+  if (threadIdx.x == 0) fd.blk[vb] = bm;
+  if (elect_last_block(fd.ticket + 0, s_flag, (unsigned)vg)) {
     double m = -CUDART_INF;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmax(m, __ldcg(fd.blk + b));
+    for (int b = threadIdx.x; b < vg; b += blockDim.x) m = fmax(m, __ldcg(fd.blk + b));
     m = block_max(m, s_red);
     if (threadIdx.x == 0) {
       ctrl->lg_max = m;
@@ -67,21 +67,21 @@ __device__ __forceinline__ void stage1_tail(const FilterDev& fd, uint32_t epoch,
 }
 
 // End of stage 2 (Step 5): block maximum of the new log weights and the count
-// of zero-weight particles; the last block stores the maximum and flags a
-// degenerate epoch.  Every thread of the block must call it.
+// of zero-weight particles; the last of the filter's vg blocks stores the
+// maximum and flags a degenerate epoch.  Every thread of the block must call it.
 __device__ __forceinline__ void stage2_tail(const FilterDev& fd, uint32_t epoch, double lwn,
-                                            double bad, double* s_red, int* s_flag) {
+                                            double bad, int vb, int vg, double* s_red, int* s_flag) {
   Ctrl* ctrl = fd.ctrl;
   const double bm = block_max(lwn, s_red);
   const double nb = block_sum(bad, s_red);
   if (threadIdx.x == 0) {
-    fd.blk[blockIdx.x] = bm;
+    fd.blk[vb] = bm;
     if (nb > 0.0)
       atomicAdd(reinterpret_cast<unsigned long long*>(&ctrl->n_nonfinite), (unsigned long long)nb);
   }
-  if (elect_last_block(fd.ticket + 2, s_flag)) {
+  if (elect_last_block(fd.ticket + 2, s_flag, (unsigned)vg)) {
     double m = -CUDART_INF;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmax(m, __ldcg(fd.blk + b));
+    for (int b = threadIdx.x; b < vg; b += blockDim.x) m = fmax(m, __ldcg(fd.blk + b));
     m = block_max(m, s_red);
     if (threadIdx.x == 0) {
       ctrl->lw_max = m;

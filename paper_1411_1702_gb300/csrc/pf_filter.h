@@ -1,0 +1,72 @@
+// pf_filter.h -- the library-owned filter object behind the opaque pf_filter
+// handle (shared by the single-filter C ABI and the batch of filters).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "pf_kernels.h"
+
+namespace pfg {
+
+struct HistoryState {
+  int64_t epochs;
+  int depth;
+  double t_prev, hprev1, hprev2;
+};
+
+void set_thread_error(const std::string& msg);
+
+}  // namespace pfg
+
+struct pf_filter {
+  // configuration
+  int ode, d, p, m, lmm, K, spacing, substeps, history, transform, noise;
+  double dt, q0, a, kappa;
+  uint64_t seed;
+  uint32_t filter_id;
+  int64_t N;
+  int obs[pfg::kMMax];
+  double sigma[pfg::kMMax];
+  int prior_kind[pfg::kPMax];
+  double prior_lo[pfg::kPMax], prior_hi[pfg::kPMax];
+  double x0[pfg::kDMax];
+  double t0;
+  // CUDA resources
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* dmem = nullptr;
+  size_t dbytes = 0;
+  pfg::FilterDev fd{};
+  pfg::EpochParams* ep_dev = nullptr;    // online parameter slot
+  pfg::EpochParams* ep_host = nullptr;   // pinned staging
+  pfg::Ctrl* ctrl_host = nullptr;        // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // committed history (host view)
+  pfg::HistoryState hist{};
+  // device-resident observation series
+  pfg::EpochParams* series_dev = nullptr;
+  int series_T = 0;
+  int series_next = 0;
+  std::vector<int> series_S;
+  std::vector<pfg::HistoryState> series_after;  // history after epoch k of the series
+  pfg::HistoryState series_start{};
+  // per-kernel timing (pf_options.timing)
+  bool timing = false;
+  std::vector<cudaEvent_t*> mark_free;     // sets of kEpochKernels + 1 events
+  std::vector<cudaEvent_t*> mark_pending;  // recorded, not yet read
+  double kernel_ms[pfg::kEpochKernels] = {0};
+  int64_t kernel_launches[pfg::kEpochKernels] = {0};
+  // bookkeeping
+  double last_ms = 0.0;
+  int64_t h2d_bytes = 0, d2h_bytes = 0;
+  bool in_batch = false;                  // epochs are driven by a pf_batch
+  std::string err;
+};
+
+namespace pfg {
+// Parameter block of one epoch of f from history h (host); returns S or -1.
+int fill_epoch(const pf_filter* f, const HistoryState& h, double t_k, const double* y,
+               EpochParams* ep, int* depth_out);
+// History after an epoch with parameter block ep.
+HistoryState advance_history(const HistoryState& h, double t_k, const EpochParams* ep, int depth_out);
+}  // namespace pfg

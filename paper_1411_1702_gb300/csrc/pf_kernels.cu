@@ -1,32 +1,37 @@
 // pf_kernels.cu -- the per-observation epoch of Algorithm 1 (Arnold, Calvetti,
-// Somersalo) for one filter, as CUDA kernels for sm_103a.
+// Somersalo) as CUDA kernels for sm_103a, for one filter or for a batch.
 //
-// One epoch j -> j+1 is six launches on the filter's stream:
-//   k_stage1    Steps 2, 3a: shrink phi, propagate by Psi, first-stage log
-//               weights log g = log w + log pi(y | xbar); the last block takes
-//               the maximum (log-sum-exp shift)
-//   k_scan_tile Step 3a/3b: g = exp(log g - max), tile-local inclusive scan;
-//               the last block scans the tile totals
-//   k_scan_add  cumulative weights c_k = tile offset + tile-local sum
-//   k_resample  Step 3b: systematic resampling, l_i = min{k : c_k > tau_i}
-//   k_stage2    Steps 3c, 4, 5: gather by l, proliferate phi, repropagate with
-//               the Milne local-error sums, innovation, new log weights; the
-//               last block takes the maximum
-//   k_moments   Steps 5-6: normalisation, weighted mean/covariance of phi,
-//               mean state, ESS; the last block commits (flips the ensemble
-//               buffer) unless the epoch is degenerate
-// Every kernel returns at once if an earlier epoch failed (Ctrl::status), so
-// epochs can be enqueued ahead without host round trips.
+// One epoch j -> j+1 is six phases:
+//   stage1      Steps 2, 3a: shrink phi, propagate by Psi, first-stage log
+//               weights log g = log w + log pi(y | xbar); the filter's last
+//               block takes the maximum (log-sum-exp shift)
+//   scan_tile   Step 3a/3b: g = exp(log g - max), tile-local inclusive scan;
+//               the filter's last block scans the tile totals
+//   scan_add    cumulative weights c_k = tile offset + tile-local sum
+//   resample    Step 3b: systematic resampling, l_i = min{k : c_k > tau_i}
+//   stage2      Steps 3c, 4, 5: gather by l, proliferate phi, repropagate with
+//               the Milne local-error sums, innovation, new log weights
+//   moments     Steps 5-6: normalisation, weighted mean/covariance of phi,
+//               mean state, ESS; the filter's last block commits (flips the
+//               ensemble buffer) unless the epoch is degenerate
+// Every phase is a device function of a virtual block index vb in [0, vg):
+// a single-filter launch runs it with (blockIdx.x, gridDim.x); a batched
+// launch reads (filter, vb) from a tile table, so one launch serves any number
+// of filters of any size.  A filter's reduction trees depend only on its N,
+// never on where its tiles land, so a filter gives bit-identical results alone
+// and in a batch.  Every phase returns at once if an earlier epoch of its
+// filter failed (Ctrl::status), so epochs can be enqueued ahead.
 #include "pf_common.cuh"
+#include "pf_epoch.cuh"
 #include "pf_kernels.h"
 #include "pf_models.cuh"
 #include "pf_scan.cuh"
-#include "pf_epoch.cuh"
 
 namespace pfg {
 
 constexpr int kSmallThreads = 128;
 constexpr int kResampleThreads = 256;
+constexpr int kInitThreads = 256;
 
 // Gaussian log-likelihood of the observed components, without the constant
 // terms (they cancel in every normalisation of Steps 3a and 5).
@@ -99,11 +104,11 @@ __device__ __forceinline__ void propagate(const typename M::Th& T, const StepCoe
 // Philox purpose INIT, epoch word 0), x = h1 = h2 = x0, unnormalised log
 // weight 0 (w = 1/N after normalisation), into the pending buffer.
 template <int D, int P>
-__global__ void __launch_bounds__(256) k_init(const FilterDev fd) {
+__device__ __forceinline__ void init_body(const FilterDev& fd, int vb) {
   const Ctrl* ctrl = fd.ctrl;
   const Ensemble dst = pending(fd, ctrl->cur);
   const int64_t N = fd.N;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = (int64_t)vb * blockDim.x + threadIdx.x;
   if (n >= N) return;
 #pragma unroll
   for (int b = 0; b < (P + 1) / 2; ++b) {
@@ -135,20 +140,15 @@ __global__ void __launch_bounds__(256) k_init(const FilterDev fd) {
 
 // ---------------------------------------------------------------- stage 1
 template <class M>
-__global__ void __launch_bounds__(kSmallThreads) k_stage1(const FilterDev fd,
-                                                          const EpochParams* __restrict__ ep) {
+__device__ __forceinline__ void stage1_body(const FilterDev& fd, const EpochParams* __restrict__ ep,
+                                            int vb, int vg, const StepCoef* s_sc, double* s_red,
+                                            int* s_flag) {
   constexpr int D = M::D, P = M::P;
-  extern __shared__ double s_dyn[];
-  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
-  __shared__ double s_red[32];
-  __shared__ int s_flag;
-  Ctrl* ctrl = fd.ctrl;
-  if (ctrl->status != PF_OK) return;
+  const Ctrl* ctrl = fd.ctrl;
   const int S = ep->S;
-  load_steps(s_sc, ep, S);
   const Ensemble E = committed(fd, ctrl->cur);
   const int64_t N = fd.N;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = (int64_t)vb * blockDim.x + threadIdx.x;
   double lg = -CUDART_INF;
   if (n < N) {
     double ph[P], th[P];
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_stage1(const FilterDev fd,
     if (!finite_bits(lg)) lg = -CUDART_INF;
     fd.lg[n] = lg;
   }
-  stage1_tail(fd, ep->epoch, lg, s_red, &s_flag);
+  stage1_tail(fd, ep->epoch, lg, vb, vg, s_red, s_flag);
 }
 
 // ------------------------------------------------------------------- scan
@@ -181,14 +181,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_stage1(const FilterDev fd,
 // passes (thread level and tile level) make c non-decreasing; the maximum is
 // exact and associative, so c is still a deterministic function of g for a
 // given N.
-__global__ void __launch_bounds__(kScanThreads) k_scan_tile(const FilterDev fd) {
-  __shared__ double s_warp[33];
-  __shared__ int s_flag;
+__device__ __forceinline__ void scan_tile_body(const FilterDev& fd, int vb, int vg, double* s_warp,
+                                               int* s_flag) {
   Ctrl* ctrl = fd.ctrl;
-  if (ctrl->status != PF_OK) return;
   const double M = ctrl->lg_max;
   const int64_t N = fd.N;
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  const int64_t base = (int64_t)vb * kScanTile + (int64_t)threadIdx.x * kScanItems;
   double v[kScanItems];
   double run = 0.0;
 #pragma unroll
@@ -209,11 +207,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tile(const FilterDev fd) 
     const int64_t k = base + j;
     if (k < N) fd.c[k] = fmax(v[j], floor_prev);
   }
-  if (threadIdx.x == 0) fd.blk[blockIdx.x] = tile_last;
-  if (elect_last_block(fd.ticket + 1, &s_flag)) {
+  if (threadIdx.x == 0) fd.blk[vb] = tile_last;
+  if (elect_last_block(fd.ticket + 1, s_flag, (unsigned)vg)) {
     // tile offsets boff_b = sum of earlier tile totals, and the running maximum
     // pmax_b of the earlier tiles' last values boff_b' + T_b'
-    const int nb = gridDim.x;
+    const int nb = vg;
     const int chunk = (nb + blockDim.x - 1) / blockDim.x;
     const int b0 = threadIdx.x * chunk;
     double acc = 0.0;
@@ -237,9 +235,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tile(const FilterDev fd) 
   }
 }
 
-__global__ void __launch_bounds__(256) k_scan_add(const FilterDev fd) {
-  if (fd.ctrl->status != PF_OK) return;
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void scan_add_body(const FilterDev& fd, int vb) {
+  const int64_t k = (int64_t)vb * blockDim.x + threadIdx.x;
   if (k < fd.N) {
     const int64_t b = k / kScanTile;
     fd.c[k] = fmax(fd.boff[b] + fd.c[k], fd.pmax[b]);
@@ -249,19 +246,15 @@ __global__ void __launch_bounds__(256) k_scan_add(const FilterDev fd) {
 // --------------------------------------------------------------- resample
 // Step 3b read as systematic resampling: tau_i = ((i + u)/N) c_{N-1} with one
 // u per epoch (Philox purpose RESAMPLE, slot 0); l_i = min{k : c_k > tau_i},
-// else the first k with c_k = c_{N-1}.  All values are >= +0, so their IEEE
-// bit patterns order like the numbers and the search compares integers.
-__global__ void __launch_bounds__(kResampleThreads) k_resample(const FilterDev fd,
-                                                               const EpochParams* __restrict__ ep) {
-  __shared__ int32_t s_l[kResampleThreads];
-  __shared__ double s_red[32];
+// else the first k with c_k = c_{N-1}.
+__device__ __forceinline__ void resample_body(const FilterDev& fd, const EpochParams* __restrict__ ep,
+                                              int vb, int32_t* s_l, double* s_red) {
   Ctrl* ctrl = fd.ctrl;
-  if (ctrl->status != PF_OK) return;
   const int64_t N = fd.N;
   const U4 w = draw_block(fd, kRngResample, 0u, ep->epoch, 0u);
   const double u = uniform53(w.x, w.y);
   const double total = __ldg(fd.c + (N - 1));
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = (int64_t)vb * blockDim.x + threadIdx.x;
   int32_t l = -1;
   if (i < N) {
     l = systematic_index(fd.c, N, i, u, total);
@@ -280,23 +273,18 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample(const FilterDev f
 
 // ---------------------------------------------------------------- stage 2
 template <class M>
-__global__ void __launch_bounds__(kSmallThreads) k_stage2(const FilterDev fd,
-                                                          const EpochParams* __restrict__ ep) {
+__device__ __forceinline__ void stage2_body(const FilterDev& fd, const EpochParams* __restrict__ ep,
+                                            int vb, int vg, const StepCoef* s_sc, double* s_red,
+                                            int* s_flag) {
   constexpr int D = M::D, P = M::P;
-  extern __shared__ double s_dyn[];
-  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
-  __shared__ double s_red[32];
-  __shared__ int s_flag;
-  Ctrl* ctrl = fd.ctrl;
-  if (ctrl->status != PF_OK) return;
+  const Ctrl* ctrl = fd.ctrl;
   const int S = ep->S;
-  load_steps(s_sc, ep, S);
   const int cur = ctrl->cur;
   const Ensemble src = committed(fd, cur);
   const Ensemble dst = pending(fd, cur);
   const int64_t N = fd.N;
   const uint32_t epoch = ep->epoch;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = (int64_t)vb * blockDim.x + threadIdx.x;
   double lwn = -CUDART_INF;
   double bad = 0.0;
   if (n < N) {
@@ -363,15 +351,15 @@ __global__ void __launch_bounds__(kSmallThreads) k_stage2(const FilterDev fd,
     for (int i = 0; i < P; ++i) dst.phi[i * N + n] = ph[i];
     dst.lw[n] = lwn;
   }
-  stage2_tail(fd, epoch, lwn, bad, s_red, &s_flag);
+  stage2_tail(fd, epoch, lwn, bad, vb, vg, s_red, s_flag);
 }
 
 // ---------------------------------------------------------------- moments
 // Weighted sums of the pending buffer with e_n = exp(lw_n - max lw):
 //   [S0 = sum e, Sw2 = sum e^2, S1 = sum e phi, S2 = sum e (phi - c)(phi - c)^T
 //    (upper triangle, shift c = the committed mean), Sx = sum e x]
-// Zero-weight particles are skipped (their state may be non-finite).  The last
-// block reduces the partial records and commits the epoch.
+// Zero-weight particles are skipped (their state may be non-finite).  The
+// filter's last block reduces the partial records and commits the epoch.
 template <int D, int P>
 struct MomentLayout {
   static constexpr int kS0 = 0, kW2 = 1, kS1 = 2, kS2 = 2 + P, kSx = kS2 + P * (P + 1) / 2,
@@ -399,14 +387,11 @@ __device__ __forceinline__ void block_sum_vec(double (&acc)[NV], double* s_part,
 }
 
 template <int D, int P>
-__global__ void __launch_bounds__(kMomentThreads) k_moments(const FilterDev fd, int is_init) {
+__device__ __forceinline__ void moments_body(const FilterDev& fd, int is_init, int vb, int vg,
+                                             double* s_part, double* s_tot, int* s_flag) {
   using Lay = MomentLayout<D, P>;
   constexpr int NV = Lay::kN;
-  __shared__ double s_part[(kMomentThreads / 32) * NV];
-  __shared__ double s_tot[NV];
-  __shared__ int s_flag;
   Ctrl* ctrl = fd.ctrl;
-  if (ctrl->status != PF_OK) return;
   const int cur = ctrl->cur;
   const Ensemble nw = pending(fd, cur);
   const int64_t N = fd.N;
@@ -417,8 +402,7 @@ __global__ void __launch_bounds__(kMomentThreads) k_moments(const FilterDev fd, 
   double acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-       n += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t n = (int64_t)vb * blockDim.x + threadIdx.x; n < N; n += (int64_t)vg * blockDim.x) {
     const double lw = nw.lw[n];
     if (is_neg_inf(lw)) continue;
     const double e = exp(lw - M);
@@ -443,11 +427,11 @@ __global__ void __launch_bounds__(kMomentThreads) k_moments(const FilterDev fd, 
 #pragma unroll
     for (int i = 0; i < D; ++i) acc[Lay::kSx + i] = fma(e, nw.x[i * N + n], acc[Lay::kSx + i]);
   }
-  block_sum_vec<NV>(acc, s_part, fd.part + (int64_t)blockIdx.x * fd.nrec);
-  if (!elect_last_block(fd.ticket + 3, &s_flag)) return;
+  block_sum_vec<NV>(acc, s_part, fd.part + (int64_t)vb * fd.nrec);
+  if (!elect_last_block(fd.ticket + 3, s_flag, (unsigned)vg)) return;
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+  for (int b = threadIdx.x; b < vg; b += blockDim.x) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] += __ldcg(fd.part + (int64_t)b * fd.nrec + k);
   }
@@ -488,10 +472,71 @@ __global__ void __launch_bounds__(kMomentThreads) k_moments(const FilterDev fd, 
   if (!is_init) ctrl->epochs_done += 1;
 }
 
+// ========================================================= single filter
+template <int D, int P>
+__global__ void __launch_bounds__(kInitThreads) k_init(const __grid_constant__ FilterDev fd) {
+  init_body<D, P>(fd, blockIdx.x);
+}
+
+template <class M>
+__global__ void __launch_bounds__(kSmallThreads) k_stage1(const __grid_constant__ FilterDev fd,
+                                                          const EpochParams* __restrict__ ep) {
+  extern __shared__ double s_dyn[];
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  if (fd.ctrl->status != PF_OK) return;
+  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
+  load_steps(s_sc, ep, ep->S);
+  stage1_body<M>(fd, ep, blockIdx.x, gridDim.x, s_sc, s_red, &s_flag);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile(const __grid_constant__ FilterDev fd) {
+  __shared__ double s_warp[33];
+  __shared__ int s_flag;
+  if (fd.ctrl->status != PF_OK) return;
+  scan_tile_body(fd, blockIdx.x, gridDim.x, s_warp, &s_flag);
+}
+
+__global__ void __launch_bounds__(256) k_scan_add(const __grid_constant__ FilterDev fd) {
+  if (fd.ctrl->status != PF_OK) return;
+  scan_add_body(fd, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kResampleThreads) k_resample(const __grid_constant__ FilterDev fd,
+                                                               const EpochParams* __restrict__ ep) {
+  __shared__ int32_t s_l[kResampleThreads];
+  __shared__ double s_red[32];
+  if (fd.ctrl->status != PF_OK) return;
+  resample_body(fd, ep, blockIdx.x, s_l, s_red);
+}
+
+template <class M>
+__global__ void __launch_bounds__(kSmallThreads) k_stage2(const __grid_constant__ FilterDev fd,
+                                                          const EpochParams* __restrict__ ep) {
+  extern __shared__ double s_dyn[];
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  if (fd.ctrl->status != PF_OK) return;
+  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
+  load_steps(s_sc, ep, ep->S);
+  stage2_body<M>(fd, ep, blockIdx.x, gridDim.x, s_sc, s_red, &s_flag);
+}
+
+template <int D, int P>
+__global__ void __launch_bounds__(kMomentThreads) k_moments(const __grid_constant__ FilterDev fd,
+                                                            int is_init) {
+  constexpr int NV = MomentLayout<D, P>::kN;
+  __shared__ double s_part[(kMomentThreads / 32) * NV];
+  __shared__ double s_tot[NV];
+  __shared__ int s_flag;
+  if (fd.ctrl->status != PF_OK) return;
+  moments_body<D, P>(fd, is_init, blockIdx.x, gridDim.x, s_part, s_tot, &s_flag);
+}
+
 // Weighted mean of theta = exp(phi) (or phi) of the committed ensemble, for
 // pf_stats only: w_n = exp(lw_n - logW).  One block, off the epoch path.
 template <int P>
-__global__ void __launch_bounds__(kMomentThreads) k_theta_mean(const FilterDev fd) {
+__global__ void __launch_bounds__(kMomentThreads) k_theta_mean(const __grid_constant__ FilterDev fd) {
   __shared__ double s_part[(kMomentThreads / 32) * P];
   __shared__ double s_tot[P];
   Ctrl* ctrl = fd.ctrl;
@@ -515,6 +560,93 @@ __global__ void __launch_bounds__(kMomentThreads) k_theta_mean(const FilterDev f
   if (threadIdx.x < P) ctrl->theta_mean[threadIdx.x] = s_tot[threadIdx.x];
 }
 
+__global__ void k_set_moments(const __grid_constant__ FilterDev fd) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double L[kPMax * kPMax];
+  cholesky_psd(fd.p, fd.ctrl->C, L);
+  for (int i = 0; i < kPMax * kPMax; ++i) fd.ctrl->L[i] = L[i];
+}
+
+// ========================================================= batch of filters
+// Every batched launch reads its block's (filter, virtual block) from a tile
+// table and the filter's descriptor through a read-only pointer.  Tiles of
+// different filters share a launch; the phases of one filter are ordered by
+// the launches of the stream.  Stage kernels are per model, so each keeps the
+// register budget of its own model.
+__global__ void __launch_bounds__(kInitThreads) k_batch_init(const FilterDev* __restrict__ fds,
+                                                           const BatchTile* __restrict__ tiles) {
+  const BatchTile t = tiles[blockIdx.x];
+  const FilterDev& fd = *(fds + t.f);
+  switch (fd.ode) {
+    case PF_ODE_LINEAR2: init_body<2, 2>(fd, t.vb); break;
+    case PF_ODE_ROBERTSON: init_body<3, 3>(fd, t.vb); break;
+    case PF_ODE_BRUSSELATOR1D: init_body<64, 3>(fd, t.vb); break;
+  }
+}
+
+template <class M, int STAGE>
+__global__ void __launch_bounds__(kSmallThreads) k_batch_stage(const FilterDev* __restrict__ fds,
+                                                             const EpochParams* const* __restrict__ eps,
+                                                             const BatchTile* __restrict__ tiles) {
+  extern __shared__ double s_dyn[];
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  const BatchTile t = tiles[blockIdx.x];
+  const FilterDev& fd = *(fds + t.f);
+  if (fd.ctrl->status != PF_OK) return;
+  const EpochParams* ep = eps[t.f];
+  StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
+  load_steps(s_sc, ep, ep->S);
+  const int vg = (int)((fd.N + kSmallThreads - 1) / kSmallThreads);
+  if (STAGE == 1) stage1_body<M>(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
+  else stage2_body<M>(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_batch_scan_tile(const FilterDev* __restrict__ fds,
+                                                                const BatchTile* __restrict__ tiles) {
+  __shared__ double s_warp[33];
+  __shared__ int s_flag;
+  const BatchTile t = tiles[blockIdx.x];
+  const FilterDev& fd = *(fds + t.f);
+  if (fd.ctrl->status != PF_OK) return;
+  scan_tile_body(fd, t.vb, (int)((fd.N + kScanTile - 1) / kScanTile), s_warp, &s_flag);
+}
+
+__global__ void __launch_bounds__(256) k_batch_scan_add(const FilterDev* __restrict__ fds,
+                                                      const BatchTile* __restrict__ tiles) {
+  const BatchTile t = tiles[blockIdx.x];
+  const FilterDev& fd = *(fds + t.f);
+  if (fd.ctrl->status != PF_OK) return;
+  scan_add_body(fd, t.vb);
+}
+
+__global__ void __launch_bounds__(kResampleThreads) k_batch_resample(
+    const FilterDev* __restrict__ fds, const EpochParams* const* __restrict__ eps,
+    const BatchTile* __restrict__ tiles) {
+  __shared__ int32_t s_l[kResampleThreads];
+  __shared__ double s_red[32];
+  const BatchTile t = tiles[blockIdx.x];
+  const FilterDev& fd = *(fds + t.f);
+  if (fd.ctrl->status != PF_OK) return;
+  resample_body(fd, eps[t.f], t.vb, s_l, s_red);
+}
+
+template <int D, int P>
+__global__ void __launch_bounds__(kMomentThreads) k_batch_moments(const FilterDev* __restrict__ fds,
+                                                                const BatchTile* __restrict__ tiles,
+                                                                int is_init) {
+  constexpr int NV = MomentLayout<D, P>::kN;
+  __shared__ double s_part[(kMomentThreads / 32) * NV];
+  __shared__ double s_tot[NV];
+  __shared__ int s_flag;
+  const BatchTile t = tiles[blockIdx.x];
+  const FilterDev& fd = *(fds + t.f);
+  if (fd.ctrl->status != PF_OK) return;
+  const int64_t b = (fd.N + kMomentThreads - 1) / kMomentThreads;
+  const int vg = (int)(b < kMomentBlocks ? b : kMomentBlocks);
+  moments_body<D, P>(fd, is_init, t.vb, vg, s_part, s_tot, &s_flag);
+}
+
 // ----------------------------------------------------------------- launch
 template <int D, int P>
 static int moment_nrec() {
@@ -531,7 +663,7 @@ int moment_record_size(int ode) {
 }
 
 int max_grid_blocks(int64_t N) {
-  const int64_t a = (N + kSmallThreads - 1) / kSmallThreads;
+  const int64_t a = (N + 31) / 32;  // at least as many as any stage launch
   const int64_t b = (N + kScanTile - 1) / kScanTile;
   const int64_t c = (N + kResampleThreads - 1) / kResampleThreads;
   int64_t m = a > b ? a : b;
@@ -541,16 +673,29 @@ int max_grid_blocks(int64_t N) {
 
 int scan_tiles(int64_t N) { return (int)((N + kScanTile - 1) / kScanTile); }
 
-static int moment_grid(int64_t N) {
-  const int64_t b = (N + kMomentThreads - 1) / kMomentThreads;
-  return (int)(b < kMomentBlocks ? b : kMomentBlocks);
+int phase_blocks(int phase, int ode, int64_t N) {
+  switch (phase) {
+    case kPhaseInit: return (int)((N + kInitThreads - 1) / kInitThreads);
+    case kPhaseStage1:
+    case kPhaseStage2:
+      return ode == PF_ODE_BRUSSELATOR1D ? bruss_stage_blocks(N)
+                                         : (int)((N + kSmallThreads - 1) / kSmallThreads);
+    case kPhaseScanTile: return scan_tiles(N);
+    case kPhaseScanAdd: return (int)((N + 255) / 256);
+    case kPhaseResample: return (int)((N + kResampleThreads - 1) / kResampleThreads);
+    case kPhaseMoments: {
+      const int64_t b = (N + kMomentThreads - 1) / kMomentThreads;
+      return (int)(b < kMomentBlocks ? b : kMomentBlocks);
+    }
+  }
+  return 0;
 }
 
 template <class M>
 static cudaError_t launch_init_t(const FilterDev& fd, cudaStream_t st) {
   const int64_t N = fd.N;
-  k_init<M::D, M::P><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(fd);
-  k_moments<M::D, M::P><<<moment_grid(N), kMomentThreads, 0, st>>>(fd, 1);
+  k_init<M::D, M::P><<<phase_blocks(kPhaseInit, M::ODE, N), kInitThreads, 0, st>>>(fd);
+  k_moments<M::D, M::P><<<phase_blocks(kPhaseMoments, M::ODE, N), kMomentThreads, 0, st>>>(fd, 1);
   return cudaGetLastError();
 }
 
@@ -559,22 +704,22 @@ static cudaError_t launch_epoch_t(const FilterDev& fd, const EpochParams* ep, in
                                   cudaStream_t st, cudaEvent_t* marks) {
   const int64_t N = fd.N;
   const size_t smem = (size_t)S * sizeof(StepCoef);
-  const unsigned g_small = (unsigned)((N + kSmallThreads - 1) / kSmallThreads);
+  const unsigned g_small = (unsigned)phase_blocks(kPhaseStage1, M::ODE, N);
   auto mark = [&](int i) {
     if (marks) cudaEventRecord(marks[i], st);
   };
   mark(0);
   k_stage1<M><<<g_small, kSmallThreads, smem, st>>>(fd, ep);
   mark(1);
-  k_scan_tile<<<(unsigned)scan_tiles(N), kScanThreads, 0, st>>>(fd);
+  k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, M::ODE, N), kScanThreads, 0, st>>>(fd);
   mark(2);
-  k_scan_add<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(fd);
+  k_scan_add<<<(unsigned)phase_blocks(kPhaseScanAdd, M::ODE, N), 256, 0, st>>>(fd);
   mark(3);
-  k_resample<<<(unsigned)((N + kResampleThreads - 1) / kResampleThreads), kResampleThreads, 0, st>>>(fd, ep);
+  k_resample<<<(unsigned)phase_blocks(kPhaseResample, M::ODE, N), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
   k_stage2<M><<<g_small, kSmallThreads, smem, st>>>(fd, ep);
   mark(5);
-  k_moments<M::D, M::P><<<moment_grid(N), kMomentThreads, 0, st>>>(fd, 0);
+  k_moments<M::D, M::P><<<phase_blocks(kPhaseMoments, M::ODE, N), kMomentThreads, 0, st>>>(fd, 0);
   mark(6);
   return cudaGetLastError();
 }
@@ -583,6 +728,7 @@ static cudaError_t launch_epoch_t(const FilterDev& fd, const EpochParams* ep, in
 static cudaError_t launch_epoch_bruss(const FilterDev& fd, const EpochParams* ep, int S,
                                       cudaStream_t st, cudaEvent_t* marks) {
   const int64_t N = fd.N;
+  const int ode = PF_ODE_BRUSSELATOR1D;
   auto mark = [&](int i) {
     if (marks) cudaEventRecord(marks[i], st);
   };
@@ -590,15 +736,15 @@ static cudaError_t launch_epoch_bruss(const FilterDev& fd, const EpochParams* ep
   mark(0);
   if ((e = launch_bruss_stage(1, fd, ep, S, st)) != cudaSuccess) return e;
   mark(1);
-  k_scan_tile<<<(unsigned)scan_tiles(N), kScanThreads, 0, st>>>(fd);
+  k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, ode, N), kScanThreads, 0, st>>>(fd);
   mark(2);
-  k_scan_add<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(fd);
+  k_scan_add<<<(unsigned)phase_blocks(kPhaseScanAdd, ode, N), 256, 0, st>>>(fd);
   mark(3);
-  k_resample<<<(unsigned)((N + kResampleThreads - 1) / kResampleThreads), kResampleThreads, 0, st>>>(fd, ep);
+  k_resample<<<(unsigned)phase_blocks(kPhaseResample, ode, N), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
   if ((e = launch_bruss_stage(2, fd, ep, S, st)) != cudaSuccess) return e;
   mark(5);
-  k_moments<64, 3><<<moment_grid(N), kMomentThreads, 0, st>>>(fd, 0);
+  k_moments<64, 3><<<phase_blocks(kPhaseMoments, ode, N), kMomentThreads, 0, st>>>(fd, 0);
   mark(6);
   return cudaGetLastError();
 }
@@ -609,8 +755,8 @@ cudaError_t launch_init(int ode, const FilterDev& fd, cudaStream_t st) {
     case PF_ODE_ROBERTSON: return launch_init_t<Robertson>(fd, st);
     case PF_ODE_BRUSSELATOR1D: {
       const int64_t N = fd.N;
-      k_init<64, 3><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(fd);
-      k_moments<64, 3><<<moment_grid(N), kMomentThreads, 0, st>>>(fd, 1);
+      k_init<64, 3><<<phase_blocks(kPhaseInit, ode, N), kInitThreads, 0, st>>>(fd);
+      k_moments<64, 3><<<phase_blocks(kPhaseMoments, ode, N), kMomentThreads, 0, st>>>(fd, 1);
       return cudaGetLastError();
     }
   }
@@ -642,15 +788,48 @@ bool ode_supported(int ode) {
   return ode == PF_ODE_LINEAR2 || ode == PF_ODE_ROBERTSON || ode == PF_ODE_BRUSSELATOR1D;
 }
 
-__global__ void k_set_moments(const FilterDev fd) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double L[kPMax * kPMax];
-  cholesky_psd(fd.p, fd.ctrl->C, L);
-  for (int i = 0; i < kPMax * kPMax; ++i) fd.ctrl->L[i] = L[i];
-}
-
 cudaError_t launch_set_moments(const FilterDev& fd, cudaStream_t st) {
   k_set_moments<<<1, 32, 0, st>>>(fd);
+  return cudaGetLastError();
+}
+
+// One batched phase over the device tile table tiles[0..ntiles).  Stage and
+// moment phases need tiles of one model only (ode); the other phases take any
+// mix.
+// smem is the step-table size of the largest interval among the filters.
+cudaError_t launch_batch_phase(int phase, int ode, const FilterDev* fds, const EpochParams* const* eps,
+                               const BatchTile* tiles, int ntiles, size_t smem, int is_init,
+                               cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  switch (phase) {
+    case kPhaseInit: k_batch_init<<<ntiles, kInitThreads, 0, st>>>(fds, tiles); break;
+    case kPhaseStage1:
+    case kPhaseStage2: {
+      const int stage = phase == kPhaseStage1 ? 1 : 2;
+      if (ode == PF_ODE_BRUSSELATOR1D)
+        return launch_batch_bruss_stage(stage, fds, eps, tiles, ntiles, smem, st);
+      if (ode == PF_ODE_ROBERTSON) {
+        if (stage == 1) k_batch_stage<Robertson, 1><<<ntiles, kSmallThreads, smem, st>>>(fds, eps, tiles);
+        else k_batch_stage<Robertson, 2><<<ntiles, kSmallThreads, smem, st>>>(fds, eps, tiles);
+      } else if (ode == PF_ODE_LINEAR2) {
+        if (stage == 1) k_batch_stage<Linear2, 1><<<ntiles, kSmallThreads, smem, st>>>(fds, eps, tiles);
+        else k_batch_stage<Linear2, 2><<<ntiles, kSmallThreads, smem, st>>>(fds, eps, tiles);
+      } else {
+        return cudaErrorInvalidValue;
+      }
+      break;
+    }
+    case kPhaseScanTile: k_batch_scan_tile<<<ntiles, kScanThreads, 0, st>>>(fds, tiles); break;
+    case kPhaseScanAdd: k_batch_scan_add<<<ntiles, 256, 0, st>>>(fds, tiles); break;
+    case kPhaseResample: k_batch_resample<<<ntiles, kResampleThreads, 0, st>>>(fds, eps, tiles); break;
+    case kPhaseMoments:
+      if (ode == PF_ODE_LINEAR2) k_batch_moments<2, 2><<<ntiles, kMomentThreads, 0, st>>>(fds, tiles, is_init);
+      else if (ode == PF_ODE_ROBERTSON) k_batch_moments<3, 3><<<ntiles, kMomentThreads, 0, st>>>(fds, tiles, is_init);
+      else if (ode == PF_ODE_BRUSSELATOR1D) k_batch_moments<64, 3><<<ntiles, kMomentThreads, 0, st>>>(fds, tiles, is_init);
+      else return cudaErrorInvalidValue;
+      break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -6,6 +6,36 @@
 
 namespace pfg {
 
+// phases of an epoch (and Step 1), in launch order
+enum : int {
+  kPhaseStage1 = 0,
+  kPhaseScanTile = 1,
+  kPhaseScanAdd = 2,
+  kPhaseResample = 3,
+  kPhaseStage2 = 4,
+  kPhaseMoments = 5,
+  kPhaseInit = 6
+};
+
+// one block of a batched launch: filter index and its virtual block index
+struct BatchTile {
+  int f;
+  int vb;
+};
+
+// blocks one filter of N particles needs in a phase
+int phase_blocks(int phase, int ode, int64_t N);
+int bruss_stage_blocks(int64_t N);
+// One batched phase over a device tile table (see pf_kernels.cu); stage
+// phases take the tiles of one model (ode).
+cudaError_t launch_batch_phase(int phase, int ode, const FilterDev* fds, const EpochParams* const* eps,
+                               const BatchTile* tiles, int ntiles, size_t smem, int is_init,
+                               cudaStream_t st);
+// Batched Brusselator stage (1 or 2) over its own tile table (pf_bruss.cu).
+cudaError_t launch_batch_bruss_stage(int stage, const FilterDev* fds, const EpochParams* const* eps,
+                                     const BatchTile* tiles, int ntiles, size_t smem,
+                                     cudaStream_t st);
+
 // Step 1 of Algorithm 1 into the pending buffer, then the moments and commit.
 cudaError_t launch_init(int ode, const FilterDev& fd, cudaStream_t st);
 // One epoch (Steps 2-6) with the parameter block ep (device) of S substeps.
@@ -28,9 +58,6 @@ int max_grid_blocks(int64_t N);
 int scan_tiles(int64_t N);
 int kernels_per_epoch(int ode);
 bool ode_supported(int ode);
-
-// Error text returned by pf_last_error(NULL) on this thread (pf_capi.cu).
-void set_thread_error(const std::string& msg);
 
 // Substep table of one observation interval (host code, pf_grid.cu).
 int build_substeps(int lmm, int spacing, double dt, int substeps, double q0, double t_prev,

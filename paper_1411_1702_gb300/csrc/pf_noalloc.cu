@@ -20,7 +20,7 @@
 // the cumulative weights and indices of pf_assimilate.
 #include <mutex>
 
-#include "pf_kernels.h"
+#include "pf_filter.h"
 #include "pf_scan.cuh"
 
 namespace pfg {
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kNaThreads) k_na_max(const double* __restrict_
     m = fmax(m, clean_logw(lg[k]));
   m = block_max(m, s_red);
   if (threadIdx.x == 0) sc.blockmax[blockIdx.x] = m;
-  if (elect_last_block(sc.ticket + 0, &s_flag)) {
+  if (elect_last_block(sc.ticket + 0, &s_flag, gridDim.x)) {
     double t = -CUDART_INF;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t = fmax(t, __ldcg(sc.blockmax + b));
     t = block_max(t, s_red);
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kScanThreads) k_na_scan_tile(const double* __r
     if (k < N) c[k] = fmax(v[j], floor_prev);
   }
   if (threadIdx.x == 0) sc.tile[blockIdx.x] = tile_last;
-  if (elect_last_block(sc.ticket + 1, &s_flag)) {
+  if (elect_last_block(sc.ticket + 1, &s_flag, gridDim.x)) {
     const int nb = gridDim.x;
     const int chunk = (nb + blockDim.x - 1) / blockDim.x;
     const int b0 = threadIdx.x * chunk;

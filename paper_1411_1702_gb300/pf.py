@@ -30,6 +30,8 @@ ABI_SYMBOLS = [
     "pf_load_observations", "pf_run", "pf_synchronize", "pf_reset", "pf_get_ensemble",
     "pf_set_ensemble", "pf_set_moments", "pf_get_work", "pf_get_history", "pf_set_history",
     "pf_substep_table", "pf_version", "pf_kernel_times", "pf_resample_systematic_noalloc",
+    "pf_batch_create", "pf_batch_assimilate", "pf_batch_stats", "pf_batch_last_error",
+    "pf_batch_destroy",
 ]
 NOALLOC_MAX_PARTICLES = 1 << 24
 KERNEL_SLOTS = ["stage1", "scan_tile", "scan_add", "resample", "stage2", "moments"]
@@ -61,6 +63,11 @@ class Stats(C.Structure):
                 ("unique_parents", C.c_int64), ("nonfinite", C.c_int64),
                 ("theta_mean", C.c_double * 8), ("last_epoch_ms", C.c_double),
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("epochs", C.c_int64), ("graph_captures", C.c_int64),
+                ("last_device_ms", C.c_double), ("last_active", C.c_int), ("last_tiles", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -102,6 +109,11 @@ def load(path: str = LIB_PATH):
         "pf_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), C.c_int]),
         "pf_resample_systematic_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
                                                      C.c_void_p, C.c_void_p]),
+        "pf_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+        "pf_batch_assimilate": (C.c_int, [C.c_void_p, _dp, C.POINTER(_dp), C.POINTER(C.c_int)]),
+        "pf_batch_stats": (C.c_int, [C.c_void_p, C.POINTER(BatchStats)]),
+        "pf_batch_last_error": (C.c_char_p, [C.c_void_p]),
+        "pf_batch_destroy": (None, [C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -270,3 +282,47 @@ class Filter:
     def pf_set_history(self, epoch, depth, t_prev, hprev1, hprev2):
         _check(load().pf_set_history(self._h, int(epoch), int(depth), float(t_prev), float(hprev1),
                                      float(hprev2)), self._h)
+
+
+class Batch:
+    """Many filters advanced together by tile-scheduled batched launches."""
+
+    def __init__(self, filters, stream=None):
+        L = load()
+        self.filters = list(filters)
+        arr = (C.c_void_p * len(self.filters))(*[f._h.value for f in self.filters])
+        h = C.c_void_p()
+        st = L.pf_batch_create(arr, len(self.filters), C.c_void_p(stream) if stream else None,
+                               C.byref(h))
+        _check(st, None)
+        self._h = h
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.pf_batch_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def pf_batch_assimilate(self, t, ys):
+        """t: n times; ys: list of n observation arrays or None (idle).
+        Returns the per-filter status codes."""
+        n = len(self.filters)
+        tt = _f64(t)
+        keep = [None if y is None else _f64(y) for y in ys]
+        ptrs = (_dp * n)(*[(_d(y) if y is not None else _dp()) for y in keep])
+        status = (C.c_int * n)()
+        st = load().pf_batch_assimilate(self._h, _d(tt), ptrs, status)
+        if st != PF_OK:
+            msg = load().pf_batch_last_error(self._h)
+            raise PfError(st, msg.decode() if msg else "")
+        return [int(s) for s in status]
+
+    def pf_batch_stats(self):
+        s = BatchStats()
+        _check(load().pf_batch_stats(self._h, C.byref(s)), None)
+        return dict(epochs=s.epochs, graph_captures=s.graph_captures,
+                    last_device_ms=s.last_device_ms, last_active=s.last_active,
+                    last_tiles=s.last_tiles)

@@ -1,0 +1,123 @@
+"""Batches of filters: bit-identical to each filter alone, idle filters,
+isolated failures, graph reuse."""
+import numpy as np
+import pytest
+
+from paper_1411_1702_gb300 import build as B
+from paper_1411_1702_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf():
+    B.build()
+    from paper_1411_1702_gb300 import pf as _pf
+    _pf.load()
+    return _pf
+
+
+def _mix(T=4):
+    specs = [("linear2", 1000, 1), ("robertson", 3001, 2), ("linear2", 2053, 3),
+             ("robertson", 129, 4), ("brusselator", 70, 5), ("linear2", 1, 6),
+             ("robertson", 20000, 7)]
+    return [W.get(name, N=N, T=T, seed=seed) for name, N, seed in specs]
+
+
+def _same(a, b):
+    ea, eb = a.pf_get_ensemble(), b.pf_get_ensemble()
+    return all(np.array_equal(ea[k], eb[k], equal_nan=True) for k in ea)
+
+
+def test_batched_equals_alone(pf):
+    ws = _mix(T=4)
+    alone = [pf.Filter.from_workload(w) for w in ws]
+    members = [pf.Filter.from_workload(w) for w in ws]
+    batch = pf.Batch(members)
+    for k in range(4):
+        for f, w in zip(alone, ws):
+            f.pf_assimilate(w.t_obs[k], w.y_obs[k])
+        st = batch.pf_batch_assimilate([w.t_obs[k] for w in ws], [w.y_obs[k] for w in ws])
+        assert st == [pf.PF_OK] * len(ws)
+        for a, m in zip(alone, members):
+            assert _same(a, m)
+            ta, Ca, xa = a.pf_estimates()
+            tm, Cm, xm = m.pf_estimates()
+            assert np.array_equal(ta, tm) and np.array_equal(Ca, Cm) and np.array_equal(xa, xm)
+            assert a.pf_get_history() == m.pf_get_history()
+    stats = batch.pf_batch_stats()
+    assert stats["epochs"] == 4 and stats["graph_captures"] == 1
+    assert stats["last_active"] == len(ws)
+
+
+def test_idle_filters_and_graph_recapture(pf):
+    ws = _mix(T=5)
+    alone = [pf.Filter.from_workload(w) for w in ws]
+    members = [pf.Filter.from_workload(w) for w in ws]
+    batch = pf.Batch(members)
+    counts = [0] * len(ws)
+    schedule = [[1, 1, 1, 1, 1, 1, 1], [1, 0, 1, 0, 1, 0, 1], [1, 0, 1, 0, 1, 0, 1],
+                [0, 1, 1, 1, 0, 1, 0], [1, 1, 1, 1, 1, 1, 1]]
+    for row in schedule:
+        ts, ys = [], []
+        for i, (w, on) in enumerate(zip(ws, row)):
+            k = counts[i]
+            ts.append(w.t_obs[k] if on else 0.0)
+            ys.append(w.y_obs[k] if on else None)
+            if on:
+                alone[i].pf_assimilate(w.t_obs[k], w.y_obs[k])
+                counts[i] += 1
+        assert batch.pf_batch_assimilate(ts, ys) == [pf.PF_OK] * len(ws)
+    for a, m in zip(alone, members):
+        assert _same(a, m)
+    # the active set changed three times (rows 1, 3, 4 differ from their predecessor)
+    assert batch.pf_batch_stats()["graph_captures"] == 4
+
+
+def test_failure_is_isolated(pf):
+    ws = _mix(T=3)
+    alone = [pf.Filter.from_workload(w) for w in ws]
+    members = [pf.Filter.from_workload(w) for w in ws]
+    batch = pf.Batch(members)
+    bad = 2
+    st = members[bad].pf_get_ensemble()
+    st["x"][:] = np.nan
+    members[bad].pf_set_ensemble(**st)
+    before = members[bad].pf_get_ensemble()
+    ts = [w.t_obs[0] for w in ws]
+    ys = [w.y_obs[0] for w in ws]
+    ys[4] = np.full_like(ws[4].y_obs[0], np.nan)        # invalid observation
+    status = batch.pf_batch_assimilate(ts, ys)
+    for i, (a, w) in enumerate(zip(alone, ws)):
+        if i == bad:
+            assert status[i] == pf.PF_ERR_DEGENERATE
+        elif i == 4:
+            assert status[i] == pf.PF_ERR_INVALID_ARG
+        else:
+            assert status[i] == pf.PF_OK
+            a.pf_assimilate(w.t_obs[0], w.y_obs[0])
+            assert _same(a, members[i])
+    after = members[bad].pf_get_ensemble()
+    assert np.array_equal(after["phi"], before["phi"]) and np.all(np.isnan(after["x"]))
+    assert members[bad].pf_get_history()["epoch"] == 0
+    # the failed filters recover and keep advancing with the batch
+    good = pf.Filter.from_workload(ws[bad])
+    members[bad].pf_set_ensemble(**good.pf_get_ensemble())
+    status = batch.pf_batch_assimilate([w.t_obs[0] if i in (bad, 4) else w.t_obs[1]
+                                        for i, w in enumerate(ws)],
+                                       [w.y_obs[0] if i in (bad, 4) else w.y_obs[1]
+                                        for i, w in enumerate(ws)])
+    assert status == [pf.PF_OK] * len(ws)
+
+
+def test_batch_membership_rules(pf):
+    ws = _mix(T=2)[:2]
+    fs = [pf.Filter.from_workload(w) for w in ws]
+    b1 = pf.Batch(fs)
+    with pytest.raises(pf.PfError):
+        pf.Batch(fs)                      # already in a batch
+    b1.close()
+    b2 = pf.Batch(fs)                     # free again after the first batch is gone
+    b2.close()
+    with pytest.raises(pf.PfError):
+        pf.Batch([fs[0], fs[0]])
