@@ -225,7 +225,8 @@ int pf_substep_table(int lmm, int spacing, double dt, int substeps, double q0, d
  * one epoch each with a handful of tile-scheduled launches -- one per phase
  * of Algorithm 1's epoch, split by model where the kernels differ -- captured
  * in a CUDA graph that is reused while the set of active filters stays the
- * same.  Each filter's results are bit-identical to running it alone: its
+ * same.  On its first epoch the batch autotunes the launch shape (tile order,
+ * concurrent per-model branches) by timing the candidates on that epoch.  Each filter's results are bit-identical to running it alone: its
  * reduction trees depend only on its own N.  The batch drives the filters'
  * own device buffers; while a filter is in a batch, advance it only through
  * the batch.  A filter belongs to at most one batch at a time. */
@@ -237,6 +238,10 @@ typedef struct {
   double last_device_ms;  /* device time of the last batched epoch         */
   int last_active;        /* filters advanced by the last batched epoch    */
   int last_tiles;         /* thread blocks (tiles) of its launches         */
+  int tile_order;         /* autotuned: 0 larger filters first, 1 interleaved */
+  int concurrent_models;  /* autotuned: per-model launches as graph branches */
+  double tune_ms[4];      /* autotuning times of the candidate shapes
+                             (order, concurrent) = (0,0), (0,1), (1,0), (1,1) */
 } pf_batch_stats_t;
 
 /* Bind n existing filters (distinct, not in another batch) into a batch that

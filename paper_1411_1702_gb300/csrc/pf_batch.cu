@@ -8,7 +8,12 @@
 //  2. rebuilds the tile tables (filter, virtual block) when the set of active
 //     filters changes, ordering each phase's tiles largest filter first;
 //  3. launches the captured graph of the phases (recaptured only when the
-//     active set or the step-table size changes);
+//     active set or the step-table size changes);  on its first epoch the
+//     batch autotunes the launch shape -- the tile order within a phase and
+//     whether the per-model launches of a phase run back to back or as
+//     concurrent graph branches -- by timing each candidate on the real
+//     epoch's phases up to stage 2 (none of which touches the committed
+//     state), then keeps the fastest;
 //  4. gathers every filter's status and epoch count with one kernel and one
 //     read-back, and commits the host-side history of the filters that
 //     succeeded.
@@ -54,6 +59,13 @@ struct Range {
   int off = 0, cnt = 0;
 };
 
+// launch shape chosen by the autotuner
+struct Shape {
+  int order;       // 0: larger filters first; 1: filters interleaved block by block
+  int concurrent;  // per-model launches of a phase as parallel graph branches
+};
+const Shape kShapes[] = {{0, 0}, {0, 1}, {1, 0}, {1, 1}};
+
 }  // namespace
 
 struct pf_batch {
@@ -61,6 +73,11 @@ struct pf_batch {
   std::vector<pf_filter*> filters;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t side = nullptr;          // second branch of the captured graph
+  cudaEvent_t fork = nullptr, join = nullptr;
+  Shape shape{0, 0};
+  bool tuned = false;
+  double tune_ms[4] = {0, 0, 0, 0};
   FilterDev* fds_dev = nullptr;
   EpochParams** eps_dev = nullptr;
   EpochParams* params_dev = nullptr;
@@ -100,9 +117,9 @@ static pf_status bfail(pf_batch* b, pf_status st, const std::string& msg) {
   } while (0)
 
 // Tile tables of one active set: per phase (and per model for the stages and
-// the moments), the filters' virtual blocks, larger filters first so that the
-// longest tails start early.
-static void build_tiles(pf_batch* b, const std::vector<char>& active) {
+// the moments), the filters' virtual blocks, either larger filters first (the
+// longest tails start early) or interleaved block by block across filters.
+static void build_tiles(pf_batch* b, const std::vector<char>& active, int order_kind) {
   std::vector<int> order;
   for (int f = 0; f < b->n; ++f)
     if (active[f]) order.push_back(f);
@@ -112,11 +129,22 @@ static void build_tiles(pf_batch* b, const std::vector<char>& active) {
   auto add = [&](int phase, int model) {
     Range r;
     r.off = (int)b->tiles_host.size();
-    for (int f : order) {
-      const pf_filter* F = b->filters[f];
-      if (model >= 0 && model_index(F->ode) != model) continue;
-      const int nb = phase_blocks(phase, F->ode, F->N);
-      for (int v = 0; v < nb; ++v) b->tiles_host.push_back(BatchTile{f, v});
+    if (order_kind == 0) {
+      for (int f : order) {
+        const pf_filter* F = b->filters[f];
+        if (model >= 0 && model_index(F->ode) != model) continue;
+        const int nb = phase_blocks(phase, F->ode, F->N);
+        for (int v = 0; v < nb; ++v) b->tiles_host.push_back(BatchTile{f, v});
+      }
+    } else {
+      int most = 0;
+      for (int f : order) most = std::max(most, phase_blocks(phase, b->filters[f]->ode, b->filters[f]->N));
+      for (int v = 0; v < most; ++v)
+        for (int f : order) {
+          const pf_filter* F = b->filters[f];
+          if (model >= 0 && model_index(F->ode) != model) continue;
+          if (v < phase_blocks(phase, F->ode, F->N)) b->tiles_host.push_back(BatchTile{f, v});
+        }
     }
     r.cnt = (int)b->tiles_host.size() - r.off;
     return r;
@@ -129,23 +157,92 @@ static void build_tiles(pf_batch* b, const std::vector<char>& active) {
   for (int m = 0; m < kModels; ++m) b->moments[m] = add(kPhaseMoments, m);
 }
 
-static cudaError_t launch_phases(pf_batch* b, size_t smem) {
+// Enqueue the phases on b->stream (inside a capture).  With a concurrent
+// shape, each per-model group of a phase forks onto two branches (the model
+// with the most tiles on the main branch) and joins before the next phase.
+static cudaError_t launch_phases(pf_batch* b, size_t smem, const Shape& shape, bool with_moments) {
   const FilterDev* fds = b->fds_dev;
   const EpochParams* const* eps = b->eps_dev;
   const BatchTile* T = b->tiles_dev;
-  cudaStream_t st = b->stream;
   cudaError_t e = cudaSuccess;
-  auto run = [&](int phase, int ode, const Range& r) {
+  auto run = [&](int phase, int ode, const Range& r, cudaStream_t st) {
     if (e == cudaSuccess && r.cnt > 0)
       e = launch_batch_phase(phase, ode, fds, eps, T + r.off, r.cnt, smem, 0, st);
   };
-  for (int m = 0; m < kModels; ++m) run(kPhaseStage1, m + 1, b->stage[0][m]);
-  run(kPhaseScanTile, 0, b->scan_tile);
-  run(kPhaseScanAdd, 0, b->scan_add);
-  run(kPhaseResample, 0, b->resample);
-  for (int m = 0; m < kModels; ++m) run(kPhaseStage2, m + 1, b->stage[1][m]);
-  for (int m = 0; m < kModels; ++m) run(kPhaseMoments, m + 1, b->moments[m]);
+  auto per_model = [&](int phase, const Range* rs) {
+    int used = 0, big = -1;
+    for (int m = 0; m < kModels; ++m)
+      if (rs[m].cnt > 0) {
+        ++used;
+        if (big < 0 || rs[m].cnt > rs[big].cnt) big = m;
+      }
+    if (!shape.concurrent || used < 2) {
+      for (int m = 0; m < kModels; ++m) run(phase, m + 1, rs[m], b->stream);
+      return;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
+    run(phase, big + 1, rs[big], b->stream);
+    for (int m = 0; m < kModels; ++m)
+      if (m != big) run(phase, m + 1, rs[m], b->side);
+    if (e == cudaSuccess) e = cudaEventRecord(b->join, b->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join, 0);
+  };
+  per_model(kPhaseStage1, b->stage[0]);
+  run(kPhaseScanTile, 0, b->scan_tile, b->stream);
+  run(kPhaseScanAdd, 0, b->scan_add, b->stream);
+  run(kPhaseResample, 0, b->resample, b->stream);
+  per_model(kPhaseStage2, b->stage[1]);
+  if (with_moments) per_model(kPhaseMoments, b->moments);
   return e;
+}
+
+static cudaError_t capture(pf_batch* b, size_t smem, const Shape& shape, bool with_moments,
+                           cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t le = launch_phases(b, smem, shape, with_moments);
+  e = cudaStreamEndCapture(b->stream, &g);
+  if (le != cudaSuccess) e = le;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  return e;
+}
+
+// Time each launch shape on the pending epoch's phases up to stage 2 (they
+// leave the committed state untouched and are idempotent), keep the fastest.
+static cudaError_t autotune(pf_batch* b, const std::vector<char>& active, size_t smem) {
+  double best = 1e300;
+  int best_i = 0;
+  for (int i = 0; i < 4; ++i) {
+    build_tiles(b, active, kShapes[i].order);
+    cudaError_t e = cudaMemcpyAsync(b->tiles_dev, b->tiles_host.data(),
+                                    sizeof(BatchTile) * b->tiles_host.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+    cudaGraphExec_t gx = nullptr;
+    if (e == cudaSuccess) e = capture(b, smem, kShapes[i], false, &gx);
+    double t = 1e300;
+    for (int rep = 0; e == cudaSuccess && rep < 2; ++rep) {
+      e = cudaEventRecord(b->ev0, b->stream);
+      if (e == cudaSuccess) e = cudaGraphLaunch(gx, b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b->ev1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+      if (e == cudaSuccess) t = std::min(t, (double)ms);
+    }
+    if (gx) cudaGraphExecDestroy(gx);
+    if (e != cudaSuccess) return e;
+    b->tune_ms[i] = t;
+    if (t < best) {
+      best = t;
+      best_i = i;
+    }
+  }
+  b->shape = kShapes[best_i];
+  b->tuned = true;
+  return cudaSuccess;
 }
 
 extern "C" {
@@ -178,6 +275,10 @@ pf_status pf_batch_create(pf_filter* const* filters, int n, void* stream, pf_bat
     if (e != cudaSuccess) return bail(bfail(b, PF_ERR_CUDA, "stream creation failed"));
     b->own_stream = true;
   }
+  e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(bfail(b, PF_ERR_CUDA, "stream/event creation failed"));
   // the filters' own streams must be idle before the batch drives them
   for (pf_filter* f : b->filters) {
     e = cudaStreamSynchronize(f->stream);
@@ -231,6 +332,9 @@ void pf_batch_destroy(pf_batch* b) {
   if (b->status_host) cudaFreeHost(b->status_host);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  if (b->side) cudaStreamDestroy(b->side);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -269,28 +373,19 @@ pf_status pf_batch_assimilate(pf_batch* b, const double* t, const double* const*
   const size_t smem = sizeof(StepCoef) * (size_t)S_max;
   const bool same = b->graph && b->graph_active == active && b->graph_smem == smem;
   if (!same) {
-    build_tiles(b, active);
-    PF_BCUDA(b, cudaMemcpyAsync(b->tiles_dev, b->tiles_host.data(),
-                                sizeof(BatchTile) * b->tiles_host.size(), cudaMemcpyHostToDevice,
-                                b->stream));
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
     }
-    cudaGraph_t g = nullptr;
-    PF_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t le = launch_phases(b, smem);
-    cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
-    if (le != cudaSuccess || ce != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      return bfail(b, PF_ERR_CUDA, std::string("graph capture failed: ") +
-                                       cudaGetErrorString(le != cudaSuccess ? le : ce));
-    }
-    cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (ie != cudaSuccess) {
+    if (!b->tuned) PF_BCUDA(b, autotune(b, active, smem));
+    build_tiles(b, active, b->shape.order);
+    PF_BCUDA(b, cudaMemcpyAsync(b->tiles_dev, b->tiles_host.data(),
+                                sizeof(BatchTile) * b->tiles_host.size(), cudaMemcpyHostToDevice,
+                                b->stream));
+    cudaError_t ce = capture(b, smem, b->shape, true, &b->graph);
+    if (ce != cudaSuccess) {
       b->graph = nullptr;
-      return bfail(b, PF_ERR_CUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(ie));
+      return bfail(b, PF_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(ce));
     }
     b->graph_active = active;
     b->graph_smem = smem;
@@ -343,6 +438,9 @@ pf_status pf_batch_stats(const pf_batch* b, pf_batch_stats_t* out) {
   out->last_device_ms = b->last_ms;
   out->last_active = b->last_active;
   out->last_tiles = b->last_tiles;
+  out->tile_order = b->shape.order;
+  out->concurrent_models = b->shape.concurrent;
+  for (int i = 0; i < 4; ++i) out->tune_ms[i] = b->tune_ms[i];
   return PF_OK;
 }
 

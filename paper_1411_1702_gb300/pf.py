@@ -67,7 +67,8 @@ class Stats(C.Structure):
 
 class BatchStats(C.Structure):
     _fields_ = [("epochs", C.c_int64), ("graph_captures", C.c_int64),
-                ("last_device_ms", C.c_double), ("last_active", C.c_int), ("last_tiles", C.c_int)]
+                ("last_device_ms", C.c_double), ("last_active", C.c_int), ("last_tiles", C.c_int),
+                ("tile_order", C.c_int), ("concurrent_models", C.c_int), ("tune_ms", C.c_double * 4)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -325,4 +326,5 @@ class Batch:
         _check(load().pf_batch_stats(self._h, C.byref(s)), None)
         return dict(epochs=s.epochs, graph_captures=s.graph_captures,
                     last_device_ms=s.last_device_ms, last_active=s.last_active,
-                    last_tiles=s.last_tiles)
+                    last_tiles=s.last_tiles, tile_order=s.tile_order,
+                    concurrent_models=s.concurrent_models, tune_ms=list(s.tune_ms))

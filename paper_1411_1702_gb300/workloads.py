@@ -116,8 +116,8 @@ def linear2_exact(theta, x0, t):
     return np.stack([x1, x2], axis=-1)
 
 
-def linear2(N: int = 2000, T: int = 50, seed: int = 0) -> Workload:
-    theta = np.array([1.0, 1000.0])
+def linear2(N: int = 2000, T: int = 50, seed: int = 0, theta=None) -> Workload:
+    theta = np.array([1.0, 1000.0]) if theta is None else np.asarray(theta, dtype=float)
     x0 = np.array([1.0, 1.0])
     t_obs = 0.1 * np.arange(1, T + 1)
     x_true = linear2_exact(theta, x0, t_obs)
@@ -154,14 +154,16 @@ def robertson_times(T: int = 40):
     return 10.0 ** (-4.0 + 8.0 * (k - 1) / 39.0)
 
 
-def robertson(N: int = 131072, T: int = 40, seed: int = 0) -> Workload:
+def robertson(N: int = 131072, T: int = 40, seed: int = 0, theta=None,
+              rtol: float = 1e-11) -> Workload:
     from scipy.integrate import solve_ivp
-    theta = np.array([0.04, 3e7, 1e4])
+    theta_star = np.array([0.04, 3e7, 1e4])
+    theta = theta_star if theta is None else np.asarray(theta, dtype=float)
     x0 = np.array([1.0, 0.0, 0.0])
     t_all = robertson_times(40)
     f, jac = robertson_rhs(theta)
-    sol = solve_ivp(f, (0.0, t_all[-1]), x0, method="Radau", t_eval=t_all, rtol=1e-11,
-                    atol=1e-18, jac=jac)
+    sol = solve_ivp(f, (0.0, t_all[-1]), x0, method="Radau", t_eval=t_all, rtol=rtol,
+                    atol=1e-18 if rtol < 1e-9 else 1e-14, jac=jac)
     x_true = sol.y.T[:T]
     t_obs = t_all[:T]
     obs_idx, sigma = [0, 2], [0.01, 0.01]
@@ -174,8 +176,9 @@ def robertson(N: int = 131072, T: int = 40, seed: int = 0) -> Workload:
         spacing=SPACING_GEOMETRIC, dt=0.0, substeps=S, q0=q0,
         history=HIST_CARRY, transform=TRANSFORM_LOG, obs_idx=obs_idx,
         noise=NOISE_RELATIVE, sigma=sigma, a=0.98, kappa=1.0, seed=seed, stream=0,
-        prior_kind=[LOGUNIFORM] * 3, prior_lo=list(theta / 10.0), prior_hi=list(theta * 10.0),
-        x0=x0, t0=0.0, theta_true=theta, t_obs=t_obs, y_obs=y, x_true=x_true)
+        prior_kind=[LOGUNIFORM] * 3, prior_lo=list(theta_star / 10.0),
+        prior_hi=list(theta_star * 10.0), x0=x0, t0=0.0, theta_true=theta, t_obs=t_obs, y_obs=y,
+        x_true=x_true)
 
 
 # ------------------------------------------------------------ brusselator
@@ -244,6 +247,29 @@ def brusselator(N: int = 65536, T: int = 30, seed: int = 0) -> Workload:
         noise=NOISE_ADDITIVE, sigma=sigma, a=0.98, kappa=1.0, seed=seed, stream=0,
         prior_kind=[UNIFORM] * 3, prior_lo=list(0.5 * theta), prior_hi=list(1.5 * theta),
         x0=x0, t0=0.0, theta_true=theta, t_obs=t_obs, y_obs=y, x_true=x_true)
+
+
+def batched(n_filters: int = 256, seed: int = 0, n_min_log2: float = 10.0,
+            n_max_log2: float = 17.0):
+    """Independent filters of uneven size and mixed problems: N_f =
+    round(2^U[10, 17]), problem linear2 or robertson with probability 1/2
+    each, the true parameter drawn from that problem's prior, seed and filter
+    id f.  Robertson reference trajectories are solved at rtol 1e-8 (ample for
+    1 % observation noise)."""
+    rng = np.random.default_rng([seed, 0xBA7C])
+    out = []
+    for f in range(n_filters):
+        N = int(round(2.0 ** rng.uniform(n_min_log2, n_max_log2)))
+        if rng.random() < 0.5:
+            lo, hi = np.array([0.1, 100.0]), np.array([10.0, 1e4])
+            th = np.exp(rng.uniform(np.log(lo), np.log(hi)))
+            w = linear2(N=N, seed=f, theta=th)
+        else:
+            star = np.array([0.04, 3e7, 1e4])
+            th = np.exp(rng.uniform(np.log(star / 10.0), np.log(star * 10.0)))
+            w = robertson(N=N, seed=f, theta=th, rtol=1e-8)
+        out.append(w.with_(stream=f))
+    return out
 
 
 BY_NAME = {"linear2": linear2, "robertson": robertson, "brusselator": brusselator}

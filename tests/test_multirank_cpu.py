@@ -1,0 +1,43 @@
+"""The multi-rank (replica) path of bench.py on CPU: two gloo ranks reduce
+their timings the way the GPU ranks do -- the slowest rank's time and the sum
+of all ranks' particle-steps."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t, s = bench.reduce_times(dist, total_ms=10.0 + 5.0 * rank, steps_done=1000 * (rank + 1))
+    out[rank] = (t, s)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_max_time_and_sum_steps():
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_worker, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
+    for r in range(world):
+        assert out[r] == (15.0, 3000.0)
+
+
+def test_single_process_reduction_is_identity():
+    import bench
+    assert bench.reduce_times(None, 12.5, 77) == (12.5, 77)
