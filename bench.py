@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -453,6 +454,130 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Serving pattern: a trace of filter sessions arriving as a Poisson
+    process, each with observations arriving at exponential intervals, served
+    in real time three ways: the server (memory-budget admission, continuous
+    batching over lanes), the server with a single lane, and serial
+    per-filter calls (each observation assimilated with pf_assimilate, in
+    arrival order, the filter created when its session opens).  Latency is
+    arrival -> device completion of the assimilation."""
+    import torch
+    from paper_1411_1702_gb300 import workloads as W
+    trace = W.serving(n_sessions=args.serve_sessions, obs_per_session=args.serve_obs)
+    torch.cuda.set_device(0)
+    from paper_1411_1702_gb300 import build as B
+    B.build()
+    from paper_1411_1702_gb300 import pf
+    events = []
+    for s, ss in enumerate(trace):
+        events.append((ss.open_s, 0, s, -1))
+        for k, ta in enumerate(ss.obs_s):
+            events.append((float(ta), 1, s, k))
+    events.sort()
+    n_obs = sum(len(ss.obs_s) for ss in trace)
+    total_steps = sum(ss.w.particle_steps(k) for ss in trace for k in range(len(ss.obs_s)))
+
+    def wait_until(t_start, te):
+        while True:
+            dt = te - (time.perf_counter() - t_start)
+            if dt <= 0:
+                return
+            if dt > 2e-3:
+                time.sleep(dt - 1e-3)
+
+    def serve(lanes):
+        srv = pf.Server(budget_bytes=int(args.serve_budget_gb * (1 << 30)), lanes=lanes)
+        sid = {}
+        lags = []
+        t_start = time.perf_counter()
+        i = 0
+        while i < len(events):
+            now = time.perf_counter() - t_start
+            while i < len(events) and events[i][0] <= now:
+                te, kind, s, k = events[i]
+                ss = trace[s]
+                if kind == 0:
+                    sid[s] = srv.pf_server_open(ss.w, filter_id=s)
+                else:
+                    srv.pf_server_submit(sid[s], ss.w.t_obs[k], ss.w.y_obs[k])
+                    lags.append(time.perf_counter() - t_start - te)
+                    if k == len(ss.obs_s) - 1:
+                        srv.pf_server_close(sid[s])
+                i += 1
+            srv.pf_server_step()
+        srv.pf_server_drain()
+        st = srv.pf_server_stats()
+        srv.close()
+        assert st["assimilations"] == n_obs, st
+        st["submit_lag_p99_ms"] = 1e3 * sorted(lags)[int(0.99 * (len(lags) - 1))]
+        return st
+
+    def serial():
+        fil = {}
+        lat = []
+        t_start = time.perf_counter()
+        first = last = None
+        for te, kind, s, k in events:
+            wait_until(t_start, te)
+            ss = trace[s]
+            if kind == 0:
+                fil[s] = pf.Filter.from_workload(ss.w, filter_id=s)
+                continue
+            fil[s].pf_assimilate(ss.w.t_obs[k], ss.w.y_obs[k])
+            done = time.perf_counter() - t_start
+            lat.append(1e3 * (done - te))
+            first = te if first is None else first
+            last = done
+            if k == len(ss.obs_s) - 1:
+                fil[s].close()
+        lat.sort()
+        pct = lambda q: lat[min(len(lat) - 1, max(0, int(math.ceil(q * len(lat))) - 1))]
+        return {"particle_steps_per_s": total_steps / (last - first), "p50_ms": pct(0.5),
+                "p99_ms": pct(0.99), "mean_ms": sum(lat) / len(lat), "max_ms": lat[-1]}
+
+    # warm-up: a short trace through both paths (kernels loaded, pools primed)
+    warm = W.serving(n_sessions=6, obs_per_session=3, seed=99)
+    srv = pf.Server(budget_bytes=8 << 30)
+    for s, ss in enumerate(warm):
+        sid = srv.pf_server_open(ss.w, filter_id=s)
+        for k in range(3):
+            srv.pf_server_submit(sid, ss.w.t_obs[k], ss.w.y_obs[k])
+    srv.pf_server_drain()
+    srv.close()
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clocks:
+        ours = serve(0)
+    one_lane = serve(1)
+    base = serial()
+    line = {
+        "metric": METRIC, "mode": "serving", "value": ours["particle_steps_per_s"], "unit": UNIT,
+        "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"serving: {len(trace)} sessions, Poisson {200.0:g}/s, "
+                               f"N = 2^U{{12..18}}, linear2/robertson/brusselator 1/3 each, "
+                               f"{args.serve_obs} observations per session at Exp(5 ms) gaps, "
+                               f"{args.serve_budget_gb:g} GB budget",
+                   "sessions": len(trace), "observations": n_obs,
+                   "particles": sum(ss.w.N for ss in trace),
+                   "brusselator_sessions": sum(ss.w.ode == W.BRUSSELATOR for ss in trace)},
+        "clocks": clocks.summary(),
+        "server": {k: ours[k] for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "epochs",
+                                        "mean_sessions_per_epoch", "admitted", "rejected",
+                                        "submit_lag_p99_ms", "step_calls", "step_ms_mean",
+                                        "step_ms_max", "collect_ms_max", "admit_ms_max",
+                                        "launch_ms_max")},
+        "server_one_lane": {k: one_lane[k] for k in ("particle_steps_per_s", "p50_ms", "p99_ms",
+                                                     "mean_ms", "max_ms", "epochs",
+                                                     "mean_sessions_per_epoch")},
+        "serial_per_filter": base,
+        "throughput_vs_serial": ours["particle_steps_per_s"] / base["particle_steps_per_s"],
+        "p99_vs_serial": ours["p99_ms"] / base["p99_ms"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -460,8 +585,11 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="robertson",
-                    choices=["robertson", "linear2", "brusselator", "batched"])
+                    choices=["robertson", "linear2", "brusselator", "batched", "serving"])
     ap.add_argument("--batch-filters", type=int, default=256)
+    ap.add_argument("--serve-sessions", type=int, default=64)
+    ap.add_argument("--serve-obs", type=int, default=10)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--e2e-steps", type=int, default=80)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-particles", type=int, default=16384)
@@ -474,6 +602,8 @@ def main(argv=None):
     from paper_1411_1702_gb300 import workloads as W
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     w = W.get(args.workload)
     if args.impl == "reference":
         return run_reference(args, w)

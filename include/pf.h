@@ -161,7 +161,8 @@ pf_status pf_kernel_times(pf_filter* f, double* ms, int64_t* launches, int n);
  * The pointer stays valid until the next call on the same filter/thread. */
 const char* pf_last_error(const pf_filter* f);
 
-/* Free the filter's device and host memory.  NULL is a no-op. */
+/* Free the filter's device and host memory.  NULL is a no-op.  A filter that
+ * is a member of a batch is destroyed only after its batch (pf_batch_destroy). */
 void pf_destroy(pf_filter* f);
 
 /* ---- device-resident observation series ---------------------------------
@@ -261,6 +262,72 @@ pf_status pf_batch_stats(const pf_batch* b, pf_batch_stats_t* out);
 const char* pf_batch_last_error(const pf_batch* b);
 /* Release the batch (the filters stay valid and leave the batch). */
 void pf_batch_destroy(pf_batch* b);
+
+/* ---- serving: sessions admitted by memory budget, continuous batching -----
+ * No counterpart in the paper, which runs one filter: the per-observation
+ * epoch of Algorithm 1 is the unit of work, and observations arrive one at a
+ * time (Section 2), so independent filters can be served as they arrive.
+ * A server keeps filter sessions resident on the device and assimilates their
+ * observations as they arrive.  Sessions are admitted in arrival order while
+ * their device memory fits the budget, otherwise they wait until closed
+ * sessions free memory; session memory comes from a stream-ordered pool owned
+ * by the server, so admission and closing never synchronise the device.
+ * Sessions are spread over `lanes` by model and size class (<= 32768 particles
+ * or more); each lane is a batch with its own stream and at most one epoch in
+ * flight, and lanes overlap on the device.  Observations queue per session
+ * with their arrival time.  pf_server_step never waits: it collects the lanes
+ * whose epoch has finished, admits waiting sessions, and launches on every
+ * idle lane one batched epoch over its sessions that have a queued
+ * observation (the oldest one of each), so requests that arrive while the
+ * device works join the next launch of their lane.  The latency of an
+ * assimilation runs from pf_server_submit to the moment the device finishes
+ * its epoch (taken on the host by a stream callback).  Session results are
+ * bit-identical to the same filter run alone.  One host thread drives a
+ * server. */
+typedef struct pf_server pf_server;
+
+typedef struct {
+  int64_t admitted, rejected, waiting, active_sessions, queued_observations;
+  int64_t assimilations;        /* completed (latency samples)              */
+  int64_t epochs;               /* batched epochs launched                  */
+  double mean_sessions_per_epoch;
+  double p50_ms, p99_ms, mean_ms, max_ms;  /* per-assimilation latency    */
+  double particle_steps_per_s;  /* from the first submit to the last result */
+  int64_t device_bytes_in_use, budget_bytes;
+  int64_t step_calls;           /* pf_server_step calls                     */
+  double step_ms_mean, step_ms_max;  /* host time inside pf_server_step     */
+  double collect_ms_max, admit_ms_max, launch_ms_max;  /* its longest parts  */
+} pf_server_stats_t;
+
+/* budget_bytes: device memory the sessions may occupy (their filters' single
+ * allocations); lanes: 1..64, or 0 for one lane per model and size class (6).
+ * Errors: INVALID_ARG, OOM, CUDA. */
+pf_status pf_server_create(int64_t budget_bytes, int lanes, pf_server** out);
+/* Queue a session (arguments as pf_create; the options' stream and timing are
+ * ignored).  It is admitted by a later pf_server_step when its memory fits.
+ * Errors: INVALID_ARG, BUDGET (it can never fit the budget). */
+pf_status pf_server_open(pf_server* s, pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
+                         const pf_prior* prior, const pf_options* opt, int64_t* session);
+/* Queue observation y_k (m doubles, copied) at time t_k for a session. */
+pf_status pf_server_submit(pf_server* s, int64_t session, double t_k, const double* y_k);
+/* Collect, admit, launch (see above; never waits); *launched = sessions in
+ * the epochs it launched. */
+pf_status pf_server_step(pf_server* s, int* launched);
+/* Step (waiting for the device between steps) until every admitted session's
+ * queue is empty and nothing is in flight. */
+pf_status pf_server_drain(pf_server* s);
+/* Close a session: it leaves once its queue is done; its memory returns to
+ * the budget. */
+pf_status pf_server_close(pf_server* s, int64_t session);
+/* A session's filter (borrowed; NULL while waiting for admission; for the
+ * read-only calls pf_estimates/pf_get_ensemble/pf_get_history, made while the
+ * session has nothing in flight, e.g. after pf_server_drain), its
+ * assimilation count and last status. */
+pf_status pf_server_session(const pf_server* s, int64_t session, pf_filter** filter,
+                            int64_t* assimilated, int* last_status);
+pf_status pf_server_stats(const pf_server* s, pf_server_stats_t* out);
+const char* pf_server_last_error(const pf_server* s);
+void pf_server_destroy(pf_server* s);
 
 /* ---- systematic resampling without allocation ----------------------------
  * No counterpart in the paper: a library convenience for callers that cannot

@@ -340,4 +340,15 @@ cudaError_t launch_batch_bruss_stage(int stage, const FilterDev* fds, const Epoc
 
 size_t bruss_work_doubles(int64_t N) { return (size_t)kBrWorkRows * (size_t)N; }
 
+cudaError_t preload_bruss_kernels() {
+  const void* ks[] = {(const void*)k_bstage<1>, (const void*)k_bstage<2>,
+                      (const void*)k_batch_bstage<1>, (const void*)k_batch_bstage<2>};
+  for (const void* k : ks) {
+    cudaFuncAttributes a;
+    const cudaError_t e = cudaFuncGetAttributes(&a, k);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace pfg

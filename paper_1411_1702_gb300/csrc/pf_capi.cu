@@ -2,6 +2,7 @@
 // the host side of each epoch (substep table, parameter upload, launch,
 // commit check) and the checkpoint/inspection calls.  All of the method's
 // arithmetic on particles runs in the kernels of pf_kernels.cu.
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -114,6 +115,18 @@ static size_t layout(pf_filter* f, char* base) {
   return off;
 }
 
+namespace pfg {
+size_t filter_device_bytes(int ode, int d, int p, int64_t N) {
+  pf_filter probe;
+  probe.ode = ode;
+  probe.d = d;
+  probe.p = p;
+  probe.N = N;
+  probe.fd.nrec = moment_record_size(ode);
+  return layout(&probe, nullptr);
+}
+}  // namespace pfg
+
 static double prior_center_phi(const pf_filter* f, int i) {
   const double lo = f->prior_lo[i], hi = f->prior_hi[i];
   if (f->prior_kind[i] == PF_PRIOR_LOGUNIFORM) {
@@ -139,8 +152,29 @@ static pf_status read_ctrl(pf_filter* f) {
   return PF_OK;
 }
 
+namespace pfg {
+
+cudaError_t preload_kernels() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0 || dev >= 64 || done[dev]) return cudaSuccess;
+  e = preload_main_kernels();
+  if (e == cudaSuccess) e = preload_bruss_kernels();
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
+}  // namespace pfg
+
 // Step 1 into the existing buffers.
-static pf_status do_init(pf_filter* f) {
+// check: wait for the initial moments and verify them.  Without it (pooled
+// filters) nothing waits; a non-finite start shows up as the sticky status of
+// the filter's first epoch.
+static pf_status do_init(pf_filter* f, bool check = true) {
   Ctrl* h = f->ctrl_host;
   std::memset(h, 0, sizeof(Ctrl));
   h->cur = 0;
@@ -150,11 +184,12 @@ static pf_status do_init(pf_filter* f) {
   PF_CUDA(f, cudaMemcpyAsync(f->fd.ctrl, h, sizeof(Ctrl), cudaMemcpyHostToDevice, f->stream));
   PF_CUDA(f, cudaMemsetAsync(f->fd.ticket, 0, sizeof(unsigned) * 8, f->stream));
   PF_CUDA(f, launch_init(f->ode, f->fd, f->stream));
+  f->hist = HistoryState{0, 0, f->t0, 0.0, 0.0};
+  if (!check) return PF_OK;
   pf_status st = read_ctrl(f);
   if (st != PF_OK) return st;
   if (f->ctrl_host->status != PF_OK)
     return fail(f, (pf_status)f->ctrl_host->status, "initial moments are not finite");
-  f->hist = HistoryState{0, 0, f->t0, 0.0, 0.0};
   return PF_OK;
 }
 
@@ -212,14 +247,10 @@ static const char* status_text(int st) {
   return "epoch failed";
 }
 
-extern "C" {
-
-const char* pf_version(void) { return "paper_1411_1702_gb300 0.1 (sm_103a, FP64)"; }
-
-pf_status pf_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
-                    const pf_prior* prior, const pf_options* opt, pf_filter** out) {
-  if (!out) return fail(nullptr, PF_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
+namespace pfg {
+// Argument checks of pf_create (no allocation, no CUDA call).
+pf_status check_create_args(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
+                            const pf_prior* prior, const pf_options* opt) {
   int dd, pp;
   if (!ode_dims(ode, &dd, &pp)) return fail(nullptr, PF_ERR_INVALID_ARG, "unknown ODE");
   if (!ode_supported(ode)) return fail(nullptr, PF_ERR_INVALID_ARG, "ODE not available in this build");
@@ -268,7 +299,37 @@ pf_status pf_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
     return fail(nullptr, PF_ERR_INVALID_ARG, "unknown noise model");
   if (!(opt->kappa >= 0.0) || !std::isfinite(opt->kappa))
     return fail(nullptr, PF_ERR_INVALID_ARG, "kappa must be >= 0");
+  return PF_OK;
+}
+}  // namespace pfg
 
+extern "C" {
+
+const char* pf_version(void) { return "paper_1411_1702_gb300 0.1 (sm_103a, FP64)"; }
+
+pf_status pf_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
+                    const pf_prior* prior, const pf_options* opt, pf_filter** out) {
+  return filter_create(ode, d, p, N, lmm, dt, prior, opt, nullptr, out);
+}
+
+}  // extern "C"
+
+namespace pfg {
+
+pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
+                        const pf_prior* prior, const pf_options* opt, cudaMemPool_t pool,
+                        pf_filter** out) {
+  if (!out) return fail(nullptr, PF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  {
+    const pf_status cs = check_create_args(ode, d, p, N, lmm, dt, prior, opt);
+    if (cs != PF_OK) return cs;
+  }
+
+  {
+    const cudaError_t pe = preload_kernels();
+    if (pe != cudaSuccess) return cuda_fail(nullptr, pe, "loading the kernels");
+  }
   pf_filter* f = new (std::nothrow) pf_filter();
   if (!f) return fail(nullptr, PF_ERR_OOM, "host allocation failed");
   f->ode = ode; f->d = d; f->p = p; f->m = opt->m; f->lmm = lmm; f->K = opt->newton_iters;
@@ -301,25 +362,39 @@ pf_status pf_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
   if (opt->stream) {
     f->stream = (cudaStream_t)opt->stream;
   } else {
-    e = cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { st = cuda_fail(nullptr, e, "cudaStreamCreateWithFlags"); pf_destroy(f); return st; }
+    // a pooled filter's own stream only initialises it: at the greatest
+    // priority, so creation is not queued behind long kernels of other streams
+    int least = 0, greatest = 0;
+    if (pool) cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    e = cudaStreamCreateWithPriority(&f->stream, cudaStreamNonBlocking, pool ? greatest : 0);
+    if (e != cudaSuccess) { st = cuda_fail(nullptr, e, "cudaStreamCreateWithPriority"); pf_destroy(f); return st; }
     f->own_stream = true;
   }
   f->dbytes = layout(f, nullptr);
-  e = cudaMalloc(&f->dmem, f->dbytes);
+  f->pool = pool;
+  e = pool ? cudaMallocFromPoolAsync(&f->dmem, f->dbytes, pool, f->stream)
+           : cudaMalloc(&f->dmem, f->dbytes);
   if (e != cudaSuccess) {
+    cudaGetLastError();
     f->dmem = nullptr;
     g_thread_error = "device allocation of " + std::to_string(f->dbytes) + " bytes failed";
     pf_destroy(f);
     return PF_ERR_OOM;
   }
   layout(f, (char*)f->dmem);
-  e = cudaMallocHost(&f->ep_host, sizeof(EpochParams));
-  if (e == cudaSuccess) e = cudaMallocHost(&f->ctrl_host, sizeof(Ctrl));
+  if (pool) {
+    f->ep_host = new (std::nothrow) EpochParams();
+    f->ctrl_host = new (std::nothrow) Ctrl();
+    e = (f->ep_host && f->ctrl_host) ? cudaSuccess : cudaErrorMemoryAllocation;
+  } else {
+    e = cudaMallocHost(&f->ep_host, sizeof(EpochParams));
+    if (e == cudaSuccess) e = cudaMallocHost(&f->ctrl_host, sizeof(Ctrl));
+  }
   if (e == cudaSuccess) e = cudaEventCreate(&f->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&f->ev1);
+  if (e == cudaSuccess && pool) e = cudaEventCreateWithFlags(&f->ready, cudaEventDisableTiming);
   if (e != cudaSuccess) { st = cuda_fail(nullptr, e, "pinned buffers/events"); pf_destroy(f); return st; }
-  st = do_init(f);
+  st = do_init(f, pool == nullptr);
   if (st != PF_OK) {
     g_thread_error = f->err;
     pf_destroy(f);
@@ -329,16 +404,27 @@ pf_status pf_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
   return PF_OK;
 }
 
+}  // namespace pfg
+
+extern "C" {
+
 void pf_destroy(pf_filter* f) {
   if (!f) return;
   if (f->stream) cudaStreamSynchronize(f->stream);
   if (f->series_dev) cudaFree(f->series_dev);
-  if (f->dmem) cudaFree(f->dmem);
-  if (f->ep_host) cudaFreeHost(f->ep_host);
-  if (f->ctrl_host) cudaFreeHost(f->ctrl_host);
+  if (f->pool) {
+    if (f->dmem) cudaFreeAsync(f->dmem, f->stream);
+    delete f->ep_host;
+    delete f->ctrl_host;
+  } else {
+    if (f->dmem) cudaFree(f->dmem);
+    if (f->ep_host) cudaFreeHost(f->ep_host);
+    if (f->ctrl_host) cudaFreeHost(f->ctrl_host);
+  }
   free_marks(f);
   if (f->ev0) cudaEventDestroy(f->ev0);
   if (f->ev1) cudaEventDestroy(f->ev1);
+  if (f->ready) cudaEventDestroy(f->ready);
   if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
   delete f;
 }

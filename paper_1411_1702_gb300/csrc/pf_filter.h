@@ -34,13 +34,15 @@ struct pf_filter {
   // CUDA resources
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaMemPool_t pool = nullptr;           // dmem is stream-ordered from this pool
   void* dmem = nullptr;
   size_t dbytes = 0;
   pfg::FilterDev fd{};
   pfg::EpochParams* ep_dev = nullptr;    // online parameter slot
-  pfg::EpochParams* ep_host = nullptr;   // pinned staging
-  pfg::Ctrl* ctrl_host = nullptr;        // pinned
+  pfg::EpochParams* ep_host = nullptr;   // staging (pinned; pageable when pooled)
+  pfg::Ctrl* ctrl_host = nullptr;        // pinned; pageable when pooled
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ready = nullptr;            // pooled: the work queued on `stream` is done
   // committed history (host view)
   pfg::HistoryState hist{};
   // device-resident observation series
@@ -67,6 +69,18 @@ namespace pfg {
 // Parameter block of one epoch of f from history h (host); returns S or -1.
 int fill_epoch(const pf_filter* f, const HistoryState& h, double t_k, const double* y,
                EpochParams* ep, int* depth_out);
+// Argument checks of pf_create (no allocation, no CUDA call).
+pf_status check_create_args(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
+                            const pf_prior* prior, const pf_options* opt);
+// pf_create with the device allocation taken, stream-ordered, from `pool` and
+// pageable host staging, so that neither creation nor pf_destroy makes an
+// implicitly device-wide synchronising call (the server's sessions).  A NULL
+// pool is pf_create.
+pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
+                        const pf_prior* prior, const pf_options* opt, cudaMemPool_t pool,
+                        pf_filter** out);
+// Device bytes of a filter of this shape (its single allocation).
+size_t filter_device_bytes(int ode, int d, int p, int64_t N);
 // History after an epoch with parameter block ep.
 HistoryState advance_history(const HistoryState& h, double t_k, const EpochParams* ep, int depth_out);
 }  // namespace pfg

@@ -784,6 +784,38 @@ cudaError_t launch_theta_mean(const FilterDev& fd, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Kernels are loaded lazily at their first launch, and a first launch may wait
+// for the device to drain.  Querying a kernel's attributes loads it, so this
+// loads every kernel of the library up front (once per process and device).
+namespace {
+template <class K>
+cudaError_t touch(K* k) {
+  cudaFuncAttributes a;
+  return cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(k));
+}
+}  // namespace
+
+cudaError_t preload_main_kernels() {
+  const void* ks[] = {
+      (const void*)k_init<2, 2>, (const void*)k_init<3, 3>, (const void*)k_init<64, 3>,
+      (const void*)k_stage1<Linear2>, (const void*)k_stage1<Robertson>,
+      (const void*)k_stage2<Linear2>, (const void*)k_stage2<Robertson>,
+      (const void*)k_moments<2, 2>, (const void*)k_moments<3, 3>, (const void*)k_moments<64, 3>,
+      (const void*)k_scan_tile, (const void*)k_scan_add, (const void*)k_resample,
+      (const void*)k_theta_mean<2>, (const void*)k_theta_mean<3>, (const void*)k_set_moments,
+      (const void*)k_batch_init, (const void*)k_batch_stage<Linear2, 1>,
+      (const void*)k_batch_stage<Linear2, 2>, (const void*)k_batch_stage<Robertson, 1>,
+      (const void*)k_batch_stage<Robertson, 2>, (const void*)k_batch_scan_tile,
+      (const void*)k_batch_scan_add, (const void*)k_batch_resample,
+      (const void*)k_batch_moments<2, 2>, (const void*)k_batch_moments<3, 3>,
+      (const void*)k_batch_moments<64, 3>};
+  for (const void* k : ks) {
+    const cudaError_t e = touch(k);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 bool ode_supported(int ode) {
   return ode == PF_ODE_LINEAR2 || ode == PF_ODE_ROBERTSON || ode == PF_ODE_BRUSSELATOR1D;
 }

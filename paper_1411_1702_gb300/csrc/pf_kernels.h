@@ -50,6 +50,11 @@ cudaError_t launch_set_moments(const FilterDev& fd, cudaStream_t st);
 int moment_record_size(int ode);
 // Weighted theta-space mean of the committed ensemble into Ctrl::theta_mean.
 cudaError_t launch_theta_mean(const FilterDev& fd, cudaStream_t st);
+// Load every kernel of the library on the current device now rather than at
+// its first launch (which may wait for the device to drain); once per device.
+cudaError_t preload_main_kernels();
+cudaError_t preload_bruss_kernels();
+cudaError_t preload_kernels();
 // Brusselator stage kernels (pf_bruss.cu): stage 1 or 2 of one epoch.
 cudaError_t launch_bruss_stage(int stage, const FilterDev& fd, const EpochParams* ep, int S,
                                cudaStream_t st);

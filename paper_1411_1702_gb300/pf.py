@@ -31,7 +31,9 @@ ABI_SYMBOLS = [
     "pf_set_ensemble", "pf_set_moments", "pf_get_work", "pf_get_history", "pf_set_history",
     "pf_substep_table", "pf_version", "pf_kernel_times", "pf_resample_systematic_noalloc",
     "pf_batch_create", "pf_batch_assimilate", "pf_batch_stats", "pf_batch_last_error",
-    "pf_batch_destroy",
+    "pf_batch_destroy", "pf_server_create", "pf_server_open", "pf_server_submit",
+    "pf_server_step", "pf_server_drain", "pf_server_close", "pf_server_session",
+    "pf_server_stats", "pf_server_last_error", "pf_server_destroy",
 ]
 NOALLOC_MAX_PARTICLES = 1 << 24
 KERNEL_SLOTS = ["stage1", "scan_tile", "scan_add", "resample", "stage2", "moments"]
@@ -69,6 +71,19 @@ class BatchStats(C.Structure):
     _fields_ = [("epochs", C.c_int64), ("graph_captures", C.c_int64),
                 ("last_device_ms", C.c_double), ("last_active", C.c_int), ("last_tiles", C.c_int),
                 ("tile_order", C.c_int), ("concurrent_models", C.c_int), ("tune_ms", C.c_double * 4)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("admitted", C.c_int64), ("rejected", C.c_int64), ("waiting", C.c_int64),
+                ("active_sessions", C.c_int64), ("queued_observations", C.c_int64),
+                ("assimilations", C.c_int64), ("epochs", C.c_int64),
+                ("mean_sessions_per_epoch", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
+                ("particle_steps_per_s", C.c_double), ("device_bytes_in_use", C.c_int64),
+                ("budget_bytes", C.c_int64), ("step_calls", C.c_int64),
+                ("step_ms_mean", C.c_double), ("step_ms_max", C.c_double),
+                ("collect_ms_max", C.c_double), ("admit_ms_max", C.c_double),
+                ("launch_ms_max", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -115,6 +130,19 @@ def load(path: str = LIB_PATH):
         "pf_batch_stats": (C.c_int, [C.c_void_p, C.POINTER(BatchStats)]),
         "pf_batch_last_error": (C.c_char_p, [C.c_void_p]),
         "pf_batch_destroy": (None, [C.c_void_p]),
+        "pf_server_create": (C.c_int, [C.c_int64, C.c_int, C.POINTER(C.c_void_p)]),
+        "pf_server_open": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int,
+                                     C.c_double, C.POINTER(Prior), C.POINTER(Options),
+                                     C.POINTER(C.c_int64)]),
+        "pf_server_submit": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, _dp]),
+        "pf_server_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+        "pf_server_drain": (C.c_int, [C.c_void_p]),
+        "pf_server_close": (C.c_int, [C.c_void_p, C.c_int64]),
+        "pf_server_session": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+        "pf_server_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+        "pf_server_last_error": (C.c_char_p, [C.c_void_p]),
+        "pf_server_destroy": (None, [C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -197,9 +225,19 @@ class Filter:
                    kappa=w.kappa, seed=w.seed if seed is None else seed, filter_id=filter_id,
                    stream=stream, timing=timing)
 
+    @classmethod
+    def borrowed(cls, handle, ode, d, p, N, m):
+        """View of a filter the library owns (e.g. a server session)."""
+        obj = cls.__new__(cls)
+        obj._h = C.c_void_p(handle)
+        obj._owned = False
+        obj._keep = []
+        obj.ode, obj.d, obj.p, obj.N, obj.m = ode, d, p, N, m
+        return obj
+
     def close(self):
         h = getattr(self, "_h", None)
-        if h and _lib is not None:
+        if h and _lib is not None and getattr(self, "_owned", True):
             _lib.pf_destroy(h)
         self._h = None
 
@@ -328,3 +366,80 @@ class Batch:
                     last_device_ms=s.last_device_ms, last_active=s.last_active,
                     last_tiles=s.last_tiles, tile_order=s.tile_order,
                     concurrent_models=s.concurrent_models, tune_ms=list(s.tune_ms))
+
+
+def _prior_options(w, N=None, seed=None, filter_id=0):
+    keep = []
+    kind = (C.c_int * len(w.prior_kind))(*[int(k) for k in w.prior_kind])
+    lo, hi, x0 = _f64(w.prior_lo), _f64(w.prior_hi), _f64(w.x0)
+    obs = (C.c_int * len(w.obs_idx))(*[int(o) for o in w.obs_idx])
+    sig = _f64(w.sigma)
+    keep += [kind, lo, hi, x0, obs, sig]
+    pr = Prior(w.p, kind, _d(lo), _d(hi), w.d, _d(x0), float(w.t0))
+    op = Options(float(w.a), int(w.newton_iters), int(w.spacing), int(w.substeps), float(w.q0),
+                 int(w.history), int(w.transform), len(w.obs_idx), obs, int(w.noise), _d(sig),
+                 float(w.kappa), int(w.seed if seed is None else seed), int(filter_id), None, 0)
+    return pr, op, keep
+
+
+class Server:
+    """Filter sessions admitted by device-memory budget and served by
+    continuous batching (see include/pf.h)."""
+
+    def __init__(self, budget_bytes, lanes=0):
+        h = C.c_void_p()
+        _check(load().pf_server_create(int(budget_bytes), int(lanes), C.byref(h)), None)
+        self._h = h
+        self._shapes = {}
+
+    def _check(self, st):
+        if st != PF_OK:
+            msg = load().pf_server_last_error(self._h)
+            raise PfError(st, msg.decode() if msg else "")
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.pf_server_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def pf_server_open(self, w, N=None, seed=None, filter_id=0):
+        N = int(N if N is not None else w.N)
+        pr, op, keep = _prior_options(w, N, seed, filter_id)
+        sid = C.c_int64()
+        self._check(load().pf_server_open(self._h, w.ode, w.d, w.p, N, w.lmm, float(w.dt),
+                                          C.byref(pr), C.byref(op), C.byref(sid)))
+        self._shapes[sid.value] = (w.ode, w.d, w.p, N, len(w.obs_idx))
+        return sid.value
+
+    def pf_server_submit(self, session, t, y):
+        y = _f64(y)
+        self._check(load().pf_server_submit(self._h, int(session), float(t), _d(y)))
+
+    def pf_server_step(self):
+        n = C.c_int()
+        self._check(load().pf_server_step(self._h, C.byref(n)))
+        return n.value
+
+    def pf_server_drain(self):
+        self._check(load().pf_server_drain(self._h))
+
+    def pf_server_close(self, session):
+        self._check(load().pf_server_close(self._h, int(session)))
+
+    def pf_server_session(self, session):
+        fh = C.c_void_p()
+        done = C.c_int64()
+        last = C.c_int()
+        self._check(load().pf_server_session(self._h, int(session), C.byref(fh), C.byref(done),
+                                             C.byref(last)))
+        f = Filter.borrowed(fh.value, *self._shapes[int(session)]) if fh.value else None
+        return f, done.value, last.value
+
+    def pf_server_stats(self):
+        s = ServerStats()
+        self._check(load().pf_server_stats(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}

@@ -25,6 +25,7 @@ the paper's workloads -- thousands to ~10^5 particles, 30-50 observations):
 from __future__ import annotations
 
 import dataclasses
+import functools
 import math
 
 import numpy as np
@@ -227,15 +228,24 @@ def brusselator_x0():
     return x0
 
 
-def brusselator(N: int = 65536, T: int = 30, seed: int = 0) -> Workload:
+@functools.lru_cache(maxsize=8)
+def _brusselator_truth(T: int) -> np.ndarray:
     from scipy.integrate import solve_ivp
+    theta = np.array([1.0, 3.0, 0.02])
+    t_obs = np.arange(1, T + 1) / 3.0
+    f, jac = brusselator_rhs(theta)
+    sol = solve_ivp(f, (0.0, t_obs[-1]), brusselator_x0(), method="Radau", t_eval=t_obs,
+                    rtol=1e-11, atol=1e-12, jac=jac)
+    x = sol.y.T.copy()
+    x.flags.writeable = False
+    return x
+
+
+def brusselator(N: int = 65536, T: int = 30, seed: int = 0) -> Workload:
     theta = np.array([1.0, 3.0, 0.02])
     x0 = brusselator_x0()
     t_obs = np.arange(1, T + 1) / 3.0
-    f, jac = brusselator_rhs(theta)
-    sol = solve_ivp(f, (0.0, t_obs[-1]), x0, method="Radau", t_eval=t_obs, rtol=1e-11,
-                    atol=1e-12, jac=jac)
-    x_true = sol.y.T
+    x_true = np.array(_brusselator_truth(T))
     obs_idx = [2 * i for i in range(2, 32, 4)]
     sigma = [0.02] * len(obs_idx)
     rng = np.random.default_rng([seed, 0xDA7A, BRUSSELATOR])
@@ -269,6 +279,46 @@ def batched(n_filters: int = 256, seed: int = 0, n_min_log2: float = 10.0,
             th = np.exp(rng.uniform(np.log(star / 10.0), np.log(star * 10.0)))
             w = robertson(N=N, seed=f, theta=th, rtol=1e-8)
         out.append(w.with_(stream=f))
+    return out
+
+
+@dataclasses.dataclass
+class Session:
+    """One filter session of a serving trace: its problem and the wall-clock
+    arrival time (seconds from the start) of the session and of each of its
+    observations."""
+    w: Workload
+    open_s: float
+    obs_s: np.ndarray
+
+
+def serving(n_sessions: int = 64, rate_hz: float = 200.0, obs_per_session: int = 10,
+            mean_gap_ms: float = 5.0, seed: int = 0, n_log2=(12, 18)) -> list:
+    """Serving trace: sessions arrive as a Poisson process (rate_hz); each is
+    linear2, robertson or brusselator with probability 1/3, N = 2^k with k
+    uniform on n_log2 (4096 ... 262144), its true parameter drawn from that
+    problem's prior (the Brusselator keeps its reference parameter), and its
+    observations arrive at exponential intervals of mean mean_gap_ms, the
+    first one a gap after the session opens."""
+    rng = np.random.default_rng([seed, 0x5E55])
+    out = []
+    t = 0.0
+    for s in range(n_sessions):
+        t += rng.exponential(1.0 / rate_hz)
+        N = 2 ** int(rng.integers(n_log2[0], n_log2[1] + 1))
+        kind = int(rng.integers(3))
+        if kind == 0:
+            lo, hi = np.array([0.1, 100.0]), np.array([10.0, 1e4])
+            w = linear2(N=N, T=obs_per_session, seed=s,
+                        theta=np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        elif kind == 1:
+            star = np.array([0.04, 3e7, 1e4])
+            w = robertson(N=N, T=obs_per_session, seed=s, rtol=1e-8,
+                          theta=np.exp(rng.uniform(np.log(star / 10.0), np.log(star * 10.0))))
+        else:
+            w = brusselator(N=N, T=obs_per_session, seed=s)
+        gaps = rng.exponential(mean_gap_ms * 1e-3, size=obs_per_session)
+        out.append(Session(w=w.with_(stream=s), open_s=t, obs_s=t + np.cumsum(gaps)))
     return out
 
 

@@ -70,8 +70,8 @@ def test_idle_filters_and_graph_recapture(pf):
         assert batch.pf_batch_assimilate(ts, ys) == [pf.PF_OK] * len(ws)
     for a, m in zip(alone, members):
         assert _same(a, m)
-    # the active set changed three times (rows 1, 3, 4 differ from their predecessor)
-    assert batch.pf_batch_stats()["graph_captures"] == 4
+    # a graph is captured when an active set repeats (row 2 repeats row 1)
+    assert batch.pf_batch_stats()["graph_captures"] == 1
 
 
 def test_failure_is_isolated(pf):

@@ -1,0 +1,108 @@
+"""Serving: sessions admitted by device-memory budget, continuous batching,
+results identical to each filter alone, latency accounting."""
+import numpy as np
+import pytest
+
+from paper_1411_1702_gb300 import build as B
+from paper_1411_1702_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf():
+    B.build()
+    from paper_1411_1702_gb300 import pf as _pf
+    _pf.load()
+    return _pf
+
+
+def _sessions():
+    specs = [("robertson", 4096, 11), ("linear2", 2048, 12), ("brusselator", 64, 13),
+             ("robertson", 1000, 14), ("linear2", 1, 15), ("robertson", 8192, 16)]
+    return [W.get(name, N=N, T=4, seed=seed) for name, N, seed in specs]
+
+
+def _same(a, b):
+    ea, eb = a.pf_get_ensemble(), b.pf_get_ensemble()
+    return all(np.array_equal(ea[k], eb[k], equal_nan=True) for k in ea)
+
+
+def test_sessions_match_alone_under_interleaved_arrivals(pf):
+    ws = _sessions()
+    srv = pf.Server(budget_bytes=8 << 30)
+    sids = [srv.pf_server_open(w, filter_id=i) for i, w in enumerate(ws)]
+    rng = np.random.default_rng(3)
+    nxt = [0] * len(ws)
+    # observations arrive in a random interleaving; the server steps in between
+    while any(k < 4 for k in nxt):
+        i = int(rng.integers(len(ws)))
+        if nxt[i] < 4:
+            srv.pf_server_submit(sids[i], ws[i].t_obs[nxt[i]], ws[i].y_obs[nxt[i]])
+            nxt[i] += 1
+        if rng.random() < 0.5:
+            srv.pf_server_step()
+    srv.pf_server_drain()
+    st = srv.pf_server_stats()
+    assert st["assimilations"] == 4 * len(ws)
+    assert 0.0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
+    for i, w in enumerate(ws):
+        f, done, last = srv.pf_server_session(sids[i])
+        assert done == 4 and last == pf.PF_OK
+        alone = pf.Filter.from_workload(w, filter_id=i)
+        for k in range(4):
+            alone.pf_assimilate(w.t_obs[k], w.y_obs[k])
+        assert _same(alone, f)
+
+
+def _session_bytes(pf, w):
+    probe = pf.Server(budget_bytes=1 << 40)
+    probe.pf_server_open(w)
+    probe.pf_server_step()
+    b = probe.pf_server_stats()["device_bytes_in_use"]
+    probe.close()
+    return b
+
+
+def test_admission_waits_for_memory(pf):
+    ws = _sessions()[:3]
+    big = W.robertson(N=200000, T=2, seed=21)
+    b_big = _session_bytes(pf, big)
+    b_rest = sum(_session_bytes(pf, w) for w in ws)
+    # room for the big session or for the rest, not for the big one and the first
+    budget = max(b_big, b_rest) + min(_session_bytes(pf, ws[0]), b_big) - 1
+    assert b_big + _session_bytes(pf, ws[0]) > budget
+    srv = pf.Server(budget_bytes=budget)
+    sid_big = srv.pf_server_open(big)
+    sids = [srv.pf_server_open(w) for w in ws]
+    srv.pf_server_step()
+    st = srv.pf_server_stats()
+    assert st["admitted"] == 1 and st["waiting"] == 3
+    assert st["device_bytes_in_use"] == b_big
+    for k in range(2):
+        srv.pf_server_submit(sid_big, big.t_obs[k], big.y_obs[k])
+    for s, w in zip(sids, ws):
+        srv.pf_server_submit(s, w.t_obs[0], w.y_obs[0])
+    srv.pf_server_drain()
+    assert srv.pf_server_stats()["waiting"] == 3      # still no room
+    f, done, _ = srv.pf_server_session(sid_big)
+    assert done == 2 and f is not None
+    assert srv.pf_server_session(sids[0])[0] is None   # not admitted yet
+    srv.pf_server_close(sid_big)                       # frees its memory
+    srv.pf_server_drain()
+    st = srv.pf_server_stats()
+    assert st["waiting"] == 0 and st["assimilations"] == 2 + len(ws)
+    assert st["device_bytes_in_use"] == b_rest <= st["budget_bytes"]
+    for s, w in zip(sids, ws):
+        f, done, _ = srv.pf_server_session(s)
+        alone = pf.Filter.from_workload(w)
+        alone.pf_assimilate(w.t_obs[0], w.y_obs[0])
+        assert done == 1 and _same(alone, f)
+
+
+def test_session_larger_than_budget_is_rejected(pf):
+    srv = pf.Server(budget_bytes=1 << 20)
+    with pytest.raises(pf.PfError) as ei:
+        srv.pf_server_open(W.robertson(N=100000, T=1))
+    assert ei.value.status == pf.PF_ERR_BUDGET
+    assert srv.pf_server_stats()["rejected"] == 1
