@@ -23,8 +23,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-DMAX, PMAX, MMAX, SMAX = 64, 8, 16, 4096
-LINEAR2, ROBERTSON, BRUSSELATOR = 1, 2, 3
+DMAX, PMAX, MMAX, SMAX = 2025, 8, 32, 4096
+LINEAR2, ROBERTSON, BRUSSELATOR, ADVDIFF = 1, 2, 3, 4
 RNG_INIT, RNG_THETA, RNG_INNOV, RNG_RESAMPLE = 1, 2, 3, 4
 UNIFORM, LOGUNIFORM = 0, 1
 SPACING_UNIFORM, SPACING_GEOMETRIC = 0, 1
@@ -81,14 +81,18 @@ def lib():
             "or_philox4x32_10": (None, [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
             "or_uniform": (C.c_double, [C.c_uint64, C.c_uint32, C.c_int, C.c_uint32, C.c_uint32, C.c_int]),
             "or_normal": (C.c_double, [C.c_uint64, C.c_uint32, C.c_int, C.c_uint32, C.c_uint32, C.c_int]),
-            "or_ode_f": (None, [C.c_int, _dp, _dp, _dp]),
-            "or_ode_jac": (None, [C.c_int, _dp, _dp, _dp]),
+            "or_ode_f": (None, [C.c_int, C.c_int, _dp, _dp, _dp]),
+            "or_ode_jac": (None, [C.c_int, C.c_int, _dp, _dp, _dp]),
             "or_ode_dims": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+            "or_ode_check_dim": (C.c_int, [C.c_int, C.c_int]),
             "or_lu_solve": (C.c_int, [C.c_int, _dp, _dp, _dp]),
+            "or_lu_factor": (C.c_int, [C.c_int, _dp, C.POINTER(C.c_int)]),
+            "or_lu_apply": (None, [C.c_int, _dp, C.POINTER(C.c_int), _dp, _dp]),
             "or_bdf_coefficients": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(Substep)]),
             "or_build_substeps": (C.c_int, [C.POINTER(Config), C.c_double, C.c_double, C.c_int, C.c_double,
                                             C.c_double, C.POINTER(Substep), C.c_int, C.POINTER(C.c_int)]),
-            "or_propagate": (C.c_int, [C.c_int, C.c_int, _dp, C.POINTER(Substep), C.c_int, _dp, _dp, _dp, _dp]),
+            "or_propagate": (C.c_int, [C.c_int, C.c_int, C.c_int, _dp, C.POINTER(Substep), C.c_int, _dp, _dp,
+                                       _dp, _dp]),
             "or_loglik": (C.c_double, [C.POINTER(Config), _dp, _dp]),
             "or_resample_systematic": (None, [C.c_int64, _dp, C.c_double, _ip]),
             "or_cholesky_psd": (None, [C.c_int, _dp, _dp]),
@@ -152,21 +156,29 @@ def ode_dims(ode):
     return d.value, p.value
 
 
+def ode_check_dim(ode, d):
+    return lib().or_ode_check_dim(ode, int(d)) == 0
+
+
 def ode_f(ode, theta, x):
-    d, _ = ode_dims(ode)
-    th = np.ascontiguousarray(theta, dtype=np.float64)
     xx = np.ascontiguousarray(x, dtype=np.float64)
+    d = len(xx)
+    if not ode_check_dim(ode, d):
+        raise ValueError((ode, d))
+    th = np.ascontiguousarray(theta, dtype=np.float64)
     f = np.zeros(d)
-    lib().or_ode_f(ode, _d(th), _d(xx), _d(f))
+    lib().or_ode_f(ode, d, _d(th), _d(xx), _d(f))
     return f
 
 
 def ode_jac(ode, theta, x):
-    d, _ = ode_dims(ode)
-    th = np.ascontiguousarray(theta, dtype=np.float64)
     xx = np.ascontiguousarray(x, dtype=np.float64)
+    d = len(xx)
+    if not ode_check_dim(ode, d):
+        raise ValueError((ode, d))
+    th = np.ascontiguousarray(theta, dtype=np.float64)
     J = np.zeros((d, d))
-    lib().or_ode_jac(ode, _d(th), _d(xx), _d(J))
+    lib().or_ode_jac(ode, d, _d(th), _d(xx), _d(J))
     return J
 
 
@@ -177,6 +189,22 @@ def lu_solve(A, b):
     if lib().or_lu_solve(len(b), _d(A), _d(b), _d(x)) != 0:
         raise np.linalg.LinAlgError("singular")
     return x
+
+
+def lu_factor_solve(A, bs):
+    """Factor A once (or_lu_factor) and solve for each right-hand side."""
+    LU = np.array(A, dtype=np.float64, order="C")
+    n = LU.shape[0]
+    piv = (C.c_int * n)()
+    if lib().or_lu_factor(n, _d(LU), piv) != 0:
+        raise np.linalg.LinAlgError("singular")
+    out = []
+    for b in bs:
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(n)
+        lib().or_lu_apply(n, _d(LU), piv, _d(b), _d(x))
+        out.append(x)
+    return out
 
 
 def bdf_coefficients(kind, h0, h1=0.0, h2=0.0):
@@ -209,7 +237,7 @@ def propagate(ode, K, theta, tab, S, x, h1, h2, with_error=False):
     h1 = np.array(h1, dtype=np.float64)
     h2 = np.array(h2, dtype=np.float64)
     E = np.zeros(len(x)) if with_error else None
-    rc = lib().or_propagate(ode, K, _d(th), tab, S, _d(x), _d(h1), _d(h2), _d(E))
+    rc = lib().or_propagate(ode, len(x), K, _d(th), tab, S, _d(x), _d(h1), _d(h2), _d(E))
     if rc != 0:
         raise np.linalg.LinAlgError("singular Newton matrix")
     return x, h1, h2, E

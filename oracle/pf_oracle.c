@@ -113,12 +113,71 @@ int or_ode_dims(int ode, int* d, int* p) {
     case OR_LINEAR2: *d = 2; *p = 2; return 0;
     case OR_ROBERTSON: *d = 3; *p = 3; return 0;
     case OR_BRUSSELATOR: *d = 2 * BR_POINTS; *p = 3; return 0;
+    case OR_ADVDIFF: *d = 0; *p = 5; return 0;
   }
   return -1;
 }
 
-void or_ode_f(int ode, const double* th, const double* x, double* f) {
-  if (ode == OR_LINEAR2) {
+/* side of the M2 grid for state dimension d, or 0 if d is not an odd square */
+static int ad_side(int d) {
+  for (int nt = 3; nt <= 45; nt += 2)
+    if (nt * nt == d) return nt;
+  return 0;
+}
+
+int or_ode_check_dim(int ode, int d) {
+  int dd, p;
+  if (or_ode_dims(ode, &dd, &p) != 0) return -1;
+  if (ode == OR_ADVDIFF) return ad_side(d) ? 0 : -1;
+  return d == dd ? 0 : -1;
+}
+
+/* M2 (Sec. 4): the forward difference matrix ell of the paper, (ell u)_j =
+ * u_j - u_{j-1} with periodic wrap, and its transpose (ell^T u)_j = u_j -
+ * u_{j+1}, applied along one axis of the nt x nt grid stored as
+ * U[iy * nt + ix] (x fastest): axis 0 is B1 = I (x) ell (the x direction),
+ * axis 1 is B2 = ell (x) I (the y direction). */
+static void ad_ell(int nt, int axis, int transpose, const double* u, double* out) {
+  for (int iy = 0; iy < nt; ++iy) {
+    for (int ix = 0; ix < nt; ++ix) {
+      int jx = ix, jy = iy;
+      int step = transpose ? 1 : nt - 1; /* +1 or -1 modulo nt */
+      if (axis == 0) jx = (ix + step) % nt;
+      else jy = (iy + step) % nt;
+      out[iy * nt + ix] = u[iy * nt + ix] - u[jy * nt + jx];
+    }
+  }
+}
+
+/* M2 right-hand side f = L U,
+ *   L = -{k1^2 B1^T B1 + k1 k3 (B1^T B2 + B2^T B1) + (k2^2 + k3^2) B2^T B2}
+ *       + c1 B1 + c2 B2,
+ * with theta = (k1, k2, k3, c1, c2) (Sec. 4), each product applied as a
+ * composition of the difference operators. */
+static void ad_rhs(int d, const double* th, const double* x, double* f) {
+  const int nt = ad_side(d);
+  const double k1 = th[0], k2 = th[1], k3 = th[2], c1 = th[3], c2 = th[4];
+  double* b1 = (double*)malloc(sizeof(double) * (size_t)d * 4);
+  double* b2 = b1 + d;
+  double* t1 = b2 + d;
+  double* t2 = t1 + d;
+  ad_ell(nt, 0, 0, x, b1); /* B1 x */
+  ad_ell(nt, 1, 0, x, b2); /* B2 x */
+  for (int i = 0; i < d; ++i) f[i] = c1 * b1[i] + c2 * b2[i];
+  ad_ell(nt, 0, 1, b1, t1); /* B1^T B1 x */
+  for (int i = 0; i < d; ++i) f[i] -= k1 * k1 * t1[i];
+  ad_ell(nt, 0, 1, b2, t1); /* B1^T B2 x */
+  ad_ell(nt, 1, 1, b1, t2); /* B2^T B1 x */
+  for (int i = 0; i < d; ++i) f[i] -= k1 * k3 * (t1[i] + t2[i]);
+  ad_ell(nt, 1, 1, b2, t1); /* B2^T B2 x */
+  for (int i = 0; i < d; ++i) f[i] -= (k2 * k2 + k3 * k3) * t1[i];
+  free(b1);
+}
+
+void or_ode_f(int ode, int d, const double* th, const double* x, double* f) {
+  if (ode == OR_ADVDIFF) {
+    ad_rhs(d, th, x, f);
+  } else if (ode == OR_LINEAR2) {
     f[0] = -th[0] * x[0] + th[1] * x[1];
     f[1] = -th[1] * x[1];
   } else if (ode == OR_ROBERTSON) {
@@ -140,12 +199,22 @@ void or_ode_f(int ode, const double* th, const double* x, double* f) {
   }
 }
 
-/* Analytic Jacobian df/dx, row-major d x d. */
-void or_ode_jac(int ode, const double* th, const double* x, double* J) {
-  int d, p;
-  or_ode_dims(ode, &d, &p);
+/* Analytic Jacobian df/dx, row-major d x d.  M2 is linear, J = L: column j
+ * is L applied to the j-th unit vector. */
+void or_ode_jac(int ode, int d, const double* th, const double* x, double* J) {
   for (int i = 0; i < d * d; ++i) J[i] = 0.0;
-  if (ode == OR_LINEAR2) {
+  if (ode == OR_ADVDIFF) {
+    double* e = (double*)calloc((size_t)d * 2, sizeof(double));
+    double* col = e + d;
+    for (int j = 0; j < d; ++j) {
+      e[j] = 1.0;
+      ad_rhs(d, th, e, col);
+      for (int i = 0; i < d; ++i) J[(size_t)i * d + j] = col[i];
+      e[j] = 0.0;
+    }
+    free(e);
+    (void)x;
+  } else if (ode == OR_LINEAR2) {
     J[0] = -th[0]; J[1] = th[1];
     J[2] = 0.0;    J[3] = -th[1];
   } else if (ode == OR_ROBERTSON) {
@@ -174,10 +243,11 @@ void or_ode_jac(int ode, const double* th, const double* x, double* J) {
   }
 }
 
-/* Dense Gaussian elimination with partial pivoting: solve A x = b (n <= 64).
+/* Dense Gaussian elimination with partial pivoting: solve A x = b.
  * Returns 0, or -1 on an exactly singular pivot. */
 int or_lu_solve(int n, const double* Ain, const double* bin, double* x) {
-  double A[OR_DMAX * OR_DMAX], b[OR_DMAX];
+  double* A = (double*)malloc(sizeof(double) * ((size_t)n * n + n));
+  double* b = A + (size_t)n * n;
   memcpy(A, Ain, sizeof(double) * n * n);
   memcpy(b, bin, sizeof(double) * n);
   for (int k = 0; k < n; ++k) {
@@ -189,7 +259,10 @@ int or_lu_solve(int n, const double* Ain, const double* bin, double* x) {
         piv = i;
       }
     }
-    if (best == 0.0) return -1;
+    if (best == 0.0) {
+      free(A);
+      return -1;
+    }
     if (piv != k) {
       for (int j = 0; j < n; ++j) {
         double t = A[k * n + j];
@@ -210,7 +283,61 @@ int or_lu_solve(int n, const double* Ain, const double* bin, double* x) {
     for (int j = i + 1; j < n; ++j) s -= A[i * n + j] * x[j];
     x[i] = s / A[i * n + i];
   }
+  free(A);
   return 0;
+}
+
+/* The same elimination split in two: or_lu_factor overwrites A with the
+ * multipliers (below the diagonal) and U, recording the row swap of every
+ * column in piv; or_lu_apply then solves for any right-hand side.  Used where
+ * one Newton matrix serves many solves (the linear M2 system). */
+int or_lu_factor(int n, double* A, int* piv) {
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = fabs(A[(size_t)k * n + k]);
+    for (int i = k + 1; i < n; ++i) {
+      if (fabs(A[(size_t)i * n + k]) > best) {
+        best = fabs(A[(size_t)i * n + k]);
+        p = i;
+      }
+    }
+    if (best == 0.0) return -1;
+    piv[k] = p;
+    if (p != k) {
+      for (int j = 0; j < n; ++j) {
+        double t = A[(size_t)k * n + j];
+        A[(size_t)k * n + j] = A[(size_t)p * n + j];
+        A[(size_t)p * n + j] = t;
+      }
+    }
+    for (int i = k + 1; i < n; ++i) {
+      double l = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+      A[(size_t)i * n + k] = l;
+      if (l == 0.0) continue;
+      for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
+    }
+  }
+  return 0;
+}
+
+void or_lu_apply(int n, const double* LU, const int* piv, const double* b, double* x) {
+  double* y = (double*)malloc(sizeof(double) * (size_t)n);
+  memcpy(y, b, sizeof(double) * n);
+  /* the rows were swapped whole (multipliers included), so P b first, then
+   * forward substitution with the unit lower factor */
+  for (int k = 0; k < n; ++k) {
+    if (piv[k] != k) {
+      double t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t;
+    }
+  }
+  for (int k = 0; k < n; ++k)
+    for (int i = k + 1; i < n; ++i) y[i] -= LU[(size_t)i * n + k] * y[k];
+  for (int i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int j = i + 1; j < n; ++j) s -= LU[(size_t)i * n + j] * x[j];
+    x[i] = s / LU[(size_t)i * n + i];
+  }
+  free(y);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -355,13 +482,19 @@ int or_build_substeps(const or_config* cfg, double t_prev, double t_next, int de
  * not NULL, the squared Milne local-error estimates are summed into E (Step 4b
  * reading: Gamma = kappa diag(sum_s e_s^2)).  Returns 0, or -1 if the Newton
  * matrix became singular. */
-int or_propagate(int ode, int K, const double* th, const or_substep* tab, int S,
+int or_propagate(int ode, int d, int K, const double* th, const or_substep* tab, int S,
                  double* x, double* h1, double* h2, double* E) {
-  int d, p;
-  or_ode_dims(ode, &d, &p);
-  double xi[OR_DMAX], xp[OR_DMAX], r[OR_DMAX], G[OR_DMAX], f[OR_DMAX], dx[OR_DMAX];
-  double J[OR_DMAX * OR_DMAX], M[OR_DMAX * OR_DMAX];
-  for (int s = 0; s < S; ++s) {
+  const int linear = (ode == OR_ADVDIFF);
+  double* xi = (double*)malloc(sizeof(double) * (size_t)d * 6);
+  double *xp = xi + d, *r = xp + d, *G = r + d, *f = G + d, *dx = f + d;
+  double* J = (double*)malloc(sizeof(double) * (size_t)d * d);
+  double* M = (double*)malloc(sizeof(double) * (size_t)d * d);
+  int* piv = (int*)malloc(sizeof(int) * (size_t)d);
+  /* M2 is linear: J = L for every iterate, so its Newton matrix I - gamma L
+   * is factored once per step size and reused */
+  int have_J = 0, have_lu = 0, rc = 0;
+  double lu_gamma = 0.0;
+  for (int s = 0; s < S && rc == 0; ++s) {
     const or_substep* c = &tab[s];
     for (int i = 0; i < d; ++i) {
       if (c->kind == 2) {
@@ -374,20 +507,38 @@ int or_propagate(int ode, int K, const double* th, const or_substep* tab, int S,
     }
     if (c->kind == 1) {
       /* explicit-Euler predictor, used only by the error estimate */
-      or_ode_f(ode, th, x, f);
+      or_ode_f(ode, d, th, x, f);
       for (int i = 0; i < d; ++i) xp[i] = x[i] + c->h * f[i];
     }
     for (int it = 0; it < K; ++it) {
-      or_ode_f(ode, th, xi, f);
-      or_ode_jac(ode, th, xi, J);
-      for (int i = 0; i < d; ++i) {
-        G[i] = xi[i] - r[i] - c->gamma * f[i];
-        for (int j = 0; j < d; ++j) M[i * d + j] = (i == j ? 1.0 : 0.0) - c->gamma * J[i * d + j];
-        G[i] = -G[i];
+      or_ode_f(ode, d, th, xi, f);
+      if (!linear || !have_J) {
+        or_ode_jac(ode, d, th, xi, J);
+        have_J = 1;
       }
-      if (or_lu_solve(d, M, G, dx) != 0) return -1;
+      for (int i = 0; i < d; ++i) G[i] = -(xi[i] - r[i] - c->gamma * f[i]);
+      if (!linear || !have_lu || lu_gamma != c->gamma) {
+        for (int i = 0; i < d; ++i)
+          for (int j = 0; j < d; ++j)
+            M[(size_t)i * d + j] = (i == j ? 1.0 : 0.0) - c->gamma * J[(size_t)i * d + j];
+      }
+      if (linear) {
+        if (!have_lu || lu_gamma != c->gamma) {
+          if (or_lu_factor(d, M, piv) != 0) {
+            rc = -1;
+            break;
+          }
+          have_lu = 1;
+          lu_gamma = c->gamma;
+        }
+        or_lu_apply(d, M, piv, G, dx);
+      } else if (or_lu_solve(d, M, G, dx) != 0) {
+        rc = -1;
+        break;
+      }
       for (int i = 0; i < d; ++i) xi[i] += dx[i];
     }
+    if (rc != 0) break;
     if (E) {
       for (int i = 0; i < d; ++i) {
         double e = c->mu * (xi[i] - xp[i]);
@@ -400,7 +551,11 @@ int or_propagate(int ode, int K, const double* th, const or_substep* tab, int S,
       x[i] = xi[i];
     }
   }
-  return 0;
+  free(xi);
+  free(J);
+  free(M);
+  free(piv);
+  return rc;
 }
 
 /* Gaussian observation model pi(y | x): log-likelihood without the constant
@@ -474,7 +629,9 @@ static double* alloc_d(int64_t n) { return (double*)calloc((size_t)(n > 0 ? n : 
 or_filter* or_create(const or_config* cfg) {
   int d, p;
   if (or_ode_dims(cfg->ode, &d, &p) != 0) return NULL;
-  if (d != cfg->d || p != cfg->p || cfg->N < 1 || cfg->m < 0 || cfg->m > OR_MMAX) return NULL;
+  d = cfg->d;
+  if (or_ode_check_dim(cfg->ode, d) != 0 || d > OR_DMAX) return NULL;
+  if (p != cfg->p || cfg->N < 1 || cfg->m < 0 || cfg->m > OR_MMAX) return NULL;
   or_filter* f = (or_filter*)calloc(1, sizeof(or_filter));
   f->cfg = *cfg;
   f->d = d; f->p = p; f->N = cfg->N;
@@ -599,7 +756,7 @@ int or_stage1(or_filter* f, const or_substep* tab, int S, const double* y) {
     memcpy(x, &f->x[n * d], sizeof(double) * d);
     memcpy(h1, &f->h1[n * d], sizeof(double) * d);
     memcpy(h2, &f->h2[n * d], sizeof(double) * d);
-    int bad = or_propagate(cfg->ode, cfg->newton_iters, th, tab, S, x, h1, h2, NULL);
+    int bad = or_propagate(cfg->ode, d, cfg->newton_iters, th, tab, S, x, h1, h2, NULL);
     double ll = bad ? NAN : or_loglik(cfg, y, x);
     f->ll1[n] = ll;
     double lg = f->lw[n] + ll;
@@ -659,7 +816,7 @@ int or_stage2(or_filter* f, const or_substep* tab, int S, const double* y, const
     memcpy(h1, &f->h1[l * d], sizeof(double) * d);
     memcpy(h2, &f->h2[l * d], sizeof(double) * d);
     for (int i = 0; i < d; ++i) E[i] = 0.0;
-    int bad = or_propagate(cfg->ode, cfg->newton_iters, th, tab, S, x, h1, h2, E);
+    int bad = or_propagate(cfg->ode, d, cfg->newton_iters, th, tab, S, x, h1, h2, E);
     for (int i = 0; i < d; ++i) {
       double zi = or_normal(cfg->seed, cfg->stream, OR_RNG_INNOV, (uint32_t)n, epoch, i);
       double v = sqrt(cfg->kappa * E[i]) * zi;

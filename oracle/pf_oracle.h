@@ -20,13 +20,14 @@
 #define PF_ORACLE_H
 #include <stdint.h>
 
-#define OR_DMAX 64
+#define OR_DMAX 2025   /* the largest M2 grid, 45 x 45 */
 #define OR_PMAX 8
-#define OR_MMAX 16
+#define OR_MMAX 32
 #define OR_SMAX 4096
 
-/* problem ids */
-enum { OR_LINEAR2 = 1, OR_ROBERTSON = 2, OR_BRUSSELATOR = 3 };
+/* problem ids; OR_ADVDIFF is the paper's 2D advection-diffusion system (M2,
+ * Sec. 4) on an nt x nt periodic grid, d = nt^2 with nt odd, 3 <= nt <= 45 */
+enum { OR_LINEAR2 = 1, OR_ROBERTSON = 2, OR_BRUSSELATOR = 3, OR_ADVDIFF = 4 };
 /* random-stream purposes (counter word 2, low byte) */
 enum { OR_RNG_INIT = 1, OR_RNG_THETA = 2, OR_RNG_INNOV = 3, OR_RNG_RESAMPLE = 4 };
 enum { OR_UNIFORM = 0, OR_LOGUNIFORM = 1 };          /* prior kinds          */
@@ -76,15 +77,22 @@ typedef struct or_filter or_filter;
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double or_uniform(uint64_t seed, uint32_t stream, int purpose, uint32_t n, uint32_t epoch, int k);
 double or_normal(uint64_t seed, uint32_t stream, int purpose, uint32_t n, uint32_t epoch, int k);
-void or_ode_f(int ode, const double* theta, const double* x, double* f);
-void or_ode_jac(int ode, const double* theta, const double* x, double* J);
+void or_ode_f(int ode, int d, const double* theta, const double* x, double* f);
+void or_ode_jac(int ode, int d, const double* theta, const double* x, double* J);
+/* parameter count and the fixed state dimension (0 when the dimension is a
+ * choice of the problem, as for OR_ADVDIFF) */
 int or_ode_dims(int ode, int* d, int* p);
+/* 0 if d is a valid state dimension of the problem */
+int or_ode_check_dim(int ode, int d);
 int or_lu_solve(int n, const double* A, const double* b, double* x);
+/* LU with partial pivoting, factor once and solve many right-hand sides */
+int or_lu_factor(int n, double* A, int* piv);
+void or_lu_apply(int n, const double* LU, const int* piv, const double* b, double* x);
 int or_bdf_coefficients(int kind, double h0, double h1, double h2, or_substep* out);
 int or_build_substeps(const or_config* cfg, double t_prev, double t_next, int depth,
                       double hprev1, double hprev2, or_substep* tab, int max_steps,
                       int* depth_out);
-int or_propagate(int ode, int K, const double* theta, const or_substep* tab, int S,
+int or_propagate(int ode, int d, int K, const double* theta, const or_substep* tab, int S,
                  double* x, double* h1, double* h2, double* E);
 double or_loglik(const or_config* cfg, const double* y, const double* x);
 void or_resample_systematic(int64_t N, const double* c, double u, int32_t* idx);

@@ -30,7 +30,7 @@ import math
 
 import numpy as np
 
-LINEAR2, ROBERTSON, BRUSSELATOR = 1, 2, 3
+LINEAR2, ROBERTSON, BRUSSELATOR, ADVDIFF = 1, 2, 3, 4
 UNIFORM, LOGUNIFORM = 0, 1
 SPACING_UNIFORM, SPACING_GEOMETRIC = 0, 1
 HIST_CARRY, HIST_RESTART = 0, 1
@@ -41,7 +41,7 @@ NOISE_ADDITIVE, NOISE_RELATIVE = 0, 1
 # same).  Each is the smallest K whose result agrees with the fully converged
 # Newton solution to 1e-12 relative along the reference trajectory and on the
 # particles of a filter run; the test-suite re-checks the reference trajectory.
-NEWTON_ITERS = {LINEAR2: 1, ROBERTSON: 2, BRUSSELATOR: 3}
+NEWTON_ITERS = {LINEAR2: 1, ROBERTSON: 2, BRUSSELATOR: 3, ADVDIFF: 1}
 
 
 @dataclasses.dataclass
@@ -282,6 +282,82 @@ def batched(n_filters: int = 256, seed: int = 0, n_min_log2: float = 10.0,
     return out
 
 
+# ---- the paper's 2D advection-diffusion system (Sec. 4) --------------------
+# Gaussian plumes of the initial state: (standard deviation, x centre,
+# y centre), the table of Sec. 4.
+AD_PLUMES = ((0.04, 0.20, 0.80), (0.08, 0.30, 0.40), (0.07, 0.40, 0.40),
+             (0.10, 0.50, 0.50), (0.05, 0.50, 0.60), (0.06, 0.70, 0.50))
+AD_THETA = (9.0, 4.0, 6.0, 2.5, -1.5)   # (k1, k2, k3, c1, c2) of Sec. 4
+
+
+def advdiff_x0(n: int) -> np.ndarray:
+    """u0 on the periodic grid: the n x n grid of [0,1]^2 without its last row
+    and column, nt = n - 1 points per side at j / (n - 1), stacked as
+    U[iy * nt + ix] (x fastest)."""
+    nt = n - 1
+    c = np.arange(nt) / (n - 1)
+    X, Y = np.meshgrid(c, c, indexing="xy")       # X[iy, ix] = c[ix]
+    u = np.zeros((nt, nt))
+    for g, xc, yc in AD_PLUMES:
+        u += np.exp(-((X - xc) ** 2 + (Y - yc) ** 2) / (2.0 * g * g)) / (g * math.sqrt(2 * math.pi))
+    return u.reshape(-1)
+
+
+def advdiff_eigenvalues(nt: int, theta) -> np.ndarray:
+    """Eigenvalues lam[my, mx] of the M2 operator on the Fourier mode
+    exp(2 pi i (mx ix + my iy) / nt): the difference matrix ell (u_j - u_{j-1},
+    periodic) is circulant with symbol a(m) = 1 - exp(-2 pi i m / nt)."""
+    k1, k2, k3, c1, c2 = (float(v) for v in theta)
+    a = 1.0 - np.exp(-2j * np.pi * np.arange(nt) / nt)
+    ax, ay = a[None, :], a[:, None]
+    return (-(k1 * k1 * np.abs(ax) ** 2 + 2.0 * k1 * k3 * np.real(np.conj(ax) * ay)
+              + (k2 * k2 + k3 * k3) * np.abs(ay) ** 2) + c1 * ax + c2 * ay)
+
+
+def advdiff_exact(n: int, theta, x0, t) -> np.ndarray:
+    """exp(t L) x0 for each time in t (rows), through the 2D DFT."""
+    nt = n - 1
+    lam = advdiff_eigenvalues(nt, theta)
+    U0 = np.fft.fft2(np.asarray(x0, dtype=np.float64).reshape(nt, nt))
+    out = [np.real(np.fft.ifft2(U0 * np.exp(tt * lam))).reshape(-1) for tt in np.atleast_1d(t)]
+    return np.array(out)
+
+
+def advdiff(n: int = 20, N: int = 5000, T: int = 30, seed: int = 0, m: int = 20) -> Workload:
+    """M2 of Sec. 4: d = (n-1)^2, theta* = (9, 4, 6, 2.5, -1.5), m = 20 fixed
+    sensors drawn without replacement from the grid, observed at t = 1..T with
+    additive noise sigma = max |u0 at the sensors| / 50; BDF2 with h = 0.1.
+    The prior (not given in the paper) is uniform on theta* -+ |theta*| / 2,
+    sampled in theta space (c2 is negative)."""
+    theta = np.array(AD_THETA)
+    nt = n - 1
+    d = nt * nt
+    x0 = advdiff_x0(n)
+    rng = np.random.default_rng([seed, 0xAD, n])
+    obs_idx = [int(i) for i in np.sort(rng.choice(d, size=m, replace=False))]
+    t_obs = np.arange(1, T + 1, dtype=np.float64)
+    x_true = advdiff_exact(n, theta, x0, t_obs)
+    sig = float(np.max(np.abs(x0[obs_idx]))) / 50.0
+    sigma = [sig] * m
+    y = _noise(rng, x_true[:, obs_idx], sigma, False)
+    half = 0.5 * np.abs(theta)
+    return Workload(
+        name=f"advdiff{n}", ode=ADVDIFF, d=d, p=5, N=N, lmm=2, newton_iters=NEWTON_ITERS[ADVDIFF],
+        spacing=SPACING_UNIFORM, dt=0.1, substeps=10, q0=0.0,
+        history=HIST_CARRY, transform=TRANSFORM_IDENTITY, obs_idx=obs_idx,
+        noise=NOISE_ADDITIVE, sigma=sigma, a=0.98, kappa=1.0, seed=seed, stream=0,
+        prior_kind=[UNIFORM] * 5, prior_lo=list(theta - half), prior_hi=list(theta + half),
+        x0=x0, t0=0.0, theta_true=theta, t_obs=t_obs, y_obs=y, x_true=x_true)
+
+
+def advdiff20(N: int = 5000, T: int = 30, seed: int = 0) -> Workload:
+    return advdiff(20, N, T, seed)
+
+
+def advdiff40(N: int = 5000, T: int = 30, seed: int = 0) -> Workload:
+    return advdiff(40, N, T, seed)
+
+
 @dataclasses.dataclass
 class Session:
     """One filter session of a serving trace: its problem and the wall-clock
@@ -322,7 +398,8 @@ def serving(n_sessions: int = 64, rate_hz: float = 200.0, obs_per_session: int =
     return out
 
 
-BY_NAME = {"linear2": linear2, "robertson": robertson, "brusselator": brusselator}
+BY_NAME = {"linear2": linear2, "robertson": robertson, "brusselator": brusselator,
+           "advdiff20": advdiff20, "advdiff40": advdiff40}
 
 
 def get(name: str, **kw) -> Workload:
