@@ -46,15 +46,36 @@ FP64_PEAK_TFLOPS = 2.0 * 152 * 2.070e9 * 2 / 1e12
 # Algorithmic FP64 flops (FMA = 2) of one BDF2 substep of one particle in the
 # stage-2 kernel: predictor 5d, history combination 3d, Milne estimate 4d,
 # per-substep constants, and K Newton iterations.
+def _advdiff_flops(K, d):
+    """M2 (2D advection-diffusion): predictor 5d, history 3d, Milne 4d, and per
+    Newton iteration the 7-point residual 16d, the forward row and column DFTs
+    4dH + 8dH, the per-mode multiply 6 nt H, the inverse column and row DFTs
+    8dH + 4d(H-1)+3d, with nt = sqrt(d), H = (nt+1)/2 modes per row."""
+    nt = int(round(math.sqrt(d)))
+    H = (nt + 1) // 2
+    return 12 * d + K * (24 * d * H + 15 * d + 6 * nt * H)
+
+
 STAGE2_FLOPS_PER_SUBSTEP = {
-    "robertson": lambda K: 15 + 9 + 12 + 8 + 42 * K,
-    "linear2": lambda K: 10 + 6 + 8 + 20 + 14 * K,
+    "robertson": lambda K, d: 15 + 9 + 12 + 8 + 42 * K,
+    "linear2": lambda K, d: 10 + 6 + 8 + 20 + 14 * K,
     # 32 grid points x 72 flops per Newton iteration (f, G, 2x2 block, Thomas
     # forward and backward), predictor 5d, history 3d, Milne 4d, constants
-    "brusselator": lambda K: 320 + 192 + 256 + 15 + 2304 * K,
+    "brusselator": lambda K, d: 320 + 192 + 256 + 15 + 2304 * K,
+    "advdiff20": _advdiff_flops,
+    "advdiff40": _advdiff_flops,
 }
 STAGE2_KERNEL = {"robertson": "k_stage2<Robertson>", "linear2": "k_stage2<Linear2>",
-                 "brusselator": "k_bstage2"}
+                 "brusselator": "k_bstage2", "advdiff20": "k_adstage<2>",
+                 "advdiff40": "k_adstage<2>"}
+# The paper's own number for the same workload, where it has one: Table 3's
+# 2D advection-diffusion runs (BDF2, h = 0.1, N = 5000, 30 unit intervals,
+# 8 MATLAB workers on an i7-3820), converted to particle-LMM-steps/s at 600
+# steps per particle per run.
+PAPER_BASELINE = {"advdiff20": 3.0e6 / 7.20e3, "advdiff40": 3.0e6 / 3.39e4}
+# Particles of the timed CPU-oracle sample, where the workload's own N would
+# take minutes per epoch on the host cores.
+CPU_SAMPLE_N = {"advdiff20": 512, "advdiff40": 48}
 
 
 def _dist():
@@ -163,7 +184,7 @@ def run_reference(args, w):
         return 0
     import oracle
     oracle.build()
-    n_ref = min(w.N, args.ref_particles)
+    n_ref = min(w.N, args.ref_particles, CPU_SAMPLE_N.get(w.name, w.N))
     o = oracle.Filter(w, N=n_ref)
     o.init()
     k = 0
@@ -292,17 +313,19 @@ def run_ours(args, w):
     if rank != 0:
         g.close()
         return 0
+    base = PAPER_BASELINE.get(w.name)
+    vs_base = value / base if base else None
     # roofline of the dominant kernel: stage 2 (repropagation)
     ms2, n2 = ktimes["stage2"]
     S = w.substeps_per_interval(1)
-    flops = STAGE2_FLOPS_PER_SUBSTEP[w.name](w.newton_iters) * S * w.N
+    flops = STAGE2_FLOPS_PER_SUBSTEP[w.name](w.newton_iters, w.d) * S * w.N
     achieved = flops / (ms2 / n2 * 1e-3) / 1e12 if n2 else None
     shares = {name: round(ms / max(1e-12, sum(v[0] for v in ktimes.values())), 4)
               for name, (ms, _) in ktimes.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": vs_base, "dtype": "f64", "data": "synthetic",
         "config": config_of(w), "clocks": clocks.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(round(h2d)),
                 "d2h_bytes_per_step": int(round(d2h))},
@@ -316,7 +339,8 @@ def run_ours(args, w):
         "kernel_ms_per_step": {k2: v[0] / max(1, v[1]) for k2, v in ktimes.items()},
     }
     if not args.no_cpu_baseline:
-        rate, cores, sample = cpu_oracle_rate(w, seconds=args.cpu_seconds)
+        rate, cores, sample = cpu_oracle_rate(w, seconds=args.cpu_seconds,
+                                              N=CPU_SAMPLE_N.get(w.name))
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": sample}
     g.close()
@@ -585,7 +609,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="robertson",
-                    choices=["robertson", "linear2", "brusselator", "batched", "serving"])
+                    choices=["robertson", "linear2", "brusselator", "advdiff20", "advdiff40",
+                             "batched", "serving"])
     ap.add_argument("--batch-filters", type=int, default=256)
     ap.add_argument("--serve-sessions", type=int, default=64)
     ap.add_argument("--serve-obs", type=int, default=10)

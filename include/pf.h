@@ -48,14 +48,28 @@ typedef enum {
   PF_ERR_STATE = 8        /* call out of order (e.g. no observation loaded) */
 } pf_status;
 
-/* Test problems x' = f(x; theta) (the paper's Sec. 2.1 and 4 systems lack
- * constants; these stiff systems stand in for them):
+/* Problems x' = f(x; theta).  The paper's Sec. 2.1 system lacks constants, so
+ * three stiff systems stand in for it; Sec. 4's system is built as given:
  *  PF_ODE_LINEAR2        d=2, p=2: x' = A x, A = [[-th1, th2], [0, -th2]].
  *  PF_ODE_ROBERTSON      d=3, p=3: Robertson kinetics, theta = (k1, k2, k3).
  *  PF_ODE_BRUSSELATOR1D  d=64, p=3: 1D Brusselator on 32 interior points,
  *                        Dirichlet u=1, v=3, theta = (A, B, alpha), state
- *                        interleaved (u_0, v_0, u_1, v_1, ...). */
-typedef enum { PF_ODE_LINEAR2 = 1, PF_ODE_ROBERTSON = 2, PF_ODE_BRUSSELATOR1D = 3 } pf_ode;
+ *                        interleaved (u_0, v_0, u_1, v_1, ...).
+ *  PF_ODE_ADVDIFF2D      d=nt^2 (nt odd, 3 <= nt <= 45), p=5: the 2D
+ *                        advection-diffusion system of Sec. 4 on the periodic
+ *                        nt x nt grid, U' = L U with
+ *                        L = -{k1^2 B1'B1 + k1 k3 (B1'B2 + B2'B1)
+ *                              + (k2^2 + k3^2) B2'B2} + c1 B1 + c2 B2,
+ *                        B1 = I (x) ell, B2 = ell (x) I, (ell u)_j = u_j - u_{j-1}
+ *                        (periodic), theta = (k1, k2, k3, c1, c2), state
+ *                        U[iy*nt + ix] (x fastest).  Linear: one Newton
+ *                        iteration solves each step. */
+typedef enum {
+  PF_ODE_LINEAR2 = 1,
+  PF_ODE_ROBERTSON = 2,
+  PF_ODE_BRUSSELATOR1D = 3,
+  PF_ODE_ADVDIFF2D = 4
+} pf_ode;
 
 /* Implicit LMM of Psi (Sec. 2.1): BDF1 = backward Euler; BDF2 = variable-step
  * BDF2, with BDF1 on the first two substeps after a cold start. */
@@ -68,7 +82,7 @@ enum { PF_TRANSFORM_LOG = 0, PF_TRANSFORM_IDENTITY = 1 };
 enum { PF_NOISE_ADDITIVE = 0, PF_NOISE_RELATIVE = 1 };
 
 /* Size limits of this build. */
-#define PF_MAX_OBS 16         /* m                                    */
+#define PF_MAX_OBS 32         /* m                                    */
 #define PF_MAX_SUBSTEPS 640   /* substeps per observation interval    */
 #define PF_MAX_PARTICLES (1LL << 30)
 
@@ -96,7 +110,7 @@ typedef struct {
                          observations (translated by the innovation);
                          PF_HISTORY_RESTART: cold start every interval    */
   int transform;      /* PF_TRANSFORM_*                                   */
-  int m;              /* observed components per epoch, 0 < m <= 16      */
+  int m;              /* observed components per epoch, 0 < m <= 32      */
   const int* obs_idx; /* m state indices                                  */
   int noise;          /* PF_NOISE_ADDITIVE: sd sigma_i; PF_NOISE_RELATIVE:
                          sd sigma_i * |y_i| (floored at 1e-300)          */

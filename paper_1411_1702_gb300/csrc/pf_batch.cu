@@ -412,6 +412,8 @@ static pf_status batch_new(void* stream, int cap, bool autotune, int priority, p
 static pf_status batch_add(pf_batch* b, pf_filter* f, int* slot_out) {
   if (!f) return bfail(b, PF_ERR_INVALID_ARG, "NULL filter");
   if (f->in_batch) return bfail(b, PF_ERR_INVALID_ARG, "filter already in a batch");
+  if (f->ode == PF_ODE_ADVDIFF2D)
+    return bfail(b, PF_ERR_INVALID_ARG, "2D advection-diffusion filters do not batch (one block per particle)");
   int s = -1;
   for (int i = 0; i < b->cap; ++i)
     if (!b->slot[i]) {
@@ -879,6 +881,8 @@ pf_status pf_server_open(pf_server* s, pf_ode ode, int d, int p, int64_t N, pf_l
     const pf_status cs = check_create_args(ode, d, p, N, lmm, dt, prior, opt);
     if (cs != PF_OK) return sfail(s, cs, pf_last_error(nullptr));
   }
+  if (ode == PF_ODE_ADVDIFF2D)
+    return sfail(s, PF_ERR_INVALID_ARG, "2D advection-diffusion sessions are not served (no batched kernels)");
   Session ss;
   ss.id = s->next_id++;
   ss.ode = ode; ss.d = d; ss.p = p; ss.N = N; ss.lmm = lmm; ss.dt = dt;

@@ -71,12 +71,21 @@ static pf_status cuda_fail(pf_filter* f, cudaError_t e, const char* what) {
     if (e__ != cudaSuccess) return cuda_fail(f, e__, #call); \
   } while (0)
 
+// Parameter count and fixed state dimension (0: a dimension the caller picks).
 static bool ode_dims(int ode, int* d, int* p) {
   switch (ode) {
     case PF_ODE_LINEAR2: *d = 2; *p = 2; return true;
     case PF_ODE_ROBERTSON: *d = 3; *p = 3; return true;
     case PF_ODE_BRUSSELATOR1D: *d = 64; *p = 3; return true;
+    case PF_ODE_ADVDIFF2D: *d = 0; *p = 5; return true;
   }
+  return false;
+}
+
+// M2 grids: d = nt^2 with nt odd, 3 <= nt <= 45
+static bool advdiff_dim_ok(int d) {
+  for (int nt = 3; nt <= 45; nt += 2)
+    if (nt * nt == d) return true;
   return false;
 }
 
@@ -109,6 +118,8 @@ static size_t layout(pf_filter* f, char* base) {
   f->fd.part = (double*)take(sizeof(double) * kMomentBlocks * f->fd.nrec);
   f->fd.wk = (f->ode == PF_ODE_BRUSSELATOR1D) ? (double*)take(sizeof(double) * bruss_work_doubles(N))
                                               : nullptr;
+  f->fd.x0 = (const double*)take(sizeof(double) * d);
+  f->fd.xbar = (double*)take(sizeof(double) * d);
   f->fd.ticket = (unsigned*)take(sizeof(unsigned) * 8);
   f->fd.ctrl = (Ctrl*)take(sizeof(Ctrl));
   f->ep_dev = (EpochParams*)take(sizeof(EpochParams));
@@ -164,6 +175,7 @@ cudaError_t preload_kernels() {
   if (dev < 0 || dev >= 64 || done[dev]) return cudaSuccess;
   e = preload_main_kernels();
   if (e == cudaSuccess) e = preload_bruss_kernels();
+  if (e == cudaSuccess) e = preload_ad_kernels();
   if (e == cudaSuccess) done[dev] = true;
   return e;
 }
@@ -182,6 +194,8 @@ static pf_status do_init(pf_filter* f, bool check = true) {
   for (int i = 0; i < f->p; ++i) h->phibar[i] = prior_center_phi(f, i);
   h->lw_max = 0.0;
   PF_CUDA(f, cudaMemcpyAsync(f->fd.ctrl, h, sizeof(Ctrl), cudaMemcpyHostToDevice, f->stream));
+  PF_CUDA(f, cudaMemcpyAsync(const_cast<double*>(f->fd.x0), f->x0.data(), sizeof(double) * f->d,
+                             cudaMemcpyHostToDevice, f->stream));
   PF_CUDA(f, cudaMemsetAsync(f->fd.ticket, 0, sizeof(unsigned) * 8, f->stream));
   PF_CUDA(f, launch_init(f->ode, f->fd, f->stream));
   f->hist = HistoryState{0, 0, f->t0, 0.0, 0.0};
@@ -254,7 +268,8 @@ pf_status check_create_args(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, dou
   int dd, pp;
   if (!ode_dims(ode, &dd, &pp)) return fail(nullptr, PF_ERR_INVALID_ARG, "unknown ODE");
   if (!ode_supported(ode)) return fail(nullptr, PF_ERR_INVALID_ARG, "ODE not available in this build");
-  if (d != dd || p != pp) return fail(nullptr, PF_ERR_INVALID_ARG, "d or p does not match the ODE");
+  if (p != pp || (dd > 0 ? d != dd : !advdiff_dim_ok(d)))
+    return fail(nullptr, PF_ERR_INVALID_ARG, "d or p does not match the ODE");
   if (N < 1 || N > PF_MAX_PARTICLES) return fail(nullptr, PF_ERR_INVALID_ARG, "N out of range");
   if (lmm != PF_LMM_BDF1 && lmm != PF_LMM_BDF2) return fail(nullptr, PF_ERR_INVALID_ARG, "unknown LMM");
   if (!prior || !opt) return fail(nullptr, PF_ERR_INVALID_ARG, "prior or options is NULL");
@@ -276,7 +291,7 @@ pf_status check_create_args(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, dou
   if (opt->newton_iters < 1 || opt->newton_iters > 64)
     return fail(nullptr, PF_ERR_INVALID_ARG, "newton_iters out of range");
   if (opt->m < 1 || opt->m > kMMax || !opt->obs_idx || !opt->sigma)
-    return fail(nullptr, PF_ERR_INVALID_ARG, "need 1 <= m <= 16 observed components");
+    return fail(nullptr, PF_ERR_INVALID_ARG, "need 1 <= m <= 32 observed components");
   for (int i = 0; i < opt->m; ++i) {
     if (opt->obs_idx[i] < 0 || opt->obs_idx[i] >= d)
       return fail(nullptr, PF_ERR_INVALID_ARG, "observation index out of range");
@@ -342,7 +357,7 @@ pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double 
   for (int i = 0; i < p; ++i) {
     f->prior_kind[i] = prior->kind[i]; f->prior_lo[i] = prior->lo[i]; f->prior_hi[i] = prior->hi[i];
   }
-  for (int i = 0; i < d; ++i) f->x0[i] = prior->x0[i];
+  f->x0.assign(prior->x0, prior->x0 + d);
 
   FilterDev& fd = f->fd;
   fd.N = N; fd.ode = ode; fd.d = d; fd.p = p; fd.m = f->m; fd.K = f->K; fd.transform = f->transform;
@@ -355,7 +370,6 @@ pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double 
     fd.prior_lo[i] = i < p ? f->prior_lo[i] : 0.0;
     fd.prior_hi[i] = i < p ? f->prior_hi[i] : 0.0;
   }
-  for (int i = 0; i < kDMax; ++i) fd.x0[i] = i < d ? f->x0[i] : 0.0;
 
   pf_status st = PF_OK;
   cudaError_t e;
@@ -466,14 +480,17 @@ pf_status pf_assimilate(pf_filter* f, double t_k, const double* y_k) {
 pf_status pf_estimates(const pf_filter* cf, double* theta_bar, double* C, double* x_bar) {
   pf_filter* f = const_cast<pf_filter*>(cf);
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
-  pf_status st = read_ctrl(f);
-  if (st != PF_OK) return st;
+  PF_CUDA(f, cudaMemcpyAsync(f->ctrl_host, f->fd.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, f->stream));
+  if (x_bar)
+    PF_CUDA(f, cudaMemcpyAsync(x_bar, f->fd.xbar, sizeof(double) * f->d, cudaMemcpyDeviceToHost,
+                               f->stream));
+  PF_CUDA(f, cudaStreamSynchronize(f->stream));
+  f->d2h_bytes += sizeof(Ctrl) + (x_bar ? sizeof(double) * f->d : 0);
   const Ctrl* h = f->ctrl_host;
   if (theta_bar) for (int i = 0; i < f->p; ++i) theta_bar[i] = h->phibar[i];
   if (C)
     for (int i = 0; i < f->p; ++i)
       for (int j = 0; j < f->p; ++j) C[i * f->p + j] = h->C[i * kPMax + j];
-  if (x_bar) for (int i = 0; i < f->d; ++i) x_bar[i] = h->xbar[i];
   return PF_OK;
 }
 

@@ -7,6 +7,7 @@
 //     phi[i*N + n]                           i < p   (working-space parameter)
 //     lw[n]                                          (unnormalised log weight)
 //   work arrays: ll1[N], lg[N], c[N] (FP64), idx[N] (int32)
+//   x0[d] (the fixed initial state) and xbar[d] (the committed weighted mean)
 //   per-block scratch, the control block and the epoch parameter block.
 #pragma once
 #include <cstdint>
@@ -17,8 +18,8 @@
 
 namespace pfg {
 
-constexpr int kDMax = 64;
-constexpr int kPMax = 4;
+constexpr int kDMax = 64;            // largest state kept in registers (small models)
+constexpr int kPMax = 5;
 constexpr int kMMax = PF_MAX_OBS;
 constexpr int kSMax = PF_MAX_SUBSTEPS;
 constexpr int kScanItems = 4;        // elements per thread in the scan
@@ -67,7 +68,7 @@ struct Ctrl {
   double logW;          // log sum exp(lw) of the committed weights
   double ess;
   double theta_mean[kPMax];
-  double xbar[kDMax];
+  double wsum;          // sum of exp(lw - lw_max) of the committed weights
   double lg_max;        // max log fitness weight of the running epoch
   double lw_max;        // max new log weight of the running epoch
   double c_total;       // total of the cumulative fitness weights
@@ -108,7 +109,8 @@ struct FilterDev {
   int nrec;
   int prior_kind[kPMax];
   double prior_lo[kPMax], prior_hi[kPMax];
-  double x0[kDMax];
+  const double* x0; // fixed initial state (d)
+  double* xbar;     // committed weighted mean of x (d)
 };
 
 // ---------------------------------------------------------------- Philox

@@ -29,7 +29,7 @@ struct pf_filter {
   double sigma[pfg::kMMax];
   int prior_kind[pfg::kPMax];
   double prior_lo[pfg::kPMax], prior_hi[pfg::kPMax];
-  double x0[pfg::kDMax];
+  std::vector<double> x0;
   double t0;
   // CUDA resources
   cudaStream_t stream = nullptr;

@@ -130,10 +130,12 @@ __device__ __forceinline__ void init_body(const FilterDev& fd, int vb) {
       dst.phi[i * N + n] = phi;
     }
   }
-  for (int i = 0; i < D; ++i) {
-    dst.x[i * N + n] = fd.x0[i];
-    dst.h1[i * N + n] = fd.x0[i];
-    dst.h2[i * N + n] = fd.x0[i];
+  const int dd = D > 0 ? D : fd.d;  // D = 0: the state dimension is a runtime choice
+  for (int i = 0; i < dd; ++i) {
+    const double v = fd.x0[i];
+    dst.x[i * N + n] = v;
+    dst.h1[i * N + n] = v;
+    dst.h2[i * N + n] = v;
   }
   dst.lw[n] = 0.0;
 }
@@ -408,19 +410,19 @@ __device__ __forceinline__ void moments_body(const FilterDev& fd, int is_init, i
     const double e = exp(lw - M);
     acc[Lay::kS0] += e;
     acc[Lay::kW2] = fma(e, e, acc[Lay::kW2]);
-    double ph[P];
+    double dp[P];
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-      ph[i] = nw.phi[i * N + n];
-      acc[Lay::kS1 + i] = fma(e, ph[i], acc[Lay::kS1 + i]);
+      dp[i] = nw.phi[i * N + n] - c[i];
+      acc[Lay::kS1 + i] = fma(e, dp[i], acc[Lay::kS1 + i]);
     }
     int q = Lay::kS2;
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-      const double di = e * (ph[i] - c[i]);
+      const double di = e * dp[i];
 #pragma unroll
       for (int j = i; j < P; ++j) {
-        acc[q] = fma(di, ph[j] - c[j], acc[q]);
+        acc[q] = fma(di, dp[j], acc[q]);
         ++q;
       }
     }
@@ -438,17 +440,21 @@ __device__ __forceinline__ void moments_body(const FilterDev& fd, int is_init, i
   block_sum_vec<NV>(acc, s_part, s_tot);
   if (threadIdx.x != 0) return;
   const double S0 = s_tot[Lay::kS0];
-  double mean[P], C[kPMax * kPMax], L[kPMax * kPMax];
+  // moments about the shift c (the previous mean): the first moment of the
+  // differences gives the mean's displacement to full relative precision, so
+  // C = E[(phi - c)(phi - c)^T] - m m^T loses only eps E[|phi - c|^2]
+  double mean[P], m1[P], C[kPMax * kPMax], L[kPMax * kPMax];
   for (int i = 0; i < kPMax * kPMax; ++i) C[i] = 0.0;
   bool ok = S0 > 0.0;
   for (int i = 0; i < P; ++i) {
-    mean[i] = s_tot[Lay::kS1 + i] / S0;
+    m1[i] = s_tot[Lay::kS1 + i] / S0;
+    mean[i] = c[i] + m1[i];
     ok = ok && finite_bits(mean[i]);
   }
   int q = Lay::kS2;
   for (int i = 0; i < P; ++i) {
     for (int j = i; j < P; ++j) {
-      const double v = s_tot[q++] / S0 - (mean[i] - c[i]) * (mean[j] - c[j]);
+      const double v = s_tot[q++] / S0 - m1[i] * m1[j];
       C[i * kPMax + j] = v;
       C[j * kPMax + i] = v;
       ok = ok && finite_bits(v);
@@ -465,7 +471,8 @@ __device__ __forceinline__ void moments_body(const FilterDev& fd, int is_init, i
     ctrl->C[i] = C[i];
     ctrl->L[i] = L[i];
   }
-  for (int i = 0; i < D; ++i) ctrl->xbar[i] = s_tot[Lay::kSx + i] / S0;
+  for (int i = 0; i < D; ++i) fd.xbar[i] = s_tot[Lay::kSx + i] / S0;
+  ctrl->wsum = S0;
   ctrl->ess = S0 * S0 / s_tot[Lay::kW2];
   ctrl->logW = M + log(S0);
   ctrl->cur = 1 - cur;
@@ -567,6 +574,30 @@ __global__ void k_set_moments(const __grid_constant__ FilterDev fd) {
   for (int i = 0; i < kPMax * kPMax; ++i) fd.ctrl->L[i] = L[i];
 }
 
+// Weighted mean of x for states too large for the per-thread moment records
+// (D = 0 moments): one block per component row of the newly committed
+// ensemble, w_n = exp(lw_n - lw_max) / wsum with the moments' own total.
+__global__ void __launch_bounds__(kMomentThreads) k_xbar(const __grid_constant__ FilterDev fd) {
+  __shared__ double s_red[32];
+  const Ctrl* ctrl = fd.ctrl;
+  if (ctrl->status != PF_OK) return;
+  const Ensemble E = committed(fd, ctrl->cur);
+  const int64_t N = fd.N;
+  const double M = ctrl->lw_max;
+  for (int i = blockIdx.x; i < fd.d; i += gridDim.x) {
+    const double* xi = E.x + (int64_t)i * N;
+    double acc = 0.0;
+    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+      const double lw = E.lw[n];
+      if (is_neg_inf(lw)) continue;
+      acc = fma(exp(lw - M), xi[n], acc);
+    }
+    acc = block_sum(acc, s_red);
+    if (threadIdx.x == 0) fd.xbar[i] = acc / ctrl->wsum;
+    __syncthreads();
+  }
+}
+
 // ========================================================= batch of filters
 // Every batched launch reads its block's (filter, virtual block) from a tile
 // table and the filter's descriptor through a read-only pointer.  Tiles of
@@ -658,12 +689,13 @@ int moment_record_size(int ode) {
     case PF_ODE_LINEAR2: return moment_nrec<2, 2>();
     case PF_ODE_ROBERTSON: return moment_nrec<3, 3>();
     case PF_ODE_BRUSSELATOR1D: return moment_nrec<64, 3>();
+    case PF_ODE_ADVDIFF2D: return moment_nrec<0, 5>();
   }
   return -1;
 }
 
 int max_grid_blocks(int64_t N) {
-  const int64_t a = (N + 31) / 32;  // at least as many as any stage launch
+  const int64_t a = N;  // at least as many as any stage launch (one block per particle for M2)
   const int64_t b = (N + kScanTile - 1) / kScanTile;
   const int64_t c = (N + kResampleThreads - 1) / kResampleThreads;
   int64_t m = a > b ? a : b;
@@ -678,6 +710,7 @@ int phase_blocks(int phase, int ode, int64_t N) {
     case kPhaseInit: return (int)((N + kInitThreads - 1) / kInitThreads);
     case kPhaseStage1:
     case kPhaseStage2:
+      if (ode == PF_ODE_ADVDIFF2D) return (int)N;
       return ode == PF_ODE_BRUSSELATOR1D ? bruss_stage_blocks(N)
                                          : (int)((N + kSmallThreads - 1) / kSmallThreads);
     case kPhaseScanTile: return scan_tiles(N);
@@ -749,8 +782,44 @@ static cudaError_t launch_epoch_bruss(const FilterDev& fd, const EpochParams* ep
   return cudaGetLastError();
 }
 
+// M2: the stage kernels live in pf_advdiff.cu; the moments take the D = 0
+// record and x-bar its own kernel
+static int xbar_blocks(const FilterDev& fd) { return fd.d < 1024 ? fd.d : 1024; }
+
+static cudaError_t launch_epoch_ad(const FilterDev& fd, const EpochParams* ep, int S,
+                                   cudaStream_t st, cudaEvent_t* marks) {
+  const int64_t N = fd.N;
+  const int ode = PF_ODE_ADVDIFF2D;
+  auto mark = [&](int i) {
+    if (marks) cudaEventRecord(marks[i], st);
+  };
+  cudaError_t e;
+  mark(0);
+  if ((e = launch_ad_stage(1, fd, ep, S, st)) != cudaSuccess) return e;
+  mark(1);
+  k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, ode, N), kScanThreads, 0, st>>>(fd);
+  mark(2);
+  k_scan_add<<<(unsigned)phase_blocks(kPhaseScanAdd, ode, N), 256, 0, st>>>(fd);
+  mark(3);
+  k_resample<<<(unsigned)phase_blocks(kPhaseResample, ode, N), kResampleThreads, 0, st>>>(fd, ep);
+  mark(4);
+  if ((e = launch_ad_stage(2, fd, ep, S, st)) != cudaSuccess) return e;
+  mark(5);
+  k_moments<0, 5><<<phase_blocks(kPhaseMoments, ode, N), kMomentThreads, 0, st>>>(fd, 0);
+  k_xbar<<<xbar_blocks(fd), kMomentThreads, 0, st>>>(fd);
+  mark(6);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init(int ode, const FilterDev& fd, cudaStream_t st) {
   switch (ode) {
+    case PF_ODE_ADVDIFF2D: {
+      const int64_t N = fd.N;
+      k_init<0, 5><<<phase_blocks(kPhaseInit, ode, N), kInitThreads, 0, st>>>(fd);
+      k_moments<0, 5><<<phase_blocks(kPhaseMoments, ode, N), kMomentThreads, 0, st>>>(fd, 1);
+      k_xbar<<<xbar_blocks(fd), kMomentThreads, 0, st>>>(fd);
+      return cudaGetLastError();
+    }
     case PF_ODE_LINEAR2: return launch_init_t<Linear2>(fd, st);
     case PF_ODE_ROBERTSON: return launch_init_t<Robertson>(fd, st);
     case PF_ODE_BRUSSELATOR1D: {
@@ -769,6 +838,7 @@ cudaError_t launch_epoch(int ode, const FilterDev& fd, const EpochParams* ep, in
     case PF_ODE_LINEAR2: return launch_epoch_t<Linear2>(fd, ep, S, st, marks);
     case PF_ODE_ROBERTSON: return launch_epoch_t<Robertson>(fd, ep, S, st, marks);
     case PF_ODE_BRUSSELATOR1D: return launch_epoch_bruss(fd, ep, S, st, marks);
+    case PF_ODE_ADVDIFF2D: return launch_epoch_ad(fd, ep, S, st, marks);
   }
   return cudaErrorInvalidValue;
 }
@@ -780,6 +850,7 @@ int kernels_per_epoch(int ode) {
 
 cudaError_t launch_theta_mean(const FilterDev& fd, cudaStream_t st) {
   if (fd.p == 2) k_theta_mean<2><<<1, kMomentThreads, 0, st>>>(fd);
+  else if (fd.p == 5) k_theta_mean<5><<<1, kMomentThreads, 0, st>>>(fd);
   else k_theta_mean<3><<<1, kMomentThreads, 0, st>>>(fd);
   return cudaGetLastError();
 }
@@ -802,7 +873,9 @@ cudaError_t preload_main_kernels() {
       (const void*)k_stage2<Linear2>, (const void*)k_stage2<Robertson>,
       (const void*)k_moments<2, 2>, (const void*)k_moments<3, 3>, (const void*)k_moments<64, 3>,
       (const void*)k_scan_tile, (const void*)k_scan_add, (const void*)k_resample,
-      (const void*)k_theta_mean<2>, (const void*)k_theta_mean<3>, (const void*)k_set_moments,
+      (const void*)k_theta_mean<2>, (const void*)k_theta_mean<3>, (const void*)k_theta_mean<5>,
+      (const void*)k_set_moments, (const void*)k_init<0, 5>, (const void*)k_moments<0, 5>,
+      (const void*)k_xbar,
       (const void*)k_batch_init, (const void*)k_batch_stage<Linear2, 1>,
       (const void*)k_batch_stage<Linear2, 2>, (const void*)k_batch_stage<Robertson, 1>,
       (const void*)k_batch_stage<Robertson, 2>, (const void*)k_batch_scan_tile,
@@ -817,7 +890,8 @@ cudaError_t preload_main_kernels() {
 }
 
 bool ode_supported(int ode) {
-  return ode == PF_ODE_LINEAR2 || ode == PF_ODE_ROBERTSON || ode == PF_ODE_BRUSSELATOR1D;
+  return ode == PF_ODE_LINEAR2 || ode == PF_ODE_ROBERTSON || ode == PF_ODE_BRUSSELATOR1D ||
+         ode == PF_ODE_ADVDIFF2D;
 }
 
 cudaError_t launch_set_moments(const FilterDev& fd, cudaStream_t st) {

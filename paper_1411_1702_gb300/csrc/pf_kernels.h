@@ -59,6 +59,13 @@ cudaError_t preload_kernels();
 cudaError_t launch_bruss_stage(int stage, const FilterDev& fd, const EpochParams* ep, int S,
                                cudaStream_t st);
 size_t bruss_work_doubles(int64_t N);
+// 2D advection-diffusion stage kernels (pf_advdiff.cu): one block per
+// particle, the whole state in shared memory.
+cudaError_t launch_ad_stage(int stage, const FilterDev& fd, const EpochParams* ep, int S,
+                            cudaStream_t st);
+size_t ad_stage_smem(int d, int S, int stage);
+int ad_threads(int nt);
+cudaError_t preload_ad_kernels();
 int max_grid_blocks(int64_t N);
 int scan_tiles(int64_t N);
 int kernels_per_epoch(int ode);

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libpf_gb300.so")
 
 PF_OK, PF_ERR_INVALID_ARG, PF_ERR_OOM, PF_ERR_BUDGET, PF_ERR_CUDA = 0, 1, 2, 3, 4
 PF_ERR_DEGENERATE, PF_ERR_NUMERIC, PF_ERR_TIMEOUT, PF_ERR_STATE = 5, 6, 7, 8
-PF_ODE_LINEAR2, PF_ODE_ROBERTSON, PF_ODE_BRUSSELATOR1D = 1, 2, 3
+PF_ODE_LINEAR2, PF_ODE_ROBERTSON, PF_ODE_BRUSSELATOR1D, PF_ODE_ADVDIFF2D = 1, 2, 3, 4
 PF_LMM_BDF1, PF_LMM_BDF2 = 1, 2
 MAX_SUBSTEPS = 640
 

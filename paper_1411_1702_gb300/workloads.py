@@ -334,6 +334,7 @@ def advdiff(n: int = 20, N: int = 5000, T: int = 30, seed: int = 0, m: int = 20)
     d = nt * nt
     x0 = advdiff_x0(n)
     rng = np.random.default_rng([seed, 0xAD, n])
+    m = min(m, d)
     obs_idx = [int(i) for i in np.sort(rng.choice(d, size=m, replace=False))]
     t_obs = np.arange(1, T + 1, dtype=np.float64)
     x_true = advdiff_exact(n, theta, x0, t_obs)
