@@ -68,6 +68,12 @@ STAGE2_FLOPS_PER_SUBSTEP = {
 STAGE2_KERNEL = {"robertson": "k_stage2<Robertson>", "linear2": "k_stage2<Linear2>",
                  "brusselator": "k_bstage2", "advdiff20": "k_adstage<2>",
                  "advdiff40": "k_adstage<2>"}
+# DRAM bytes (read + write) of one stage-2 launch from an ncu capture of the
+# same command on a GB300 (profiles/ names each capture); None where no capture
+# of the kernel as it stands exists.
+STAGE2_TRAFFIC = {"robertson": 11550976 + 0,
+                  "brusselator": 11188473344 + 10732750592,
+                  "advdiff20": 2615808 + 336896}
 # The paper's own number for the same workload, where it has one: Table 3's
 # 2D advection-diffusion runs (BDF2, h = 0.1, N = 5000, 30 unit intervals,
 # 8 MATLAB workers on an i7-3820), converted to particle-LMM-steps/s at 600
@@ -333,7 +339,7 @@ def run_ours(args, w):
         "roofline": {"bound": "alu", "kernel": STAGE2_KERNEL[w.name], "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                     "traffic": None,
+                     "traffic": STAGE2_TRAFFIC.get(w.name),
                      "peak_source": "2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (nominal GB300 FP64)"},
         "kernel_share": shares,
         "kernel_ms_per_step": {k2: v[0] / max(1, v[1]) for k2, v in ktimes.items()},
