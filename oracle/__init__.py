@@ -24,7 +24,10 @@ _lock = threading.Lock()
 _lib = None
 
 DMAX, PMAX, MMAX, SMAX = 2025, 8, 32, 4096
-LINEAR2, ROBERTSON, BRUSSELATOR, ADVDIFF = 1, 2, 3, 4
+LINEAR2, ROBERTSON, BRUSSELATOR, ADVDIFF, MICHAELIS = 1, 2, 3, 4, 5
+LMM_BDF1, LMM_BDF2, LMM_BDF3 = 1, 2, 3
+LMM_AM1, LMM_AM2, LMM_AM3 = 11, 12, 13
+LMM_AB1, LMM_AB2, LMM_AB3 = 21, 22, 23
 RNG_INIT, RNG_THETA, RNG_INNOV, RNG_RESAMPLE = 1, 2, 3, 4
 UNIFORM, LOGUNIFORM = 0, 1
 SPACING_UNIFORM, SPACING_GEOMETRIC = 0, 1
@@ -65,7 +68,9 @@ class Config(C.Structure):
 class Substep(C.Structure):
     _fields_ = [("kind", C.c_int), ("h", C.c_double), ("gamma", C.c_double),
                 ("rho1", C.c_double), ("rho2", C.c_double), ("pi0", C.c_double),
-                ("pi1", C.c_double), ("pi2", C.c_double), ("mu", C.c_double)]
+                ("pi1", C.c_double), ("pi2", C.c_double), ("mu", C.c_double),
+                ("rho3", C.c_double), ("pi3", C.c_double), ("beta", C.c_double * 3),
+                ("bab", C.c_double * 3), ("tn", C.c_double), ("t", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -81,7 +86,10 @@ def lib():
             "or_philox4x32_10": (None, [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
             "or_uniform": (C.c_double, [C.c_uint64, C.c_uint32, C.c_int, C.c_uint32, C.c_uint32, C.c_int]),
             "or_normal": (C.c_double, [C.c_uint64, C.c_uint32, C.c_int, C.c_uint32, C.c_uint32, C.c_int]),
-            "or_ode_f": (None, [C.c_int, C.c_int, _dp, _dp, _dp]),
+            "or_ode_f": (None, [C.c_int, C.c_int, _dp, C.c_double, _dp, _dp]),
+            "or_mm_constants": (None, [_dp]),
+            "or_mm_input": (C.c_double, [C.c_double]),
+            "or_lmm_coefficients": (C.c_int, [C.c_int, C.c_double, C.POINTER(Substep)]),
             "or_ode_jac": (None, [C.c_int, C.c_int, _dp, _dp, _dp]),
             "or_ode_dims": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
             "or_ode_check_dim": (C.c_int, [C.c_int, C.c_int]),
@@ -160,15 +168,26 @@ def ode_check_dim(ode, d):
     return lib().or_ode_check_dim(ode, int(d)) == 0
 
 
-def ode_f(ode, theta, x):
+def ode_f(ode, theta, x, t=0.0):
     xx = np.ascontiguousarray(x, dtype=np.float64)
     d = len(xx)
     if not ode_check_dim(ode, d):
         raise ValueError((ode, d))
     th = np.ascontiguousarray(theta, dtype=np.float64)
     f = np.zeros(d)
-    lib().or_ode_f(ode, d, _d(th), _d(xx), _d(f))
+    lib().or_ode_f(ode, d, _d(th), float(t), _d(xx), _d(f))
     return f
+
+
+def mm_constants():
+    """M1's known constants (lambda, c0, A0, A, t0, tau) as the oracle reads them."""
+    out = np.zeros(6)
+    lib().or_mm_constants(_d(out))
+    return dict(zip(("lam", "c0", "A0", "A", "t0", "tau"), out.tolist()))
+
+
+def mm_input(t):
+    return lib().or_mm_input(float(t))
 
 
 def ode_jac(ode, theta, x):
@@ -214,10 +233,18 @@ def bdf_coefficients(kind, h0, h1=0.0, h2=0.0):
     return s
 
 
+def lmm_coefficients(kind, h):
+    s = Substep()
+    if lib().or_lmm_coefficients(kind, h, C.byref(s)) != 0:
+        raise ValueError(kind)
+    return s
+
+
 def substep_dicts(tab, S):
     return [dict(kind=tab[i].kind, h=tab[i].h, gamma=tab[i].gamma, rho1=tab[i].rho1,
                  rho2=tab[i].rho2, pi0=tab[i].pi0, pi1=tab[i].pi1, pi2=tab[i].pi2,
-                 mu=tab[i].mu) for i in range(S)]
+                 mu=tab[i].mu, rho3=tab[i].rho3, pi3=tab[i].pi3, beta=list(tab[i].beta),
+                 bab=list(tab[i].bab), tn=tab[i].tn, t=tab[i].t) for i in range(S)]
 
 
 def build_substeps(cfg: Config, t_prev, t_next, depth, hprev1, hprev2):

@@ -103,7 +103,21 @@ double or_normal(uint64_t seed, uint32_t stream, int purpose, uint32_t n, uint32
 /*              u_i' = A + u_i^2 v_i - (B+1) u_i + alpha 33^2 (u_{i-1}-2u_i+u_{i+1}), */
 /*              v_i' = B u_i - u_i^2 v_i + alpha 33^2 (v_{i-1}-2v_i+v_{i+1}),  */
 /*              state interleaved (u_0, v_0, u_1, v_1, ...).                  */
+/*  MICHAELIS:  M1 of Sec. 2.1, three compartments with Michaelis-Menten      */
+/*              fluxes and the input Phi(t) = A0 + A (t - t0)_+ e^{-(t-t0)/tau}: */
+/*              x1' = Phi(t) - V1 x1/(x1+k1),                                  */
+/*              x2' = V1 x1/(x1+k1) - V2 x2/(x2+k2),                           */
+/*              x3' = V2 x2/(x2+k2) - lambda (x3 - c0),                        */
+/*              theta = (V1, V2, k1, k2).  The paper calls lambda, c0, A0, A,  */
+/*              t0, tau known but prints no values; the reading takes          */
+/*              lambda = 0.5, c0 = 2, A0 = 1, A = 0.5, t0 = 0.5, tau = 4.      */
 /* ------------------------------------------------------------------------ */
+#define MM_LAMBDA 0.5
+#define MM_C0 2.0
+#define MM_A0 1.0
+#define MM_A 0.5
+#define MM_T0 0.5
+#define MM_TAU 4.0
 #define BR_POINTS 32
 #define BR_UB 1.0
 #define BR_VB 3.0
@@ -114,8 +128,21 @@ int or_ode_dims(int ode, int* d, int* p) {
     case OR_ROBERTSON: *d = 3; *p = 3; return 0;
     case OR_BRUSSELATOR: *d = 2 * BR_POINTS; *p = 3; return 0;
     case OR_ADVDIFF: *d = 0; *p = 5; return 0;
+    case OR_MICHAELIS: *d = 3; *p = 4; return 0;
   }
   return -1;
+}
+
+void or_mm_constants(double* out6) {
+  out6[0] = MM_LAMBDA; out6[1] = MM_C0; out6[2] = MM_A0;
+  out6[3] = MM_A; out6[4] = MM_T0; out6[5] = MM_TAU;
+}
+
+/* the input function of M1: Phi(t) = A0 + A (t - t0)_+ exp(-(t - t0)/tau) */
+double or_mm_input(double t) {
+  double s = t - MM_T0;
+  if (!(s > 0.0)) return MM_A0;
+  return MM_A0 + MM_A * s * exp(-s / MM_TAU);
 }
 
 /* side of the M2 grid for state dimension d, or 0 if d is not an odd square */
@@ -174,8 +201,15 @@ static void ad_rhs(int d, const double* th, const double* x, double* f) {
   free(b1);
 }
 
-void or_ode_f(int ode, int d, const double* th, const double* x, double* f) {
-  if (ode == OR_ADVDIFF) {
+void or_ode_f(int ode, int d, const double* th, double t, const double* x, double* f) {
+  if (ode == OR_MICHAELIS) {
+    double V1 = th[0], V2 = th[1], k1 = th[2], k2 = th[3];
+    double flux1 = V1 * x[0] / (x[0] + k1);
+    double flux2 = V2 * x[1] / (x[1] + k2);
+    f[0] = or_mm_input(t) - flux1;
+    f[1] = flux1 - flux2;
+    f[2] = flux2 - MM_LAMBDA * (x[2] - MM_C0);
+  } else if (ode == OR_ADVDIFF) {
     ad_rhs(d, th, x, f);
   } else if (ode == OR_LINEAR2) {
     f[0] = -th[0] * x[0] + th[1] * x[1];
@@ -203,7 +237,15 @@ void or_ode_f(int ode, int d, const double* th, const double* x, double* f) {
  * is L applied to the j-th unit vector. */
 void or_ode_jac(int ode, int d, const double* th, const double* x, double* J) {
   for (int i = 0; i < d * d; ++i) J[i] = 0.0;
-  if (ode == OR_ADVDIFF) {
+  if (ode == OR_MICHAELIS) {
+    /* d/dx [V x/(x+k)] = V k/(x+k)^2; the input does not depend on x */
+    double V1 = th[0], V2 = th[1], k1 = th[2], k2 = th[3];
+    double a = V1 * k1 / ((x[0] + k1) * (x[0] + k1));
+    double b = V2 * k2 / ((x[1] + k2) * (x[1] + k2));
+    J[0] = -a;
+    J[3] = a;  J[4] = -b;
+    J[7] = b;  J[8] = -MM_LAMBDA;
+  } else if (ode == OR_ADVDIFF) {
     double* e = (double*)calloc((size_t)d * 2, sizeof(double));
     double* col = e + d;
     for (int j = 0; j < d; ++j) {
@@ -363,14 +405,18 @@ static double lagrange_dbasis_at0(const double* s, int m, int j) {
   return total;
 }
 
-/* value at 0 of the j-th Lagrange basis polynomial on nodes s[0..m-1] */
-static double lagrange_basis_at0(const double* s, int m, int j) {
+/* value at z of the j-th Lagrange basis polynomial on nodes s[0..m-1] */
+static double lagrange_basis_at(const double* s, int m, int j, double z) {
   double v = 1.0;
   for (int k = 0; k < m; ++k) {
     if (k == j) continue;
-    v *= (0.0 - s[k]) / (s[j] - s[k]);
+    v *= (z - s[k]) / (s[j] - s[k]);
   }
   return v;
+}
+
+static double lagrange_basis_at0(const double* s, int m, int j) {
+  return lagrange_basis_at(s, m, j, 0.0);
 }
 
 /* Coefficients of one substep.
@@ -423,6 +469,115 @@ int or_bdf_coefficients(int kind, double h0, double h1, double h2, or_substep* o
   return -1;
 }
 
+/* ------------------------------------------------------------------------ */
+/* BDF3 and the Adams families at constant step h (the first three methods  */
+/* of each family, Sec. 3, Tables 1-2).  Nodes are measured from t_{n+1}.   */
+/*  AB_q: x_{n+1} = x_n + integral over [t_n, t_{n+1}] of the polynomial     */
+/*        through f_n, ..., f_{n-q+1} (nodes -h, ..., -qh).                  */
+/*  AM_q: the same with the polynomial through f_{n+1}, ..., f_{n-q+2}       */
+/*        (nodes 0, ..., -(q-1)h); implicit in f_{n+1}.                     */
+/*  BDF3: the derivative at t_{n+1} of the cubic through x_{n+1}, ...,      */
+/*        x_{n-2} equals f_{n+1}.  Its predictor (reading) is the cubic     */
+/*        through x_n, x_{n-1}, x_{n-2} with slope f(t_n, x_n) at t_n, which */
+/*        needs no more stored history than BDF2.                           */
+/* Milne's device pairs each corrector with a predictor of the same order q */
+/* (AM_q with AB_q; BDF3 with the cubic above): with Cc, Cp the residuals   */
+/* of the two formulas on y(s) = s^{q+1}/(q+1)!, the corrector's local      */
+/* error is Cc/(Cp - Cc) (x_corr - x_pred).  An AB_q step is the predictor  */
+/* itself, so its error is Cp/(Cp - Cc) (x_corr - x_pred), with AM_q        */
+/* evaluated once at the new point.                                        */
+/* ------------------------------------------------------------------------ */
+
+/* s^k / k! */
+static double mono(double s, int k) {
+  double v = 1.0;
+  for (int i = 1; i <= k; ++i) v *= s / (double)i;
+  return v;
+}
+
+/* integral over [-h, 0] of the j-th Lagrange basis polynomial on nodes
+ * s[0..m-1]; Simpson's rule is exact for the degrees used here (m - 1 <= 2) */
+static double lagrange_basis_integral(const double* s, int m, int j, double h) {
+  return (h / 6.0) * (lagrange_basis_at(s, m, j, -h) + 4.0 * lagrange_basis_at(s, m, j, -0.5 * h) +
+                      lagrange_basis_at(s, m, j, 0.0));
+}
+
+/* AB_q weights of f_n, ..., f_{n-q+1} and AM_q weights of f_{n+1}, ..., f_{n-q+2} */
+static void adams_weights(int q, double h, double* bab, double* beta) {
+  double sb[3], sm[3];
+  for (int j = 0; j < q; ++j) {
+    sb[j] = -(double)(j + 1) * h;
+    sm[j] = -(double)j * h;
+  }
+  for (int j = 0; j < 3; ++j) {
+    bab[j] = j < q ? lagrange_basis_integral(sb, q, j, h) : 0.0;
+    beta[j] = j < q ? lagrange_basis_integral(sm, q, j, h) : 0.0;
+  }
+}
+
+/* residuals on y = s^{q+1}/(q+1)! of AB_q (Cp) and AM_q (Cc) */
+static void adams_error_constants(int q, double h, const double* bab, const double* beta,
+                                  double* Cp, double* Cc) {
+  double p = mono(0.0, q + 1) - mono(-h, q + 1);
+  double c = p;
+  for (int j = 0; j < q; ++j) {
+    p -= bab[j] * mono(-(double)(j + 1) * h, q);
+    c -= beta[j] * mono(-(double)j * h, q);
+  }
+  *Cp = p;
+  *Cc = c;
+}
+
+int or_lmm_coefficients(int kind, double h, or_substep* out) {
+  memset(out, 0, sizeof(*out));
+  out->kind = kind;
+  out->h = h;
+  if (!(h > 0.0)) return -1;
+  if (kind == 3) {
+    /* corrector: derivative at 0 of the cubic through nodes 0, -h, -2h, -3h */
+    double s[4] = {0.0, -h, -2.0 * h, -3.0 * h};
+    double l[4];
+    for (int j = 0; j < 4; ++j) l[j] = lagrange_dbasis_at0(s, 4, j);
+    out->gamma = 1.0 / l[0];
+    out->rho1 = -l[1] / l[0];
+    out->rho2 = -l[2] / l[0];
+    out->rho3 = -l[3] / l[0];
+    /* predictor: weights of x(-h), x(-2h), x(-3h), x'(-h) reproducing the
+     * value at 0 of every cubic (a 4 x 4 linear system, row k = monomial s^k) */
+    double A[16], e[4] = {1.0, 0.0, 0.0, 0.0}, w[4];
+    for (int k = 0; k < 4; ++k) {
+      A[k * 4 + 0] = pow(-h, k);
+      A[k * 4 + 1] = pow(-2.0 * h, k);
+      A[k * 4 + 2] = pow(-3.0 * h, k);
+      A[k * 4 + 3] = k == 0 ? 0.0 : (double)k * pow(-h, k - 1);
+    }
+    if (or_lu_solve(4, A, e, w) != 0) return -1;
+    out->pi0 = w[0];
+    out->pi1 = w[1];
+    out->pi2 = w[2];
+    out->pi3 = w[3];
+    double Cc = mono(0.0, 4) - (out->rho1 * mono(-h, 4) + out->rho2 * mono(-2.0 * h, 4) +
+                                out->rho3 * mono(-3.0 * h, 4) + out->gamma * mono(0.0, 3));
+    double Cp = mono(0.0, 4) - (out->pi0 * mono(-h, 4) + out->pi1 * mono(-2.0 * h, 4) +
+                                out->pi2 * mono(-3.0 * h, 4) + out->pi3 * mono(-h, 3));
+    out->mu = Cc / (Cp - Cc);
+    return 0;
+  }
+  int q = kind % 10;
+  if ((kind / 10 != 1 && kind / 10 != 2) || q < 1 || q > 3) return -1;
+  adams_weights(q, h, out->bab, out->beta);
+  out->gamma = out->beta[0];
+  double Cp, Cc;
+  adams_error_constants(q, h, out->bab, out->beta, &Cp, &Cc);
+  out->mu = (kind / 10 == 1) ? Cc / (Cp - Cc) : Cp / (Cp - Cc);
+  return 0;
+}
+
+static int or_lmm_valid(int lmm) {
+  return lmm == OR_LMM_BDF1 || lmm == OR_LMM_BDF2 || lmm == OR_LMM_BDF3 ||
+         (lmm >= OR_LMM_AM1 && lmm <= OR_LMM_AM3) || (lmm >= OR_LMM_AB1 && lmm <= OR_LMM_AB3);
+}
+
 /* Substep grid of one observation interval (t_prev, t_next] and the BDF kind
  * of every substep (Sec. 3.1: the same fixed steps for every particle).
  *  UNIFORM:   S = round((t_next - t_prev)/dt), which must be an integer to
@@ -431,12 +586,17 @@ int or_bdf_coefficients(int kind, double h0, double h1, double h2, or_substep* o
  *             or, from t_prev = 0, t_next (q0^i - 1)/(q0^S - 1).
  *  The last substep time is t_next exactly; h_i is the difference of times.
  * History depth = number of stored past points beyond x_n (0, 1 or 2).  A BDF2
- * step needs depth 2; otherwise the step is BDF1.  A step ratio h_n/h_{n-1} >= 2
- * forces a cold start (depth 0), keeping variable-step BDF2 zero-stable. */
+ * or BDF3 step needs depth 2; otherwise the step is BDF1.  An Adams method of
+ * order q runs at order min(q, depth + 1).  A step ratio h_n/h_{n-1} >= 2
+ * forces a cold start (depth 0), keeping variable-step BDF2 zero-stable.
+ * BDF3 and the Adams families need uniform spacing (constant step). */
 int or_build_substeps(const or_config* cfg, double t_prev, double t_next, int depth,
                       double hprev1, double hprev2, or_substep* tab, int max_steps,
                       int* depth_out) {
   if (!(t_next > t_prev)) return -1;
+  if (!or_lmm_valid(cfg->lmm)) return -1;
+  if (cfg->lmm != OR_LMM_BDF1 && cfg->lmm != OR_LMM_BDF2 && cfg->spacing != OR_SPACING_UNIFORM)
+    return -1; /* the higher-order families are built for a constant step */
   int S;
   double times[OR_SMAX + 1];
   if (cfg->spacing == OR_SPACING_UNIFORM) {
@@ -460,17 +620,31 @@ int or_build_substeps(const or_config* cfg, double t_prev, double t_next, int de
     }
   }
   times[S] = t_next;
-  if (cfg->lmm == 1) depth = 0;
+  const int lmm = cfg->lmm;
+  if (lmm == OR_LMM_BDF1) depth = 0;
   for (int i = 0; i < S; ++i) {
     double h0 = times[i + 1] - times[i];
     if (depth >= 1 && h0 / hprev1 >= 2.0) depth = 0;
-    int kind = (cfg->lmm == 2 && depth >= 2) ? 2 : 1;
-    or_bdf_coefficients(kind, h0, hprev1, hprev2, &tab[i]);
+    if (lmm == OR_LMM_BDF1 || lmm == OR_LMM_BDF2) {
+      int kind = (lmm == OR_LMM_BDF2 && depth >= 2) ? 2 : 1;
+      or_bdf_coefficients(kind, h0, hprev1, hprev2, &tab[i]);
+    } else if (lmm == OR_LMM_BDF3) {
+      /* BDF3 and its predictor need x_n, x_{n-1}, x_{n-2}; BDF1 until then */
+      if (depth >= 2) or_lmm_coefficients(3, h0, &tab[i]);
+      else or_bdf_coefficients(1, h0, 0.0, 0.0, &tab[i]);
+    } else {
+      /* Adams order q needs f_n, ..., f_{n-q+1}: the order grows by one per
+       * step after a cold start */
+      int q = lmm % 10, order = depth + 1 < q ? depth + 1 : q;
+      or_lmm_coefficients((lmm / 10) * 10 + order, h0, &tab[i]);
+    }
+    tab[i].tn = times[i];
+    tab[i].t = times[i + 1];
     hprev2 = hprev1;
     hprev1 = h0;
     depth = depth < 2 ? depth + 1 : 2;
   }
-  if (cfg->lmm == 1) depth = 0;
+  if (lmm == OR_LMM_BDF1) depth = 0;
   if (depth_out) *depth_out = depth;
   return S;
 }
@@ -482,8 +656,12 @@ int or_build_substeps(const or_config* cfg, double t_prev, double t_next, int de
  * not NULL, the squared Milne local-error estimates are summed into E (Step 4b
  * reading: Gamma = kappa diag(sum_s e_s^2)).  Returns 0, or -1 if the Newton
  * matrix became singular. */
+static int propagate_adams(int ode, int d, int K, const double* th, const or_substep* tab, int S,
+                           double* x, double* h1, double* h2, double* E);
+
 int or_propagate(int ode, int d, int K, const double* th, const or_substep* tab, int S,
                  double* x, double* h1, double* h2, double* E) {
+  if (S >= 1 && tab[0].kind > 10) return propagate_adams(ode, d, K, th, tab, S, x, h1, h2, E);
   const int linear = (ode == OR_ADVDIFF);
   double* xi = (double*)malloc(sizeof(double) * (size_t)d * 6);
   double *xp = xi + d, *r = xp + d, *G = r + d, *f = G + d, *dx = f + d;
@@ -496,22 +674,26 @@ int or_propagate(int ode, int d, int K, const double* th, const or_substep* tab,
   double lu_gamma = 0.0;
   for (int s = 0; s < S && rc == 0; ++s) {
     const or_substep* c = &tab[s];
+    if (c->kind == 3) or_ode_f(ode, d, th, c->tn, x, f); /* BDF3 predictor slope */
     for (int i = 0; i < d; ++i) {
       if (c->kind == 2) {
         xp[i] = c->pi0 * x[i] + c->pi1 * h1[i] + c->pi2 * h2[i];
+      } else if (c->kind == 3) {
+        xp[i] = c->pi0 * x[i] + c->pi1 * h1[i] + c->pi2 * h2[i] + c->pi3 * f[i];
       } else {
         xp[i] = x[i];
       }
       r[i] = c->rho1 * x[i] + c->rho2 * h1[i];
+      if (c->kind == 3) r[i] += c->rho3 * h2[i];
       xi[i] = xp[i];
     }
     if (c->kind == 1) {
       /* explicit-Euler predictor, used only by the error estimate */
-      or_ode_f(ode, d, th, x, f);
+      or_ode_f(ode, d, th, c->tn, x, f);
       for (int i = 0; i < d; ++i) xp[i] = x[i] + c->h * f[i];
     }
     for (int it = 0; it < K; ++it) {
-      or_ode_f(ode, d, th, xi, f);
+      or_ode_f(ode, d, th, c->t, xi, f);
       if (!linear || !have_J) {
         or_ode_jac(ode, d, th, xi, J);
         have_J = 1;
@@ -555,6 +737,90 @@ int or_propagate(int ode, int d, int K, const double* th, const or_substep* tab,
   free(J);
   free(M);
   free(piv);
+  return rc;
+}
+
+/* Psi by an Adams method (Sec. 3, Tables 1-2): the stored history is the
+ * states x_n, x_{n-1}, x_{n-2} (as for BDF), and the derivative history
+ * f_n, f_{n-1}, f_{n-2} is evaluated from them with the particle's current
+ * theta at the interval's start, at times t_n, t_n - h, t_n - 2h (constant
+ * step).  Each substep:
+ *   predictor (AB_q)  x_p = x_n + sum_j bab_j f_{n-j};
+ *   AM_q: K Newton iterations on x - (x_n + sum_{j>=1} beta_j f_{n+1-j})
+ *         - gamma f(t_{n+1}, x) = 0 from x_p; error mu (x_{n+1} - x_p);
+ *   AB_q: x_{n+1} = x_p; error mu (x_c - x_p) with the AM_q value
+ *         x_c = x_n + gamma f_{n+1} + sum_{j>=1} beta_j f_{n+1-j};
+ * then f_{n+1} = f(t_{n+1}, x_{n+1}) joins the derivative history. */
+static int propagate_adams(int ode, int d, int K, const double* th, const or_substep* tab, int S,
+                           double* x, double* h1, double* h2, double* E) {
+  double* F = (double*)malloc(sizeof(double) * (size_t)d * 10);
+  double *F0 = F, *F1 = F + d, *F2 = F + 2 * d; /* f_n, f_{n-1}, f_{n-2} */
+  double *xp = F + 3 * d, *r = F + 4 * d, *xi = F + 5 * d, *G = F + 6 * d, *fn = F + 7 * d;
+  double *dx = F + 8 * d, *xc = F + 9 * d;
+  double* J = (double*)malloc(sizeof(double) * (size_t)d * d);
+  double* M = (double*)malloc(sizeof(double) * (size_t)d * d);
+  int rc = 0;
+  const int q0 = tab[0].kind % 10;
+  or_ode_f(ode, d, th, tab[0].tn, x, F0);
+  if (q0 >= 2) or_ode_f(ode, d, th, tab[0].tn - tab[0].h, h1, F1);
+  if (q0 >= 3) or_ode_f(ode, d, th, tab[0].tn - 2.0 * tab[0].h, h2, F2);
+  for (int s = 0; s < S && rc == 0; ++s) {
+    const or_substep* c = &tab[s];
+    const int q = c->kind % 10, implicit = c->kind < 20;
+    const double* Fh[3] = {F0, F1, F2};
+    for (int i = 0; i < d; ++i) {
+      double v = x[i];
+      for (int j = 0; j < q; ++j) v += c->bab[j] * Fh[j][i];
+      xp[i] = v;
+      double w = x[i];
+      for (int j = 1; j < q; ++j) w += c->beta[j] * Fh[j - 1][i];
+      r[i] = w;
+      xi[i] = xp[i];
+    }
+    if (implicit) {
+      for (int it = 0; it < K; ++it) {
+        or_ode_f(ode, d, th, c->t, xi, fn);
+        or_ode_jac(ode, d, th, xi, J);
+        for (int i = 0; i < d; ++i) G[i] = -(xi[i] - r[i] - c->gamma * fn[i]);
+        for (int i = 0; i < d; ++i)
+          for (int j = 0; j < d; ++j)
+            M[(size_t)i * d + j] = (i == j ? 1.0 : 0.0) - c->gamma * J[(size_t)i * d + j];
+        if (or_lu_solve(d, M, G, dx) != 0) {
+          rc = -1;
+          break;
+        }
+        for (int i = 0; i < d; ++i) xi[i] += dx[i];
+      }
+      if (rc != 0) break;
+    }
+    or_ode_f(ode, d, th, c->t, xi, fn); /* f_{n+1} */
+    if (E) {
+      for (int i = 0; i < d; ++i) {
+        double e;
+        if (implicit) {
+          e = c->mu * (xi[i] - xp[i]);
+        } else {
+          xc[i] = r[i] + c->gamma * fn[i];
+          e = c->mu * (xc[i] - xp[i]);
+        }
+        E[i] += e * e;
+      }
+    }
+    /* rotate the histories: x_{n+1} becomes x_n, f_{n+1} becomes f_n */
+    double* t = F2;
+    F2 = F1;
+    F1 = F0;
+    F0 = t;
+    for (int i = 0; i < d; ++i) {
+      F0[i] = fn[i];
+      h2[i] = h1[i];
+      h1[i] = x[i];
+      x[i] = xi[i];
+    }
+  }
+  free(F);
+  free(J);
+  free(M);
   return rc;
 }
 
@@ -632,6 +898,9 @@ or_filter* or_create(const or_config* cfg) {
   d = cfg->d;
   if (or_ode_check_dim(cfg->ode, d) != 0 || d > OR_DMAX) return NULL;
   if (p != cfg->p || cfg->N < 1 || cfg->m < 0 || cfg->m > OR_MMAX) return NULL;
+  if (!or_lmm_valid(cfg->lmm)) return NULL;
+  if (cfg->lmm != OR_LMM_BDF1 && cfg->lmm != OR_LMM_BDF2 && cfg->spacing != OR_SPACING_UNIFORM)
+    return NULL;
   or_filter* f = (or_filter*)calloc(1, sizeof(or_filter));
   f->cfg = *cfg;
   f->d = d; f->p = p; f->N = cfg->N;

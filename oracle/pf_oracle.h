@@ -26,8 +26,17 @@
 #define OR_SMAX 4096
 
 /* problem ids; OR_ADVDIFF is the paper's 2D advection-diffusion system (M2,
- * Sec. 4) on an nt x nt periodic grid, d = nt^2 with nt odd, 3 <= nt <= 45 */
-enum { OR_LINEAR2 = 1, OR_ROBERTSON = 2, OR_BRUSSELATOR = 3, OR_ADVDIFF = 4 };
+ * Sec. 4) on an nt x nt periodic grid, d = nt^2 with nt odd, 3 <= nt <= 45;
+ * OR_MICHAELIS is the paper's three-compartment Michaelis-Menten system (M1,
+ * Sec. 2.1), d = 3, theta = (V1, V2, k1, k2), with the known constants taken
+ * as stated in or_mm_constants */
+enum { OR_LINEAR2 = 1, OR_ROBERTSON = 2, OR_BRUSSELATOR = 3, OR_ADVDIFF = 4, OR_MICHAELIS = 5 };
+/* LMMs (Sec. 3, Tables 1-2): the first three methods of each family */
+enum {
+  OR_LMM_BDF1 = 1, OR_LMM_BDF2 = 2, OR_LMM_BDF3 = 3,
+  OR_LMM_AM1 = 11, OR_LMM_AM2 = 12, OR_LMM_AM3 = 13,
+  OR_LMM_AB1 = 21, OR_LMM_AB2 = 22, OR_LMM_AB3 = 23
+};
 /* random-stream purposes (counter word 2, low byte) */
 enum { OR_RNG_INIT = 1, OR_RNG_THETA = 2, OR_RNG_INNOV = 3, OR_RNG_RESAMPLE = 4 };
 enum { OR_UNIFORM = 0, OR_LOGUNIFORM = 1 };          /* prior kinds          */
@@ -40,7 +49,9 @@ enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_DEGENERATE = 5 };
 typedef struct {
   int ode, d, p, m;
   int64_t N;
-  int lmm;          /* 1 = BDF1 only, 2 = BDF2 (BDF1 on cold starts)        */
+  int lmm;          /* OR_LMM_*: BDF1, BDF2 (BDF1 on cold starts), BDF3,
+                       AM1-3, AB1-3 (lower orders of the family on cold
+                       starts); all but BDF1/BDF2 need uniform spacing     */
   int newton_iters; /* fixed Newton count K                                 */
   int spacing;      /* OR_SPACING_*                                          */
   double dt;        /* uniform substep length                               */
@@ -61,14 +72,28 @@ typedef struct {
   double t0;        /* time of the initial state                            */
 } or_config;
 
-/* One substep of the LMM on the shared grid. */
+/* One substep of the LMM on the shared grid.
+ * BDF kinds 1, 2: x_{n+1} - rho1 x_n - rho2 x_{n-1} = gamma f(t_{n+1}, x_{n+1}),
+ *   predictor pi0 x_n + pi1 x_{n-1} + pi2 x_{n-2} (kind 2) or the explicit
+ *   Euler step (kind 1), local error mu (x_{n+1} - x_p).
+ * BDF kind 3: x_{n+1} - rho1 x_n - rho2 x_{n-1} - rho3 x_{n-2} = gamma f_{n+1},
+ *   predictor pi0 x_n + pi1 x_{n-1} + pi2 x_{n-2} + pi3 f(t_n, x_n).
+ * Adams-Moulton kinds 10 + q: x_{n+1} = x_n + beta0 f_{n+1} + beta1 f_n +
+ *   beta2 f_{n-1} (gamma = beta0), predictor AB_q.
+ * Adams-Bashforth kinds 20 + q: x_{n+1} = x_n + bab0 f_n + bab1 f_{n-1} +
+ *   bab2 f_{n-2}; its error is measured against AM_q evaluated at x_{n+1}.
+ * Adams weights are scaled by h; f_j = f(t_j, x_j). */
 typedef struct {
-  int kind;         /* 1 = BDF1 (cold start), 2 = BDF2                      */
+  int kind;         /* 1, 2, 3 (BDF); 11-13 (AM order q); 21-23 (AB order q) */
   double h;         /* step length                                          */
-  double gamma;     /* x_{n+1} - rho1 x_n - rho2 x_{n-1} = gamma f(x_{n+1})  */
+  double gamma;     /* weight of f(t_{n+1}, x_{n+1}) in the implicit equation */
   double rho1, rho2;
-  double pi0, pi1, pi2; /* predictor: x_p = pi0 x_n + pi1 x_{n-1} + pi2 x_{n-2} */
-  double mu;        /* local error = mu (x_{n+1} - x_p)                      */
+  double pi0, pi1, pi2;
+  double mu;        /* local error = mu (x_corr - x_pred)                    */
+  double rho3, pi3;
+  double beta[3];   /* AM_q weights of f_{n+1}, f_n, f_{n-1}                 */
+  double bab[3];    /* AB_q weights of f_n, f_{n-1}, f_{n-2}                 */
+  double tn, t;     /* t_n and t_{n+1}                                       */
 } or_substep;
 
 typedef struct or_filter or_filter;
@@ -77,8 +102,12 @@ typedef struct or_filter or_filter;
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double or_uniform(uint64_t seed, uint32_t stream, int purpose, uint32_t n, uint32_t epoch, int k);
 double or_normal(uint64_t seed, uint32_t stream, int purpose, uint32_t n, uint32_t epoch, int k);
-void or_ode_f(int ode, int d, const double* theta, const double* x, double* f);
+/* f(t, x; theta); only OR_MICHAELIS depends on t (its input function) */
+void or_ode_f(int ode, int d, const double* theta, double t, const double* x, double* f);
 void or_ode_jac(int ode, int d, const double* theta, const double* x, double* J);
+/* M1's known constants (lambda, c0, A0, A, t0, tau) and its input Phi(t) */
+void or_mm_constants(double* out6);
+double or_mm_input(double t);
 /* parameter count and the fixed state dimension (0 when the dimension is a
  * choice of the problem, as for OR_ADVDIFF) */
 int or_ode_dims(int ode, int* d, int* p);
@@ -89,6 +118,8 @@ int or_lu_solve(int n, const double* A, const double* b, double* x);
 int or_lu_factor(int n, double* A, int* piv);
 void or_lu_apply(int n, const double* LU, const int* piv, const double* b, double* x);
 int or_bdf_coefficients(int kind, double h0, double h1, double h2, or_substep* out);
+/* constant-step coefficients of BDF3 (kind 3), AM_q (10 + q), AB_q (20 + q) */
+int or_lmm_coefficients(int kind, double h, or_substep* out);
 int or_build_substeps(const or_config* cfg, double t_prev, double t_next, int depth,
                       double hprev1, double hprev2, or_substep* tab, int max_steps,
                       int* depth_out);

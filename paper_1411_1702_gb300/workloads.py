@@ -30,7 +30,13 @@ import math
 
 import numpy as np
 
-LINEAR2, ROBERTSON, BRUSSELATOR, ADVDIFF = 1, 2, 3, 4
+LINEAR2, ROBERTSON, BRUSSELATOR, ADVDIFF, MICHAELIS = 1, 2, 3, 4, 5
+# LMMs of the paper's Tables 1-2 (the first three of each family)
+LMM_BDF1, LMM_BDF2, LMM_BDF3 = 1, 2, 3
+LMM_AM1, LMM_AM2, LMM_AM3 = 11, 12, 13
+LMM_AB1, LMM_AB2, LMM_AB3 = 21, 22, 23
+LMM_NAMES = {"BDF1": LMM_BDF1, "BDF2": LMM_BDF2, "BDF3": LMM_BDF3, "AM1": LMM_AM1,
+             "AM2": LMM_AM2, "AM3": LMM_AM3, "AB1": LMM_AB1, "AB2": LMM_AB2, "AB3": LMM_AB3}
 UNIFORM, LOGUNIFORM = 0, 1
 SPACING_UNIFORM, SPACING_GEOMETRIC = 0, 1
 HIST_CARRY, HIST_RESTART = 0, 1
@@ -41,7 +47,7 @@ NOISE_ADDITIVE, NOISE_RELATIVE = 0, 1
 # same).  Each is the smallest K whose result agrees with the fully converged
 # Newton solution to 1e-12 relative along the reference trajectory and on the
 # particles of a filter run; the test-suite re-checks the reference trajectory.
-NEWTON_ITERS = {LINEAR2: 1, ROBERTSON: 2, BRUSSELATOR: 3, ADVDIFF: 1}
+NEWTON_ITERS = {LINEAR2: 1, ROBERTSON: 2, BRUSSELATOR: 3, ADVDIFF: 1, MICHAELIS: 4}
 
 
 @dataclasses.dataclass
@@ -180,6 +186,95 @@ def robertson(N: int = 131072, T: int = 40, seed: int = 0, theta=None,
         prior_kind=[LOGUNIFORM] * 3, prior_lo=list(theta_star / 10.0),
         prior_hi=list(theta_star * 10.0), x0=x0, t0=0.0, theta_true=theta, t_obs=t_obs, y_obs=y,
         x_true=x_true)
+
+
+# -------------------------------------------------------------- michaelis
+# M1 of Sec. 2.1.  The paper names lambda, c0, A0, A, t0, tau as known but
+# prints no values, nor the true (V1, V2, k1, k2), the noise or the time span;
+# the values below are this project's reading (see the design notes).
+MM_THETA = (3.0, 2.5, 0.5, 0.3)          # (V1, V2, k1, k2)
+MM_KNOWN = dict(lam=0.5, c0=2.0, A0=1.0, A=0.5, t0=0.5, tau=4.0)
+
+
+def mm_input(t):
+    k = MM_KNOWN
+    s = t - k["t0"]
+    return k["A0"] + (k["A"] * s * math.exp(-s / k["tau"]) if s > 0.0 else 0.0)
+
+
+def michaelis_rhs(theta):
+    V1, V2, k1, k2 = (float(v) for v in theta)
+    lam, c0 = MM_KNOWN["lam"], MM_KNOWN["c0"]
+
+    def f(t, x):
+        j1 = V1 * x[0] / (x[0] + k1)
+        j2 = V2 * x[1] / (x[1] + k2)
+        return np.array([mm_input(t) - j1, j1 - j2, j2 - lam * (x[2] - c0)])
+
+    def jac(t, x):
+        a = V1 * k1 / (x[0] + k1) ** 2
+        b = V2 * k2 / (x[1] + k2) ** 2
+        return np.array([[-a, 0.0, 0.0], [a, -b, 0.0], [0.0, b, -lam]])
+    return f, jac
+
+
+def michaelis_x0(theta=MM_THETA):
+    """The steady state of the true system under the constant input A0 (the
+    input is A0 until t0): V1 x1/(x1+k1) = A0, V2 x2/(x2+k2) = A0,
+    lambda (x3 - c0) = A0."""
+    V1, V2, k1, k2 = theta
+    A0, lam, c0 = MM_KNOWN["A0"], MM_KNOWN["lam"], MM_KNOWN["c0"]
+    return np.array([A0 * k1 / (V1 - A0), A0 * k2 / (V2 - A0), c0 + A0 / lam])
+
+
+def michaelis_truth(theta, x0, t_obs, rtol=1e-11):
+    """Reference trajectory by Radau, split at t0 where the input's slope jumps."""
+    from scipy.integrate import solve_ivp
+    f, jac = michaelis_rhs(theta)
+    t0 = MM_KNOWN["t0"]
+    out = np.empty((len(t_obs), 3))
+    first = t_obs <= t0
+    x = np.array(x0, dtype=float)
+    if first.any():
+        sol = solve_ivp(f, (0.0, t0), x, method="Radau", t_eval=t_obs[first], rtol=rtol,
+                        atol=1e-14, jac=jac, dense_output=False)
+        out[first] = sol.y.T
+    rest = ~first
+    if not rest.any():
+        return out
+    sol0 = solve_ivp(f, (0.0, t0), x, method="Radau", rtol=rtol, atol=1e-14, jac=jac)
+    x = sol0.y[:, -1]
+    sol = solve_ivp(f, (t0, float(t_obs[-1])), x, method="Radau", t_eval=t_obs[rest], rtol=rtol,
+                    atol=1e-14, jac=jac)
+    out[rest] = sol.y.T
+    return out
+
+
+def michaelis(N: int = 50000, T: int = 50, seed: int = 0, lmm: int = LMM_BDF2,
+              theta=None) -> Workload:
+    """M1 of Sec. 2.1 as Tables 1-2 run it: all three states observed at 50
+    times, fixed step h = 0.05.  Reading: t_k = 0.5 k (10 steps per interval),
+    2 % relative noise, log-uniform priors one decade either side of
+    theta* = (V1, V2, k1, k2) = (3, 2.5, 0.5, 0.3), x0 the steady state under
+    the input A0.  The prior reaches V/k ~ 600, where h |lambda| ~ 30: stiff
+    for part of the ensemble, as the paper describes."""
+    theta_star = np.array(MM_THETA)
+    theta = theta_star if theta is None else np.asarray(theta, dtype=float)
+    x0 = michaelis_x0(MM_THETA)
+    t_obs = 0.5 * np.arange(1, T + 1)
+    x_true = michaelis_truth(theta, x0, t_obs)
+    obs_idx, sigma = [0, 1, 2], [0.02, 0.02, 0.02]
+    rng = np.random.default_rng([seed, 0xDA7A, MICHAELIS])
+    y = _noise(rng, x_true[:, obs_idx], sigma, True)
+    name = "michaelis" + next((k for k, v in LMM_NAMES.items() if v == lmm), str(lmm))
+    return Workload(
+        name=name, ode=MICHAELIS, d=3, p=4, N=N, lmm=lmm, newton_iters=NEWTON_ITERS[MICHAELIS],
+        spacing=SPACING_UNIFORM, dt=0.05, substeps=10, q0=0.0,
+        history=HIST_CARRY, transform=TRANSFORM_LOG, obs_idx=obs_idx,
+        noise=NOISE_RELATIVE, sigma=sigma, a=0.98, kappa=1.0, seed=seed, stream=0,
+        prior_kind=[LOGUNIFORM] * 4, prior_lo=list(theta_star / 10.0),
+        prior_hi=list(theta_star * 10.0), x0=x0, t0=0.0, theta_true=theta, t_obs=t_obs,
+        y_obs=y, x_true=x_true)
 
 
 # ------------------------------------------------------------ brusselator
@@ -400,7 +495,9 @@ def serving(n_sessions: int = 64, rate_hz: float = 200.0, obs_per_session: int =
 
 
 BY_NAME = {"linear2": linear2, "robertson": robertson, "brusselator": brusselator,
-           "advdiff20": advdiff20, "advdiff40": advdiff40}
+           "advdiff20": advdiff20, "advdiff40": advdiff40, "michaelis": michaelis}
+for _lname, _lmm in LMM_NAMES.items():
+    BY_NAME["michaelis" + _lname] = functools.partial(michaelis, lmm=_lmm)
 
 
 def get(name: str, **kw) -> Workload:
