@@ -35,6 +35,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_1411_1702_gb300.workloads import LMM_NAMES as W_LMM_NAMES  # noqa: E402
+
 METRIC = "particle-LMM-steps/s"
 UNIT = "particle-steps/s"
 # FP64 ALU peak of one GB300: 2 FP64 FMA lanes per clock per SM (the
@@ -43,9 +45,9 @@ UNIT = "particle-steps/s"
 # = 1.259 TFLOP/s, the nominal GB300 FP64 rate.
 FP64_PEAK_TFLOPS = 2.0 * 152 * 2.070e9 * 2 / 1e12
 
-# Algorithmic FP64 flops (FMA = 2) of one BDF2 substep of one particle in the
-# stage-2 kernel: predictor 5d, history combination 3d, Milne estimate 4d,
-# per-substep constants, and K Newton iterations.
+# Algorithmic FP64 flops (FMA = 2, a reciprocal = 1) of one substep of one
+# particle in the stage-2 kernel: predictor 5d, history combination 3d, Milne
+# estimate 4d, per-substep constants, and K Newton iterations.
 def _advdiff_flops(K, d):
     """M2 (2D advection-diffusion): predictor 5d, history 3d, Milne 4d, and per
     Newton iteration the 7-point residual 16d, the forward row and column DFTs
@@ -54,6 +56,24 @@ def _advdiff_flops(K, d):
     nt = int(round(math.sqrt(d)))
     H = (nt + 1) // 2
     return 12 * d + K * (24 * d * H + 15 * d + 6 * nt * H)
+
+
+def _michaelis_flops(lmm):
+    """M1 (Sec. 2.1), d = 3: one Newton iteration (two flux reciprocals, the
+    lower-triangular substitution with two pivot reciprocals) is 41 flops, one
+    evaluation of f 17.  Per substep, by family: BDF1/BDF2 predictor 15,
+    history 9, input 2, pivot constant 3, Milne 12; BDF3 adds the slope f(t_n,
+    x_n) and its term (70 in all); Adams-Moulton: AB predictor 18, AM
+    history 12, input 2, pivot 3, f(x_{n+1}) 17, Milne 12; Adams-Bashforth:
+    predictor 18, history 12, f 17, Milne against AM 18 (no Newton)."""
+    fam = lmm // 10
+    if fam == 2:
+        return lambda K, d: 65
+    if fam == 1:
+        return lambda K, d: 64 + 41 * K
+    if lmm == 3:
+        return lambda K, d: 70 + 41 * K
+    return lambda K, d: 41 + 41 * K
 
 
 STAGE2_FLOPS_PER_SUBSTEP = {
@@ -65,9 +85,17 @@ STAGE2_FLOPS_PER_SUBSTEP = {
     "advdiff20": _advdiff_flops,
     "advdiff40": _advdiff_flops,
 }
+for _name, _lmm in W_LMM_NAMES.items():
+    STAGE2_FLOPS_PER_SUBSTEP["michaelis" + _name] = _michaelis_flops(_lmm)
+STAGE2_FLOPS_PER_SUBSTEP["michaelis"] = _michaelis_flops(2)
 STAGE2_KERNEL = {"robertson": "k_stage2<Robertson>", "linear2": "k_stage2<Linear2>",
                  "brusselator": "k_bstage2", "advdiff20": "k_adstage<2>",
                  "advdiff40": "k_adstage<2>"}
+_FAMILY_ID = {0: 0, 1: 2, 2: 3}
+for _name, _lmm in W_LMM_NAMES.items():
+    _fam = 1 if _lmm == 3 else _FAMILY_ID[_lmm // 10]
+    STAGE2_KERNEL["michaelis" + _name] = f"k_stage2<Michaelis, {_fam}>"
+STAGE2_KERNEL["michaelis"] = "k_stage2<Michaelis, 0>"
 # DRAM bytes (read + write) of one stage-2 launch from an ncu capture of the
 # same command on a GB300 (profiles/ names each capture); None where no capture
 # of the kernel as it stands exists.
@@ -225,8 +253,9 @@ def run_reference(args, w):
 
 
 def config_of(w):
-    return {"workload": f"{w.name}: N={w.N} d={w.d} p={w.p} m={w.m} S={w.substeps} "
-                        f"{'geometric' if w.spacing else 'uniform'} substeps, T={w.T}, BDF2, "
+    lmm = next((k for k, v in W_LMM_NAMES.items() if v == w.lmm), str(w.lmm))
+    return {"workload": f"{w.name}: N={w.N} d={w.d} p={w.p} m={w.m} S={w.substeps_per_interval(1)} "
+                        f"{'geometric' if w.spacing else 'uniform'} substeps, T={w.T}, {lmm}, "
                         f"K={w.newton_iters} Newton, FP64",
             "N": w.N, "substeps": w.substeps_per_interval(1), "newton_iters": w.newton_iters,
             "epochs_per_step": 1, "l2": "flushed before every step (256 MiB write)",
@@ -616,6 +645,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="robertson",
                     choices=["robertson", "linear2", "brusselator", "advdiff20", "advdiff40",
+                             "michaelis"] + ["michaelis" + n for n in W_LMM_NAMES] + [
                              "batched", "serving"])
     ap.add_argument("--batch-filters", type=int, default=256)
     ap.add_argument("--serve-sessions", type=int, default=64)

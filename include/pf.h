@@ -4,10 +4,10 @@
  * The library runs the per-observation epoch of Algorithm 1 ("LMM PF-SMC
  * Sampler") of Arnold, Calvetti, Somersalo, "Vectorized and Parallel Particle
  * Filter SMC Parameter Estimation for Stiff ODEs": a Liu-West auxiliary
- * particle filter over (x, theta) whose particles are propagated by an implicit
- * linear multistep method (BDF2, BDF1 on cold starts) with a full Newton solve
- * per particle and per substep, and whose innovation variance comes from the
- * LMM's local error estimate (Step 4b).  All arithmetic is FP64 and runs in
+ * particle filter over (x, theta) whose particles are propagated by a linear
+ * multistep method (BDF1-3, Adams-Moulton 1-3 with a full Newton solve per
+ * particle and per substep, or Adams-Bashforth 1-3), and whose innovation
+ * variance comes from the LMM's local error estimate (Step 4b).  All arithmetic is FP64 and runs in
  * hand-written CUDA kernels; nothing falls back to the CPU.
  *
  * Conventions
@@ -48,8 +48,9 @@ typedef enum {
   PF_ERR_STATE = 8        /* call out of order (e.g. no observation loaded) */
 } pf_status;
 
-/* Problems x' = f(x; theta).  The paper's Sec. 2.1 system lacks constants, so
- * three stiff systems stand in for it; Sec. 4's system is built as given:
+/* Problems x' = f(t, x; theta).  Three textbook stiff systems, and the paper's
+ * own two (Sec. 2.1's M1, whose unprinted constants are a stated reading, and
+ * Sec. 4's system as given):
  *  PF_ODE_LINEAR2        d=2, p=2: x' = A x, A = [[-th1, th2], [0, -th2]].
  *  PF_ODE_ROBERTSON      d=3, p=3: Robertson kinetics, theta = (k1, k2, k3).
  *  PF_ODE_BRUSSELATOR1D  d=64, p=3: 1D Brusselator on 32 interior points,
@@ -63,17 +64,48 @@ typedef enum {
  *                        B1 = I (x) ell, B2 = ell (x) I, (ell u)_j = u_j - u_{j-1}
  *                        (periodic), theta = (k1, k2, k3, c1, c2), state
  *                        U[iy*nt + ix] (x fastest).  Linear: one Newton
- *                        iteration solves each step. */
+ *                        iteration solves each step.
+ *  PF_ODE_MICHAELIS3     d=3, p=4: the three-compartment Michaelis-Menten
+ *                        system of Sec. 2.1 (M1),
+ *                          x1' = Phi(t) - V1 x1/(x1+k1),
+ *                          x2' = V1 x1/(x1+k1) - V2 x2/(x2+k2),
+ *                          x3' = V2 x2/(x2+k2) - lambda (x3 - c0),
+ *                        Phi(t) = A0 + A (t - t0)_+ exp(-(t - t0)/tau),
+ *                        theta = (V1, V2, k1, k2).  The paper calls lambda,
+ *                        c0, A0, A, t0, tau known but prints no values; this
+ *                        library fixes lambda = 0.5, c0 = 2, A0 = 1, A = 0.5,
+ *                        t0 = 0.5, tau = 4. */
 typedef enum {
   PF_ODE_LINEAR2 = 1,
   PF_ODE_ROBERTSON = 2,
   PF_ODE_BRUSSELATOR1D = 3,
-  PF_ODE_ADVDIFF2D = 4
+  PF_ODE_ADVDIFF2D = 4,
+  PF_ODE_MICHAELIS3 = 5
 } pf_ode;
 
-/* Implicit LMM of Psi (Sec. 2.1): BDF1 = backward Euler; BDF2 = variable-step
- * BDF2, with BDF1 on the first two substeps after a cold start. */
-typedef enum { PF_LMM_BDF1 = 1, PF_LMM_BDF2 = 2 } pf_lmm;
+/* LMM of Psi (Sec. 2.1, Sec. 3 and Tables 1-2: the first three methods of
+ * each family, numbered by order).
+ *  BDF1 = backward Euler; BDF2 = variable-step BDF2 (BDF1 on the first two
+ *  substeps after a cold start); BDF3 (BDF1 until two past states exist).
+ *  AM1-AM3: Adams-Moulton of order 1-3 (AM1 is backward Euler, AM2 the
+ *  trapezoidal rule), Newton-solved like BDF.  AB1-AB3: explicit
+ *  Adams-Bashforth of order 1-3 (no Newton solve; not suited to stiff
+ *  problems).  Adams methods start at order 1 and gain one order per step.
+ *  Local errors by Milne's device against a same-order predictor (AB_q for
+ *  AM_q, AM_q evaluated once for AB_q, a cubic through three states and one
+ *  slope for BDF3).  BDF3 and the Adams methods need PF_SPACING_UNIFORM and
+ *  one of PF_ODE_LINEAR2, PF_ODE_ROBERTSON, PF_ODE_MICHAELIS3. */
+typedef enum {
+  PF_LMM_BDF1 = 1,
+  PF_LMM_BDF2 = 2,
+  PF_LMM_BDF3 = 3,
+  PF_LMM_AM1 = 11,
+  PF_LMM_AM2 = 12,
+  PF_LMM_AM3 = 13,
+  PF_LMM_AB1 = 21,
+  PF_LMM_AB2 = 22,
+  PF_LMM_AB3 = 23
+} pf_lmm;
 
 enum { PF_PRIOR_UNIFORM = 0, PF_PRIOR_LOGUNIFORM = 1 };
 enum { PF_SPACING_UNIFORM = 0, PF_SPACING_GEOMETRIC = 1 };
@@ -127,7 +159,8 @@ typedef struct {
 /* Create a filter and run Step 1 of Algorithm 1 (prior draws, w = 1/N,
  * weighted mean and covariance).  dt is the uniform substep length (the
  * interval length must be an integer multiple of it to 1e-9 relative); it is
- * ignored with geometric spacing.  Allocates about
+ * ignored with geometric spacing.  BDF3 and the Adams methods need uniform
+ * spacing and a problem of dimension <= 3 (INVALID_ARG otherwise).  Allocates about
  * 8 * N * (2 * (3d + p + 1) + 4) bytes of device memory.  Errors:
  * INVALID_ARG (dimensions do not match the ODE, N < 1 or > PF_MAX_PARTICLES,
  * bad prior or options), OOM, CUDA.  *out is NULL on error. */
@@ -217,7 +250,9 @@ pf_status pf_get_work(const pf_filter* f, double* loglik1, double* log_g, double
                       int32_t* idx);
 
 /* LMM history bookkeeping: committed epoch count, history depth (0-2 stored
- * past points), time of the last observation and the last two step lengths. */
+ * past points), time of the last observation and the last two step lengths.
+ * (For the Adams methods the stored states also rebuild the derivative
+ * history f_{n-1}, f_{n-2}, at t_n - h and t_n - 2h.) */
 pf_status pf_get_history(const pf_filter* f, int64_t* epochs, int* depth, double* t_prev,
                          double* hprev1, double* hprev2);
 pf_status pf_set_history(pf_filter* f, int64_t epochs, int depth, double t_prev, double hprev1,
@@ -225,12 +260,18 @@ pf_status pf_set_history(pf_filter* f, int64_t epochs, int depth, double t_prev,
 
 /* ---- host-only helper (no GPU needed) -----------------------------------
  * Substep table of one interval (t_prev, t_next] for the given history state,
- * as the filter builds it.  Per substep i, row i of coef (9 doubles):
- * kind, h, gamma, rho1, rho2, pi0, pi1, pi2, mu, with
- * x_{n+1} - rho1 x_n - rho2 x_{n-1} = gamma f(x_{n+1}),
- * predictor pi0 x_n + pi1 x_{n-1} + pi2 x_{n-2}, Milne factor mu.
+ * as the filter builds it.  Per substep i, row i of coef (PF_SUBSTEP_ROW = 11
+ * doubles): kind, h, gamma, rho1, rho2, pi0, pi1, pi2, mu, rho3, pi3.
+ *  BDF kinds 1-3: x_{n+1} - rho1 x_n - rho2 x_{n-1} - rho3 x_{n-2}
+ *    = gamma f(x_{n+1}); predictor pi0 x_n + pi1 x_{n-1} + pi2 x_{n-2}
+ *    + pi3 f(x_n) (kind 1: Newton starts at x_n, predictor x_n + h f(x_n)).
+ *  Adams kinds 10 + q (Moulton) and 20 + q (Bashforth), order q: predictor
+ *    x_n + pi0 f_n + pi1 f_{n-1} + pi2 f_{n-2}; corrector x_n + gamma f_{n+1}
+ *    + rho1 f_n + rho2 f_{n-1}.
+ *  mu is Milne's factor: local error = mu (x_corr - x_pred).
  * Returns the substep count S (> 0) or -1; *depth_out gets the history depth
  * after the interval.  lmm, spacing, dt, substeps, q0 as in pf_create. */
+#define PF_SUBSTEP_ROW 11
 int pf_substep_table(int lmm, int spacing, double dt, int substeps, double q0, double t_prev,
                      double t_next, int depth, double hprev1, double hprev2, double* coef,
                      int max_steps, int* depth_out);

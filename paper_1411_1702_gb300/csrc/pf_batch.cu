@@ -414,6 +414,8 @@ static pf_status batch_add(pf_batch* b, pf_filter* f, int* slot_out) {
   if (f->in_batch) return bfail(b, PF_ERR_INVALID_ARG, "filter already in a batch");
   if (f->ode == PF_ODE_ADVDIFF2D)
     return bfail(b, PF_ERR_INVALID_ARG, "2D advection-diffusion filters do not batch (one block per particle)");
+  if (f->ode == PF_ODE_MICHAELIS3 || (f->lmm != PF_LMM_BDF1 && f->lmm != PF_LMM_BDF2))
+    return bfail(b, PF_ERR_INVALID_ARG, "batches run BDF1/BDF2 filters of the linear, Robertson and Brusselator problems");
   int s = -1;
   for (int i = 0; i < b->cap; ++i)
     if (!b->slot[i]) {
@@ -883,6 +885,8 @@ pf_status pf_server_open(pf_server* s, pf_ode ode, int d, int p, int64_t N, pf_l
   }
   if (ode == PF_ODE_ADVDIFF2D)
     return sfail(s, PF_ERR_INVALID_ARG, "2D advection-diffusion sessions are not served (no batched kernels)");
+  if (ode == PF_ODE_MICHAELIS3 || (lmm != PF_LMM_BDF1 && lmm != PF_LMM_BDF2))
+    return sfail(s, PF_ERR_INVALID_ARG, "sessions run BDF1/BDF2 filters of the linear, Robertson and Brusselator problems");
   Session ss;
   ss.id = s->next_id++;
   ss.ode = ode; ss.d = d; ss.p = p; ss.N = N; ss.lmm = lmm; ss.dt = dt;

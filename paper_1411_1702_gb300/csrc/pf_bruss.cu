@@ -344,8 +344,7 @@ cudaError_t preload_bruss_kernels() {
   const void* ks[] = {(const void*)k_bstage<1>, (const void*)k_bstage<2>,
                       (const void*)k_batch_bstage<1>, (const void*)k_batch_bstage<2>};
   for (const void* k : ks) {
-    cudaFuncAttributes a;
-    const cudaError_t e = cudaFuncGetAttributes(&a, k);
+    const cudaError_t e = allow_step_table(k);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

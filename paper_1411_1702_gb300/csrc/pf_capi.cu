@@ -78,6 +78,7 @@ static bool ode_dims(int ode, int* d, int* p) {
     case PF_ODE_ROBERTSON: *d = 3; *p = 3; return true;
     case PF_ODE_BRUSSELATOR1D: *d = 64; *p = 3; return true;
     case PF_ODE_ADVDIFF2D: *d = 0; *p = 5; return true;
+    case PF_ODE_MICHAELIS3: *d = 3; *p = 4; return true;
   }
   return false;
 }
@@ -212,9 +213,22 @@ namespace pfg {
 int fill_epoch(const pf_filter* f, const HistoryState& h, double t_k, const double* y,
                EpochParams* ep, int* depth_out) {
   const int depth = (f->history == PF_HISTORY_RESTART) ? 0 : h.depth;
+  static thread_local double times[kSMax + 1];
   const int S = build_substeps(f->lmm, f->spacing, f->dt, f->substeps, f->q0, h.t_prev, t_k, depth,
-                               h.hprev1, h.hprev2, ep->sc, kSMax, depth_out);
+                               h.hprev1, h.hprev2, ep->sc, kSMax, depth_out, times);
   if (S < 1) return -1;
+  ep->in_hist[0] = ep->in_hist[1] = 0.0;
+  if (f->ode == PF_ODE_MICHAELIS3) {
+    // M1's input at every substep's end points, and at t_n - h, t_n - 2h for
+    // the Adams derivative history (constant step h)
+    for (int i = 0; i < S; ++i) {
+      ep->sc[i].in0 = mm_input(times[i]);
+      ep->sc[i].in1 = mm_input(times[i + 1]);
+    }
+    const double h0 = times[1] - times[0];
+    ep->in_hist[0] = mm_input(times[0] - h0);
+    ep->in_hist[1] = mm_input(times[0] - 2.0 * h0);
+  }
   ep->t = t_k;
   ep->S = S;
   ep->epoch = (uint32_t)h.epochs;
@@ -271,7 +285,10 @@ pf_status check_create_args(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, dou
   if (p != pp || (dd > 0 ? d != dd : !advdiff_dim_ok(d)))
     return fail(nullptr, PF_ERR_INVALID_ARG, "d or p does not match the ODE");
   if (N < 1 || N > PF_MAX_PARTICLES) return fail(nullptr, PF_ERR_INVALID_ARG, "N out of range");
-  if (lmm != PF_LMM_BDF1 && lmm != PF_LMM_BDF2) return fail(nullptr, PF_ERR_INVALID_ARG, "unknown LMM");
+  if (!lmm_known(lmm)) return fail(nullptr, PF_ERR_INVALID_ARG, "unknown LMM");
+  if (lmm_needs_uniform(lmm) && ode != PF_ODE_LINEAR2 && ode != PF_ODE_ROBERTSON &&
+      ode != PF_ODE_MICHAELIS3)
+    return fail(nullptr, PF_ERR_INVALID_ARG, "BDF3 and the Adams methods run on the small problems only");
   if (!prior || !opt) return fail(nullptr, PF_ERR_INVALID_ARG, "prior or options is NULL");
   if (prior->p != p || prior->d != d || !prior->kind || !prior->lo || !prior->hi || !prior->x0)
     return fail(nullptr, PF_ERR_INVALID_ARG, "prior does not match the ODE");
@@ -298,6 +315,8 @@ pf_status check_create_args(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, dou
     if (!(opt->sigma[i] > 0.0) || !std::isfinite(opt->sigma[i]))
       return fail(nullptr, PF_ERR_INVALID_ARG, "sigma must be positive");
   }
+  if (lmm_needs_uniform(lmm) && opt->spacing != PF_SPACING_UNIFORM)
+    return fail(nullptr, PF_ERR_INVALID_ARG, "BDF3 and the Adams methods need uniform spacing");
   if (opt->spacing == PF_SPACING_UNIFORM) {
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, PF_ERR_INVALID_ARG, "dt must be positive");
   } else if (opt->spacing == PF_SPACING_GEOMETRIC) {
@@ -360,7 +379,7 @@ pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double 
   f->x0.assign(prior->x0, prior->x0 + d);
 
   FilterDev& fd = f->fd;
-  fd.N = N; fd.ode = ode; fd.d = d; fd.p = p; fd.m = f->m; fd.K = f->K; fd.transform = f->transform;
+  fd.N = N; fd.ode = ode; fd.lmm = lmm; fd.d = d; fd.p = p; fd.m = f->m; fd.K = f->K; fd.transform = f->transform;
   for (int i = 0; i < kMMax; ++i) fd.obs[i] = i < f->m ? f->obs[i] : 0;
   fd.a = f->a; fd.s = std::sqrt(1.0 - f->a * f->a); fd.kappa = f->kappa;
   fd.seed = f->seed; fd.stream_id = f->filter_id;

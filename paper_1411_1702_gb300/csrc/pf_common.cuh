@@ -31,16 +31,28 @@ constexpr int kMomentThreads = 256;
 // Random-stream purposes (Philox counter word 2, low byte).
 enum : uint32_t { kRngInit = 1, kRngTheta = 2, kRngInnov = 3, kRngResample = 4 };
 
-// One substep of the shared grid:
-//   x_{n+1} - rho1 x_n - rho2 x_{n-1} = gamma f(x_{n+1}),
-//   predictor x_p = pi0 x_n + pi1 x_{n-1} + pi2 x_{n-2} (BDF2 steps),
+// One substep of the shared grid.
+// BDF kinds 1, 2 (BDF1 and BDF2):
+//   x_{n+1} - rho1 x_n - rho2 x_{n-1} = gamma f(t_{n+1}, x_{n+1}),
+//   predictor x_p = pi0 x_n + pi1 x_{n-1} + pi2 x_{n-2} (kind 2),
 //   Milne local error e = mu (x_{n+1} - x_p).
-// kind 1 (BDF1, cold start): Newton starts at x_n and the error predictor is
-// the explicit-Euler step x_n + h f(x_n).
+//   Kind 1 (cold start): Newton starts at x_n and the error predictor is the
+//   explicit-Euler step x_n + h f(t_n, x_n).
+// BDF kind 3: x_{n+1} - rho1 x_n - rho2 x_{n-1} - rho3 x_{n-2} = gamma f_{n+1},
+//   predictor pi0 x_n + pi1 x_{n-1} + pi2 x_{n-2} + pi3 f(t_n, x_n).
+// Adams kinds 10 + q (Moulton, implicit) and 20 + q (Bashforth, explicit), q
+// the order, with f_j = f(t_j, x_j):
+//   predictor AB_q:  x_p = x_n + pi0 f_n + pi1 f_{n-1} + pi2 f_{n-2};
+//   corrector AM_q:  x_c = x_n + gamma f_{n+1} + rho1 f_n + rho2 f_{n-1}
+//   (weights include h and are zero beyond the order).
+// in0, in1: the problem's time-dependent input at t_n and t_{n+1} (M1's Phi;
+// zero for autonomous problems).
 struct StepCoef {
   double h, gamma, rho1, rho2, pi0, pi1, pi2, mu;
   int kind;
   int pad;
+  double rho3, pi3;
+  double in0, in1;
 };
 
 // Per-epoch parameters (one observation).  Only the header and the first S
@@ -52,6 +64,8 @@ struct EpochParams {
   int S;
   uint32_t epoch;   // Philox epoch word = committed epoch count before this one
   int64_t pad;
+  double in_hist[2]; // the input at t_n - h and t_n - 2h (h = the first
+                     // substep): rebuilds the Adams derivative history
   StepCoef sc[kSMax];
 };
 constexpr size_t kEpochHeaderBytes = offsetof(EpochParams, sc);
@@ -88,6 +102,7 @@ struct Ensemble {
 struct FilterDev {
   int64_t N;
   int ode;
+  int lmm;          // pf_lmm (selects the propagation kernels)
   int d, p, m, K;
   int transform;
   int obs[kMMax];

@@ -50,51 +50,133 @@ __device__ __forceinline__ double loglik(const FilterDev& fd, const EpochParams*
   return -0.5 * s;
 }
 
+// LMM families of the propagation kernels (one instantiation each).
+enum : int { kFamBdf12 = 0, kFamBdf3 = 1, kFamAm = 2, kFamAb = 3 };
+
+__host__ __device__ constexpr int lmm_family(int lmm) {
+  return lmm == PF_LMM_BDF3 ? kFamBdf3 : lmm / 10 == 1 ? kFamAm : lmm / 10 == 2 ? kFamAb : kFamBdf12;
+}
+
+// f(t, x) with the input value u = input(t) for forced problems
+template <class M>
+__device__ __forceinline__ void feval(const typename M::Th& T, double u, const double* x, double* out) {
+  M::gf(T, 1.0, x, out);
+  if constexpr (M::kForced) out[0] += u;
+}
+
 // Psi of Algorithm 1 for one particle over the S substeps of the interval.
 // (x, h1, h2) = (x_n, x_{n-1}, x_{n-2}).  With ERR the squared Milne local
 // error estimates are summed into E (Step 4b).
-template <class M, bool ERR>
+//  F = kFamBdf12: BDF1/BDF2 steps (kinds 1, 2).
+//  F = kFamBdf3:  BDF1 cold starts and BDF3 steps, whose predictor needs the
+//                 slope f(t_n, x_n).
+//  F = kFamAm / kFamAb: Adams-Moulton / Adams-Bashforth; the derivative
+//                 history f_n, f_{n-1}, f_{n-2} is rebuilt from the stored
+//                 states with this particle's theta at the interval's start
+//                 and then carried in registers (weights beyond the step's
+//                 order are zero, the unused slots hold a finite copy).
+template <class M, bool ERR, int F>
 __device__ __forceinline__ void propagate(const typename M::Th& T, const StepCoef* sc, int S, int K,
-                                          double (&x)[M::D], double (&h1)[M::D],
-                                          double (&h2)[M::D], double (&E)[M::D]) {
+                                          const EpochParams* __restrict__ ep, double (&x)[M::D],
+                                          double (&h1)[M::D], double (&h2)[M::D], double (&E)[M::D]) {
   constexpr int D = M::D;
-  for (int s = 0; s < S; ++s) {
-    const StepCoef& c = sc[s];
-    double xp[D], r[D], y[D];
-    if (c.kind == 2) {
+  if constexpr (F == kFamBdf12 || F == kFamBdf3) {
+    for (int s = 0; s < S; ++s) {
+      const StepCoef& c = sc[s];
+      double xp[D], r[D], y[D];
+      if (F == kFamBdf3 && c.kind == 3) {
+        double fx[D];
+        feval<M>(T, c.in0, x, fx);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          xp[i] = fma(c.pi3, fx[i], fma(c.pi2, h2[i], fma(c.pi1, h1[i], c.pi0 * x[i])));
+          r[i] = fma(c.rho3, h2[i], fma(c.rho2, h1[i], c.rho1 * x[i]));
+          y[i] = xp[i];
+        }
+      } else if (F == kFamBdf12 && c.kind == 2) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          xp[i] = fma(c.pi2, h2[i], fma(c.pi1, h1[i], c.pi0 * x[i]));
+          r[i] = fma(c.rho2, h1[i], c.rho1 * x[i]);
+          y[i] = xp[i];
+        }
+      } else {
+        // BDF1 (cold start): r = x_n, Newton from x_n, error predictor x_n + h f(t_n, x_n)
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          r[i] = x[i];
+          y[i] = x[i];
+        }
+        if (ERR) {
+          double g[D];
+          M::gf(T, c.h, x, g);
+          if constexpr (M::kForced) g[0] = fma(c.h, c.in0, g[0]);
+#pragma unroll
+          for (int i = 0; i < D; ++i) xp[i] = x[i] + g[i];
+        }
+      }
+      if constexpr (M::kForced) r[0] = fma(c.gamma, c.in1, r[0]);
+      M::newton(T, c.gamma, r, y, K);
+      if (ERR) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          const double e = c.mu * (y[i] - xp[i]);
+          E[i] = fma(e, e, E[i]);
+        }
+      }
 #pragma unroll
       for (int i = 0; i < D; ++i) {
-        xp[i] = fma(c.pi2, h2[i], fma(c.pi1, h1[i], c.pi0 * x[i]));
-        r[i] = fma(c.rho2, h1[i], c.rho1 * x[i]);
+        h2[i] = h1[i];
+        h1[i] = x[i];
+        x[i] = y[i];
+      }
+    }
+  } else {
+    double f0[D], f1[D], f2[D];
+    const int q0 = sc[0].kind % 10;
+    feval<M>(T, sc[0].in0, x, f0);
+    if (q0 >= 2) feval<M>(T, ep->in_hist[0], h1, f1);
+    else
+#pragma unroll
+      for (int i = 0; i < D; ++i) f1[i] = f0[i];
+    if (q0 >= 3) feval<M>(T, ep->in_hist[1], h2, f2);
+    else
+#pragma unroll
+      for (int i = 0; i < D; ++i) f2[i] = f1[i];
+    for (int s = 0; s < S; ++s) {
+      const StepCoef& c = sc[s];
+      double xp[D], r[D], y[D], fn[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        xp[i] = fma(c.pi2, f2[i], fma(c.pi1, f1[i], fma(c.pi0, f0[i], x[i])));
+        r[i] = fma(c.rho2, f1[i], fma(c.rho1, f0[i], x[i]));
         y[i] = xp[i];
       }
-    } else {
-      // BDF1 (cold start): r = x_n, Newton from x_n, error predictor x_n + h f(x_n)
+      if constexpr (F == kFamAm) {
+        double rr[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) {
-        r[i] = x[i];
-        y[i] = x[i];
+        for (int i = 0; i < D; ++i) rr[i] = r[i];
+        if constexpr (M::kForced) rr[0] = fma(c.gamma, c.in1, rr[0]);
+        M::newton(T, c.gamma, rr, y, K);
       }
+      feval<M>(T, c.in1, y, fn);
       if (ERR) {
-        double g[D];
-        M::gf(T, c.h, x, g);
 #pragma unroll
-        for (int i = 0; i < D; ++i) xp[i] = x[i] + g[i];
+        for (int i = 0; i < D; ++i) {
+          // AM: corrector y against the AB predictor; AB: the AM value at y
+          const double e = (F == kFamAm) ? c.mu * (y[i] - xp[i]) : c.mu * (fma(c.gamma, fn[i], r[i]) - y[i]);
+          E[i] = fma(e, e, E[i]);
+        }
       }
-    }
-    M::newton(T, c.gamma, r, y, K);
-    if (ERR) {
 #pragma unroll
       for (int i = 0; i < D; ++i) {
-        const double e = c.mu * (y[i] - xp[i]);
-        E[i] = fma(e, e, E[i]);
+        f2[i] = f1[i];
+        f1[i] = f0[i];
+        f0[i] = fn[i];
+        h2[i] = h1[i];
+        h1[i] = x[i];
+        x[i] = y[i];
       }
-    }
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      h2[i] = h1[i];
-      h1[i] = x[i];
-      x[i] = y[i];
     }
   }
 }
@@ -141,7 +223,7 @@ __device__ __forceinline__ void init_body(const FilterDev& fd, int vb) {
 }
 
 // ---------------------------------------------------------------- stage 1
-template <class M>
+template <class M, int F>
 __device__ __forceinline__ void stage1_body(const FilterDev& fd, const EpochParams* __restrict__ ep,
                                             int vb, int vg, const StepCoef* s_sc, double* s_red,
                                             int* s_flag) {
@@ -165,7 +247,7 @@ __device__ __forceinline__ void stage1_body(const FilterDev& fd, const EpochPara
       h1[i] = E.h1[i * N + n];
       h2[i] = E.h2[i * N + n];
     }
-    propagate<M, false>(T, s_sc, S, fd.K, x, h1, h2, Eunused);
+    propagate<M, false, F>(T, s_sc, S, fd.K, ep, x, h1, h2, Eunused);
     const double ll = loglik<D>(fd, ep, x);
     fd.ll1[n] = ll;
     lg = (E.lw[n] - ctrl->logW) + ll;
@@ -274,7 +356,7 @@ __device__ __forceinline__ void resample_body(const FilterDev& fd, const EpochPa
 }
 
 // ---------------------------------------------------------------- stage 2
-template <class M>
+template <class M, int F>
 __device__ __forceinline__ void stage2_body(const FilterDev& fd, const EpochParams* __restrict__ ep,
                                             int vb, int vg, const StepCoef* s_sc, double* s_red,
                                             int* s_flag) {
@@ -318,7 +400,7 @@ __device__ __forceinline__ void stage2_body(const FilterDev& fd, const EpochPara
       Eacc[i] = 0.0;
     }
     // 4b, 4d: repropagate, summing the squared Milne estimates
-    propagate<M, true>(T, s_sc, S, fd.K, x, h1, h2, Eacc);
+    propagate<M, true, F>(T, s_sc, S, fd.K, ep, x, h1, h2, Eacc);
     // 4c, 4d: v ~ N(0, kappa diag(E)), added to x and to the stored history
 #pragma unroll
     for (int b = 0; b < (D + 1) / 2; ++b) {
@@ -485,7 +567,7 @@ __global__ void __launch_bounds__(kInitThreads) k_init(const __grid_constant__ F
   init_body<D, P>(fd, blockIdx.x);
 }
 
-template <class M>
+template <class M, int F>
 __global__ void __launch_bounds__(kSmallThreads) k_stage1(const __grid_constant__ FilterDev fd,
                                                           const EpochParams* __restrict__ ep) {
   extern __shared__ double s_dyn[];
@@ -494,7 +576,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_stage1(const __grid_constant_
   if (fd.ctrl->status != PF_OK) return;
   StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
   load_steps(s_sc, ep, ep->S);
-  stage1_body<M>(fd, ep, blockIdx.x, gridDim.x, s_sc, s_red, &s_flag);
+  stage1_body<M, F>(fd, ep, blockIdx.x, gridDim.x, s_sc, s_red, &s_flag);
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_tile(const __grid_constant__ FilterDev fd) {
@@ -517,7 +599,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample(const __grid_cons
   resample_body(fd, ep, blockIdx.x, s_l, s_red);
 }
 
-template <class M>
+template <class M, int F>
 __global__ void __launch_bounds__(kSmallThreads) k_stage2(const __grid_constant__ FilterDev fd,
                                                           const EpochParams* __restrict__ ep) {
   extern __shared__ double s_dyn[];
@@ -526,7 +608,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_stage2(const __grid_constant_
   if (fd.ctrl->status != PF_OK) return;
   StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
   load_steps(s_sc, ep, ep->S);
-  stage2_body<M>(fd, ep, blockIdx.x, gridDim.x, s_sc, s_red, &s_flag);
+  stage2_body<M, F>(fd, ep, blockIdx.x, gridDim.x, s_sc, s_red, &s_flag);
 }
 
 template <int D, int P>
@@ -629,8 +711,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_batch_stage(const FilterDev* 
   StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
   load_steps(s_sc, ep, ep->S);
   const int vg = (int)((fd.N + kSmallThreads - 1) / kSmallThreads);
-  if (STAGE == 1) stage1_body<M>(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
-  else stage2_body<M>(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
+  if (STAGE == 1) stage1_body<M, kFamBdf12>(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
+  else stage2_body<M, kFamBdf12>(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_batch_scan_tile(const FilterDev* __restrict__ fds,
@@ -690,6 +772,7 @@ int moment_record_size(int ode) {
     case PF_ODE_ROBERTSON: return moment_nrec<3, 3>();
     case PF_ODE_BRUSSELATOR1D: return moment_nrec<64, 3>();
     case PF_ODE_ADVDIFF2D: return moment_nrec<0, 5>();
+    case PF_ODE_MICHAELIS3: return moment_nrec<3, 4>();
   }
   return -1;
 }
@@ -732,17 +815,33 @@ static cudaError_t launch_init_t(const FilterDev& fd, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+using StageKernel = void (*)(const FilterDev, const EpochParams*);
+
+// the stage kernels of model M for the filter's LMM family
+template <class M>
+static void stage_kernels(int lmm, StageKernel& k1, StageKernel& k2) {
+  switch (lmm_family(lmm)) {
+    case kFamBdf3: k1 = k_stage1<M, kFamBdf3>; k2 = k_stage2<M, kFamBdf3>; return;
+    case kFamAm: k1 = k_stage1<M, kFamAm>; k2 = k_stage2<M, kFamAm>; return;
+    case kFamAb: k1 = k_stage1<M, kFamAb>; k2 = k_stage2<M, kFamAb>; return;
+  }
+  k1 = k_stage1<M, kFamBdf12>;
+  k2 = k_stage2<M, kFamBdf12>;
+}
+
 template <class M>
 static cudaError_t launch_epoch_t(const FilterDev& fd, const EpochParams* ep, int S,
                                   cudaStream_t st, cudaEvent_t* marks) {
   const int64_t N = fd.N;
   const size_t smem = (size_t)S * sizeof(StepCoef);
+  StageKernel k1, k2;
+  stage_kernels<M>(fd.lmm, k1, k2);
   const unsigned g_small = (unsigned)phase_blocks(kPhaseStage1, M::ODE, N);
   auto mark = [&](int i) {
     if (marks) cudaEventRecord(marks[i], st);
   };
   mark(0);
-  k_stage1<M><<<g_small, kSmallThreads, smem, st>>>(fd, ep);
+  k1<<<g_small, kSmallThreads, smem, st>>>(fd, ep);
   mark(1);
   k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, M::ODE, N), kScanThreads, 0, st>>>(fd);
   mark(2);
@@ -750,7 +849,7 @@ static cudaError_t launch_epoch_t(const FilterDev& fd, const EpochParams* ep, in
   mark(3);
   k_resample<<<(unsigned)phase_blocks(kPhaseResample, M::ODE, N), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
-  k_stage2<M><<<g_small, kSmallThreads, smem, st>>>(fd, ep);
+  k2<<<g_small, kSmallThreads, smem, st>>>(fd, ep);
   mark(5);
   k_moments<M::D, M::P><<<phase_blocks(kPhaseMoments, M::ODE, N), kMomentThreads, 0, st>>>(fd, 0);
   mark(6);
@@ -822,6 +921,7 @@ cudaError_t launch_init(int ode, const FilterDev& fd, cudaStream_t st) {
     }
     case PF_ODE_LINEAR2: return launch_init_t<Linear2>(fd, st);
     case PF_ODE_ROBERTSON: return launch_init_t<Robertson>(fd, st);
+    case PF_ODE_MICHAELIS3: return launch_init_t<Michaelis>(fd, st);
     case PF_ODE_BRUSSELATOR1D: {
       const int64_t N = fd.N;
       k_init<64, 3><<<phase_blocks(kPhaseInit, ode, N), kInitThreads, 0, st>>>(fd);
@@ -837,6 +937,7 @@ cudaError_t launch_epoch(int ode, const FilterDev& fd, const EpochParams* ep, in
   switch (ode) {
     case PF_ODE_LINEAR2: return launch_epoch_t<Linear2>(fd, ep, S, st, marks);
     case PF_ODE_ROBERTSON: return launch_epoch_t<Robertson>(fd, ep, S, st, marks);
+    case PF_ODE_MICHAELIS3: return launch_epoch_t<Michaelis>(fd, ep, S, st, marks);
     case PF_ODE_BRUSSELATOR1D: return launch_epoch_bruss(fd, ep, S, st, marks);
     case PF_ODE_ADVDIFF2D: return launch_epoch_ad(fd, ep, S, st, marks);
   }
@@ -850,6 +951,7 @@ int kernels_per_epoch(int ode) {
 
 cudaError_t launch_theta_mean(const FilterDev& fd, cudaStream_t st) {
   if (fd.p == 2) k_theta_mean<2><<<1, kMomentThreads, 0, st>>>(fd);
+  else if (fd.p == 4) k_theta_mean<4><<<1, kMomentThreads, 0, st>>>(fd);
   else if (fd.p == 5) k_theta_mean<5><<<1, kMomentThreads, 0, st>>>(fd);
   else k_theta_mean<3><<<1, kMomentThreads, 0, st>>>(fd);
   return cudaGetLastError();
@@ -866,11 +968,17 @@ cudaError_t touch(K* k) {
 }
 }  // namespace
 
+// A kernel that stages the substep table in dynamic shared memory may need
+// more than the default 48 KB (PF_MAX_SUBSTEPS entries); loads it as well.
+cudaError_t allow_step_table(const void* k) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(StepCoef) * (size_t)kSMax));
+}
+
 cudaError_t preload_main_kernels() {
   const void* ks[] = {
       (const void*)k_init<2, 2>, (const void*)k_init<3, 3>, (const void*)k_init<64, 3>,
-      (const void*)k_stage1<Linear2>, (const void*)k_stage1<Robertson>,
-      (const void*)k_stage2<Linear2>, (const void*)k_stage2<Robertson>,
+      (const void*)k_init<3, 4>, (const void*)k_moments<3, 4>, (const void*)k_theta_mean<4>,
       (const void*)k_moments<2, 2>, (const void*)k_moments<3, 3>, (const void*)k_moments<64, 3>,
       (const void*)k_scan_tile, (const void*)k_scan_add, (const void*)k_resample,
       (const void*)k_theta_mean<2>, (const void*)k_theta_mean<3>, (const void*)k_theta_mean<5>,
@@ -886,12 +994,30 @@ cudaError_t preload_main_kernels() {
     const cudaError_t e = touch(k);
     if (e != cudaSuccess) return e;
   }
+  const void* batched[] = {(const void*)k_batch_stage<Linear2, 1>, (const void*)k_batch_stage<Linear2, 2>,
+                           (const void*)k_batch_stage<Robertson, 1>,
+                           (const void*)k_batch_stage<Robertson, 2>};
+  for (const void* k : batched) {
+    const cudaError_t e = allow_step_table(k);
+    if (e != cudaSuccess) return e;
+  }
+  static const int lmms[] = {PF_LMM_BDF2, PF_LMM_BDF3, PF_LMM_AM2, PF_LMM_AB2};
+  for (int lmm : lmms) {
+    StageKernel k[6];
+    stage_kernels<Linear2>(lmm, k[0], k[1]);
+    stage_kernels<Robertson>(lmm, k[2], k[3]);
+    stage_kernels<Michaelis>(lmm, k[4], k[5]);
+    for (StageKernel kk : k) {
+      const cudaError_t e = allow_step_table(reinterpret_cast<const void*>(kk));
+      if (e != cudaSuccess) return e;
+    }
+  }
   return cudaSuccess;
 }
 
 bool ode_supported(int ode) {
   return ode == PF_ODE_LINEAR2 || ode == PF_ODE_ROBERTSON || ode == PF_ODE_BRUSSELATOR1D ||
-         ode == PF_ODE_ADVDIFF2D;
+         ode == PF_ODE_ADVDIFF2D || ode == PF_ODE_MICHAELIS3;
 }
 
 cudaError_t launch_set_moments(const FilterDev& fd, cudaStream_t st) {

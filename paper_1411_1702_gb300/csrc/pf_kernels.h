@@ -53,6 +53,9 @@ cudaError_t launch_theta_mean(const FilterDev& fd, cudaStream_t st);
 // Load every kernel of the library on the current device now rather than at
 // its first launch (which may wait for the device to drain); once per device.
 cudaError_t preload_main_kernels();
+// Let kernel k stage a full substep table (PF_MAX_SUBSTEPS entries) in dynamic
+// shared memory; loads the kernel.
+cudaError_t allow_step_table(const void* k);
 cudaError_t preload_bruss_kernels();
 cudaError_t preload_kernels();
 // Brusselator stage kernels (pf_bruss.cu): stage 1 or 2 of one epoch.
@@ -74,6 +77,10 @@ bool ode_supported(int ode);
 // Substep table of one observation interval (host code, pf_grid.cu).
 int build_substeps(int lmm, int spacing, double dt, int substeps, double q0, double t_prev,
                    double t_next, int depth, double hprev1, double hprev2, StepCoef* tab,
-                   int max_steps, int* depth_out);
+                   int max_steps, int* depth_out, double* times_out = nullptr);
+bool lmm_known(int lmm);
+bool lmm_needs_uniform(int lmm);
+// M1's input Phi(t) (host, pf_grid.cu)
+double mm_input(double t);
 
 }  // namespace pfg

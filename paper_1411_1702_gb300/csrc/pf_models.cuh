@@ -2,7 +2,10 @@
 //
 // Each model solves the implicit substep equation of the LMM (the paper's
 // Sec. 2.1: implicit methods need a Newton-type solve every step)
-//     G(y) = y - r - gamma f(y) = 0,   r = rho1 x_n + rho2 x_{n-1},
+//     G(y) = y - r - gamma f(y) = 0,
+// with r the method's explicit part (rho1 x_n + rho2 x_{n-1} for BDF2); a
+// time-dependent input (kForced, added to component 0) is folded into r by
+// the caller, so newton() and gf() see only the autonomous part of f.
 // by K full Newton iterations (I - gamma J(y)) dy = -G(y) with the analytic
 // Jacobian re-evaluated at every iterate.  State, Jacobian and elimination
 // live in registers, one particle per thread.  Each elimination below is exact
@@ -16,6 +19,7 @@ namespace pfg {
 // x' = A x, A = [[-th1, th2], [0, -th2]].
 struct Linear2 {
   static constexpr int D = 2, P = 2, ODE = PF_ODE_LINEAR2;
+  static constexpr bool kForced = false;
   struct Th {
     double t1, t2;
   };
@@ -60,6 +64,7 @@ struct Linear2 {
 // inverse.
 struct Robertson {
   static constexpr int D = 3, P = 3, ODE = PF_ODE_ROBERTSON;
+  static constexpr bool kForced = false;
   struct Th {
     double k1, k2, k3;
   };
@@ -98,6 +103,56 @@ struct Robertson {
       y[0] += d1;
       y[1] += d2;
       y[2] += d3;
+    }
+  }
+};
+
+// M1 of Sec. 2.1, three compartments with Michaelis-Menten fluxes:
+//   x1' = Phi(t) - V1 x1/(x1+k1), x2' = V1 x1/(x1+k1) - V2 x2/(x2+k2),
+//   x3' = V2 x2/(x2+k2) - lambda (x3 - c0),  theta = (V1, V2, k1, k2).
+// The input Phi(t) is the same for every particle and comes per substep from
+// the host (kForced).  lambda and c0 are the known constants of the problem
+// (the paper names them without values; lambda = 0.5, c0 = 2 is the reading
+// the library is built with).  J is lower triangular,
+//   I - gamma J = [[1 + g a, 0, 0], [-g a, 1 + g b, 0], [0, -g b, 1 + g lambda]],
+// a = V1 k1/(x1+k1)^2, b = V2 k2/(x2+k2)^2, so each Newton step is a forward
+// substitution with one reciprocal per row.
+struct Michaelis {
+  static constexpr int D = 3, P = 4, ODE = PF_ODE_MICHAELIS3;
+  static constexpr bool kForced = true;
+  static constexpr double kLambda = 0.5, kC0 = 2.0;
+  struct Th {
+    double v1, v2, k1, k2;
+  };
+  __device__ __forceinline__ static Th theta(const double* t) { return Th{t[0], t[1], t[2], t[3]}; }
+
+  // gamma times the autonomous part of f (everything but the input)
+  __device__ __forceinline__ static void gf(const Th& T, double g, const double* x, double* out) {
+    const double j1 = T.v1 * x[0] * rcp_nr2(x[0] + T.k1);
+    const double j2 = T.v2 * x[1] * rcp_nr2(x[1] + T.k2);
+    out[0] = -g * j1;
+    out[1] = g * (j1 - j2);
+    out[2] = g * fma(-kLambda, x[2] - kC0, j2);
+  }
+
+  __device__ __forceinline__ static void newton(const Th& T, double g, const double* r, double* y,
+                                                int K) {
+    const double gl = rcp_nr2(fma(g, kLambda, 1.0));
+    for (int it = 0; it < K; ++it) {
+      const double q1 = rcp_nr2(y[0] + T.k1), q2 = rcp_nr2(y[1] + T.k2);
+      const double u1 = T.v1 * q1, u2 = T.v2 * q2;
+      const double j1 = u1 * y[0], j2 = u2 * y[1];
+      const double ga = g * (u1 * T.k1 * q1), gb = g * (u2 * T.k2 * q2);
+      // G = y - r - gamma f_aut(y)
+      const double G0 = fma(g, j1, y[0] - r[0]);
+      const double G1 = fma(-g, j1 - j2, y[1] - r[1]);
+      const double G2 = fma(-g, fma(-kLambda, y[2] - kC0, j2), y[2] - r[2]);
+      const double d0 = -G0 * rcp_nr(1.0 + ga);
+      const double d1 = fma(ga, d0, -G1) * rcp_nr(1.0 + gb);
+      const double d2 = fma(gb, d1, -G2) * gl;
+      y[0] += d0;
+      y[1] += d1;
+      y[2] += d2;
     }
   }
 };

@@ -17,7 +17,11 @@ LIB_PATH = os.path.join(HERE, "libpf_gb300.so")
 PF_OK, PF_ERR_INVALID_ARG, PF_ERR_OOM, PF_ERR_BUDGET, PF_ERR_CUDA = 0, 1, 2, 3, 4
 PF_ERR_DEGENERATE, PF_ERR_NUMERIC, PF_ERR_TIMEOUT, PF_ERR_STATE = 5, 6, 7, 8
 PF_ODE_LINEAR2, PF_ODE_ROBERTSON, PF_ODE_BRUSSELATOR1D, PF_ODE_ADVDIFF2D = 1, 2, 3, 4
-PF_LMM_BDF1, PF_LMM_BDF2 = 1, 2
+PF_ODE_MICHAELIS3 = 5
+PF_LMM_BDF1, PF_LMM_BDF2, PF_LMM_BDF3 = 1, 2, 3
+PF_LMM_AM1, PF_LMM_AM2, PF_LMM_AM3 = 11, 12, 13
+PF_LMM_AB1, PF_LMM_AB2, PF_LMM_AB3 = 21, 22, 23
+PF_SUBSTEP_ROW = 11
 MAX_SUBSTEPS = 640
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_INVALID_ARG", 2: "PF_ERR_OOM", 3: "PF_ERR_BUDGET",
@@ -180,8 +184,9 @@ def pf_resample_systematic_noalloc(log_g_ptr, N, u, cumulative_ptr, idx_ptr, str
 
 
 def pf_substep_table(lmm, spacing, dt, substeps, q0, t_prev, t_next, depth, hprev1, hprev2):
-    """Host-only: the substep table of one interval, shape (S, 9)."""
-    coef = np.zeros((MAX_SUBSTEPS, 9))
+    """Host-only: the substep table of one interval, shape (S, PF_SUBSTEP_ROW):
+    kind, h, gamma, rho1, rho2, pi0, pi1, pi2, mu, rho3, pi3."""
+    coef = np.zeros((MAX_SUBSTEPS, PF_SUBSTEP_ROW))
     dout = C.c_int()
     S = load().pf_substep_table(lmm, spacing, dt, substeps, q0, t_prev, t_next, depth, hprev1,
                                 hprev2, _d(coef), MAX_SUBSTEPS, C.byref(dout))

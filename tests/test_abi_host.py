@@ -63,7 +63,8 @@ def _create(pf, **over):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(d=4), dict(p=2), dict(N=0), dict(ode=9), dict(lmm=3), dict(a=0.0), dict(a=1.5),
+    dict(d=4), dict(p=2), dict(N=0), dict(ode=9), dict(lmm=4), dict(lmm=14), dict(lmm=3),
+    dict(lmm=12), dict(a=0.0), dict(a=1.5),
     dict(newton_iters=0), dict(obs_idx=[5]), dict(sigma=[0.0, 0.01]), dict(substeps=0),
     dict(substeps=100000), dict(prior_lo=[-1.0, 1.0, 1.0]), dict(kappa=-1.0), dict(spacing=7),
 ])
@@ -83,8 +84,17 @@ def _compare_tables(w, t_prev, t_next, depth, h1, h2, pf):
     for i in range(S):
         assert coef[i, 0] == o[i]["kind"]
         assert coef[i, 1] == o[i]["h"]  # the same grid formula gives the same steps
-        for j, key in enumerate(["gamma", "rho1", "rho2", "pi0", "pi1", "pi2", "mu"], start=2):
-            assert coef[i, j] == pytest.approx(o[i][key], rel=1e-12, abs=1e-15), (i, key)
+        if o[i]["kind"] > 10:
+            # Adams: the library packs the AM weights of f_n, f_{n-1} into
+            # rho1, rho2 and the AB weights into pi0..pi2
+            want = dict(gamma=o[i]["gamma"], rho1=o[i]["beta"][1], rho2=o[i]["beta"][2],
+                        pi0=o[i]["bab"][0], pi1=o[i]["bab"][1], pi2=o[i]["bab"][2], mu=o[i]["mu"],
+                        rho3=0.0, pi3=0.0)
+        else:
+            want = o[i]
+        keys = ["gamma", "rho1", "rho2", "pi0", "pi1", "pi2", "mu", "rho3", "pi3"]
+        for j, key in enumerate(keys, start=2):
+            assert coef[i, j] == pytest.approx(want[key], rel=1e-12, abs=1e-15), (i, key)
     return coef
 
 
@@ -102,6 +112,22 @@ def test_substep_table_matches_oracle(pf):
     _compare_tables(rw, t[20], t[21], 2, 0.3, 0.29, pf)
     bw = W.brusselator(N=4, T=3)
     _compare_tables(bw, 1.0 / 3.0, 2.0 / 3.0, 2, 1.0 / 60.0, 1.0 / 60.0, pf)
+
+
+@pytest.mark.parametrize("lmm", [3, 11, 12, 13, 21, 22, 23])
+def test_substep_table_other_lmms_match_oracle(pf, lmm):
+    """BDF3 and the Adams methods: the library's textbook weights against the
+    oracle's weights derived from Lagrange polynomials, cold start (the order
+    ramp) and carried history."""
+    mw = W.michaelis(N=4, T=2, lmm=lmm)
+    _compare_tables(mw, 0.0, 0.5, 0, 0.0, 0.0, pf)
+    _compare_tables(mw, 0.5, 1.0, 2, 0.05, 0.05, pf)
+    _compare_tables(mw, 0.5, 1.0, 1, 0.05, 0.05, pf)
+    lw = W.linear2(N=4, T=3).with_(lmm=lmm)
+    _compare_tables(lw, 0.1, 0.2, 2, 0.005, 0.005, pf)
+    # uniform spacing only
+    with pytest.raises(ValueError):
+        pf.pf_substep_table(lmm, 1, 0.0, 50, 1.01, 1e-4, 2e-4, 2, 1e-6, 1e-6)
 
 
 def test_substep_table_rejects_bad_intervals(pf):
