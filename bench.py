@@ -99,9 +99,12 @@ STAGE2_KERNEL["michaelis"] = "k_stage2<Michaelis, 0>"
 # DRAM bytes (read + write) of one stage-2 launch from an ncu capture of the
 # same command on a GB300 (profiles/ names each capture); None where no capture
 # of the kernel as it stands exists.
-STAGE2_TRAFFIC = {"robertson": 11550976 + 0,
-                  "brusselator": 11188473344 + 10732750592,
-                  "advdiff20": 2615808 + 336896}
+STAGE2_TRAFFIC = {"robertson": 11552512 + 0,
+                  "brusselator": 11202826752 + 10732933888,
+                  "advdiff20": 2621184 + 379648,
+                  "michaelisBDF2": 4353024 + 0,
+                  "michaelisAM3": 4586752 + 0,
+                  "michaelisAB3": 4459520 + 0}
 # The paper's own number for the same workload, where it has one: Table 3's
 # 2D advection-diffusion runs (BDF2, h = 0.1, N = 5000, 30 unit intervals,
 # 8 MATLAB workers on an i7-3820), converted to particle-LMM-steps/s at 600
