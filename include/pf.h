@@ -244,6 +244,23 @@ pf_status pf_set_ensemble(pf_filter* f, const double* x, const double* h1, const
                           const double* phi, const double* logw);
 pf_status pf_set_moments(pf_filter* f, const double* phibar, const double* C);
 
+/* Checkpoint and resume.  pf_save copies the committed state of f -- the
+ * ensemble (states, LMM history, parameters, log weights), the moments and
+ * their Cholesky factor, the weighted mean state, the epoch count and the LMM
+ * history bookkeeping -- into a caller-owned host buffer of at least
+ * pf_checkpoint_size bytes (about 8 * N * (3d + p + 1) bytes).  It waits for
+ * the filter's stream first.  pf_load restores such a blob into a filter
+ * created with the same problem, d, p, N, LMM, seed and filter id (checked:
+ * INVALID_ARG otherwise) and discards any loaded observation series.  The
+ * random streams are counter-based (seed, epoch, particle), so a resumed filter
+ * continues bit-identically to one that was never interrupted.  The blob is
+ * in this library's own layout and native byte order.  Errors: INVALID_ARG
+ * (NULL, short or foreign buffer, mismatched filter), STATE (pf_save with a
+ * failed epoch pending, pf_load into a batch member), CUDA. */
+pf_status pf_checkpoint_size(const pf_filter* f, size_t* bytes);
+pf_status pf_save(const pf_filter* f, void* buf, size_t bytes);
+pf_status pf_load(pf_filter* f, const void* buf, size_t bytes);
+
 /* Work arrays of the last epoch (N each): first-stage log-likelihoods, log
  * fitness weights, cumulative fitness weights c_k and resampled indices. */
 pf_status pf_get_work(const pf_filter* f, double* loglik1, double* log_g, double* cumulative,

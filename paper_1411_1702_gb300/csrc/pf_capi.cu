@@ -740,6 +740,120 @@ pf_status pf_get_work(const pf_filter* cf, double* loglik1, double* log_g, doubl
   return PF_OK;
 }
 
+// ---- checkpoint / resume ---------------------------------------------------
+// Blob: a header, the raw control block, the committed ensemble in its device
+// layout (x, h1, h2: d*N each, component-major; phi: p*N; unnormalised log
+// weights: N) and the committed weighted mean state (d).  Native byte order.
+namespace {
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t ode, d, p, lmm;
+  int32_t depth;
+  int64_t N;
+  int64_t epochs;
+  double t_prev, hprev1, hprev2;
+  uint64_t seed;
+  uint32_t filter_id;
+  uint32_t pad;
+  uint64_t total_bytes;
+};
+constexpr char kCkptMagic[8] = {'P', 'F', 'C', 'K', 'P', 'T', '0', '1'};
+
+size_t ckpt_bytes(const pf_filter* f) {
+  const size_t N = (size_t)f->N;
+  return sizeof(CkptHeader) + sizeof(Ctrl) +
+         sizeof(double) * (N * (3 * (size_t)f->d + (size_t)f->p + 1) + (size_t)f->d);
+}
+}  // namespace
+
+pf_status pf_checkpoint_size(const pf_filter* f, size_t* bytes) {
+  if (!f || !bytes) return fail(nullptr, PF_ERR_INVALID_ARG, "NULL argument");
+  *bytes = ckpt_bytes(f);
+  return PF_OK;
+}
+
+pf_status pf_save(const pf_filter* cf, void* buf, size_t bytes) {
+  pf_filter* f = const_cast<pf_filter*>(cf);
+  if (!f || !buf) return fail(nullptr, PF_ERR_INVALID_ARG, "NULL argument");
+  const size_t need = ckpt_bytes(f);
+  if (bytes < need) return fail(f, PF_ERR_INVALID_ARG, "checkpoint buffer too small");
+  PF_CUDA(f, cudaStreamSynchronize(f->stream));
+  pf_status st = read_ctrl(f);
+  if (st != PF_OK) return st;
+  if (f->ctrl_host->status != PF_OK) return fail(f, PF_ERR_STATE, "the filter has a failed epoch pending");
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, 8);
+  h.version = 1;
+  h.ode = f->ode; h.d = f->d; h.p = f->p; h.lmm = f->lmm;
+  h.depth = f->hist.depth;
+  h.N = f->N;
+  h.epochs = f->hist.epochs;
+  h.t_prev = f->hist.t_prev; h.hprev1 = f->hist.hprev1; h.hprev2 = f->hist.hprev2;
+  h.seed = f->seed; h.filter_id = f->filter_id;
+  h.total_bytes = need;
+  char* out = static_cast<char*>(buf);
+  std::memcpy(out, &h, sizeof h);
+  out += sizeof h;
+  std::memcpy(out, f->ctrl_host, sizeof(Ctrl));
+  out += sizeof(Ctrl);
+  const Ensemble& E = f->ctrl_host->cur ? f->fd.ens[1] : f->fd.ens[0];
+  const size_t N = (size_t)f->N, d = (size_t)f->d, p = (size_t)f->p;
+  const struct { const double* src; size_t n; } parts[] = {
+      {E.x, d * N}, {E.h1, d * N}, {E.h2, d * N}, {E.phi, p * N}, {E.lw, N}, {f->fd.xbar, d}};
+  for (const auto& part : parts) {
+    PF_CUDA(f, copy_sync(f, out, part.src, sizeof(double) * part.n, cudaMemcpyDeviceToHost));
+    f->d2h_bytes += (int64_t)(sizeof(double) * part.n);
+    out += sizeof(double) * part.n;
+  }
+  return PF_OK;
+}
+
+pf_status pf_load(pf_filter* f, const void* buf, size_t bytes) {
+  if (!f || !buf) return fail(nullptr, PF_ERR_INVALID_ARG, "NULL argument");
+  if (f->in_batch) return fail(f, PF_ERR_STATE, "the filter is a member of a batch");
+  CkptHeader h;
+  if (bytes < sizeof h) return fail(f, PF_ERR_INVALID_ARG, "checkpoint too short");
+  std::memcpy(&h, buf, sizeof h);
+  if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+    return fail(f, PF_ERR_INVALID_ARG, "not a checkpoint of this library");
+  if (h.ode != f->ode || h.d != f->d || h.p != f->p || h.lmm != f->lmm || h.N != f->N)
+    return fail(f, PF_ERR_INVALID_ARG, "checkpoint of a different problem, LMM or N");
+  if (h.seed != f->seed || h.filter_id != f->filter_id)
+    return fail(f, PF_ERR_INVALID_ARG, "checkpoint of a filter with another seed or filter id");
+  const size_t need = ckpt_bytes(f);
+  if (h.total_bytes != need || bytes < need) return fail(f, PF_ERR_INVALID_ARG, "checkpoint truncated");
+  if (h.epochs < 0 || h.depth < 0 || h.depth > 2 || !std::isfinite(h.t_prev))
+    return fail(f, PF_ERR_INVALID_ARG, "checkpoint history out of range");
+  PF_CUDA(f, cudaStreamSynchronize(f->stream));
+  const char* in = static_cast<const char*>(buf) + sizeof h;
+  Ctrl c;
+  std::memcpy(&c, in, sizeof c);
+  in += sizeof c;
+  c.cur = 0;
+  c.status = PF_OK;
+  const Ensemble& E = f->fd.ens[0];
+  const size_t N = (size_t)f->N, d = (size_t)f->d, p = (size_t)f->p;
+  const struct { double* dst; size_t n; } parts[] = {
+      {E.x, d * N}, {E.h1, d * N}, {E.h2, d * N}, {E.phi, p * N}, {E.lw, N}, {f->fd.xbar, d}};
+  for (const auto& part : parts) {
+    PF_CUDA(f, copy_sync(f, part.dst, in, sizeof(double) * part.n, cudaMemcpyHostToDevice));
+    f->h2d_bytes += (int64_t)(sizeof(double) * part.n);
+    in += sizeof(double) * part.n;
+  }
+  *f->ctrl_host = c;
+  PF_CUDA(f, copy_sync(f, f->fd.ctrl, f->ctrl_host, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  PF_CUDA(f, cudaMemsetAsync(f->fd.ticket, 0, sizeof(unsigned) * 8, f->stream));
+  PF_CUDA(f, cudaStreamSynchronize(f->stream));
+  f->hist = HistoryState{h.epochs, h.depth, h.t_prev, h.hprev1, h.hprev2};
+  if (f->series_dev) {
+    cudaFree(f->series_dev);
+    f->series_dev = nullptr;
+    f->series_T = 0;
+  }
+  return PF_OK;
+}
+
 pf_status pf_get_history(const pf_filter* f, int64_t* epochs, int* depth, double* t_prev,
                          double* hprev1, double* hprev2) {
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");

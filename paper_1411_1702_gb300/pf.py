@@ -37,7 +37,8 @@ ABI_SYMBOLS = [
     "pf_batch_create", "pf_batch_assimilate", "pf_batch_stats", "pf_batch_last_error",
     "pf_batch_destroy", "pf_server_create", "pf_server_open", "pf_server_submit",
     "pf_server_step", "pf_server_drain", "pf_server_close", "pf_server_session",
-    "pf_server_stats", "pf_server_last_error", "pf_server_destroy",
+    "pf_server_stats", "pf_server_last_error", "pf_server_destroy", "pf_checkpoint_size",
+    "pf_save", "pf_load",
 ]
 NOALLOC_MAX_PARTICLES = 1 << 24
 KERNEL_SLOTS = ["stage1", "scan_tile", "scan_add", "resample", "stage2", "moments"]
@@ -122,6 +123,9 @@ def load(path: str = LIB_PATH):
         "pf_get_work": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
         "pf_get_history": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int), _dp, _dp, _dp]),
         "pf_set_history": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_double]),
+        "pf_checkpoint_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+        "pf_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+        "pf_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
         "pf_substep_table": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
                                        C.c_double, C.c_int, C.c_double, C.c_double, _dp, C.c_int,
                                        C.POINTER(C.c_int)]),
@@ -326,6 +330,18 @@ class Filter:
     def pf_set_history(self, epoch, depth, t_prev, hprev1, hprev2):
         _check(load().pf_set_history(self._h, int(epoch), int(depth), float(t_prev), float(hprev1),
                                      float(hprev2)), self._h)
+
+    def pf_save(self) -> bytes:
+        """Checkpoint of the committed state (pf_checkpoint_size + pf_save)."""
+        n = C.c_size_t()
+        _check(load().pf_checkpoint_size(self._h, C.byref(n)), self._h)
+        buf = C.create_string_buffer(n.value)
+        _check(load().pf_save(self._h, buf, n.value), self._h)
+        return buf.raw
+
+    def pf_load(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(load().pf_load(self._h, buf, len(blob)), self._h)
 
 
 class Batch:
