@@ -88,13 +88,12 @@ struct Robertson {
       const double q = gk3 * y[1];  // g k3 y2
       const double p = gk3 * y[2];  // g k3 y3
       const double t = gk2 * y[1];  // g k2 y2
-      const double c = t * y[1];    // g k2 y2^2
       const double w = t + t;       // 2 g k2 y2
-      const double b = q * y[2];    // g k3 y2 y3
-      // G = y - r - gamma f(y)
-      const double G1 = fma(gk1, y[0], (y[0] - r[0]) - b);
-      const double G2 = fma(-gk1, y[0], ((y[1] - r[1]) + b) + c);
-      const double G3 = (y[2] - r[2]) - c;
+      // G = y - r - gamma f(y), the products g k3 y2 y3 = q y3 and
+      // g k2 y2^2 = t y2 fused into the sums
+      const double G1 = fma(-q, y[2], fma(gk1, y[0], y[0] - r[0]));
+      const double G2 = fma(-gk1, y[0], fma(q, y[2], fma(t, y[1], y[1] - r[1])));
+      const double G3 = fma(-t, y[1], y[2] - r[2]);
       const double den = fma(im, fma(q, w, p), 1.0 + w);
       const double num = fma(q * im, G3, -fma(l, G1, G2));
       const double d2 = num * rcp_nr(den);
