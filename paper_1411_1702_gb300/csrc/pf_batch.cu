@@ -788,6 +788,7 @@ void pf_batch_destroy(pf_batch* b) {
 const char* pf_batch_last_error(const pf_batch* b) { return b ? b->err.c_str() : ""; }
 
 pf_status pf_batch_assimilate(pf_batch* b, const double* t, const double* const* y, int* status) {
+  const pfg::NvtxRange nvtx_range("pf_batch_assimilate");
   if (!b) return bfail(nullptr, PF_ERR_INVALID_ARG, "batch is NULL");
   if (!t || !y || !status) return bfail(b, PF_ERR_INVALID_ARG, "NULL argument");
   pf_status st = batch_launch(b, t, y, status);
@@ -926,6 +927,7 @@ pf_status pf_server_submit(pf_server* s, int64_t session, double t_k, const doub
 static pf_status server_step(pf_server* s, int* launched);
 
 pf_status pf_server_step(pf_server* s, int* launched) {
+  const pfg::NvtxRange nvtx_range("pf_server_step");
   if (!s) return sfail(nullptr, PF_ERR_INVALID_ARG, "server is NULL");
   const double t0 = now_ms();
   const pf_status st = server_step(s, launched);

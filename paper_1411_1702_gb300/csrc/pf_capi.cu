@@ -343,6 +343,7 @@ const char* pf_version(void) { return "paper_1411_1702_gb300 0.1 (sm_103a, FP64)
 
 pf_status pf_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
                     const pf_prior* prior, const pf_options* opt, pf_filter** out) {
+  const pfg::NvtxRange nvtx_range("pf_create");
   return filter_create(ode, d, p, N, lmm, dt, prior, opt, nullptr, out);
 }
 
@@ -467,6 +468,7 @@ const char* pf_last_error(const pf_filter* f) {
 }
 
 pf_status pf_assimilate(pf_filter* f, double t_k, const double* y_k) {
+  const pfg::NvtxRange nvtx_range("pf_assimilate");
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
   if (!y_k) return fail(f, PF_ERR_INVALID_ARG, "y_k is NULL");
   for (int i = 0; i < f->m; ++i)
@@ -602,6 +604,7 @@ pf_status pf_load_observations(pf_filter* f, int T, const double* t, const doubl
 }
 
 pf_status pf_run(pf_filter* f, int k0, int k1) {
+  const pfg::NvtxRange nvtx_range("pf_run");
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
   if (!f->series_dev) return fail(f, PF_ERR_STATE, "no observation series loaded");
   if (k0 != f->series_next) return fail(f, PF_ERR_STATE, "epochs must run in order");

@@ -1,12 +1,23 @@
 // pf_filter.h -- the library-owned filter object behind the opaque pf_filter
 // handle (shared by the single-filter C ABI and the batch of filters).
 #pragma once
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 #include <vector>
 
 #include "pf_kernels.h"
 
 namespace pfg {
+
+// NVTX range over one host call (visible in Nsight Systems / Compute
+// timelines; free when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct HistoryState {
   int64_t epochs;
