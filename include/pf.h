@@ -294,9 +294,11 @@ int pf_substep_table(int lmm, int spacing, double dt, int substeps, double q0, d
                      int max_steps, int* depth_out);
 
 /* ---- batches of filters ---------------------------------------------------
- * A batch advances many independent filters (any mix of ODEs and sizes) by
- * one epoch each with a handful of tile-scheduled launches -- one per phase
- * of Algorithm 1's epoch, split by model where the kernels differ -- captured
+ * A batch advances many independent filters (any mix of problems, LMMs and
+ * sizes, except PF_ODE_ADVDIFF2D, whose one-block-per-particle kernels do not
+ * batch: INVALID_ARG) by one epoch each with a handful of tile-scheduled
+ * launches -- one per phase of Algorithm 1's epoch, split by problem and LMM
+ * family where the kernels differ -- captured
  * in a CUDA graph that is reused while the set of active filters stays the
  * same.  On its first epoch the batch autotunes the launch shape (tile order,
  * concurrent per-model branches) by timing the candidates on that epoch.  Each filter's results are bit-identical to running it alone: its

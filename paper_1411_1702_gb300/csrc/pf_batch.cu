@@ -73,9 +73,36 @@ __global__ void k_batch_clear(const FilterDev* __restrict__ fds, const int* __re
 
 namespace {
 
-constexpr int kModels = 3;  // linear2, robertson, brusselator
+// Launch groups: the stage kernels differ by problem and LMM family, the
+// moments kernel by problem.  Group g's kernels are those of (kGroupOde[g],
+// kGroupLmm[g]).
+constexpr int kStageGroups = 13;
+constexpr int kGroupOde[kStageGroups] = {1, 1, 1, 1, 2, 2, 2, 2, 3, 5, 5, 5, 5};
+constexpr int kGroupLmm[kStageGroups] = {2, 3, 12, 22, 2, 3, 12, 22, 2, 2, 3, 12, 22};
+constexpr int kMomentGroups = 4;
+constexpr int kMomentOde[kMomentGroups] = {1, 2, 3, 5};
+int family_of(int lmm) { return lmm == PF_LMM_BDF3 ? 1 : lmm / 10 == 1 ? 2 : lmm / 10 == 2 ? 3 : 0; }
+int stage_group(int ode, int lmm) {
+  const int fam = family_of(lmm);
+  switch (ode) {
+    case PF_ODE_LINEAR2: return fam;
+    case PF_ODE_ROBERTSON: return 4 + fam;
+    case PF_ODE_BRUSSELATOR1D: return 8;
+    case PF_ODE_MICHAELIS3: return 9 + fam;
+  }
+  return -1;
+}
+int moment_group(int ode) {
+  for (int g = 0; g < kMomentGroups; ++g)
+    if (kMomentOde[g] == ode) return g;
+  return -1;
+}
+// cost classes of the server's lanes: linear2, Robertson and M1, Brusselator
+constexpr int kCostModels = 3;
+int cost_model(int ode) {
+  return ode == PF_ODE_BRUSSELATOR1D ? 2 : ode == PF_ODE_LINEAR2 ? 0 : 1;
+}
 constexpr size_t kInitialTiles = 1 << 18;
-int model_index(int ode) { return ode - 1; }
 
 struct Range {
   int off = 0, cnt = 0;
@@ -113,8 +140,8 @@ struct pf_batch {
   size_t tiles_cap = 0;
   std::vector<BatchTile> tiles_host;
   BatchTile* tiles_pin = nullptr;        // pinned staging of the tile upload (tiles_cap)
-  Range stage[2][kModels];
-  Range moments[kModels];
+  Range stage[2][kStageGroups];
+  Range moments[kMomentGroups];
   Range scan_tile, scan_add, resample;
   int* slots_dev = nullptr;              // active slots of the epoch in flight
   int* slots_pin = nullptr;              // pinned staging (cap)
@@ -162,13 +189,19 @@ static void build_tiles(pf_batch* b, const std::vector<char>& active, int order_
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return b->slot[x]->N > b->slot[y]->N; });
   b->tiles_host.clear();
+  // group: -1 every filter; else the stage group (stage phases) or the
+  // moment group (moments) the filter must belong to
+  auto member = [&](const pf_filter* F, int phase, int group) {
+    if (group < 0) return true;
+    return phase == kPhaseMoments ? moment_group(F->ode) == group : stage_group(F->ode, F->lmm) == group;
+  };
   auto add = [&](int phase, int model) {
     Range r;
     r.off = (int)b->tiles_host.size();
     if (order_kind == 0) {
       for (int f : order) {
         const pf_filter* F = b->slot[f];
-        if (model >= 0 && model_index(F->ode) != model) continue;
+        if (!member(F, phase, model)) continue;
         const int nb = phase_blocks(phase, F->ode, F->N);
         for (int v = 0; v < nb; ++v) b->tiles_host.push_back(BatchTile{f, v});
       }
@@ -178,19 +211,19 @@ static void build_tiles(pf_batch* b, const std::vector<char>& active, int order_
       for (int v = 0; v < most; ++v)
         for (int f : order) {
           const pf_filter* F = b->slot[f];
-          if (model >= 0 && model_index(F->ode) != model) continue;
+          if (!member(F, phase, model)) continue;
           if (v < phase_blocks(phase, F->ode, F->N)) b->tiles_host.push_back(BatchTile{f, v});
         }
     }
     r.cnt = (int)b->tiles_host.size() - r.off;
     return r;
   };
-  for (int m = 0; m < kModels; ++m) b->stage[0][m] = add(kPhaseStage1, m);
+  for (int g = 0; g < kStageGroups; ++g) b->stage[0][g] = add(kPhaseStage1, g);
   b->scan_tile = add(kPhaseScanTile, -1);
   b->scan_add = add(kPhaseScanAdd, -1);
   b->resample = add(kPhaseResample, -1);
-  for (int m = 0; m < kModels; ++m) b->stage[1][m] = add(kPhaseStage2, m);
-  for (int m = 0; m < kModels; ++m) b->moments[m] = add(kPhaseMoments, m);
+  for (int g = 0; g < kStageGroups; ++g) b->stage[1][g] = add(kPhaseStage2, g);
+  for (int g = 0; g < kMomentGroups; ++g) b->moments[g] = add(kPhaseMoments, g);
 }
 
 // Host copies go through pinned staging, so they never wait for the device.
@@ -225,35 +258,38 @@ static cudaError_t launch_phases(pf_batch* b, size_t smem, const Shape& shape, b
   const EpochParams* const* eps = b->eps_dev;
   const BatchTile* T = b->tiles_dev;
   cudaError_t e = cudaSuccess;
-  auto run = [&](int phase, int ode, const Range& r, cudaStream_t st) {
+  auto run = [&](int phase, int ode, int lmm, const Range& r, cudaStream_t st) {
     if (e == cudaSuccess && r.cnt > 0)
-      e = launch_batch_phase(phase, ode, fds, eps, T + r.off, r.cnt, smem, 0, st);
+      e = launch_batch_phase(phase, ode, lmm, fds, eps, T + r.off, r.cnt, smem, 0, st);
   };
-  auto per_model = [&](int phase, const Range* rs) {
+  // the groups of a phase, the largest on the main branch and (concurrent
+  // shape) the others on the side branch
+  auto per_model = [&](int phase, const Range* rs, int ngroups, const int* odes, const int* lmms) {
     int used = 0, big = -1;
-    for (int m = 0; m < kModels; ++m)
+    for (int m = 0; m < ngroups; ++m)
       if (rs[m].cnt > 0) {
         ++used;
         if (big < 0 || rs[m].cnt > rs[big].cnt) big = m;
       }
+    auto lmm_of = [&](int m) { return lmms ? lmms[m] : PF_LMM_BDF2; };
     if (!shape.concurrent || used < 2) {
-      for (int m = 0; m < kModels; ++m) run(phase, m + 1, rs[m], b->stream);
+      for (int m = 0; m < ngroups; ++m) run(phase, odes[m], lmm_of(m), rs[m], b->stream);
       return;
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
-    run(phase, big + 1, rs[big], b->stream);
-    for (int m = 0; m < kModels; ++m)
-      if (m != big) run(phase, m + 1, rs[m], b->side);
+    run(phase, odes[big], lmm_of(big), rs[big], b->stream);
+    for (int m = 0; m < ngroups; ++m)
+      if (m != big) run(phase, odes[m], lmm_of(m), rs[m], b->side);
     if (e == cudaSuccess) e = cudaEventRecord(b->join, b->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join, 0);
   };
-  per_model(kPhaseStage1, b->stage[0]);
-  run(kPhaseScanTile, 0, b->scan_tile, b->stream);
-  run(kPhaseScanAdd, 0, b->scan_add, b->stream);
-  run(kPhaseResample, 0, b->resample, b->stream);
-  per_model(kPhaseStage2, b->stage[1]);
-  if (with_moments) per_model(kPhaseMoments, b->moments);
+  per_model(kPhaseStage1, b->stage[0], kStageGroups, kGroupOde, kGroupLmm);
+  run(kPhaseScanTile, 0, 0, b->scan_tile, b->stream);
+  run(kPhaseScanAdd, 0, 0, b->scan_add, b->stream);
+  run(kPhaseResample, 0, 0, b->resample, b->stream);
+  per_model(kPhaseStage2, b->stage[1], kStageGroups, kGroupOde, kGroupLmm);
+  if (with_moments) per_model(kPhaseMoments, b->moments, kMomentGroups, kMomentOde, nullptr);
   return e;
 }
 
@@ -414,8 +450,6 @@ static pf_status batch_add(pf_batch* b, pf_filter* f, int* slot_out) {
   if (f->in_batch) return bfail(b, PF_ERR_INVALID_ARG, "filter already in a batch");
   if (f->ode == PF_ODE_ADVDIFF2D)
     return bfail(b, PF_ERR_INVALID_ARG, "2D advection-diffusion filters do not batch (one block per particle)");
-  if (f->ode == PF_ODE_MICHAELIS3 || (f->lmm != PF_LMM_BDF1 && f->lmm != PF_LMM_BDF2))
-    return bfail(b, PF_ERR_INVALID_ARG, "batches run BDF1/BDF2 filters of the linear, Robertson and Brusselator problems");
   int s = -1;
   for (int i = 0; i < b->cap; ++i)
     if (!b->slot[i]) {
@@ -583,7 +617,7 @@ static pf_status batch_collect(pf_batch* b, int* status) {
 // ============================================================== the server
 namespace {
 
-constexpr int kDefaultLanes = 2 * kModels;
+constexpr int kDefaultLanes = 2 * kCostModels;
 constexpr int64_t kLargeSession = 32768;  // particles; larger sessions get their own lanes
 
 struct Pending {
@@ -638,20 +672,21 @@ static pf_status sfail(pf_server* s, pf_status st, const std::string& msg) {
   return st;
 }
 
-// Sessions of one model and size class share a lane, so a long epoch of large
-// or expensive filters does not hold back the small ones.
+// Sessions of one cost class (linear2; Robertson and M1; Brusselator) and
+// size class share a lane, so a long epoch of large or expensive filters does
+// not hold back the small ones.  A lane's batch mixes any problems and LMMs.
 static int session_class(pf_ode ode, int64_t N) {
-  return model_index(ode) * 2 + (N > kLargeSession ? 1 : 0);
+  return cost_model(ode) * 2 + (N > kLargeSession ? 1 : 0);
 }
 static int lane_of(const pf_server* s, pf_ode ode, int64_t N) {
   return session_class(ode, N) % (int)s->lanes.size();
 }
-// Cost rank of a class's epochs (0 = cheapest): small linear2 and Robertson,
+// Cost rank of a class's epochs (0 = cheapest): small linear2, Robertson and M1,
 // large ones, small Brusselator, large Brusselator.  Lanes of cheaper classes
 // run on higher-priority streams, so their short epochs are scheduled ahead of
 // the pending blocks of long ones (shortest job first).
 static int class_rank(int cls) {
-  static const int rank[2 * kModels] = {0, 1, 0, 1, 2, 3};
+  static const int rank[2 * kCostModels] = {0, 1, 0, 1, 2, 3};
   return rank[cls];
 }
 
@@ -845,7 +880,7 @@ pf_status pf_server_create(int64_t budget_bytes, int lanes, pf_server** out) {
   cudaDeviceGetStreamPriorityRange(&least, &greatest);
   for (int i = 0; i < lanes; ++i) {
     int rank = 3;
-    for (int cls = 0; cls < 2 * kModels; ++cls)
+    for (int cls = 0; cls < 2 * kCostModels; ++cls)
       if (cls % lanes == i) rank = std::min(rank, class_rank(cls));
     const int prio = lanes == 1 ? least : std::min(least, greatest + rank);
     pf_batch* b = nullptr;
@@ -886,8 +921,6 @@ pf_status pf_server_open(pf_server* s, pf_ode ode, int d, int p, int64_t N, pf_l
   }
   if (ode == PF_ODE_ADVDIFF2D)
     return sfail(s, PF_ERR_INVALID_ARG, "2D advection-diffusion sessions are not served (no batched kernels)");
-  if (ode == PF_ODE_MICHAELIS3 || (lmm != PF_LMM_BDF1 && lmm != PF_LMM_BDF2))
-    return sfail(s, PF_ERR_INVALID_ARG, "sessions run BDF1/BDF2 filters of the linear, Robertson and Brusselator problems");
   Session ss;
   ss.id = s->next_id++;
   ss.ode = ode; ss.d = d; ss.p = p; ss.N = N; ss.lmm = lmm; ss.dt = dt;

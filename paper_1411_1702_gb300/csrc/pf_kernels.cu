@@ -694,10 +694,11 @@ __global__ void __launch_bounds__(kInitThreads) k_batch_init(const FilterDev* __
     case PF_ODE_LINEAR2: init_body<2, 2>(fd, t.vb); break;
     case PF_ODE_ROBERTSON: init_body<3, 3>(fd, t.vb); break;
     case PF_ODE_BRUSSELATOR1D: init_body<64, 3>(fd, t.vb); break;
+    case PF_ODE_MICHAELIS3: init_body<3, 4>(fd, t.vb); break;
   }
 }
 
-template <class M, int STAGE>
+template <class M, int STAGE, int F>
 __global__ void __launch_bounds__(kSmallThreads) k_batch_stage(const FilterDev* __restrict__ fds,
                                                              const EpochParams* const* __restrict__ eps,
                                                              const BatchTile* __restrict__ tiles) {
@@ -711,8 +712,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_batch_stage(const FilterDev* 
   StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
   load_steps(s_sc, ep, ep->S);
   const int vg = (int)((fd.N + kSmallThreads - 1) / kSmallThreads);
-  if (STAGE == 1) stage1_body<M, kFamBdf12>(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
-  else stage2_body<M, kFamBdf12>(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
+  if (STAGE == 1) stage1_body<M, F>(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
+  else stage2_body<M, F>(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_batch_scan_tile(const FilterDev* __restrict__ fds,
@@ -827,6 +828,20 @@ static void stage_kernels(int lmm, StageKernel& k1, StageKernel& k2) {
   }
   k1 = k_stage1<M, kFamBdf12>;
   k2 = k_stage2<M, kFamBdf12>;
+}
+
+using BatchStageKernel = void (*)(const FilterDev*, const EpochParams* const*, const BatchTile*);
+
+// the batched stage kernels of model M for an LMM family
+template <class M>
+static void batch_stage_kernels(int lmm, BatchStageKernel& k1, BatchStageKernel& k2) {
+  switch (lmm_family(lmm)) {
+    case kFamBdf3: k1 = k_batch_stage<M, 1, kFamBdf3>; k2 = k_batch_stage<M, 2, kFamBdf3>; return;
+    case kFamAm: k1 = k_batch_stage<M, 1, kFamAm>; k2 = k_batch_stage<M, 2, kFamAm>; return;
+    case kFamAb: k1 = k_batch_stage<M, 1, kFamAb>; k2 = k_batch_stage<M, 2, kFamAb>; return;
+  }
+  k1 = k_batch_stage<M, 1, kFamBdf12>;
+  k2 = k_batch_stage<M, 2, kFamBdf12>;
 }
 
 template <class M>
@@ -984,31 +999,27 @@ cudaError_t preload_main_kernels() {
       (const void*)k_theta_mean<2>, (const void*)k_theta_mean<3>, (const void*)k_theta_mean<5>,
       (const void*)k_set_moments, (const void*)k_init<0, 5>, (const void*)k_moments<0, 5>,
       (const void*)k_xbar,
-      (const void*)k_batch_init, (const void*)k_batch_stage<Linear2, 1>,
-      (const void*)k_batch_stage<Linear2, 2>, (const void*)k_batch_stage<Robertson, 1>,
-      (const void*)k_batch_stage<Robertson, 2>, (const void*)k_batch_scan_tile,
+      (const void*)k_batch_init, (const void*)k_batch_scan_tile,
       (const void*)k_batch_scan_add, (const void*)k_batch_resample,
       (const void*)k_batch_moments<2, 2>, (const void*)k_batch_moments<3, 3>,
-      (const void*)k_batch_moments<64, 3>};
+      (const void*)k_batch_moments<64, 3>, (const void*)k_batch_moments<3, 4>};
   for (const void* k : ks) {
     const cudaError_t e = touch(k);
-    if (e != cudaSuccess) return e;
-  }
-  const void* batched[] = {(const void*)k_batch_stage<Linear2, 1>, (const void*)k_batch_stage<Linear2, 2>,
-                           (const void*)k_batch_stage<Robertson, 1>,
-                           (const void*)k_batch_stage<Robertson, 2>};
-  for (const void* k : batched) {
-    const cudaError_t e = allow_step_table(k);
     if (e != cudaSuccess) return e;
   }
   static const int lmms[] = {PF_LMM_BDF2, PF_LMM_BDF3, PF_LMM_AM2, PF_LMM_AB2};
   for (int lmm : lmms) {
     StageKernel k[6];
+    BatchStageKernel kb[6];
     stage_kernels<Linear2>(lmm, k[0], k[1]);
     stage_kernels<Robertson>(lmm, k[2], k[3]);
     stage_kernels<Michaelis>(lmm, k[4], k[5]);
-    for (StageKernel kk : k) {
-      const cudaError_t e = allow_step_table(reinterpret_cast<const void*>(kk));
+    batch_stage_kernels<Linear2>(lmm, kb[0], kb[1]);
+    batch_stage_kernels<Robertson>(lmm, kb[2], kb[3]);
+    batch_stage_kernels<Michaelis>(lmm, kb[4], kb[5]);
+    for (int i = 0; i < 6; ++i) {
+      cudaError_t e = allow_step_table(reinterpret_cast<const void*>(k[i]));
+      if (e == cudaSuccess) e = allow_step_table(reinterpret_cast<const void*>(kb[i]));
       if (e != cudaSuccess) return e;
     }
   }
@@ -1029,9 +1040,9 @@ cudaError_t launch_set_moments(const FilterDev& fd, cudaStream_t st) {
 // moment phases need tiles of one model only (ode); the other phases take any
 // mix.
 // smem is the step-table size of the largest interval among the filters.
-cudaError_t launch_batch_phase(int phase, int ode, const FilterDev* fds, const EpochParams* const* eps,
-                               const BatchTile* tiles, int ntiles, size_t smem, int is_init,
-                               cudaStream_t st) {
+cudaError_t launch_batch_phase(int phase, int ode, int lmm, const FilterDev* fds,
+                               const EpochParams* const* eps, const BatchTile* tiles, int ntiles,
+                               size_t smem, int is_init, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   switch (phase) {
     case kPhaseInit: k_batch_init<<<ntiles, kInitThreads, 0, st>>>(fds, tiles); break;
@@ -1040,15 +1051,12 @@ cudaError_t launch_batch_phase(int phase, int ode, const FilterDev* fds, const E
       const int stage = phase == kPhaseStage1 ? 1 : 2;
       if (ode == PF_ODE_BRUSSELATOR1D)
         return launch_batch_bruss_stage(stage, fds, eps, tiles, ntiles, smem, st);
-      if (ode == PF_ODE_ROBERTSON) {
-        if (stage == 1) k_batch_stage<Robertson, 1><<<ntiles, kSmallThreads, smem, st>>>(fds, eps, tiles);
-        else k_batch_stage<Robertson, 2><<<ntiles, kSmallThreads, smem, st>>>(fds, eps, tiles);
-      } else if (ode == PF_ODE_LINEAR2) {
-        if (stage == 1) k_batch_stage<Linear2, 1><<<ntiles, kSmallThreads, smem, st>>>(fds, eps, tiles);
-        else k_batch_stage<Linear2, 2><<<ntiles, kSmallThreads, smem, st>>>(fds, eps, tiles);
-      } else {
-        return cudaErrorInvalidValue;
-      }
+      BatchStageKernel k1, k2;
+      if (ode == PF_ODE_ROBERTSON) batch_stage_kernels<Robertson>(lmm, k1, k2);
+      else if (ode == PF_ODE_LINEAR2) batch_stage_kernels<Linear2>(lmm, k1, k2);
+      else if (ode == PF_ODE_MICHAELIS3) batch_stage_kernels<Michaelis>(lmm, k1, k2);
+      else return cudaErrorInvalidValue;
+      (stage == 1 ? k1 : k2)<<<ntiles, kSmallThreads, smem, st>>>(fds, eps, tiles);
       break;
     }
     case kPhaseScanTile: k_batch_scan_tile<<<ntiles, kScanThreads, 0, st>>>(fds, tiles); break;
@@ -1058,6 +1066,7 @@ cudaError_t launch_batch_phase(int phase, int ode, const FilterDev* fds, const E
       if (ode == PF_ODE_LINEAR2) k_batch_moments<2, 2><<<ntiles, kMomentThreads, 0, st>>>(fds, tiles, is_init);
       else if (ode == PF_ODE_ROBERTSON) k_batch_moments<3, 3><<<ntiles, kMomentThreads, 0, st>>>(fds, tiles, is_init);
       else if (ode == PF_ODE_BRUSSELATOR1D) k_batch_moments<64, 3><<<ntiles, kMomentThreads, 0, st>>>(fds, tiles, is_init);
+      else if (ode == PF_ODE_MICHAELIS3) k_batch_moments<3, 4><<<ntiles, kMomentThreads, 0, st>>>(fds, tiles, is_init);
       else return cudaErrorInvalidValue;
       break;
     default: return cudaErrorInvalidValue;

@@ -27,10 +27,11 @@ struct BatchTile {
 int phase_blocks(int phase, int ode, int64_t N);
 int bruss_stage_blocks(int64_t N);
 // One batched phase over a device tile table (see pf_kernels.cu); stage
-// phases take the tiles of one model (ode).
-cudaError_t launch_batch_phase(int phase, int ode, const FilterDev* fds, const EpochParams* const* eps,
-                               const BatchTile* tiles, int ntiles, size_t smem, int is_init,
-                               cudaStream_t st);
+// phases take the tiles of one model (ode) and LMM family (that of lmm), the
+// moments those of one model.
+cudaError_t launch_batch_phase(int phase, int ode, int lmm, const FilterDev* fds,
+                               const EpochParams* const* eps, const BatchTile* tiles, int ntiles,
+                               size_t smem, int is_init, cudaStream_t st);
 // Batched Brusselator stage (1 or 2) over its own tile table (pf_bruss.cu).
 cudaError_t launch_batch_bruss_stage(int stage, const FilterDev* fds, const EpochParams* const* eps,
                                      const BatchTile* tiles, int ntiles, size_t smem,

@@ -121,3 +121,27 @@ def test_batch_membership_rules(pf):
     b2.close()
     with pytest.raises(pf.PfError):
         pf.Batch([fs[0], fs[0]])
+
+
+def test_batched_lmm_families_and_m1_equal_alone(pf):
+    """Every LMM family and the paper's M1 system in one batch (each family is
+    a separate group of launches): bit-identical to each filter alone."""
+    ws = [W.michaelis(N=3001, T=4, seed=1, lmm=W.LMM_AM3),
+          W.michaelis(N=700, T=4, seed=2, lmm=W.LMM_AB2),
+          W.michaelis(N=1500, T=4, seed=3, lmm=W.LMM_BDF3),
+          W.michaelis(N=257, T=4, seed=4, lmm=W.LMM_BDF2),
+          W.linear2(N=1000, T=4, seed=5).with_(lmm=W.LMM_AM2),
+          W.linear2(N=513, T=4, seed=6).with_(lmm=W.LMM_AB3),
+          W.robertson(N=2000, T=4, seed=7),
+          W.brusselator(N=65, T=4, seed=8)]
+    alone = [pf.Filter.from_workload(w) for w in ws]
+    members = [pf.Filter.from_workload(w) for w in ws]
+    batch = pf.Batch(members)
+    for k in range(4):
+        for f, w in zip(alone, ws):
+            f.pf_assimilate(w.t_obs[k], w.y_obs[k])
+        st = batch.pf_batch_assimilate([w.t_obs[k] for w in ws], [w.y_obs[k] for w in ws])
+        assert st == [pf.PF_OK] * len(ws)
+        for a, m in zip(alone, members):
+            assert _same(a, m)
+            assert all(np.array_equal(u, v) for u, v in zip(a.pf_estimates(), m.pf_estimates()))

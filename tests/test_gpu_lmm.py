@@ -123,13 +123,11 @@ def test_lmm_argument_rules(pf):
     with pytest.raises(pf.PfError) as ei:
         pf.Filter.from_workload(W.brusselator(N=8, T=2).with_(lmm=W.LMM_BDF3))
     assert ei.value.status == pf.PF_ERR_INVALID_ARG
-    # batches run BDF1/BDF2 filters of the three batched problems only
+    # M1 and every family batch (the batch launches one group per problem and family)
     f = pf.Filter.from_workload(w)
-    with pytest.raises(pf.PfError):
-        pf.Batch([f])
     f2 = pf.Filter.from_workload(W.linear2(N=8, T=2).with_(lmm=W.LMM_AM3))
-    with pytest.raises(pf.PfError):
-        pf.Batch([f2])
+    b = pf.Batch([f, f2])
+    assert b.pf_batch_assimilate([w.t_obs[0], 0.1], [w.y_obs[0], [1.0]]) == [pf.PF_OK] * 2
 
 
 @pytest.mark.parametrize("lmm", [W.LMM_BDF2, W.LMM_AM3])

@@ -23,13 +23,23 @@ def _sessions():
     return [W.get(name, N=N, T=4, seed=seed) for name, N, seed in specs]
 
 
+def _sessions_lmm():
+    """The paper's M1 system and the other LMM families among the sessions."""
+    return [W.michaelis(N=4096, T=4, seed=21, lmm=W.LMM_AM3),
+            W.michaelis(N=40000, T=4, seed=22, lmm=W.LMM_AB3),
+            W.linear2(N=2048, T=4, seed=23).with_(lmm=W.LMM_BDF3),
+            W.robertson(N=1000, T=4, seed=24),
+            W.michaelis(N=512, T=4, seed=25, lmm=W.LMM_BDF2)]
+
+
 def _same(a, b):
     ea, eb = a.pf_get_ensemble(), b.pf_get_ensemble()
     return all(np.array_equal(ea[k], eb[k], equal_nan=True) for k in ea)
 
 
-def test_sessions_match_alone_under_interleaved_arrivals(pf):
-    ws = _sessions()
+@pytest.mark.parametrize("make", [_sessions, _sessions_lmm])
+def test_sessions_match_alone_under_interleaved_arrivals(pf, make):
+    ws = make()
     srv = pf.Server(budget_bytes=8 << 30)
     sids = [srv.pf_server_open(w, filter_id=i) for i, w in enumerate(ws)]
     rng = np.random.default_rng(3)
