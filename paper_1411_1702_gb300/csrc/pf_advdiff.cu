@@ -4,24 +4,30 @@
 // B1 = I (x) ell, B2 = ell (x) I, (ell u)_j = u_j - u_{j-1} (periodic), state
 // U[iy*nt + ix], theta = (k1, k2, k3, c1, c2).
 //
-// The system is linear, so Newton's method (Sec. 2.1) with the exact Jacobian
-// L solves each BDF step in one iteration; the work is the linear solve with
-// I - gamma L, which differs per particle (theta) and per step size.  L is
-// built from circulant difference matrices, so the 2D DFT diagonalises it:
-// with a(m) = 1 - exp(-2 pi i m / nt) the symbol of ell,
+// L is built from circulant difference matrices, so the 2D DFT diagonalises
+// it: with a(m) = 1 - exp(-2 pi i m / nt) the symbol of ell,
 //   lambda(mx, my) = -(k1^2 |a_x|^2 + 2 k1 k3 Re(conj(a_x) a_y) + (k2^2 + k3^2) |a_y|^2)
-//                    + c1 a_x + c2 a_y,
-// and (I - gamma L)^{-1} is a division by 1 - gamma lambda mode by mode.  One
-// Newton iteration therefore costs a 7-point stencil for the residual
-// G = x - r - gamma L x, a forward real 2D DFT, one complex multiply per mode
-// and an inverse DFT -- O(d nt) flops instead of a sparse or banded LU.
+//                    + c1 a_x + c2 a_y.
+// The system is linear, so Newton's method with the exact Jacobian L solves
+// each implicit BDF step in one iteration (Sec. 2.1), and the solution of
+//   x_{n+1} - rho1 x_n - rho2 x_{n-1} = gamma L x_{n+1}
+// is, mode by mode, X_{n+1} = (rho1 X_n + rho2 X_{n-1}) / (1 - gamma lambda).
+// Every quantity of an interval's S substeps is a fixed linear combination of
+// the modes of (x_n, x_{n-1}, x_{n-2}): the predictor pi0 X_n + pi1 X_{n-1} +
+// pi2 X_{n-2}, the explicit-Euler predictor (1 + h lambda) X_n of a cold
+// start, the corrector, and Milne's estimate mu (X_{n+1} - X_p).  So each
+// particle's history is transformed once at the interval's start and stays in
+// the Fourier basis, each thread stepping its own modes in registers through
+// all S substeps; only what is needed in physical space is transformed back:
+// the final states, and in stage 2 each substep's local error, whose squares
+// are summed per grid point (Step 4b: Gamma = kappa diag(sum_s e_s^2)).
 //
-// One block per particle: its history ring (x_n, x_{n-1}, x_{n-2}, iterate),
-// the half spectrum (nt odd, so modes mx = 0..(nt-1)/2 and Hermitian symmetry
-// give the rest), the per-mode multipliers, and in stage 2 the Milne predictor
-// and error sums all live in shared memory; the DFTs are direct sums over a
-// cos/sin table (nt is small and prime or nearly so), split over the block's
-// threads by output.  Global memory is touched once per particle per stage.
+// One block per particle.  Shared memory holds the substep table, a cos/sin
+// table of nt entries, the physical states, one half-spectrum transform
+// buffer (nt odd: modes mx = 0..(nt-1)/2, Hermitian symmetry gives the rest)
+// and in stage 2 the error sums.  The transforms are direct sums over the
+// table (nt is small and prime or nearly so), split over the block's threads
+// by output.  Global memory is touched once per particle per stage.
 #include "pf_epoch.cuh"
 #include "pf_kernels.h"
 
@@ -29,6 +35,7 @@ namespace pfg {
 
 constexpr int kAdMaxSide = 45;
 constexpr int kAdScDoubles = (int)(sizeof(StepCoef) / sizeof(double));
+constexpr int kAdMaxModesPerThread = 4;  // modes a thread steps in registers (MPT <= this)
 
 __host__ __device__ inline int ad_side(int d) {
   for (int nt = 3; nt <= kAdMaxSide; nt += 2)
@@ -41,12 +48,9 @@ struct AdLayout {
   int nt, d, H;
   int sc;    // step table, S entries
   int tw;    // cos(2 pi k / nt), then sin(2 pi k / nt), k < nt
-  int X[4];  // x_n, x_{n-1}, x_{n-2} and the iterate (roles rotate)
-  int s1;    // half spectrum [row][mx] (complex), also the inverse column output
-  int s2;    // half spectrum [my][mx] (complex); the residual G (real, d) before it
-  int wi;    // -1 / (nt^2 (1 - gamma lambda)) per mode (complex)
-  int xp;    // stage 2: Milne predictor
-  int ee;    // stage 2: error sums
+  int X[3];  // physical x_n, x_{n-1}, x_{n-2}
+  int sp;    // half-spectrum transform buffer [row][mx] (complex)
+  int ee;    // stage 2: error sums per grid point
   int total;
 };
 
@@ -60,154 +64,147 @@ __host__ __device__ inline AdLayout ad_layout(int d, int S, bool err) {
   off += S * kAdScDoubles;
   L.tw = off;
   off += 2 * L.nt;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 3; ++k) {
     L.X[k] = off;
     off += d;
   }
-  const int spec = 2 * L.nt * L.H;  // >= d
-  L.s1 = off;
-  off += spec;
-  L.s2 = off;
-  off += spec;
-  L.wi = off;
-  off += spec;
-  L.xp = off;
-  off += err ? d : 0;
+  L.sp = off;
+  off += 2 * L.nt * L.H;
   L.ee = off;
   off += err ? d : 0;
   L.total = off;
   return L;
 }
 
-// The operator for one parameter vector: the 7-point stencil of L (derived
-// from the products of the difference matrices) and the symbol's weights.
+// The operator's Fourier symbol for one parameter vector.
 struct AdOp {
-  double c0, xm, xp, ym, yp, pm, mp;  // u(x,y), u(x-1,y), u(x+1,y), u(x,y-1), u(x,y+1), u(x+1,y-1), u(x-1,y+1)
-  double kxx, kxy, kyy, c1, c2;       // k1^2, k1 k3, k2^2 + k3^2, c1, c2
+  double kxx, kxy, kyy, c1, c2;  // k1^2, k1 k3, k2^2 + k3^2, c1, c2
 };
 
 __device__ __forceinline__ AdOp ad_op(const double* th) {
-  const double k1 = th[0], k2 = th[1], k3 = th[2], c1 = th[3], c2 = th[4];
+  const double k1 = th[0], k2 = th[1], k3 = th[2];
   AdOp o;
   o.kxx = k1 * k1;
   o.kxy = k1 * k3;
-  o.kyy = k2 * k2 + k3 * k3;
-  o.c1 = c1;
-  o.c2 = c2;
-  o.c0 = -2.0 * (o.kxx + o.kxy + o.kyy) + c1 + c2;
-  o.xm = o.kxx + o.kxy - c1;
-  o.xp = o.kxx + o.kxy;
-  o.ym = o.kxy + o.kyy - c2;
-  o.yp = o.kxy + o.kyy;
-  o.pm = -o.kxy;
-  o.mp = -o.kxy;
+  o.kyy = fma(k2, k2, k3 * k3);
+  o.c1 = th[3];
+  o.c2 = th[4];
   return o;
 }
 
-__device__ __forceinline__ double ad_apply(const AdOp& o, const double* u, int nt, int ix, int iy) {
-  const int xm = ix == 0 ? nt - 1 : ix - 1, xp = ix == nt - 1 ? 0 : ix + 1;
-  const int rm = (iy == 0 ? nt - 1 : iy - 1) * nt, rp = (iy == nt - 1 ? 0 : iy + 1) * nt;
-  const int r = iy * nt;
-  double s = o.c0 * u[r + ix];
-  s = fma(o.xm, u[r + xm], s);
-  s = fma(o.xp, u[r + xp], s);
-  s = fma(o.ym, u[rm + ix], s);
-  s = fma(o.yp, u[rp + ix], s);
-  s = fma(o.pm, u[rm + xp], s);
-  s = fma(o.mp, u[rp + xm], s);
-  return s;
-}
-
-// wi(my, mx) = -1 / (nt^2 (1 - gamma lambda(mx, my))): the inverse of the
-// Newton matrix per mode, with the inverse DFT's 1/nt^2 and the sign of -G.
-__device__ void ad_multipliers(const AdLayout& L, const AdOp& o, double gamma, const double* tw,
-                               double* wi) {
+// lambda(mx, my) for mode index t = my * H + mx
+__device__ __forceinline__ void ad_lambda(const AdLayout& L, const AdOp& o, const double* tw, int t,
+                                          double& lr, double& li) {
   const int nt = L.nt, H = L.H;
-  const double inv = 1.0 / (double)(nt * nt);
-  for (int t = threadIdx.x; t < nt * H; t += blockDim.x) {
-    const int my = t / H, mx = t - my * H;
-    const double axr = 1.0 - tw[mx], axi = tw[nt + mx];
-    const double ayr = 1.0 - tw[my], ayi = tw[nt + my];
-    const double ax2 = fma(axr, axr, axi * axi), ay2 = fma(ayr, ayr, ayi * ayi);
-    const double cr = fma(axr, ayr, axi * ayi);
-    const double lr = fma(o.c1, axr, o.c2 * ayr) - fma(o.kxx, ax2, fma(2.0 * o.kxy, cr, o.kyy * ay2));
-    const double li = fma(o.c1, axi, o.c2 * ayi);
-    const double p = fma(-gamma, lr, 1.0), q = -gamma * li;
-    const double s = -inv / fma(p, p, q * q);
-    wi[2 * t] = s * p;
-    wi[2 * t + 1] = -s * q;
-  }
+  const int my = t / H, mx = t - my * H;
+  const double axr = 1.0 - tw[mx], axi = tw[nt + mx];
+  const double ayr = 1.0 - tw[my], ayi = tw[nt + my];
+  const double ax2 = fma(axr, axr, axi * axi), ay2 = fma(ayr, ayr, ayi * ayi);
+  const double cr = fma(axr, ayr, axi * ayi);
+  lr = fma(o.c1, axr, o.c2 * ayr) - fma(o.kxx, ax2, fma(2.0 * o.kxy, cr, o.kyy * ay2));
+  li = fma(o.c1, axi, o.c2 * ayi);
 }
 
-// One Newton iteration on the iterate XI: G = XI - (rho1 X0 + rho2 X1) -
-// gamma L XI, then XI += -(I - gamma L)^{-1} G through the DFT.
-__device__ void ad_newton(const AdLayout& L, const AdOp& o, const StepCoef& c, const double* tw,
-                          const double* X0, const double* X1, double* XI, double* S1, double* S2,
-                          const double* WI) {
-  const int nt = L.nt, H = L.H, d = L.d, T = blockDim.x, tid = threadIdx.x;
-  double* G = S2;
-  for (int i = tid; i < d; i += T) {
-    const int iy = i / nt, ix = i - iy * nt;
-    const double lx = ad_apply(o, XI, nt, ix, iy);
-    const double r = fma(c.rho1, X0[i], c.rho2 * X1[i]);
-    G[i] = fma(-c.gamma, lx, XI[i] - r);
-  }
-  __syncthreads();
-  // rows: S1[iy][mx] = sum_ix G[iy][ix] exp(-i phi mx ix)
+// Forward real 2D DFT of u (physical, shared) into the calling thread's own
+// modes: spec[j] = sum_{iy,ix} u[iy][ix] exp(-i phi (mx ix + my iy)) for the
+// modes t = tid + j T.  Uses the block's transform buffer; ends with a barrier.
+template <int MPT>
+__device__ void ad_forward(const AdLayout& L, const double* tw, const double* u, double* buf,
+                           double (&re)[MPT], double (&im)[MPT]) {
+  const int nt = L.nt, H = L.H, T = blockDim.x, tid = threadIdx.x;
+  // rows: buf[iy][mx] = sum_ix u[iy][ix] exp(-i phi mx ix)
   for (int t = tid; t < nt * H; t += T) {
     const int iy = t / H, mx = t - iy * H;
-    const double* g = G + iy * nt;
-    double re = 0.0, im = 0.0;
+    const double* g = u + iy * nt;
+    double sr = 0.0, si = 0.0;
     int k = 0;
     for (int ix = 0; ix < nt; ++ix) {
-      re = fma(g[ix], tw[k], re);
-      im = fma(-g[ix], tw[nt + k], im);
+      sr = fma(g[ix], tw[k], sr);
+      si = fma(-g[ix], tw[nt + k], si);
       k += mx;
       if (k >= nt) k -= nt;
     }
-    S1[2 * t] = re;
-    S1[2 * t + 1] = im;
+    buf[2 * t] = sr;
+    buf[2 * t + 1] = si;
   }
   __syncthreads();
-  // columns and the per-mode solve: S2[my][mx] = WI * sum_iy S1[iy][mx] exp(-i phi my iy)
-  for (int t = tid; t < nt * H; t += T) {
-    const int my = t / H, mx = t - my * H;
-    double re = 0.0, im = 0.0;
-    int k = 0;
-    for (int iy = 0; iy < nt; ++iy) {
-      const double ar = S1[2 * (iy * H + mx)], ai = S1[2 * (iy * H + mx) + 1];
-      const double cs = tw[k], sn = tw[nt + k];
-      re = fma(ar, cs, fma(ai, sn, re));
-      im = fma(ai, cs, fma(-ar, sn, im));
-      k += my;
-      if (k >= nt) k -= nt;
+  // columns: mode (my, mx) = sum_iy buf[iy][mx] exp(-i phi my iy)
+#pragma unroll
+  for (int j = 0; j < MPT; ++j) {
+    const int t = tid + j * T;
+    double sr = 0.0, si = 0.0;
+    if (t < nt * H) {
+      const int my = t / H, mx = t - my * H;
+      int k = 0;
+      for (int iy = 0; iy < nt; ++iy) {
+        const double ar = buf[2 * (iy * H + mx)], ai = buf[2 * (iy * H + mx) + 1];
+        const double cs = tw[k], sn = tw[nt + k];
+        sr = fma(ar, cs, fma(ai, sn, sr));
+        si = fma(ai, cs, fma(-ar, sn, si));
+        k += my;
+        if (k >= nt) k -= nt;
+      }
     }
-    const double wr = WI[2 * t], wm = WI[2 * t + 1];
-    S2[2 * t] = fma(re, wr, -im * wm);
-    S2[2 * t + 1] = fma(re, wm, im * wr);
+    re[j] = sr;
+    im[j] = si;
   }
   __syncthreads();
-  // inverse columns: S1[iy][mx] = sum_my S2[my][mx] exp(+i phi my iy)
-  for (int t = tid; t < nt * H; t += T) {
-    const int iy = t / H, mx = t - iy * H;
-    double re = 0.0, im = 0.0;
-    int k = 0;
-    for (int my = 0; my < nt; ++my) {
-      const double ar = S2[2 * (my * H + mx)], ai = S2[2 * (my * H + mx) + 1];
-      const double cs = tw[k], sn = tw[nt + k];
-      re = fma(ar, cs, fma(-ai, sn, re));
-      im = fma(ai, cs, fma(ar, sn, im));
-      k += iy;
-      if (k >= nt) k -= nt;
+}
+
+// Inverse: the threads' modes (already scaled) are written to the transform
+// buffer, then u[iy][ix] = sum over all modes of spec exp(+i phi (mx ix + my
+// iy)) (Hermitian in mx), delivered per grid point to `out(i, value)`.
+// Ends with a barrier.
+template <int MPT, class Out>
+__device__ void ad_inverse(const AdLayout& L, const double* tw, double* buf, const double (&re)[MPT],
+                           const double (&im)[MPT], Out out) {
+  const int nt = L.nt, H = L.H, d = L.d, T = blockDim.x, tid = threadIdx.x;
+  double* spec = buf;
+#pragma unroll
+  for (int j = 0; j < MPT; ++j) {
+    const int t = tid + j * T;
+    if (t < nt * H) {
+      spec[2 * t] = re[j];
+      spec[2 * t + 1] = im[j];
     }
-    S1[2 * t] = re;
-    S1[2 * t + 1] = im;
   }
   __syncthreads();
-  // inverse rows (Hermitian in mx): dx = Re z0 + 2 sum_{mx>0} Re(z_mx exp(+i phi mx ix))
+  // columns: col[iy][mx] = sum_my spec[my][mx] exp(+i phi my iy), computed
+  // into registers and written back in place after a barrier
+  double cr[MPT], ci[MPT];
+#pragma unroll
+  for (int j = 0; j < MPT; ++j) {
+    const int t = tid + j * T;
+    double sr = 0.0, si = 0.0;
+    if (t < nt * H) {
+      const int iy = t / H, mx = t - iy * H;
+      int k = 0;
+      for (int my = 0; my < nt; ++my) {
+        const double ar = spec[2 * (my * H + mx)], ai = spec[2 * (my * H + mx) + 1];
+        const double cs = tw[k], sn = tw[nt + k];
+        sr = fma(ar, cs, fma(-ai, sn, sr));
+        si = fma(ai, cs, fma(ar, sn, si));
+        k += iy;
+        if (k >= nt) k -= nt;
+      }
+    }
+    cr[j] = sr;
+    ci[j] = si;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < MPT; ++j) {
+    const int t = tid + j * T;
+    if (t < nt * H) {
+      spec[2 * t] = cr[j];
+      spec[2 * t + 1] = ci[j];
+    }
+  }
+  __syncthreads();
+  // rows (Hermitian in mx): u = Re z0 + 2 sum_{mx>0} Re(z_mx exp(+i phi mx ix))
   for (int i = tid; i < d; i += T) {
     const int iy = i / nt, ix = i - iy * nt;
-    const double* z = S1 + 2 * iy * H;
+    const double* z = spec + 2 * iy * H;
     double acc = 0.0;
     int k = ix;
     for (int mx = 1; mx < H; ++mx) {
@@ -215,65 +212,9 @@ __device__ void ad_newton(const AdLayout& L, const AdOp& o, const StepCoef& c, c
       k += ix;
       if (k >= nt) k -= nt;
     }
-    XI[i] += fma(2.0, acc, z[0]);
+    out(i, fma(2.0, acc, z[0]));
   }
   __syncthreads();
-}
-
-// Psi over the S substeps on the block's shared history ring (Steps 2 and
-// 4b/4d).  On exit X[0], X[1], X[2] (after rotation, see ring) hold x_n,
-// x_{n-1}, x_{n-2}; with ERR the squared Milne estimates are summed into EE.
-template <bool ERR>
-__device__ void ad_propagate(const AdLayout& L, const AdOp& o, const StepCoef* sc, int S, int K,
-                             double* sm, int (&ring)[4]) {
-  const int nt = L.nt, d = L.d, T = blockDim.x, tid = threadIdx.x;
-  const double* tw = sm + L.tw;
-  double* S1 = sm + L.s1;
-  double* S2 = sm + L.s2;
-  double* WI = sm + L.wi;
-  double* XP = sm + L.xp;
-  double* EE = sm + L.ee;
-  double gamma_wi = CUDART_NAN;
-  for (int s = 0; s < S; ++s) {
-    const StepCoef c = sc[s];
-    double* X0 = sm + ring[0];
-    double* X1 = sm + ring[1];
-    double* X2 = sm + ring[2];
-    double* XI = sm + ring[3];
-    for (int i = tid; i < d; i += T) {
-      double xp;
-      if (c.kind == 2) {
-        xp = fma(c.pi0, X0[i], fma(c.pi1, X1[i], c.pi2 * X2[i]));
-        if (ERR) XP[i] = xp;
-      } else {
-        xp = X0[i];
-        if (ERR) {  // explicit-Euler error predictor of a cold-start step
-          const int iy = i / nt, ix = i - iy * nt;
-          XP[i] = fma(c.h, ad_apply(o, X0, nt, ix, iy), X0[i]);
-        }
-      }
-      XI[i] = xp;
-    }
-    if (!(c.gamma == gamma_wi)) {
-      ad_multipliers(L, o, c.gamma, tw, WI);
-      gamma_wi = c.gamma;
-    }
-    __syncthreads();
-    for (int it = 0; it < K; ++it) ad_newton(L, o, c, tw, X0, X1, XI, S1, S2, WI);
-    if (ERR) {
-      for (int i = tid; i < d; i += T) {
-        const double e = c.mu * (XI[i] - XP[i]);
-        EE[i] = fma(e, e, EE[i]);
-      }
-    }
-    const int r3 = ring[3];
-    ring[3] = ring[2];
-    ring[2] = ring[1];
-    ring[1] = ring[0];
-    ring[0] = r3;
-    // the next substep reads neighbours of the new x_n written by other threads;
-    // ad_newton ended with a barrier, and EE/XP are per-thread indices
-  }
 }
 
 __device__ __forceinline__ double ad_loglik(const FilterDev& fd, const EpochParams* __restrict__ ep,
@@ -296,8 +237,14 @@ __device__ __forceinline__ void ad_tables(const AdLayout& L, double* sm) {
   }
 }
 
-template <int STAGE>
-__global__ void __launch_bounds__(512) k_adstage(const __grid_constant__ FilterDev fd,
+// complex a * b
+__device__ __forceinline__ void cmul(double ar, double ai, double br, double bi, double& r, double& i) {
+  r = fma(ar, br, -ai * bi);
+  i = fma(ar, bi, ai * br);
+}
+
+template <int STAGE, int MPT>
+__global__ void __launch_bounds__(512, 1) k_adstage(const __grid_constant__ FilterDev fd,
                                                  const EpochParams* __restrict__ ep) {
   extern __shared__ double s_dyn[];
   __shared__ double s_red[32];
@@ -309,13 +256,15 @@ __global__ void __launch_bounds__(512) k_adstage(const __grid_constant__ FilterD
   const AdLayout L = ad_layout(fd.d, S, STAGE == 2);
   double* sm = s_dyn;
   load_steps(reinterpret_cast<StepCoef*>(sm + L.sc), ep, S);  // ends with a barrier
+  const StepCoef* sc = reinterpret_cast<const StepCoef*>(sm + L.sc);
   const int cur = ctrl->cur;
   const Ensemble src = committed(fd, cur);
   const Ensemble dst = pending(fd, cur);
   const int64_t N = fd.N;
   const int64_t n = blockIdx.x;
   const uint32_t epoch = ep->epoch;
-  const int d = L.d, T = blockDim.x, tid = threadIdx.x;
+  const int d = L.d, T = blockDim.x, tid = threadIdx.x, modes = L.nt * L.H;
+  const double inv_d = 1.0 / (double)d;
   int64_t l = n;
   if (STAGE == 2) l = fd.idx[n];
   if (tid == 0) {
@@ -352,9 +301,93 @@ __global__ void __launch_bounds__(512) k_adstage(const __grid_constant__ FilterD
   double th[5];
   for (int i = 0; i < 5; ++i) th[i] = s_th[i];
   const AdOp op = ad_op(th);
-  int ring[4] = {L.X[0], L.X[1], L.X[2], L.X[3]};
-  ad_propagate<STAGE == 2>(L, op, reinterpret_cast<const StepCoef*>(sm + L.sc), S, fd.K, sm, ring);
-  double* X0 = sm + ring[0];
+  const double* tw = sm + L.tw;
+  double* buf = sm + L.sp;
+
+  // the history in the Fourier basis, each thread holding its own modes
+  double x0r[MPT], x0i[MPT];
+  double x1r[MPT], x1i[MPT];
+  double x2r[MPT], x2i[MPT];
+  ad_forward<MPT>(L, tw, sm + L.X[0], buf, x0r, x0i);
+  ad_forward<MPT>(L, tw, sm + L.X[1], buf, x1r, x1i);
+  ad_forward<MPT>(L, tw, sm + L.X[2], buf, x2r, x2i);
+  double lr[MPT], li[MPT];
+#pragma unroll
+  for (int j = 0; j < MPT; ++j) {
+    lr[j] = li[j] = 0.0;
+    if (tid + j * T < modes) ad_lambda(L, op, tw, tid + j * T, lr[j], li[j]);
+  }
+
+  // Psi over the S substeps (Steps 2 and 4b/4d), mode by mode
+  double wr[MPT], wi[MPT];
+  double gamma_w = CUDART_NAN;
+  for (int s = 0; s < S; ++s) {
+    const StepCoef c = sc[s];
+    if (!(c.gamma == gamma_w)) {
+      // w = 1 / (1 - gamma lambda) per mode
+#pragma unroll
+      for (int j = 0; j < MPT; ++j) {
+        const double p = fma(-c.gamma, lr[j], 1.0), q = -c.gamma * li[j];
+        const double inv = 1.0 / fma(p, p, q * q);
+        wr[j] = p * inv;
+        wi[j] = -q * inv;
+      }
+      gamma_w = c.gamma;
+    }
+    double er[MPT], ei[MPT];
+#pragma unroll
+    for (int j = 0; j < MPT; ++j) {
+      double rr, ri, pr = 0.0, pi = 0.0;
+      if (c.kind == 2) {
+        rr = fma(c.rho2, x1r[j], c.rho1 * x0r[j]);
+        ri = fma(c.rho2, x1i[j], c.rho1 * x0i[j]);
+        if (STAGE == 2) {
+          pr = fma(c.pi2, x2r[j], fma(c.pi1, x1r[j], c.pi0 * x0r[j]));
+          pi = fma(c.pi2, x2i[j], fma(c.pi1, x1i[j], c.pi0 * x0i[j]));
+        }
+      } else {
+        // BDF1 (cold start): r = x_n; error predictor x_n + h L x_n
+        rr = x0r[j];
+        ri = x0i[j];
+        if (STAGE == 2) {
+          double gr, gi;
+          cmul(c.h * lr[j], c.h * li[j], x0r[j], x0i[j], gr, gi);
+          pr = x0r[j] + gr;
+          pi = x0i[j] + gi;
+        }
+      }
+      double yr, yi;
+      cmul(rr, ri, wr[j], wi[j], yr, yi);
+      if (STAGE == 2) {
+        // Milne's estimate, with the inverse transform's 1/d
+        const double f = c.mu * inv_d;
+        er[j] = f * (yr - pr);
+        ei[j] = f * (yi - pi);
+      }
+      x2r[j] = x1r[j];
+      x2i[j] = x1i[j];
+      x1r[j] = x0r[j];
+      x1i[j] = x0i[j];
+      x0r[j] = yr;
+      x0i[j] = yi;
+    }
+    if (STAGE == 2) {
+      double* EE = sm + L.ee;
+      ad_inverse<MPT>(L, tw, buf, er, ei, [&](int i, double e) { EE[i] = fma(e, e, EE[i]); });
+    }
+  }
+
+  // back to physical space (scaled by 1/d)
+  auto back = [&](double (&re)[MPT], double (&im)[MPT], double* u) {
+#pragma unroll
+    for (int j = 0; j < MPT; ++j) {
+      re[j] *= inv_d;
+      im[j] *= inv_d;
+    }
+    ad_inverse<MPT>(L, tw, buf, re, im, [&](int i, double v) { u[i] = v; });
+  };
+  double* X0 = sm + L.X[0];
+  back(x0r, x0i, X0);
   if (STAGE == 1) {
     double lg = -CUDART_INF;
     if (tid == 0) {
@@ -366,9 +399,11 @@ __global__ void __launch_bounds__(512) k_adstage(const __grid_constant__ FilterD
     }
     stage1_tail(fd, epoch, lg, (int)blockIdx.x, (int)gridDim.x, s_red, &s_flag);
   } else {
+    double* X1 = sm + L.X[1];
+    double* X2 = sm + L.X[2];
+    back(x1r, x1i, X1);
+    back(x2r, x2i, X2);
     // Steps 4c, 4d: innovation v = sqrt(kappa E) z', written in (x, h1, h2) order
-    const double* X1 = sm + ring[1];
-    const double* X2 = sm + ring[2];
     const double* EE = sm + L.ee;
     for (int b = tid; b < (d + 1) / 2; b += T) {
       const U4 w = draw_block(fd, kRngInnov, (uint32_t)n, epoch, (uint32_t)b);
@@ -401,24 +436,22 @@ __global__ void __launch_bounds__(512) k_adstage(const __grid_constant__ FilterD
   }
 }
 
-// Threads per block for a grid side: the DFT passes have nt*H outputs and the
-// pointwise passes d; pick the multiple of 32 (64..512) with the fewest idle
-// lane-cycles, counting the ~10 nt-long sums of a spectral output against the
-// ~(2H + 9) of a pointwise one, and one barrier round each.
+// Launch shape for a grid side: modes per thread MPT (1, 2 or 4: fewer modes
+// per thread keep fewer registers, so more blocks fit an SM) and threads per
+// block, a multiple of 32 covering the nt * H modes.
+static void ad_shape(int nt, int* threads, int* mpt) {
+  const int modes = nt * ((nt + 1) / 2);
+  int m = 1;
+  while (m < kAdMaxModesPerThread && (modes + m - 1) / m > 512) m *= 2;
+  const int need = (modes + m - 1) / m;
+  *mpt = m;
+  *threads = ((need > 64 ? need : 64) + 31) / 32 * 32;
+}
+
 int ad_threads(int nt) {
-  const int H = (nt + 1) / 2, d = nt * nt, spec = nt * H;
-  int best = 64;
-  double best_cost = 1e300;
-  for (int T = 64; T <= 512; T += 32) {
-    const int rs = (spec + T - 1) / T, rp = (d + T - 1) / T;
-    const double cost = (double)rs * T * (10.0 * nt) + (double)rp * T * (2.0 * H + 9.0) +
-                        (double)(3 * rs + 2 * rp) * 32.0 * 40.0;
-    if (cost < best_cost) {
-      best_cost = cost;
-      best = T;
-    }
-  }
-  return best;
+  int T, m;
+  ad_shape(nt, &T, &m);
+  return T;
 }
 
 size_t ad_stage_smem(int d, int S, int stage) {
@@ -430,17 +463,24 @@ cudaError_t launch_ad_stage(int stage, const FilterDev& fd, const EpochParams* e
   const int nt = ad_side(fd.d);
   if (nt == 0) return cudaErrorInvalidValue;
   const size_t smem = ad_stage_smem(fd.d, S, stage);
-  const int T = ad_threads(nt);
-  const void* k = stage == 1 ? (const void*)k_adstage<1> : (const void*)k_adstage<2>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int T, mpt;
+  ad_shape(nt, &T, &mpt);
+  if (T * mpt < nt * ((nt + 1) / 2) || T > 512) return cudaErrorInvalidValue;
+  using K = void (*)(const FilterDev, const EpochParams*);
+  K k;
+  if (mpt == 1) k = stage == 1 ? k_adstage<1, 1> : k_adstage<2, 1>;
+  else if (mpt == 2) k = stage == 1 ? k_adstage<1, 2> : k_adstage<2, 2>;
+  else k = stage == 1 ? k_adstage<1, 4> : k_adstage<2, 4>;
+  cudaError_t e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (stage == 1) k_adstage<1><<<(unsigned)fd.N, T, smem, st>>>(fd, ep);
-  else k_adstage<2><<<(unsigned)fd.N, T, smem, st>>>(fd, ep);
+  k<<<(unsigned)fd.N, T, smem, st>>>(fd, ep);
   return cudaGetLastError();
 }
 
 cudaError_t preload_ad_kernels() {
-  const void* ks[] = {(const void*)k_adstage<1>, (const void*)k_adstage<2>};
+  const void* ks[] = {(const void*)k_adstage<1, 1>, (const void*)k_adstage<2, 1>,
+                      (const void*)k_adstage<1, 2>, (const void*)k_adstage<2, 2>,
+                      (const void*)k_adstage<1, 4>, (const void*)k_adstage<2, 4>};
   for (const void* k : ks) {
     cudaFuncAttributes a;
     const cudaError_t e = cudaFuncGetAttributes(&a, k);
