@@ -48,25 +48,36 @@ FP64_PEAK_TFLOPS = 2.0 * 152 * 2.070e9 * 2 / 1e12
 # Algorithmic FP64 flops (FMA = 2, a reciprocal = 1) of one substep of one
 # particle in the stage-2 kernel: predictor 5d, history combination 3d, Milne
 # estimate 4d, per-substep constants, and K Newton iterations.
+def _advdiff_inverse_flops(nt, H):
+    """One inverse transform of the half spectrum organised by twiddle
+    symmetry: pair sums and differences 4 per unit (H^2 units), columns
+    8 (H-1) + 4 per unit, Hermitian rows 4 (H-1) + 6 per (row, pair) unit."""
+    units = H * H
+    return 4 * units + units * (8 * (H - 1) + 4) + nt * H * (4 * (H - 1) + 6)
+
+
 def _advdiff_flops(K, d):
     """M2 (2D advection-diffusion), stage 2 per substep, with nt = sqrt(d) and
-    H = (nt+1)/2 modes per row: per mode the history combination, predictor,
-    division by 1 - gamma lambda and Milne estimate (26 flops); the inverse
-    transform of the local error, columns 8dH and Hermitian rows 4dH - 2d;
-    the squared-error sums 2d."""
+    H = (nt+1)/2: per mode (nt H of them) the history combination,
+    predictor, division by 1 - gamma lambda and Milne estimate (26 flops);
+    the inverse transform of the local error; the squared-error sums 2d."""
     nt = int(round(math.sqrt(d)))
     H = (nt + 1) // 2
-    return 12 * d * H + 26 * nt * H
+    return 26 * nt * H + _advdiff_inverse_flops(nt, H) + 2 * d
 
 
 def _advdiff_flops_interval(K, d):
     """M2, stage 2 once per interval: three forward transforms of the history
-    (rows 4dH, columns 8dH each), the symbol per mode (20) and its inverse
-    factor (10), three inverse transforms of the final states (12dH + 2 per
-    mode each) and the innovation (5d)."""
+    (rows of both members of a row pair, 8 nt per unit, and their sums and
+    differences 4; columns 8 (H-1) + 4 per unit), the symbol of both modes of
+    a unit (40) and its inverse factor (20), three inverse transforms of the
+    final states with their 1/d scaling, and the innovation (5d)."""
     nt = int(round(math.sqrt(d)))
     H = (nt + 1) // 2
-    return 72 * d * H + 36 * nt * H + 5 * d
+    units = H * H
+    forward = units * (8 * nt + 4) + units * (8 * (H - 1) + 4)
+    return (3 * forward + 60 * units + 3 * (_advdiff_inverse_flops(nt, H) + 4 * units)
+            + 5 * d)
 
 
 def _michaelis_flops(lmm):

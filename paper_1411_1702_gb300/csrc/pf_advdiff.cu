@@ -22,12 +22,24 @@
 // the final states, and in stage 2 each substep's local error, whose squares
 // are summed per grid point (Step 4b: Gamma = kappa diag(sum_s e_s^2)).
 //
-// One block per particle.  Shared memory holds the substep table, a cos/sin
-// table of nt entries, the physical states, one half-spectrum transform
-// buffer (nt odd: modes mx = 0..(nt-1)/2, Hermitian symmetry gives the rest)
-// and in stage 2 the error sums.  The transforms are direct sums over the
-// table (nt is small and prime or nearly so), split over the block's threads
-// by output.  Global memory is touched once per particle per stage.
+// Transforms.  nt is odd and the state real, so the half spectrum mx =
+// 0..H-1, H = (nt+1)/2, carries everything.  The transforms are direct sums
+// over a cos/sin table (nt is small and prime or nearly so), organised by
+// the symmetry of the twiddles: the DFT terms of indices m and nt - m share
+// their cosine and have opposite sines, so
+//   sum_m z_m e^{+i phi m k} = z_0 + sum_{m=1}^{H-1} [(z_m + z_{nt-m}) cos(phi m k)
+//                                              + i (z_m - z_{nt-m}) sin(phi m k)],
+// and the outputs k and nt - k differ only in the sign of the sine part.
+// One work unit computes such an output pair from the sum and difference
+// of an input pair: 4 (H-1) FMAs for two complex outputs instead of 8 nt.
+// A thread owns the mode pairs (my, mx) and (nt - my, mx) of its units, in
+// registers, so the forward transform ends and the inverse begins in the
+// owning thread.
+//
+// One block per particle.  Shared memory holds the substep table, the twiddle
+// table, the physical states, the pair buffers of the transforms, and in
+// stage 2 the error sums.  Global memory is touched once per particle per
+// stage.
 #include "pf_epoch.cuh"
 #include "pf_kernels.h"
 
@@ -35,7 +47,7 @@ namespace pfg {
 
 constexpr int kAdMaxSide = 45;
 constexpr int kAdScDoubles = (int)(sizeof(StepCoef) / sizeof(double));
-constexpr int kAdMaxModesPerThread = 4;  // modes a thread steps in registers (MPT <= this)
+constexpr int kAdMaxUnitsPerThread = 2;  // mode-pair units a thread steps in registers
 
 __host__ __device__ inline int ad_side(int d) {
   for (int nt = 3; nt <= kAdMaxSide; nt += 2)
@@ -49,7 +61,9 @@ struct AdLayout {
   int sc;    // step table, S entries
   int tw;    // cos(2 pi k / nt), then sin(2 pi k / nt), k < nt
   int X[3];  // physical x_n, x_{n-1}, x_{n-2}
-  int sp;    // half-spectrum transform buffer [row][mx] (complex)
+  int ps;    // pair sums [p][mx] (complex), p < H; p = 0 holds the unpaired entry
+  int pd;    // pair differences [p][mx] (complex)
+  int cy;    // inverse columns [iy][mx] (complex), iy < nt
   int ee;    // stage 2: error sums per grid point
   int total;
 };
@@ -68,7 +82,11 @@ __host__ __device__ inline AdLayout ad_layout(int d, int S, bool err) {
     L.X[k] = off;
     off += d;
   }
-  L.sp = off;
+  L.ps = off;
+  off += 2 * L.H * L.H;
+  L.pd = off;
+  off += 2 * L.H * L.H;
+  L.cy = off;
   off += 2 * L.nt * L.H;
   L.ee = off;
   off += err ? d : 0;
@@ -92,11 +110,10 @@ __device__ __forceinline__ AdOp ad_op(const double* th) {
   return o;
 }
 
-// lambda(mx, my) for mode index t = my * H + mx
-__device__ __forceinline__ void ad_lambda(const AdLayout& L, const AdOp& o, const double* tw, int t,
-                                          double& lr, double& li) {
-  const int nt = L.nt, H = L.H;
-  const int my = t / H, mx = t - my * H;
+// lambda(mx, my)
+__device__ __forceinline__ void ad_lambda(const AdLayout& L, const AdOp& o, const double* tw, int my,
+                                          int mx, double& lr, double& li) {
+  const int nt = L.nt;
   const double axr = 1.0 - tw[mx], axi = tw[nt + mx];
   const double ayr = 1.0 - tw[my], ayi = tw[nt + my];
   const double ax2 = fma(axr, axr, axi * axi), ay2 = fma(ayr, ayr, ayi * ayi);
@@ -105,114 +122,141 @@ __device__ __forceinline__ void ad_lambda(const AdLayout& L, const AdOp& o, cons
   li = fma(o.c1, axi, o.c2 * ayi);
 }
 
+// A thread's modes: unit u = p * H + mx holds mode A = (my = p, mx) and, for
+// p >= 1, mode B = (my = nt - p, mx).  Index [j][0] is A, [j][1] is B.
+template <int U>
+struct Modes {
+  double re[U][2], im[U][2];
+};
+
 // Forward real 2D DFT of u (physical, shared) into the calling thread's own
-// modes: spec[j] = sum_{iy,ix} u[iy][ix] exp(-i phi (mx ix + my iy)) for the
-// modes t = tid + j T.  Uses the block's transform buffer; ends with a barrier.
-template <int MPT>
-__device__ void ad_forward(const AdLayout& L, const double* tw, const double* u, double* buf,
-                           double (&re)[MPT], double (&im)[MPT]) {
-  const int nt = L.nt, H = L.H, T = blockDim.x, tid = threadIdx.x;
-  // rows: buf[iy][mx] = sum_ix u[iy][ix] exp(-i phi mx ix)
-  for (int t = tid; t < nt * H; t += T) {
-    const int iy = t / H, mx = t - iy * H;
-    const double* g = u + iy * nt;
-    double sr = 0.0, si = 0.0;
+// modes: X(my, mx) = sum_{iy,ix} u[iy][ix] exp(-i phi (mx ix + my iy)).
+// Ends with a barrier.
+template <int U>
+__device__ void ad_forward(const AdLayout& L, const double* tw, const double* u, double* ps, double* pd,
+                           Modes<U>& out) {
+  const int nt = L.nt, H = L.H, T = blockDim.x, tid = threadIdx.x, units = H * H;
+  // rows py and nt - py at column mx, stored as their sum and difference
+  for (int t = tid; t < units; t += T) {
+    const int py = t / H, mx = t - py * H;
+    const double* g1 = u + py * nt;
+    const double* g2 = u + (py == 0 ? 0 : nt - py) * nt;
+    double r1 = 0.0, i1 = 0.0, r2 = 0.0, i2 = 0.0;
     int k = 0;
     for (int ix = 0; ix < nt; ++ix) {
-      sr = fma(g[ix], tw[k], sr);
-      si = fma(-g[ix], tw[nt + k], si);
+      const double cs = tw[k], sn = tw[nt + k];
+      r1 = fma(g1[ix], cs, r1);
+      i1 = fma(-g1[ix], sn, i1);
+      r2 = fma(g2[ix], cs, r2);
+      i2 = fma(-g2[ix], sn, i2);
       k += mx;
       if (k >= nt) k -= nt;
     }
-    buf[2 * t] = sr;
-    buf[2 * t + 1] = si;
+    if (py == 0) {
+      ps[2 * t] = r1;
+      ps[2 * t + 1] = i1;
+    } else {
+      ps[2 * t] = r1 + r2;
+      ps[2 * t + 1] = i1 + i2;
+      pd[2 * t] = r1 - r2;
+      pd[2 * t + 1] = i1 - i2;
+    }
   }
   __syncthreads();
-  // columns: mode (my, mx) = sum_iy buf[iy][mx] exp(-i phi my iy)
+  // columns: X(my) = R0 + sum_{iy=1}^{H-1} [s_iy cos(phi my iy) - i d_iy sin(phi my iy)]
+  // for my = p, and the conjugate sine part for my = nt - p
 #pragma unroll
-  for (int j = 0; j < MPT; ++j) {
+  for (int j = 0; j < U; ++j) {
     const int t = tid + j * T;
-    double sr = 0.0, si = 0.0;
-    if (t < nt * H) {
-      const int my = t / H, mx = t - my * H;
-      int k = 0;
-      for (int iy = 0; iy < nt; ++iy) {
-        const double ar = buf[2 * (iy * H + mx)], ai = buf[2 * (iy * H + mx) + 1];
+    double cr = 0.0, ci = 0.0, dr = 0.0, di = 0.0;
+    if (t < units) {
+      const int p = t / H, mx = t - p * H;
+      cr = ps[2 * mx];
+      ci = ps[2 * mx + 1];
+      int k = p;
+      for (int iy = 1; iy < H; ++iy) {
+        const int q = 2 * (iy * H + mx);
         const double cs = tw[k], sn = tw[nt + k];
-        sr = fma(ar, cs, fma(ai, sn, sr));
-        si = fma(ai, cs, fma(-ar, sn, si));
-        k += my;
+        cr = fma(ps[q], cs, cr);
+        ci = fma(ps[q + 1], cs, ci);
+        dr = fma(pd[q], sn, dr);
+        di = fma(pd[q + 1], sn, di);
+        k += p;
         if (k >= nt) k -= nt;
       }
     }
-    re[j] = sr;
-    im[j] = si;
+    // A: C - i D, B: C + i D
+    out.re[j][0] = cr + di;
+    out.im[j][0] = ci - dr;
+    out.re[j][1] = cr - di;
+    out.im[j][1] = ci + dr;
   }
   __syncthreads();
 }
 
-// Inverse: the threads' modes (already scaled) are written to the transform
-// buffer, then u[iy][ix] = sum over all modes of spec exp(+i phi (mx ix + my
-// iy)) (Hermitian in mx), delivered per grid point to `out(i, value)`.
-// Ends with a barrier.
-template <int MPT, class Out>
-__device__ void ad_inverse(const AdLayout& L, const double* tw, double* buf, const double (&re)[MPT],
-                           const double (&im)[MPT], Out out) {
-  const int nt = L.nt, H = L.H, d = L.d, T = blockDim.x, tid = threadIdx.x;
-  double* spec = buf;
+// Inverse: the threads' modes z (already scaled) give
+//   u[iy][ix] = sum over all modes z exp(+i phi (mx ix + my iy))
+// (Hermitian in mx), delivered per grid point to `out(i, value)`.  Ends with
+// a barrier.
+template <int U, class Out>
+__device__ void ad_inverse(const AdLayout& L, const double* tw, double* ps, double* pd, double* cy,
+                           const Modes<U>& z, Out out) {
+  const int nt = L.nt, H = L.H, T = blockDim.x, tid = threadIdx.x, units = H * H;
 #pragma unroll
-  for (int j = 0; j < MPT; ++j) {
+  for (int j = 0; j < U; ++j) {
     const int t = tid + j * T;
-    if (t < nt * H) {
-      spec[2 * t] = re[j];
-      spec[2 * t + 1] = im[j];
-    }
-  }
-  __syncthreads();
-  // columns: col[iy][mx] = sum_my spec[my][mx] exp(+i phi my iy), computed
-  // into registers and written back in place after a barrier
-  double cr[MPT], ci[MPT];
-#pragma unroll
-  for (int j = 0; j < MPT; ++j) {
-    const int t = tid + j * T;
-    double sr = 0.0, si = 0.0;
-    if (t < nt * H) {
-      const int iy = t / H, mx = t - iy * H;
-      int k = 0;
-      for (int my = 0; my < nt; ++my) {
-        const double ar = spec[2 * (my * H + mx)], ai = spec[2 * (my * H + mx) + 1];
-        const double cs = tw[k], sn = tw[nt + k];
-        sr = fma(ar, cs, fma(-ai, sn, sr));
-        si = fma(ai, cs, fma(ar, sn, si));
-        k += iy;
-        if (k >= nt) k -= nt;
+    if (t < units) {
+      if (t < H) {  // p = 0: the unpaired my = 0
+        ps[2 * t] = z.re[j][0];
+        ps[2 * t + 1] = z.im[j][0];
+      } else {
+        ps[2 * t] = z.re[j][0] + z.re[j][1];
+        ps[2 * t + 1] = z.im[j][0] + z.im[j][1];
+        pd[2 * t] = z.re[j][0] - z.re[j][1];
+        pd[2 * t + 1] = z.im[j][0] - z.im[j][1];
       }
     }
-    cr[j] = sr;
-    ci[j] = si;
   }
   __syncthreads();
-#pragma unroll
-  for (int j = 0; j < MPT; ++j) {
-    const int t = tid + j * T;
-    if (t < nt * H) {
-      spec[2 * t] = cr[j];
-      spec[2 * t + 1] = ci[j];
-    }
-  }
-  __syncthreads();
-  // rows (Hermitian in mx): u = Re z0 + 2 sum_{mx>0} Re(z_mx exp(+i phi mx ix))
-  for (int i = tid; i < d; i += T) {
-    const int iy = i / nt, ix = i - iy * nt;
-    const double* z = spec + 2 * iy * H;
-    double acc = 0.0;
-    int k = ix;
-    for (int mx = 1; mx < H; ++mx) {
-      acc = fma(z[2 * mx], tw[k], fma(-z[2 * mx + 1], tw[nt + k], acc));
-      k += ix;
+  // columns: Y(iy) = Z0 + sum_{m=1}^{H-1} [s_m cos(phi m iy) + i d_m sin(phi m iy)]
+  // for iy = py, and the conjugate sine part for iy = nt - py
+  for (int t = tid; t < units; t += T) {
+    const int py = t / H, mx = t - py * H;
+    double cr = ps[2 * mx], ci = ps[2 * mx + 1], dr = 0.0, di = 0.0;
+    int k = py;
+    for (int m = 1; m < H; ++m) {
+      const int q = 2 * (m * H + mx);
+      const double cs = tw[k], sn = tw[nt + k];
+      cr = fma(ps[q], cs, cr);
+      ci = fma(ps[q + 1], cs, ci);
+      dr = fma(pd[q], sn, dr);
+      di = fma(pd[q + 1], sn, di);
+      k += py;
       if (k >= nt) k -= nt;
     }
-    out(i, fma(2.0, acc, z[0]));
+    cy[2 * (py * H + mx)] = cr - di;
+    cy[2 * (py * H + mx) + 1] = ci + dr;
+    if (py > 0) {
+      cy[2 * ((nt - py) * H + mx)] = cr + di;
+      cy[2 * ((nt - py) * H + mx) + 1] = ci - dr;
+    }
+  }
+  __syncthreads();
+  // rows (Hermitian in mx): u[px] = Re Y0 + 2 (A - B), u[nt - px] = Re Y0 + 2 (A + B),
+  // A = sum_{mx>=1} Re Y cos(phi mx px), B = sum_{mx>=1} Im Y sin(phi mx px)
+  for (int t = tid; t < nt * H; t += T) {
+    const int iy = t / H, px = t - iy * H;
+    const double* y = cy + 2 * iy * H;
+    double a = 0.0, b = 0.0;
+    int k = px;
+    for (int mx = 1; mx < H; ++mx) {
+      a = fma(y[2 * mx], tw[k], a);
+      b = fma(y[2 * mx + 1], tw[nt + k], b);
+      k += px;
+      if (k >= nt) k -= nt;
+    }
+    out(iy * nt + px, fma(2.0, a - b, y[0]));
+    if (px > 0) out(iy * nt + nt - px, fma(2.0, a + b, y[0]));
   }
   __syncthreads();
 }
@@ -243,9 +287,10 @@ __device__ __forceinline__ void cmul(double ar, double ai, double br, double bi,
   i = fma(ar, bi, ai * br);
 }
 
-template <int STAGE, int MPT>
-__global__ void __launch_bounds__(512, 1) k_adstage(const __grid_constant__ FilterDev fd,
-                                                 const EpochParams* __restrict__ ep) {
+// U = 2 serves grids of more than 512 units (nt >= 45), at most 288 threads
+template <int STAGE, int U>
+__global__ void __launch_bounds__(U == 1 ? 512 : 384, 1) k_adstage(const __grid_constant__ FilterDev fd,
+                                                    const EpochParams* __restrict__ ep) {
   extern __shared__ double s_dyn[];
   __shared__ double s_red[32];
   __shared__ double s_th[kPMax];
@@ -263,7 +308,7 @@ __global__ void __launch_bounds__(512, 1) k_adstage(const __grid_constant__ Filt
   const int64_t N = fd.N;
   const int64_t n = blockIdx.x;
   const uint32_t epoch = ep->epoch;
-  const int d = L.d, T = blockDim.x, tid = threadIdx.x, modes = L.nt * L.H;
+  const int d = L.d, nt = L.nt, H = L.H, T = blockDim.x, tid = threadIdx.x, units = H * H;
   const double inv_d = 1.0 / (double)d;
   int64_t l = n;
   if (STAGE == 2) l = fd.idx[n];
@@ -302,92 +347,103 @@ __global__ void __launch_bounds__(512, 1) k_adstage(const __grid_constant__ Filt
   for (int i = 0; i < 5; ++i) th[i] = s_th[i];
   const AdOp op = ad_op(th);
   const double* tw = sm + L.tw;
-  double* buf = sm + L.sp;
+  double* ps = sm + L.ps;
+  double* pd = sm + L.pd;
+  double* cy = sm + L.cy;
 
-  // the history in the Fourier basis, each thread holding its own modes
-  double x0r[MPT], x0i[MPT];
-  double x1r[MPT], x1i[MPT];
-  double x2r[MPT], x2i[MPT];
-  ad_forward<MPT>(L, tw, sm + L.X[0], buf, x0r, x0i);
-  ad_forward<MPT>(L, tw, sm + L.X[1], buf, x1r, x1i);
-  ad_forward<MPT>(L, tw, sm + L.X[2], buf, x2r, x2i);
-  double lr[MPT], li[MPT];
+  // the history in the Fourier basis, each thread holding its own mode pairs
+  Modes<U> x0, x1, x2;
+  ad_forward<U>(L, tw, sm + L.X[0], ps, pd, x0);
+  ad_forward<U>(L, tw, sm + L.X[1], ps, pd, x1);
+  ad_forward<U>(L, tw, sm + L.X[2], ps, pd, x2);
+  double lr[U][2], li[U][2];
 #pragma unroll
-  for (int j = 0; j < MPT; ++j) {
-    lr[j] = li[j] = 0.0;
-    if (tid + j * T < modes) ad_lambda(L, op, tw, tid + j * T, lr[j], li[j]);
+  for (int j = 0; j < U; ++j) {
+    const int t = tid + j * T;
+    const int p = t / H, mx = t - p * H;
+    lr[j][0] = li[j][0] = lr[j][1] = li[j][1] = 0.0;
+    if (t < units) {
+      ad_lambda(L, op, tw, p, mx, lr[j][0], li[j][0]);
+      if (p > 0) ad_lambda(L, op, tw, nt - p, mx, lr[j][1], li[j][1]);
+    }
   }
 
   // Psi over the S substeps (Steps 2 and 4b/4d), mode by mode
-  double wr[MPT], wi[MPT];
+  double wr[U][2], wi[U][2];
   double gamma_w = CUDART_NAN;
   for (int s = 0; s < S; ++s) {
     const StepCoef c = sc[s];
     if (!(c.gamma == gamma_w)) {
       // w = 1 / (1 - gamma lambda) per mode
 #pragma unroll
-      for (int j = 0; j < MPT; ++j) {
-        const double p = fma(-c.gamma, lr[j], 1.0), q = -c.gamma * li[j];
-        const double inv = 1.0 / fma(p, p, q * q);
-        wr[j] = p * inv;
-        wi[j] = -q * inv;
-      }
+      for (int j = 0; j < U; ++j)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const double p = fma(-c.gamma, lr[j][b], 1.0), q = -c.gamma * li[j][b];
+          const double inv = 1.0 / fma(p, p, q * q);
+          wr[j][b] = p * inv;
+          wi[j][b] = -q * inv;
+        }
       gamma_w = c.gamma;
     }
-    double er[MPT], ei[MPT];
+    Modes<U> e;
 #pragma unroll
-    for (int j = 0; j < MPT; ++j) {
-      double rr, ri, pr = 0.0, pi = 0.0;
-      if (c.kind == 2) {
-        rr = fma(c.rho2, x1r[j], c.rho1 * x0r[j]);
-        ri = fma(c.rho2, x1i[j], c.rho1 * x0i[j]);
-        if (STAGE == 2) {
-          pr = fma(c.pi2, x2r[j], fma(c.pi1, x1r[j], c.pi0 * x0r[j]));
-          pi = fma(c.pi2, x2i[j], fma(c.pi1, x1i[j], c.pi0 * x0i[j]));
+    for (int j = 0; j < U; ++j)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        double rr, ri, pr = 0.0, pi = 0.0;
+        if (c.kind == 2) {
+          rr = fma(c.rho2, x1.re[j][b], c.rho1 * x0.re[j][b]);
+          ri = fma(c.rho2, x1.im[j][b], c.rho1 * x0.im[j][b]);
+          if (STAGE == 2) {
+            pr = fma(c.pi2, x2.re[j][b], fma(c.pi1, x1.re[j][b], c.pi0 * x0.re[j][b]));
+            pi = fma(c.pi2, x2.im[j][b], fma(c.pi1, x1.im[j][b], c.pi0 * x0.im[j][b]));
+          }
+        } else {
+          // BDF1 (cold start): r = x_n; error predictor x_n + h L x_n
+          rr = x0.re[j][b];
+          ri = x0.im[j][b];
+          if (STAGE == 2) {
+            double gr, gi;
+            cmul(c.h * lr[j][b], c.h * li[j][b], x0.re[j][b], x0.im[j][b], gr, gi);
+            pr = x0.re[j][b] + gr;
+            pi = x0.im[j][b] + gi;
+          }
         }
-      } else {
-        // BDF1 (cold start): r = x_n; error predictor x_n + h L x_n
-        rr = x0r[j];
-        ri = x0i[j];
+        double yr, yi;
+        cmul(rr, ri, wr[j][b], wi[j][b], yr, yi);
         if (STAGE == 2) {
-          double gr, gi;
-          cmul(c.h * lr[j], c.h * li[j], x0r[j], x0i[j], gr, gi);
-          pr = x0r[j] + gr;
-          pi = x0i[j] + gi;
+          // Milne's estimate, with the inverse transform's 1/d
+          const double f = c.mu * inv_d;
+          e.re[j][b] = f * (yr - pr);
+          e.im[j][b] = f * (yi - pi);
         }
+        x2.re[j][b] = x1.re[j][b];
+        x2.im[j][b] = x1.im[j][b];
+        x1.re[j][b] = x0.re[j][b];
+        x1.im[j][b] = x0.im[j][b];
+        x0.re[j][b] = yr;
+        x0.im[j][b] = yi;
       }
-      double yr, yi;
-      cmul(rr, ri, wr[j], wi[j], yr, yi);
-      if (STAGE == 2) {
-        // Milne's estimate, with the inverse transform's 1/d
-        const double f = c.mu * inv_d;
-        er[j] = f * (yr - pr);
-        ei[j] = f * (yi - pi);
-      }
-      x2r[j] = x1r[j];
-      x2i[j] = x1i[j];
-      x1r[j] = x0r[j];
-      x1i[j] = x0i[j];
-      x0r[j] = yr;
-      x0i[j] = yi;
-    }
     if (STAGE == 2) {
       double* EE = sm + L.ee;
-      ad_inverse<MPT>(L, tw, buf, er, ei, [&](int i, double e) { EE[i] = fma(e, e, EE[i]); });
+      ad_inverse<U>(L, tw, ps, pd, cy, e, [&](int i, double v) { EE[i] = fma(v, v, EE[i]); });
     }
   }
 
   // back to physical space (scaled by 1/d)
-  auto back = [&](double (&re)[MPT], double (&im)[MPT], double* u) {
+  auto back = [&](Modes<U>& z, double* u) {
 #pragma unroll
-    for (int j = 0; j < MPT; ++j) {
-      re[j] *= inv_d;
-      im[j] *= inv_d;
-    }
-    ad_inverse<MPT>(L, tw, buf, re, im, [&](int i, double v) { u[i] = v; });
+    for (int j = 0; j < U; ++j)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        z.re[j][b] *= inv_d;
+        z.im[j][b] *= inv_d;
+      }
+    ad_inverse<U>(L, tw, ps, pd, cy, z, [&](int i, double v) { u[i] = v; });
   };
   double* X0 = sm + L.X[0];
-  back(x0r, x0i, X0);
+  back(x0, X0);
   if (STAGE == 1) {
     double lg = -CUDART_INF;
     if (tid == 0) {
@@ -401,8 +457,8 @@ __global__ void __launch_bounds__(512, 1) k_adstage(const __grid_constant__ Filt
   } else {
     double* X1 = sm + L.X[1];
     double* X2 = sm + L.X[2];
-    back(x1r, x1i, X1);
-    back(x2r, x2i, X2);
+    back(x1, X1);
+    back(x2, X2);
     // Steps 4c, 4d: innovation v = sqrt(kappa E) z', written in (x, h1, h2) order
     const double* EE = sm + L.ee;
     for (int b = tid; b < (d + 1) / 2; b += T) {
@@ -436,21 +492,21 @@ __global__ void __launch_bounds__(512, 1) k_adstage(const __grid_constant__ Filt
   }
 }
 
-// Launch shape for a grid side: modes per thread MPT (1, 2 or 4: fewer modes
-// per thread keep fewer registers, so more blocks fit an SM) and threads per
-// block, a multiple of 32 covering the nt * H modes.
-static void ad_shape(int nt, int* threads, int* mpt) {
-  const int modes = nt * ((nt + 1) / 2);
-  int m = 1;
-  while (m < kAdMaxModesPerThread && (modes + m - 1) / m > 512) m *= 2;
-  const int need = (modes + m - 1) / m;
-  *mpt = m;
+// Launch shape for a grid side: units (mode pairs) per thread U (1 or 2:
+// fewer units per thread keep fewer registers, so more blocks fit an SM) and
+// threads per block, a multiple of 32 covering the H^2 units.
+static void ad_shape(int nt, int* threads, int* upt) {
+  const int H = (nt + 1) / 2, units = H * H;
+  int u = 1;
+  while (u < kAdMaxUnitsPerThread && (units + u - 1) / u > 512) u *= 2;
+  const int need = (units + u - 1) / u;
+  *upt = u;
   *threads = ((need > 64 ? need : 64) + 31) / 32 * 32;
 }
 
 int ad_threads(int nt) {
-  int T, m;
-  ad_shape(nt, &T, &m);
+  int T, u;
+  ad_shape(nt, &T, &u);
   return T;
 }
 
@@ -463,14 +519,14 @@ cudaError_t launch_ad_stage(int stage, const FilterDev& fd, const EpochParams* e
   const int nt = ad_side(fd.d);
   if (nt == 0) return cudaErrorInvalidValue;
   const size_t smem = ad_stage_smem(fd.d, S, stage);
-  int T, mpt;
-  ad_shape(nt, &T, &mpt);
-  if (T * mpt < nt * ((nt + 1) / 2) || T > 512) return cudaErrorInvalidValue;
+  int T, upt;
+  ad_shape(nt, &T, &upt);
+  const int H = (nt + 1) / 2;
+  if (T * upt < H * H || T > (upt == 1 ? 512 : 384)) return cudaErrorInvalidValue;
   using K = void (*)(const FilterDev, const EpochParams*);
   K k;
-  if (mpt == 1) k = stage == 1 ? k_adstage<1, 1> : k_adstage<2, 1>;
-  else if (mpt == 2) k = stage == 1 ? k_adstage<1, 2> : k_adstage<2, 2>;
-  else k = stage == 1 ? k_adstage<1, 4> : k_adstage<2, 4>;
+  if (upt == 1) k = stage == 1 ? k_adstage<1, 1> : k_adstage<2, 1>;
+  else k = stage == 1 ? k_adstage<1, 2> : k_adstage<2, 2>;
   cudaError_t e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<(unsigned)fd.N, T, smem, st>>>(fd, ep);
@@ -479,8 +535,7 @@ cudaError_t launch_ad_stage(int stage, const FilterDev& fd, const EpochParams* e
 
 cudaError_t preload_ad_kernels() {
   const void* ks[] = {(const void*)k_adstage<1, 1>, (const void*)k_adstage<2, 1>,
-                      (const void*)k_adstage<1, 2>, (const void*)k_adstage<2, 2>,
-                      (const void*)k_adstage<1, 4>, (const void*)k_adstage<2, 4>};
+                      (const void*)k_adstage<1, 2>, (const void*)k_adstage<2, 2>};
   for (const void* k : ks) {
     cudaFuncAttributes a;
     const cudaError_t e = cudaFuncGetAttributes(&a, k);
