@@ -275,6 +275,15 @@ pf_status pf_get_history(const pf_filter* f, int64_t* epochs, int* depth, double
 pf_status pf_set_history(pf_filter* f, int64_t epochs, int depth, double t_prev, double hprev1,
                          double hprev2);
 
+/* ---- diagnostics ----------------------------------------------------------
+ * The FP64 FMA throughput this GPU sustains, in TFLOP/s (an FMA counts 2):
+ * independent FMA chains over every SM for about ms milliseconds (best of
+ * three launches after a calibration) on `stream` (cudaStream_t, NULL = the
+ * legacy default stream).  The propagation kernels are bound by FP64 issue;
+ * this is the roofline denominator they are compared with.  Synchronous.
+ * Errors: INVALID_ARG (tflops NULL, ms <= 0), CUDA. */
+pf_status pf_fp64_fma_rate(void* stream, double ms, double* tflops);
+
 /* ---- host-only helper (no GPU needed) -----------------------------------
  * Substep table of one interval (t_prev, t_next] for the given history state,
  * as the filter builds it.  Per substep i, row i of coef (PF_SUBSTEP_ROW = 11

@@ -1,0 +1,100 @@
+// pf_diag.cu -- the FP64 FMA throughput this GPU sustains: the denominator of
+// the roofline of the propagation kernels (one particle per thread, bound by
+// FP64 issue), measured rather than taken from a datasheet.
+//
+// Every thread runs kChains independent FMA recurrences acc <- acc * a + b
+// (a < 1, so each converges to b / (1 - a) and never over- or underflows),
+// enough warps per SM sub-partition to keep the FP64 pipe issuing every
+// cycle it can.  The result is stored only under a condition that never
+// holds, so the work is not removed.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+
+#include "pf_filter.h"
+
+namespace pfg {
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kDiagThreads = 256;
+constexpr int kDiagBlocksPerSm = 4;
+
+__global__ void __launch_bounds__(kDiagThreads) k_fp64_fma(int iters, double a, double b, double* sink) {
+  double acc[kChains];
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) acc[k] = (double)(threadIdx.x + k);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) acc[k] = fma(acc[k], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += acc[k];
+  if (s == -1.0) sink[blockIdx.x] = s;  // never true: keeps the chains alive
+}
+
+}  // namespace
+}  // namespace pfg
+
+extern "C" pf_status pf_fp64_fma_rate(void* stream, double ms, double* tflops) {
+  using namespace pfg;
+  if (!tflops || !(ms > 0.0) || !std::isfinite(ms)) {
+    set_thread_error("pf_fp64_fma_rate: need tflops != NULL and ms > 0");
+    return PF_ERR_INVALID_ARG;
+  }
+  *tflops = 0.0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+  const int blocks = sms * kDiagBlocksPerSm;
+  auto timed = [&](int iters, float* out_ms) -> cudaError_t {
+    cudaError_t r = cudaEventRecord(ev0, st);
+    if (r == cudaSuccess) {
+      k_fp64_fma<<<blocks, kDiagThreads, 0, st>>>(iters, 0.999999, 1e-7, nullptr);
+      r = cudaGetLastError();
+    }
+    if (r == cudaSuccess) r = cudaEventRecord(ev1, st);
+    if (r == cudaSuccess) r = cudaEventSynchronize(ev1);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(out_ms, ev0, ev1);
+    return r;
+  };
+  // calibrate: after a warm-up, grow the iteration count until a launch takes
+  // at least 2 ms, then scale it to about ms milliseconds; take the best of
+  // three such launches
+  int iters = 1 << 8;
+  float t = 0.0f;
+  if (e == cudaSuccess) e = timed(iters, &t);
+  if (e == cudaSuccess) e = timed(iters, &t);
+  while (e == cudaSuccess && t < 2.0f && iters < (1 << 24)) {
+    iters *= 4;
+    e = timed(iters, &t);
+  }
+  if (e == cudaSuccess && t > 0.0f) {
+    const double scale = ms / (double)t;
+    const double want = (double)iters * (scale > 1.0 ? scale : 1.0);
+    iters = (int)(want < (double)(1 << 28) ? want : (double)(1 << 28));
+  }
+  double best = 0.0;
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+    e = timed(iters, &t);
+    if (e == cudaSuccess && t > 0.0f) {
+      const double flops = 2.0 * kChains * (double)iters * (double)kDiagThreads * (double)blocks;
+      const double r = flops / ((double)t * 1e-3) / 1e12;
+      best = r > best ? r : best;
+    }
+  }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  if (e != cudaSuccess) {
+    set_thread_error(std::string("pf_fp64_fma_rate: ") + cudaGetErrorString(e));
+    return PF_ERR_CUDA;
+  }
+  *tflops = best;
+  return PF_OK;
+}

@@ -38,7 +38,7 @@ ABI_SYMBOLS = [
     "pf_batch_destroy", "pf_server_create", "pf_server_open", "pf_server_submit",
     "pf_server_step", "pf_server_drain", "pf_server_close", "pf_server_session",
     "pf_server_stats", "pf_server_last_error", "pf_server_destroy", "pf_checkpoint_size",
-    "pf_save", "pf_load",
+    "pf_save", "pf_load", "pf_fp64_fma_rate",
 ]
 NOALLOC_MAX_PARTICLES = 1 << 24
 KERNEL_SLOTS = ["stage1", "scan_tile", "scan_add", "resample", "stage2", "moments"]
@@ -124,6 +124,7 @@ def load(path: str = LIB_PATH):
         "pf_get_history": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int), _dp, _dp, _dp]),
         "pf_set_history": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_double]),
         "pf_checkpoint_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+        "pf_fp64_fma_rate": (C.c_int, [C.c_void_p, C.c_double, _dp]),
         "pf_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
         "pf_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
         "pf_substep_table": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
@@ -185,6 +186,14 @@ def pf_resample_systematic_noalloc(log_g_ptr, N, u, cumulative_ptr, idx_ptr, str
                                                C.c_void_p(cumulative_ptr), C.c_void_p(idx_ptr),
                                                C.c_void_p(stream) if stream else None)
     _check(st, None)
+
+
+def pf_fp64_fma_rate(ms=200.0, stream=None):
+    """Sustained FP64 FMA throughput of the current GPU in TFLOP/s."""
+    out = C.c_double()
+    _check(load().pf_fp64_fma_rate(C.c_void_p(stream) if stream else None, float(ms), C.byref(out)),
+           None)
+    return out.value
 
 
 def pf_substep_table(lmm, spacing, dt, substeps, q0, t_prev, t_next, depth, hprev1, hprev2):

@@ -97,3 +97,13 @@ def test_checkpoint_rejects_a_different_filter(pf):
     b.pf_assimilate(w.t_obs[0], w.y_obs[0])
     c.pf_assimilate(w.t_obs[0], w.y_obs[0])
     _same(_snapshot(b), _snapshot(c))
+
+
+def test_fp64_fma_rate_reaches_the_nominal_peak(pf):
+    """The diagnostic FMA kernel sustains close to the FP64 rate the roofline
+    divides by (2 FMA lanes per clock per SM at the maximum clock, 1.259
+    TFLOP/s on a 152-SM GB300): between half and 110 % of it."""
+    r = pf.pf_fp64_fma_rate(50.0)
+    assert 0.5 * 1.259 < r < 1.1 * 1.259, r
+    with pytest.raises(pf.PfError):
+        pf.pf_fp64_fma_rate(0.0)
