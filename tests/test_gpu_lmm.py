@@ -138,3 +138,38 @@ def test_long_substep_table(pf, lmm):
     g, o = _pair(pf, w)
     for k in range(w.T):
         check_epoch(g, o, w.t_obs[k], w.y_obs[k])
+
+
+@pytest.mark.parametrize("lmm", [W.LMM_BDF3, W.LMM_AM3, W.LMM_AB3])
+def test_michaelis_independent_runs_agree(pf, lmm):
+    """GPU and oracle each run the whole M1 filter on their own (own scan and
+    resampling) with the same seed: the same resampled indices every epoch,
+    and the same posterior."""
+    w = W.michaelis(N=3000, lmm=lmm)
+    g, o = _pair(pf, w)
+    for k in range(w.T):
+        g.pf_assimilate(w.t_obs[k], w.y_obs[k])
+        assert o.epoch(w.t_obs[k], w.y_obs[k]) == oracle.OK
+        assert np.array_equal(g.pf_get_work()["idx"], o.work()["idx"]), k
+    tb, Cm, xb = g.pf_estimates()
+    om = o.moments()
+    assert np.allclose(tb, om["phibar"], rtol=1e-9, atol=1e-12)
+    assert np.allclose(xb, om["xbar"], rtol=1e-9)
+
+
+def test_michaelis_posterior_within_three_mc_standard_errors(pf):
+    """Across seeds, the GPU and oracle posterior means of M1 (AM2) agree
+    within 3 Monte Carlo standard errors."""
+    R = 6
+    gm, om = [], []
+    for seed in range(R):
+        w = W.michaelis(N=2000, seed=seed, lmm=W.LMM_AM2)
+        g, o = _pair(pf, w)
+        for k in range(w.T):
+            g.pf_assimilate(w.t_obs[k], w.y_obs[k])
+            assert o.epoch(w.t_obs[k], w.y_obs[k]) == oracle.OK
+        gm.append(g.pf_estimates()[0])
+        om.append(o.moments()["phibar"])
+    gm, om = np.array(gm), np.array(om)
+    se = np.sqrt(gm.var(axis=0, ddof=1) / R + om.var(axis=0, ddof=1) / R) + 1e-15
+    assert np.all(np.abs(gm.mean(axis=0) - om.mean(axis=0)) <= 3 * se)
