@@ -425,6 +425,13 @@ def run_ours(args, w):
                                               N=CPU_SAMPLE_N.get(w.name))
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": sample}
+        # and on one core, a shorter sample
+        import oracle
+        oracle.set_threads(1)
+        rate1, _, sample1 = cpu_oracle_rate(w, seconds=args.cpu_seconds / 3.0,
+                                            N=CPU_SAMPLE_N.get(w.name))
+        oracle.set_threads(cores)
+        line["cpu_baseline"]["single_thread"] = {"value": rate1, "sample": sample1}
     g.close()
     print(json.dumps(line), flush=True)
     return 0

@@ -123,6 +123,7 @@ def lib():
             "or_get_history": (None, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp, _dp, _dp]),
             "or_set_history": (None, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double]),
             "or_threads": (C.c_int, []),
+            "or_set_threads": (None, [C.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -295,6 +296,10 @@ def liu_west_shrink(a, phi, phibar):
 
 def threads():
     return lib().or_threads()
+
+
+def set_threads(n):
+    lib().or_set_threads(int(n))
 
 
 # -------------------------------------------------------------------- filter

@@ -1205,3 +1205,13 @@ int or_threads(void) {
   return 1;
 #endif
 }
+
+/* threads of the particle loops from now on (CPU-baseline timing only; the
+ * result does not depend on it) */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}

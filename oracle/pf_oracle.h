@@ -155,4 +155,5 @@ void or_get_history(const or_filter* f, int* epoch, int* depth, double* t_prev,
 void or_set_history(or_filter* f, int epoch, int depth, double t_prev, double hprev1,
                     double hprev2);
 int or_threads(void);
+void or_set_threads(int n);
 #endif
