@@ -453,6 +453,19 @@ def run_profile(args, w, pf, stream):
     return 0
 
 
+def shard_by_work(work, world):
+    """Independent filters over ranks: largest first, each to the rank with
+    the least work so far (ties to the lower rank).  Returns one list of
+    filter indices per rank; deterministic, disjoint, covering."""
+    loads = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(work)), key=lambda j: (-work[j], j)):
+        r = min(range(world), key=lambda q: (loads[q], q))
+        out[r].append(i)
+        loads[r] += work[i]
+    return [sorted(o) for o in out]
+
+
 def run_batched(args):
     """Batched pattern: 256 independent filters of uneven N (2^10..2^17) and
     mixed problems advanced round by round (a round = every filter that still
@@ -462,15 +475,25 @@ def run_batched(args):
     with each filter on its own stream."""
     import torch
     from paper_1411_1702_gb300 import workloads as W
-    ws = W.batched(args.batch_filters)
-    torch.cuda.set_device(0)
+    dist, rank, world = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ws_all = W.batched(args.batch_filters)
+    # with several ranks, the filters are sharded (no collective on the data
+    # path); each keeps its global filter id, so its results do not change
+    # (work: the stage-2 flops of the whole series, as the roofline counts them)
+    mine = shard_by_work([STAGE2_FLOPS_PER_SUBSTEP[w.name](w.newton_iters, w.d) * w.N *
+                          sum(w.substeps_per_interval(k) for k in range(w.T)) for w in ws_all],
+                         world)[rank]
+    ws = [ws_all[i] for i in mine]
+    ids = list(mine)
+    torch.cuda.set_device(local)
     from paper_1411_1702_gb300 import build as B
     B.build()
     from paper_1411_1702_gb300 import pf
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    n = len(ws)
-    R = max(w.T for w in ws)
+    n = len(ws_all)
+    R = max(w.T for w in ws_all)
 
     def inputs(r):
         return ([w.t_obs[r] if r < w.T else 0.0 for w in ws],
@@ -481,15 +504,21 @@ def run_batched(args):
 
     K = min(args.steps, R - args.warmup)
     timed = range(args.warmup, args.warmup + K)
-    total_steps = sum(steps(r) for r in timed)
+    my_steps = sum(steps(r) for r in timed)
+
+    def sync_ranks():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
 
     # 1. the batch
-    fb = [pf.Filter.from_workload(w, stream=stream.cuda_stream, filter_id=i) for i, w in enumerate(ws)]
+    fb = [pf.Filter.from_workload(w, stream=stream.cuda_stream, filter_id=i) for i, w in zip(ids, ws)]
     batch = pf.Batch(fb, stream=stream.cuda_stream)
     for r in range(args.warmup):
         batch.pf_batch_assimilate(*inputs(r))
     dev_ms, wall = 0.0, 0.0
-    with ClockSampler(0) as clocks:
+    sync_ranks()
+    with ClockSampler(local) as clocks:
         for r in timed:
             t0 = time.perf_counter()
             st = batch.pf_batch_assimilate(*inputs(r))
@@ -502,13 +531,14 @@ def run_batched(args):
         f.close()
     torch.cuda.synchronize()
     # 2. per-filter synchronous calls
-    fs = [pf.Filter.from_workload(w, filter_id=i) for i, w in enumerate(ws)]
+    fs = [pf.Filter.from_workload(w, filter_id=i) for i, w in zip(ids, ws)]
     for r in range(args.warmup):
         t, y = inputs(r)
         for i, f in enumerate(fs):
             if y[i] is not None:
                 f.pf_assimilate(t[i], y[i])
     wall_sync = 0.0
+    sync_ranks()
     for r in timed:
         t, y = inputs(r)
         t0 = time.perf_counter()
@@ -519,7 +549,7 @@ def run_batched(args):
     for f in fs:
         f.close()
     # 3. per-filter asynchronous launches, one stream per filter
-    fa = [pf.Filter.from_workload(w, filter_id=i) for i, w in enumerate(ws)]
+    fa = [pf.Filter.from_workload(w, filter_id=i) for i, w in zip(ids, ws)]
     for f, w in zip(fa, ws):
         f.pf_load_observations(w.t_obs, w.y_obs)
     for r in range(args.warmup):
@@ -529,6 +559,7 @@ def run_batched(args):
         for f in fa:
             f.pf_synchronize()
     wall_async = 0.0
+    sync_ranks()
     for r in timed:
         t0 = time.perf_counter()
         for f, w in zip(fa, ws):
@@ -539,17 +570,27 @@ def run_batched(args):
         wall_async += time.perf_counter() - t0
     for f in fa:
         f.close()
+    # the slowest rank's times, every rank's particle-steps
+    dev_ms, total_steps = reduce_times(dist, dev_ms, my_steps, device="cuda")
+    wall, _ = reduce_times(dist, wall * 1e3, 0, device="cuda")
+    wall_sync, _ = reduce_times(dist, wall_sync * 1e3, 0, device="cuda")
+    wall_async, _ = reduce_times(dist, wall_async * 1e3, 0, device="cuda")
+    wall, wall_sync, wall_async = wall * 1e-3, wall_sync * 1e-3, wall_async * 1e-3
+    if rank != 0:
+        return 0
     value = total_steps / (dev_ms * 1e-3)
     line = {
-        "metric": METRIC, "mode": "batched", "value": value, "unit": UNIT, "n_gpus": 1,
+        "metric": METRIC, "mode": "batched", "value": value, "unit": UNIT, "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": dev_ms / K, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"batched: {n} filters, N = round(2^U[10,17]) "
-                               f"(total {sum(w.N for w in ws)}), linear2/robertson 50/50, "
+                               f"(total {sum(w.N for w in ws_all)}), linear2/robertson 50/50, "
                                "one round per step", "filters": n,
-                   "robertson_filters": sum(w.ode == W.ROBERTSON for w in ws),
-                   "particles": sum(w.N for w in ws),
-                   "l2": "working set ~2 GB > L2, no flush", "parallelism": "replicas"},
+                   "robertson_filters": sum(w.ode == W.ROBERTSON for w in ws_all),
+                   "particles": sum(w.N for w in ws_all),
+                   "l2": "working set ~2 GB > L2, no flush",
+                   "parallelism": ("one GPU" if world == 1 else
+                                   f"filters sharded over {world} ranks by work, no collective")},
         "clocks": clocks.summary(),
         "e2e": {"value": total_steps / wall, "unit": UNIT},
         "per_filter_sync": {"value": total_steps / wall_sync, "unit": UNIT,

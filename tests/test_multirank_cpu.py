@@ -41,3 +41,36 @@ def test_two_gloo_ranks_reduce_max_time_and_sum_steps():
 def test_single_process_reduction_is_identity():
     import bench
     assert bench.reduce_times(None, 12.5, 77) == (12.5, 77)
+
+
+def _shard_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    work = [float((7 * i) % 23 + 1) for i in range(50)]
+    mine = bench.shard_by_work(work, world)[rank]
+    # each rank's particle-steps summed and its time maxed, as run_batched does
+    t, s = bench.reduce_times(dist, total_ms=1.0 + sum(work[i] for i in mine), steps_done=len(mine))
+    out[rank] = (mine, t, s)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_batched_filters_shard_over_two_gloo_ranks():
+    """The batched benchmark's sharding: every filter on exactly one rank, the
+    ranks' work balanced to within the largest filter, the reduction giving
+    the slowest rank's time and all filters."""
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_shard_worker, args=(world, port, out), nprocs=world, start_method="spawn",
+                       join=True)
+    work = [float((7 * i) % 23 + 1) for i in range(50)]
+    shards = [out[r][0] for r in range(world)]
+    assert sorted(i for s in shards for i in s) == list(range(50))
+    loads = [sum(work[i] for i in s) for s in shards]
+    assert max(loads) - min(loads) <= max(work)
+    for r in range(world):
+        assert out[r][1] == 1.0 + max(loads) and out[r][2] == 50
