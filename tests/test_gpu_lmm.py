@@ -173,3 +173,31 @@ def test_michaelis_posterior_within_three_mc_standard_errors(pf):
     gm, om = np.array(gm), np.array(om)
     se = np.sqrt(gm.var(axis=0, ddof=1) / R + om.var(axis=0, ddof=1) / R) + 1e-15
     assert np.all(np.abs(gm.mean(axis=0) - om.mean(axis=0)) <= 3 * se)
+
+
+@pytest.mark.parametrize("lmm", [W.LMM_BDF3, W.LMM_AM3, W.LMM_AB2])
+def test_michaelis_restart_history_parity(pf, lmm):
+    """RESTART history (a cold start every interval, the literal Psi(x_j)
+    reading): the order ramp runs in every interval."""
+    w = W.michaelis(N=700, T=3, lmm=lmm).with_(history=W.HIST_RESTART)
+    g, o = _pair(pf, w)
+    for k in range(w.T):
+        check_epoch(g, o, w.t_obs[k], w.y_obs[k], exempt_dead=True)
+
+
+@pytest.mark.parametrize("lmm", [W.LMM_BDF3, W.LMM_AM2, W.LMM_AB3])
+def test_device_series_equals_host_calls(pf, lmm):
+    """pf_load_observations + pf_run (M1's inputs tabulated for the whole
+    series up front) give the same ensemble as one pf_assimilate per
+    observation."""
+    w = W.michaelis(N=1500, T=12, lmm=lmm)
+    a = pf.Filter.from_workload(w)
+    for k in range(w.T):
+        a.pf_assimilate(w.t_obs[k], w.y_obs[k])
+    b = pf.Filter.from_workload(w)
+    b.pf_load_observations(w.t_obs, w.y_obs)
+    b.pf_run(0, w.T)
+    b.pf_synchronize()
+    ea, eb = a.pf_get_ensemble(), b.pf_get_ensemble()
+    for key in ea:
+        assert np.array_equal(ea[key], eb[key], equal_nan=True), key
