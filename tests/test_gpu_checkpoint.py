@@ -37,7 +37,8 @@ def _same(a, b):
 
 
 @pytest.mark.parametrize("name,N,lmm", [("robertson", 4096, None), ("michaelis", 3001, W.LMM_AM3),
-                                        ("linear2", 1029, W.LMM_BDF3), ("brusselator", 513, None)])
+                                        ("linear2", 1029, W.LMM_BDF3), ("brusselator", 513, None),
+                                        ("advdiff20", 300, None)])
 def test_resume_is_bit_identical(pf, name, N, lmm):
     w = W.get(name, N=N)
     if lmm is not None:
