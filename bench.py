@@ -115,8 +115,8 @@ STAGE2_FLOPS_PER_SUBSTEP["michaelis"] = _michaelis_flops(2)
 STAGE2_FLOPS_PER_INTERVAL = {"advdiff20": _advdiff_flops_interval,
                              "advdiff40": _advdiff_flops_interval}
 STAGE2_KERNEL = {"robertson": "k_stage2<Robertson>", "linear2": "k_stage2<Linear2>",
-                 "brusselator": "k_bstage2", "advdiff20": "k_adstage<2>",
-                 "advdiff40": "k_adstage<2>"}
+                 "brusselator": "k_bstage2", "advdiff20": "k_adstage<2, 1, 2>",
+                 "advdiff40": "k_adstage<2, 1, 1>"}
 _FAMILY_ID = {0: 0, 1: 2, 2: 3}
 for _name, _lmm in W_LMM_NAMES.items():
     _fam = 1 if _lmm == 3 else _FAMILY_ID[_lmm // 10]
@@ -127,7 +127,6 @@ STAGE2_KERNEL["michaelis"] = "k_stage2<Michaelis, 0>"
 # of the kernel as it stands exists.
 STAGE2_TRAFFIC = {"robertson": 11552512 + 0,
                   "brusselator": 11202826752 + 10732933888,
-                  "advdiff20": 2705920 + 292608,
                   "michaelisBDF2": 4353024 + 0,
                   "michaelisAM3": 4586752 + 0,
                   "michaelisAB3": 4459520 + 0}

@@ -36,8 +36,10 @@
 // registers, so the forward transform ends and the inverse begins in the
 // owning thread.
 //
-// One block per particle.  Shared memory holds the substep table, the twiddle
-// table, the physical states, the pair buffers of the transforms, and in
+// A block advances PB particles (1, 2 or 4: on small grids several
+// particles fill the block's warps), all in step through the same substeps.
+// Shared memory holds the substep table and the twiddle table, and per
+// particle the physical states, the pair buffers of the transforms and in
 // stage 2 the error sums.  Global memory is touched once per particle per
 // stage.
 #include "pf_epoch.cuh"
@@ -55,11 +57,15 @@ __host__ __device__ inline int ad_side(int d) {
   return 0;
 }
 
-// Shared-memory layout of one particle's block, in doubles.
+// Shared-memory layout of one block, in doubles: the substep table and the
+// twiddle table, then one region per particle of the block.
 struct AdLayout {
-  int nt, d, H;
+  int nt, d, H, PB;
   int sc;    // step table, S entries
   int tw;    // cos(2 pi k / nt), then sin(2 pi k / nt), k < nt
+  int base;  // particle 0's region; particle q's is at base + q * per
+  int per;   // doubles per particle region
+  // offsets within a particle's region:
   int X[3];  // physical x_n, x_{n-1}, x_{n-2}
   int ps;    // pair sums [p][mx] (complex), p < H; p = 0 holds the unpaired entry
   int pd;    // pair differences [p][mx] (complex)
@@ -68,29 +74,33 @@ struct AdLayout {
   int total;
 };
 
-__host__ __device__ inline AdLayout ad_layout(int d, int S, bool err) {
+__host__ __device__ inline AdLayout ad_layout(int d, int S, bool err, int PB) {
   AdLayout L;
   L.nt = ad_side(d);
   L.d = d;
   L.H = (L.nt + 1) / 2;
+  L.PB = PB;
   int off = 0;
   L.sc = off;
   off += S * kAdScDoubles;
   L.tw = off;
   off += 2 * L.nt;
+  L.base = off;
+  int r = 0;
   for (int k = 0; k < 3; ++k) {
-    L.X[k] = off;
-    off += d;
+    L.X[k] = r;
+    r += d;
   }
-  L.ps = off;
-  off += 2 * L.H * L.H;
-  L.pd = off;
-  off += 2 * L.H * L.H;
-  L.cy = off;
-  off += 2 * L.nt * L.H;
-  L.ee = off;
-  off += err ? d : 0;
-  L.total = off;
+  L.ps = r;
+  r += 2 * L.H * L.H;
+  L.pd = r;
+  r += 2 * L.H * L.H;
+  L.cy = r;
+  r += 2 * L.nt * L.H;
+  L.ee = r;
+  r += err ? d : 0;
+  L.per = r;
+  L.total = off + PB * r;
   return L;
 }
 
@@ -122,23 +132,31 @@ __device__ __forceinline__ void ad_lambda(const AdLayout& L, const AdOp& o, cons
   li = fma(o.c1, axi, o.c2 * ayi);
 }
 
-// A thread's modes: unit u = p * H + mx holds mode A = (my = p, mx) and, for
-// p >= 1, mode B = (my = nt - p, mx).  Index [j][0] is A, [j][1] is B.
+// A thread's modes: work item t = q * H^2 + p * H + mx (particle q of the
+// block) holds mode A = (my = p, mx) and, for p >= 1, mode B = (my = nt - p,
+// mx).  Index [j][0] is A, [j][1] is B, for the items t = tid + j T.
 template <int U>
 struct Modes {
   double re[U][2], im[U][2];
 };
 
-// Forward real 2D DFT of u (physical, shared) into the calling thread's own
-// modes: X(my, mx) = sum_{iy,ix} u[iy][ix] exp(-i phi (mx ix + my iy)).
+// Forward real 2D DFT of state k of every particle of the block (physical,
+// shared) into the calling thread's own modes:
+// X(my, mx) = sum_{iy,ix} u[iy][ix] exp(-i phi (mx ix + my iy)).
 // Ends with a barrier.
 template <int U>
-__device__ void ad_forward(const AdLayout& L, const double* tw, const double* u, double* ps, double* pd,
+__device__ void ad_forward(const AdLayout& L, const double* tw, double* sm, int k_state,
                            Modes<U>& out) {
   const int nt = L.nt, H = L.H, T = blockDim.x, tid = threadIdx.x, units = H * H;
+  const int items = L.PB * units;
   // rows py and nt - py at column mx, stored as their sum and difference
-  for (int t = tid; t < units; t += T) {
-    const int py = t / H, mx = t - py * H;
+  for (int t = tid; t < items; t += T) {
+    const int q = t / units, v = t - q * units;
+    double* R = sm + L.base + q * L.per;
+    const double* u = R + L.X[k_state];
+    double* ps = R + L.ps;
+    double* pd = R + L.pd;
+    const int py = v / H, mx = v - py * H;
     const double* g1 = u + py * nt;
     const double* g2 = u + (py == 0 ? 0 : nt - py) * nt;
     double r1 = 0.0, i1 = 0.0, r2 = 0.0, i2 = 0.0;
@@ -153,13 +171,13 @@ __device__ void ad_forward(const AdLayout& L, const double* tw, const double* u,
       if (k >= nt) k -= nt;
     }
     if (py == 0) {
-      ps[2 * t] = r1;
-      ps[2 * t + 1] = i1;
+      ps[2 * v] = r1;
+      ps[2 * v + 1] = i1;
     } else {
-      ps[2 * t] = r1 + r2;
-      ps[2 * t + 1] = i1 + i2;
-      pd[2 * t] = r1 - r2;
-      pd[2 * t + 1] = i1 - i2;
+      ps[2 * v] = r1 + r2;
+      ps[2 * v + 1] = i1 + i2;
+      pd[2 * v] = r1 - r2;
+      pd[2 * v + 1] = i1 - i2;
     }
   }
   __syncthreads();
@@ -169,18 +187,22 @@ __device__ void ad_forward(const AdLayout& L, const double* tw, const double* u,
   for (int j = 0; j < U; ++j) {
     const int t = tid + j * T;
     double cr = 0.0, ci = 0.0, dr = 0.0, di = 0.0;
-    if (t < units) {
-      const int p = t / H, mx = t - p * H;
+    if (t < items) {
+      const int q = t / units, v = t - q * units;
+      const double* R = sm + L.base + q * L.per;
+      const double* ps = R + L.ps;
+      const double* pd = R + L.pd;
+      const int p = v / H, mx = v - p * H;
       cr = ps[2 * mx];
       ci = ps[2 * mx + 1];
       int k = p;
       for (int iy = 1; iy < H; ++iy) {
-        const int q = 2 * (iy * H + mx);
+        const int o = 2 * (iy * H + mx);
         const double cs = tw[k], sn = tw[nt + k];
-        cr = fma(ps[q], cs, cr);
-        ci = fma(ps[q + 1], cs, ci);
-        dr = fma(pd[q], sn, dr);
-        di = fma(pd[q + 1], sn, di);
+        cr = fma(ps[o], cs, cr);
+        ci = fma(ps[o + 1], cs, ci);
+        dr = fma(pd[o], sn, dr);
+        di = fma(pd[o + 1], sn, di);
         k += p;
         if (k >= nt) k -= nt;
       }
@@ -194,43 +216,52 @@ __device__ void ad_forward(const AdLayout& L, const double* tw, const double* u,
   __syncthreads();
 }
 
-// Inverse: the threads' modes z (already scaled) give
+// Inverse: the threads' modes z (already scaled) give, per particle q,
 //   u[iy][ix] = sum over all modes z exp(+i phi (mx ix + my iy))
-// (Hermitian in mx), delivered per grid point to `out(i, value)`.  Ends with
-// a barrier.
+// (Hermitian in mx), delivered per grid point to `out(q, i, value)`.  Ends
+// with a barrier.
 template <int U, class Out>
-__device__ void ad_inverse(const AdLayout& L, const double* tw, double* ps, double* pd, double* cy,
-                           const Modes<U>& z, Out out) {
+__device__ void ad_inverse(const AdLayout& L, const double* tw, double* sm, const Modes<U>& z, Out out) {
   const int nt = L.nt, H = L.H, T = blockDim.x, tid = threadIdx.x, units = H * H;
+  const int items = L.PB * units;
 #pragma unroll
   for (int j = 0; j < U; ++j) {
     const int t = tid + j * T;
-    if (t < units) {
-      if (t < H) {  // p = 0: the unpaired my = 0
-        ps[2 * t] = z.re[j][0];
-        ps[2 * t + 1] = z.im[j][0];
+    if (t < items) {
+      const int q = t / units, v = t - q * units;
+      double* R = sm + L.base + q * L.per;
+      double* ps = R + L.ps;
+      double* pd = R + L.pd;
+      if (v < H) {  // p = 0: the unpaired my = 0
+        ps[2 * v] = z.re[j][0];
+        ps[2 * v + 1] = z.im[j][0];
       } else {
-        ps[2 * t] = z.re[j][0] + z.re[j][1];
-        ps[2 * t + 1] = z.im[j][0] + z.im[j][1];
-        pd[2 * t] = z.re[j][0] - z.re[j][1];
-        pd[2 * t + 1] = z.im[j][0] - z.im[j][1];
+        ps[2 * v] = z.re[j][0] + z.re[j][1];
+        ps[2 * v + 1] = z.im[j][0] + z.im[j][1];
+        pd[2 * v] = z.re[j][0] - z.re[j][1];
+        pd[2 * v + 1] = z.im[j][0] - z.im[j][1];
       }
     }
   }
   __syncthreads();
   // columns: Y(iy) = Z0 + sum_{m=1}^{H-1} [s_m cos(phi m iy) + i d_m sin(phi m iy)]
   // for iy = py, and the conjugate sine part for iy = nt - py
-  for (int t = tid; t < units; t += T) {
-    const int py = t / H, mx = t - py * H;
+  for (int t = tid; t < items; t += T) {
+    const int q = t / units, v = t - q * units;
+    double* R = sm + L.base + q * L.per;
+    const double* ps = R + L.ps;
+    const double* pd = R + L.pd;
+    double* cy = R + L.cy;
+    const int py = v / H, mx = v - py * H;
     double cr = ps[2 * mx], ci = ps[2 * mx + 1], dr = 0.0, di = 0.0;
     int k = py;
     for (int m = 1; m < H; ++m) {
-      const int q = 2 * (m * H + mx);
+      const int o = 2 * (m * H + mx);
       const double cs = tw[k], sn = tw[nt + k];
-      cr = fma(ps[q], cs, cr);
-      ci = fma(ps[q + 1], cs, ci);
-      dr = fma(pd[q], sn, dr);
-      di = fma(pd[q + 1], sn, di);
+      cr = fma(ps[o], cs, cr);
+      ci = fma(ps[o + 1], cs, ci);
+      dr = fma(pd[o], sn, dr);
+      di = fma(pd[o + 1], sn, di);
       k += py;
       if (k >= nt) k -= nt;
     }
@@ -244,8 +275,11 @@ __device__ void ad_inverse(const AdLayout& L, const double* tw, double* ps, doub
   __syncthreads();
   // rows (Hermitian in mx): u[px] = Re Y0 + 2 (A - B), u[nt - px] = Re Y0 + 2 (A + B),
   // A = sum_{mx>=1} Re Y cos(phi mx px), B = sum_{mx>=1} Im Y sin(phi mx px)
-  for (int t = tid; t < nt * H; t += T) {
-    const int iy = t / H, px = t - iy * H;
+  const int rows = nt * H;
+  for (int t = tid; t < L.PB * rows; t += T) {
+    const int q = t / rows, v = t - q * rows;
+    const double* cy = sm + L.base + q * L.per + L.cy;
+    const int iy = v / H, px = v - iy * H;
     const double* y = cy + 2 * iy * H;
     double a = 0.0, b = 0.0;
     int k = px;
@@ -255,8 +289,8 @@ __device__ void ad_inverse(const AdLayout& L, const double* tw, double* ps, doub
       k += px;
       if (k >= nt) k -= nt;
     }
-    out(iy * nt + px, fma(2.0, a - b, y[0]));
-    if (px > 0) out(iy * nt + nt - px, fma(2.0, a + b, y[0]));
+    out(q, iy * nt + px, fma(2.0, a - b, y[0]));
+    if (px > 0) out(q, iy * nt + nt - px, fma(2.0, a + b, y[0]));
   }
   __syncthreads();
 }
@@ -287,18 +321,19 @@ __device__ __forceinline__ void cmul(double ar, double ai, double br, double bi,
   i = fma(ar, bi, ai * br);
 }
 
-// U = 2 serves grids of more than 512 units (nt >= 45), at most 288 threads
-template <int STAGE, int U>
+// One block advances PB particles (PB > 1 fills the warps on small grids);
+// U = 2 serves grids of more than 512 units (nt = 45), at most 288 threads.
+template <int STAGE, int U, int PB>
 __global__ void __launch_bounds__(U == 1 ? 512 : 384, 1) k_adstage(const __grid_constant__ FilterDev fd,
-                                                    const EpochParams* __restrict__ ep) {
+                                                                   const EpochParams* __restrict__ ep) {
   extern __shared__ double s_dyn[];
   __shared__ double s_red[32];
-  __shared__ double s_th[kPMax];
+  __shared__ double s_th[PB][kPMax];
   __shared__ int s_flag;
   const Ctrl* ctrl = fd.ctrl;
   if (ctrl->status != PF_OK) return;
   const int S = ep->S;
-  const AdLayout L = ad_layout(fd.d, S, STAGE == 2);
+  const AdLayout L = ad_layout(fd.d, S, STAGE == 2, PB);
   double* sm = s_dyn;
   load_steps(reinterpret_cast<StepCoef*>(sm + L.sc), ep, S);  // ends with a barrier
   const StepCoef* sc = reinterpret_cast<const StepCoef*>(sm + L.sc);
@@ -306,63 +341,73 @@ __global__ void __launch_bounds__(U == 1 ? 512 : 384, 1) k_adstage(const __grid_
   const Ensemble src = committed(fd, cur);
   const Ensemble dst = pending(fd, cur);
   const int64_t N = fd.N;
-  const int64_t n = blockIdx.x;
+  const int64_t n0 = (int64_t)blockIdx.x * PB;  // the block's first particle
   const uint32_t epoch = ep->epoch;
   const int d = L.d, nt = L.nt, H = L.H, T = blockDim.x, tid = threadIdx.x, units = H * H;
   const double inv_d = 1.0 / (double)d;
-  int64_t l = n;
-  if (STAGE == 2) l = fd.idx[n];
-  if (tid == 0) {
-    double ph[5];
-    if (STAGE == 1) {
-      // Step 2: phibar^n = a phi^n + (1 - a) phibar
-      for (int i = 0; i < 5; ++i) ph[i] = fd.a * src.phi[i * N + n] + (1.0 - fd.a) * ctrl->phibar[i];
-    } else {
-      // Step 4a: phi_{j+1}^n = phibar^l + s L z
-      double z[6];
-      for (int b = 0; b < 3; ++b) {
-        const U4 w = draw_block(fd, kRngTheta, (uint32_t)n, epoch, (uint32_t)b);
-        normal_pair(w, z[2 * b], z[2 * b + 1]);
-      }
-      for (int i = 0; i < 5; ++i) {
-        double lz = 0.0;
-        for (int k = 0; k <= i; ++k) lz = fma(ctrl->L[i * kPMax + k], z[k], lz);
-        const double shr = fd.a * src.phi[i * N + l] + (1.0 - fd.a) * ctrl->phibar[i];
-        ph[i] = fma(fd.s, lz, shr);
-        dst.phi[i * N + n] = ph[i];
+  // particle q of the block is n0 + q, gathered from slot l (stage 2: the
+  // resampled parent); slots past N are idle and stay zero
+  auto slot_of = [&](int q) -> int64_t { return STAGE == 2 ? (int64_t)fd.idx[n0 + q] : n0 + q; };
+  if (tid < PB) {
+    const int q = tid;
+    const int64_t n = n0 + q;
+    double ph[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (n < N) {
+      const int64_t l = slot_of(q);
+      if (STAGE == 1) {
+        // Step 2: phibar^n = a phi^n + (1 - a) phibar
+        for (int i = 0; i < 5; ++i) ph[i] = fd.a * src.phi[i * N + n] + (1.0 - fd.a) * ctrl->phibar[i];
+      } else {
+        // Step 4a: phi_{j+1}^n = phibar^l + s L z
+        double z[6];
+        for (int b = 0; b < 3; ++b) {
+          const U4 w = draw_block(fd, kRngTheta, (uint32_t)n, epoch, (uint32_t)b);
+          normal_pair(w, z[2 * b], z[2 * b + 1]);
+        }
+        for (int i = 0; i < 5; ++i) {
+          double lz = 0.0;
+          for (int k = 0; k <= i; ++k) lz = fma(ctrl->L[i * kPMax + k], z[k], lz);
+          const double shr = fd.a * src.phi[i * N + l] + (1.0 - fd.a) * ctrl->phibar[i];
+          ph[i] = fma(fd.s, lz, shr);
+          dst.phi[i * N + n] = ph[i];
+        }
       }
     }
-    for (int i = 0; i < 5; ++i) s_th[i] = (fd.transform == PF_TRANSFORM_LOG) ? exp(ph[i]) : ph[i];
+    for (int i = 0; i < 5; ++i) s_th[q][i] = (fd.transform == PF_TRANSFORM_LOG) ? exp(ph[i]) : ph[i];
   }
   ad_tables(L, sm);
-  for (int i = tid; i < d; i += T) {
-    const int64_t o = (int64_t)i * N + l;
-    sm[L.X[0] + i] = src.x[o];
-    sm[L.X[1] + i] = src.h1[o];
-    sm[L.X[2] + i] = src.h2[o];
-    if (STAGE == 2) sm[L.ee + i] = 0.0;
+  for (int t = tid; t < PB * d; t += T) {
+    const int q = t / d, i = t - q * d;
+    double* R = sm + L.base + q * L.per;
+    double x0 = 0.0, x1 = 0.0, x2 = 0.0;
+    if (n0 + q < N) {
+      const int64_t o = (int64_t)i * N + slot_of(q);
+      x0 = src.x[o];
+      x1 = src.h1[o];
+      x2 = src.h2[o];
+    }
+    R[L.X[0] + i] = x0;
+    R[L.X[1] + i] = x1;
+    R[L.X[2] + i] = x2;
+    if (STAGE == 2) R[L.ee + i] = 0.0;
   }
   __syncthreads();
-  double th[5];
-  for (int i = 0; i < 5; ++i) th[i] = s_th[i];
-  const AdOp op = ad_op(th);
   const double* tw = sm + L.tw;
-  double* ps = sm + L.ps;
-  double* pd = sm + L.pd;
-  double* cy = sm + L.cy;
 
   // the history in the Fourier basis, each thread holding its own mode pairs
   Modes<U> x0, x1, x2;
-  ad_forward<U>(L, tw, sm + L.X[0], ps, pd, x0);
-  ad_forward<U>(L, tw, sm + L.X[1], ps, pd, x1);
-  ad_forward<U>(L, tw, sm + L.X[2], ps, pd, x2);
+  ad_forward<U>(L, tw, sm, 0, x0);
+  ad_forward<U>(L, tw, sm, 1, x1);
+  ad_forward<U>(L, tw, sm, 2, x2);
   double lr[U][2], li[U][2];
 #pragma unroll
   for (int j = 0; j < U; ++j) {
     const int t = tid + j * T;
-    const int p = t / H, mx = t - p * H;
     lr[j][0] = li[j][0] = lr[j][1] = li[j][1] = 0.0;
-    if (t < units) {
+    if (t < PB * units) {
+      const int q = t / units, v = t - q * units;
+      const int p = v / H, mx = v - p * H;
+      const AdOp op = ad_op(s_th[q]);
       ad_lambda(L, op, tw, p, mx, lr[j][0], li[j][0]);
       if (p > 0) ad_lambda(L, op, tw, nt - p, mx, lr[j][1], li[j][1]);
     }
@@ -426,13 +471,15 @@ __global__ void __launch_bounds__(U == 1 ? 512 : 384, 1) k_adstage(const __grid_
         x0.im[j][b] = yi;
       }
     if (STAGE == 2) {
-      double* EE = sm + L.ee;
-      ad_inverse<U>(L, tw, ps, pd, cy, e, [&](int i, double v) { EE[i] = fma(v, v, EE[i]); });
+      ad_inverse<U>(L, tw, sm, e, [&](int q, int i, double v) {
+        double* EE = sm + L.base + q * L.per + L.ee;
+        EE[i] = fma(v, v, EE[i]);
+      });
     }
   }
 
   // back to physical space (scaled by 1/d)
-  auto back = [&](Modes<U>& z, double* u) {
+  auto back = [&](Modes<U>& z, int k_state) {
 #pragma unroll
     for (int j = 0; j < U; ++j)
 #pragma unroll
@@ -440,14 +487,16 @@ __global__ void __launch_bounds__(U == 1 ? 512 : 384, 1) k_adstage(const __grid_
         z.re[j][b] *= inv_d;
         z.im[j][b] *= inv_d;
       }
-    ad_inverse<U>(L, tw, ps, pd, cy, z, [&](int i, double v) { u[i] = v; });
+    ad_inverse<U>(L, tw, sm, z, [&](int q, int i, double v) {
+      sm[L.base + q * L.per + L.X[k_state] + i] = v;
+    });
   };
-  double* X0 = sm + L.X[0];
-  back(x0, X0);
+  back(x0, 0);
   if (STAGE == 1) {
     double lg = -CUDART_INF;
-    if (tid == 0) {
-      const double ll = ad_loglik(fd, ep, X0);
+    if (tid < PB && n0 + tid < N) {
+      const int64_t n = n0 + tid;
+      const double ll = ad_loglik(fd, ep, sm + L.base + tid * L.per + L.X[0]);
       fd.ll1[n] = ll;
       lg = (src.lw[n] - ctrl->logW) + ll;
       if (!finite_bits(lg)) lg = -CUDART_INF;
@@ -455,33 +504,36 @@ __global__ void __launch_bounds__(U == 1 ? 512 : 384, 1) k_adstage(const __grid_
     }
     stage1_tail(fd, epoch, lg, (int)blockIdx.x, (int)gridDim.x, s_red, &s_flag);
   } else {
-    double* X1 = sm + L.X[1];
-    double* X2 = sm + L.X[2];
-    back(x1, X1);
-    back(x2, X2);
+    back(x1, 1);
+    back(x2, 2);
     // Steps 4c, 4d: innovation v = sqrt(kappa E) z', written in (x, h1, h2) order
-    const double* EE = sm + L.ee;
-    for (int b = tid; b < (d + 1) / 2; b += T) {
+    const int halves = (d + 1) / 2;
+    for (int t = tid; t < PB * halves; t += T) {
+      const int q = t / halves, b = t - q * halves;
+      const int64_t n = n0 + q;
+      if (n >= N) continue;
+      double* R = sm + L.base + q * L.per;
       const U4 w = draw_block(fd, kRngInnov, (uint32_t)n, epoch, (uint32_t)b);
       double z0, z1;
       normal_pair(w, z0, z1);
       for (int h = 0; h < 2; ++h) {
         const int i = 2 * b + h;
         if (i >= d) break;
-        const double v = sqrt(fd.kappa * EE[i]) * (h == 0 ? z0 : z1);
+        const double v = sqrt(fd.kappa * R[L.ee + i]) * (h == 0 ? z0 : z1);
         const int64_t o = (int64_t)i * N + n;
-        const double xv = X0[i] + v;
-        X0[i] = xv;
+        const double xv = R[L.X[0] + i] + v;
+        R[L.X[0] + i] = xv;
         dst.x[o] = xv;
-        dst.h1[o] = X1[i] + v;
-        dst.h2[o] = X2[i] + v;
+        dst.h1[o] = R[L.X[1] + i] + v;
+        dst.h2[o] = R[L.X[2] + i] + v;
       }
     }
     __syncthreads();
     double lwn = -CUDART_INF, bad = 0.0;
-    if (tid == 0) {
+    if (tid < PB && n0 + tid < N) {
       // Step 5: new log weight
-      lwn = ad_loglik(fd, ep, X0) - fd.ll1[l];
+      const int64_t n = n0 + tid;
+      lwn = ad_loglik(fd, ep, sm + L.base + tid * L.per + L.X[0]) - fd.ll1[slot_of(tid)];
       if (!finite_bits(lwn)) {
         lwn = -CUDART_INF;
         bad = 1.0;
@@ -492,50 +544,78 @@ __global__ void __launch_bounds__(U == 1 ? 512 : 384, 1) k_adstage(const __grid_
   }
 }
 
-// Launch shape for a grid side: units (mode pairs) per thread U (1 or 2:
-// fewer units per thread keep fewer registers, so more blocks fit an SM) and
-// threads per block, a multiple of 32 covering the H^2 units.
-static void ad_shape(int nt, int* threads, int* upt) {
+// Launch shape for a grid side and stage: particles per block PB and units
+// (mode pairs) per thread U, and threads per block, a multiple of 32
+// covering PB H^2 units.  PB (1, 2 or 4) wastes the fewest lanes in the unit
+// and row passes while the block keeps at least two blocks per SM resident
+// (stage 2 keeps more registers per thread: at most 288 threads); U = 2 only
+// where one particle's units exceed 512.
+static void ad_shape(int nt, int stage, int* threads, int* upt, int* pb) {
   const int H = (nt + 1) / 2, units = H * H;
+  const int cap = stage == 2 ? 288 : 512;
   int u = 1;
   while (u < kAdMaxUnitsPerThread && (units + u - 1) / u > 512) u *= 2;
-  const int need = (units + u - 1) / u;
+  int best_pb = 1, best_T = 0;
+  double best_eff = -1.0;
+  for (int p = 1; p <= 4; p *= 2) {
+    if (u > 1 && p > 1) break;
+    const int need = (p * units + u - 1) / u;
+    const int T = ((need > 64 ? need : 64) + 31) / 32 * 32;
+    if (p > 1 && T > cap) break;
+    // lane efficiency of the unit passes and of the row passes
+    const double e_units = (double)(p * units) / (double)(((p * units + T - 1) / T) * T);
+    const double e_rows = (double)(p * nt * H) / (double)(((p * nt * H + T - 1) / T) * T);
+    const double eff = 0.7 * e_units + 0.3 * e_rows;
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best_pb = p;
+      best_T = T;
+    }
+  }
   *upt = u;
-  *threads = ((need > 64 ? need : 64) + 31) / 32 * 32;
+  *pb = best_pb;
+  *threads = best_T;
 }
 
 int ad_threads(int nt) {
-  int T, u;
-  ad_shape(nt, &T, &u);
+  int T, u, pb;
+  ad_shape(nt, 2, &T, &u, &pb);
   return T;
 }
 
 size_t ad_stage_smem(int d, int S, int stage) {
-  return sizeof(double) * (size_t)ad_layout(d, S, stage == 2).total;
+  int T, u, pb;
+  ad_shape(ad_side(d), stage, &T, &u, &pb);
+  return sizeof(double) * (size_t)ad_layout(d, S, stage == 2, pb).total;
 }
 
 cudaError_t launch_ad_stage(int stage, const FilterDev& fd, const EpochParams* ep, int S,
                             cudaStream_t st) {
   const int nt = ad_side(fd.d);
   if (nt == 0) return cudaErrorInvalidValue;
-  const size_t smem = ad_stage_smem(fd.d, S, stage);
-  int T, upt;
-  ad_shape(nt, &T, &upt);
+  int T, upt, pb;
+  ad_shape(nt, stage, &T, &upt, &pb);
+  const size_t smem = sizeof(double) * (size_t)ad_layout(fd.d, S, stage == 2, pb).total;
   const int H = (nt + 1) / 2;
-  if (T * upt < H * H || T > (upt == 1 ? 512 : 384)) return cudaErrorInvalidValue;
+  if (T * upt < pb * H * H || T > (upt == 1 ? 512 : 384)) return cudaErrorInvalidValue;
   using K = void (*)(const FilterDev, const EpochParams*);
   K k;
-  if (upt == 1) k = stage == 1 ? k_adstage<1, 1> : k_adstage<2, 1>;
-  else k = stage == 1 ? k_adstage<1, 2> : k_adstage<2, 2>;
+  if (upt == 2) k = stage == 1 ? k_adstage<1, 2, 1> : k_adstage<2, 2, 1>;
+  else if (pb == 4) k = stage == 1 ? k_adstage<1, 1, 4> : k_adstage<2, 1, 4>;
+  else if (pb == 2) k = stage == 1 ? k_adstage<1, 1, 2> : k_adstage<2, 1, 2>;
+  else k = stage == 1 ? k_adstage<1, 1, 1> : k_adstage<2, 1, 1>;
   cudaError_t e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)fd.N, T, smem, st>>>(fd, ep);
+  const unsigned blocks = (unsigned)((fd.N + pb - 1) / pb);
+  k<<<blocks, T, smem, st>>>(fd, ep);
   return cudaGetLastError();
 }
 
 cudaError_t preload_ad_kernels() {
-  const void* ks[] = {(const void*)k_adstage<1, 1>, (const void*)k_adstage<2, 1>,
-                      (const void*)k_adstage<1, 2>, (const void*)k_adstage<2, 2>};
+  const void* ks[] = {(const void*)k_adstage<1, 1, 1>, (const void*)k_adstage<2, 1, 1>,
+                      (const void*)k_adstage<1, 1, 2>, (const void*)k_adstage<2, 1, 2>,
+                      (const void*)k_adstage<1, 1, 4>, (const void*)k_adstage<2, 1, 4>,
+                      (const void*)k_adstage<1, 2, 1>, (const void*)k_adstage<2, 2, 1>};
   for (const void* k : ks) {
     cudaFuncAttributes a;
     const cudaError_t e = cudaFuncGetAttributes(&a, k);
