@@ -127,6 +127,8 @@ STAGE2_KERNEL["michaelis"] = "k_stage2<Michaelis, 0>"
 # of the kernel as it stands exists.
 STAGE2_TRAFFIC = {"robertson": 11552512 + 0,
                   "brusselator": 11202826752 + 10732933888,
+                  "advdiff20": 3081472 + 670720,
+                  "advdiff40": 177671424 + 140111872,
                   "michaelisBDF2": 4353024 + 0,
                   "michaelisAM3": 4586752 + 0,
                   "michaelisAB3": 4459520 + 0}
