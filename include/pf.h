@@ -444,6 +444,22 @@ void pf_server_destroy(pf_server* s);
 pf_status pf_resample_systematic_noalloc(const double* log_g, int64_t N, double u,
                                          double* cumulative, int32_t* idx, void* stream);
 
+/* ---- the systematic search alone ------------------------------------------
+ * Algorithm 1, Step 3b: the parent index of each of the N resampled particles,
+ * idx_i = min{k : c_k > tau_i} with tau_i = ((i + u)/N) c_{N-1} (else the first
+ * k with c_k = c_{N-1}), for given cumulative weights c.  It is the filter's own
+ * search (the merge-path kernel pf_assimilate launches), so for the same c and
+ * u the indices are bit-identical to the filter's.  Runs on `stream` (NULL =
+ * the legacy default stream) without waiting, allocating nothing.
+ *
+ * cumulative: N doubles of device memory, read; must be non-decreasing and
+ * >= +0, as a cumulative sum of non-negative weights is (other input gives
+ * unspecified indices, each still in [0, N)).  idx: N int32 of device memory,
+ * written.  Both are owned by the caller.  Errors: INVALID_ARG (NULL buffer,
+ * N < 1 or N > 2^31 - 1, u outside [0, 1)), CUDA (launch). */
+pf_status pf_systematic_indices(const double* cumulative, int64_t N, double u, int32_t* idx,
+                                void* stream);
+
 /* Library version string. */
 const char* pf_version(void);
 

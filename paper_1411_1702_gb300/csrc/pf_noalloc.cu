@@ -15,9 +15,11 @@
 // cudaGetSymbolAddress while that device is current, and caches it.
 //
 // The kernels repeat the filter's cumulative-weight scan (same tiles, same
-// order of additions, same exact prefix-maximum fix-ups) and its systematic
-// search, so for the same log weights and u the results are bit-identical to
-// the cumulative weights and indices of pf_assimilate.
+// order of additions, same exact prefix-maximum fix-ups) and run its
+// systematic search, so for the same log weights and u the results are
+// bit-identical to the cumulative weights and indices of pf_assimilate.
+// pf_systematic_indices runs that search alone on given cumulative weights;
+// it needs no scratch at all.
 #include <mutex>
 
 #include "pf_filter.h"
@@ -141,11 +143,15 @@ __global__ void __launch_bounds__(256) k_na_scan_add(int64_t N, double* c, NaScr
   }
 }
 
-__global__ void __launch_bounds__(256) k_na_resample(const double* __restrict__ c, int64_t N,
-                                                   double u, int32_t* idx) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) idx[i] = systematic_index(c, N, i, u, __ldg(c + (N - 1)));
+// the filter's merge-path search (resample_tile), one block per diagonal tile
+__global__ void __launch_bounds__(kResampleThreads) k_na_resample(const double* __restrict__ c,
+                                                                  int64_t N, double u,
+                                                                  int32_t* __restrict__ idx) {
+  __shared__ RsShared sh;
+  resample_tile(c, N, u, idx, nullptr, blockIdx.x, sh);
 }
+
+static unsigned resample_blocks(int64_t N) { return (unsigned)((2 * N + kRsTile - 1) / kRsTile); }
 
 // device address of the scratch array, looked up once per device
 constexpr int kMaxDevices = 64;
@@ -209,12 +215,37 @@ extern "C" pf_status pf_resample_systematic_noalloc(const double* log_g, int64_t
     k_na_scan_tile<<<(unsigned)((N + kScanTile - 1) / kScanTile), kScanThreads, 0, st>>>(
         log_g, N, cumulative, sc);
     k_na_scan_add<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, cumulative, sc);
-    k_na_resample<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(cumulative, N, u, idx);
+    k_na_resample<<<resample_blocks(N), kResampleThreads, 0, st>>>(cumulative, N, u, idx);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {
     set_thread_error(std::string("pf_resample_systematic_noalloc: launch failed: ") +
                      cudaGetErrorString(e));
+    return PF_ERR_CUDA;
+  }
+  return PF_OK;
+}
+
+extern "C" pf_status pf_systematic_indices(const double* cumulative, int64_t N, double u,
+                                           int32_t* idx, void* stream) {
+  using namespace pfg;
+  if (!cumulative || !idx) {
+    set_thread_error("pf_systematic_indices: NULL buffer");
+    return PF_ERR_INVALID_ARG;
+  }
+  if (N < 1 || N > (int64_t)INT32_MAX) {
+    set_thread_error("pf_systematic_indices: need 1 <= N <= 2^31 - 1");
+    return PF_ERR_INVALID_ARG;
+  }
+  if (!(u >= 0.0 && u < 1.0)) {
+    set_thread_error("pf_systematic_indices: need 0 <= u < 1");
+    return PF_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_na_resample<<<resample_blocks(N), kResampleThreads, 0, st>>>(cumulative, N, u, idx);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_thread_error(std::string("pf_systematic_indices: launch failed: ") + cudaGetErrorString(e));
     return PF_ERR_CUDA;
   }
   return PF_OK;

@@ -1,5 +1,6 @@
-// pf_scan.cuh -- block scans and the systematic-resampling search shared by
-// the epoch kernels (pf_kernels.cu) and the stand-alone resampling call.
+// pf_scan.cuh -- block scans and the systematic-resampling searches shared by
+// the epoch kernels (pf_kernels.cu) and the stand-alone resampling calls
+// (pf_noalloc.cu).
 #pragma once
 #include "pf_common.cuh"
 
@@ -72,6 +73,185 @@ __device__ __forceinline__ int32_t systematic_index(const double* c, int64_t N, 
   int64_t k = upper_bound_bits(c, N, __double_as_longlong(tau));
   if (k == N) k = lower_bound_bits(c, N, __double_as_longlong(total));
   return (int32_t)k;
+}
+
+// ------------------------------------------------------ merge-path search
+// Systematic resampling (Step 3b): tau_i = ((i + u)/N) c_{N-1} with one
+// u per epoch; l_i = min{k : c_k > tau_i},
+// else the first k with c_k = c_{N-1}.
+//
+// Both tau and c are sorted, so l is read off their merge: merging with c_k
+// first on ties (c_k <= tau_i), tau_i is taken at the position where exactly
+// the c_k <= tau_i have gone before it, i.e. at k = l_i.  The merged sequence
+// (2N items) is cut into equal diagonal tiles (merge path): one warp per
+// diagonal finds the block's two corners, the block stages its c segment and
+// its tau estimates in shared memory with coalesced accesses, and each thread
+// walks kRsItems items from its own corner, found by a search in shared
+// memory.  Every block does the same work whatever the weights.
+//
+// FP64 instructions are scarce on this chip (two lanes a clock per SM), so
+// the search compares bit patterns: for non-negative doubles their order as
+// integers is their numeric order.  Each test tau_i < c_k is first decided
+// from the estimate (i + u) * (c_{N-1} / N): the estimate and tau_i each lie
+// within two roundings of the real (i + u) c_{N-1} / N, so for a normal
+// estimate they are under 4 ulps apart and their bit patterns at most 10;
+// a c_k more than kRsUlps patterns away lies on the same side of both, and
+// only closer calls (or tiny estimates) compute tau_i itself.  The one FP64
+// operation per output is the estimate's multiply.
+constexpr int kResampleThreads = 256;
+constexpr int kRsItems = 4;
+constexpr int kRsTile = kResampleThreads * kRsItems;
+constexpr long long kRsUlps = 64;
+constexpr long long kRsTiny = 0x0170000000000000LL;  // bit pattern of 2^-1000
+
+struct RsTau {
+  double u, total, step;  // step = total / N, rounded
+  int64_t N;
+};
+
+struct RsShared {
+  long long c[kRsTile];  // the tile's c segment, as bit patterns
+  long long t[kRsTile];  // the tile's tau estimates, as bit patterns
+  RsTau tau;
+  int64_t corner[2];
+  unsigned fresh;
+};
+
+__device__ __forceinline__ double rs_tau(int64_t i, const RsTau& t) {
+  return ((double)i + t.u) / (double)t.N * t.total;
+}
+
+__device__ __forceinline__ long long rs_estimate(int64_t i, const RsTau& t) {
+  return __double_as_longlong(__dmul_rn((double)i + t.u, t.step));
+}
+
+// tau_i < c, exactly, given e = rs_estimate(i); e and c are bit patterns
+__device__ __forceinline__ bool rs_before(int64_t i, long long e, long long c, const RsTau& t) {
+  if (e >= kRsTiny) {
+    if (c - e > kRsUlps) return true;
+    if (e - c > kRsUlps) return false;
+  }
+  return __double_as_longlong(rs_tau(i, t)) < c;
+}
+
+// Taus among the first dg items of the merge: the largest a with
+// tau_{a-1} < c_{dg-a} (or dg - a = N).  One full warp; each round spreads 32
+// probes over (lo, hi], and the first failing probe bounds the next range.
+__device__ __forceinline__ int64_t rs_corner(const double* c, int64_t dg, const RsTau& t) {
+  const int lane = threadIdx.x & 31;
+  const int64_t N = t.N;
+  int64_t lo = dg > N ? dg - N : 0, hi = dg < N ? dg : N;
+  while (lo < hi) {
+    const int64_t span = hi - lo;
+    const int64_t a = lo + (span * (lane + 1) + 31) / 32;  // in (lo, hi]
+    const int64_t b = dg - a;
+    const bool ok = b >= N || rs_before(a - 1, rs_estimate(a - 1, t),
+                                        __double_as_longlong(__ldg(c + b)), t);
+    const unsigned fail = __ballot_sync(0xffffffffu, !ok);
+    const int k = fail ? __ffs(fail) - 1 : 32;  // probes 0 .. k-1 hold
+    const int64_t nlo = lo + (span * k + 31) / 32;
+    if (k < 32) hi = lo + (span * (k + 1) + 31) / 32 - 1;
+    lo = nlo;
+  }
+  return lo;
+}
+
+// One block's tile of the merge (blockDim.x == kResampleThreads): writes
+// idx over the tile's taus and, if n_unique is not null, adds the number of
+// outputs whose index differs from the previous output's (the distinct
+// parents) to it.
+__device__ __forceinline__ void resample_tile(const double* __restrict__ c, int64_t N, double u,
+                                              int32_t* __restrict__ idx,
+                                              unsigned long long* n_unique, int vb, RsShared& sh) {
+  // the block's tile of the merge: items [d0, d1), taus [a0, a1), c [b0, b1)
+  const int64_t d0 = (int64_t)vb * kRsTile;
+  const int64_t d1 = d0 + kRsTile < 2 * N ? d0 + kRsTile : 2 * N;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (wid < 2) {
+    RsTau t;
+    t.u = u;
+    t.total = __ldg(c + (N - 1));
+    t.N = N;
+    t.step = t.total / (double)N;
+    const int64_t a = rs_corner(c, wid == 0 ? d0 : d1, t);
+    if (lane == 0) {
+      sh.corner[wid] = a;
+      if (wid == 0) {
+        sh.tau = t;
+        sh.fresh = 0u;
+      }
+    }
+  }
+  __syncthreads();
+  const RsTau t = sh.tau;
+  const int64_t a0 = sh.corner[0], a1 = sh.corner[1];
+  const int64_t b0 = d0 - a0, b1 = d1 - a1;
+  for (int64_t k = b0 + threadIdx.x; k < b1; k += blockDim.x)
+    sh.c[k - b0] = __double_as_longlong(__ldg(c + k));
+  for (int64_t k = a0 + threadIdx.x; k < a1; k += blockDim.x) sh.t[k - a0] = rs_estimate(k, t);
+  __syncthreads();
+  // this thread's corner: a merge-path search in shared memory
+  const int64_t ds = d0 + (int64_t)threadIdx.x * kRsItems;
+  const int64_t de = ds + kRsItems < d1 ? ds + kRsItems : d1;
+  unsigned fresh = 0u;
+  if (ds < d1) {
+    const int64_t dl = ds - d0, na = a1 - a0, nb = b1 - b0;
+    int64_t lo = dl > nb ? dl - nb : 0, hi = dl < na ? dl : na;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      const int64_t bl = dl - mid;
+      if (bl >= nb || rs_before(a0 + mid - 1, sh.t[mid - 1], sh.c[bl], t)) lo = mid;
+      else hi = mid - 1;
+    }
+    int64_t a = a0 + lo, b = b0 + (dl - lo);
+    // the previous output's index, for the count of distinct parents: if
+    // the item just before this corner is tau_{a-1}, it was taken at b
+    // (l = b), if it is c_{b-1}, l_{a-1} < b
+    bool prev_tau_at_b = false;
+    if (a > 0) {
+      if (b == 0) {
+        prev_tau_at_b = true;
+      } else {
+        const long long cp = b - 1 >= b0 ? sh.c[b - 1 - b0] : __double_as_longlong(__ldg(c + (b - 1)));
+        const long long tp = a - 1 >= a0 ? sh.t[a - 1 - a0] : rs_estimate(a - 1, t);
+        prev_tau_at_b = !rs_before(a - 1, tp, cp, t);
+      }
+    }
+    int64_t prev_l = -2;  // unknown until this thread's first output
+    int64_t fallback = -1;
+    for (int64_t dd = ds; dd < de; ++dd) {
+      if (a < a1 && (b >= b1 || rs_before(a, sh.t[a - a0], sh.c[b - b0], t))) {
+        // tau_a goes before c_b: l_a = b
+        int64_t l = b;
+        if (b >= N) {
+          if (fallback < 0) fallback = lower_bound_bits(c, N, __double_as_longlong(t.total));
+          l = fallback;
+        }
+        idx[a] = (int32_t)l;
+        bool is_new;
+        if (prev_l != -2) {
+          is_new = l != prev_l;
+        } else if (a == 0) {
+          is_new = true;
+        } else if (b < N) {
+          is_new = !prev_tau_at_b;
+        } else {
+          // past the last c (tau rounded up to the total): compare directly
+          is_new = l != systematic_index(c, N, a - 1, t.u, t.total);
+        }
+        fresh += is_new ? 1u : 0u;
+        prev_l = l;
+        ++a;
+      } else {
+        ++b;
+        prev_tau_at_b = false;  // a c_k goes between the previous output and the next
+      }
+    }
+  }
+  fresh = __reduce_add_sync(0xffffffffu, fresh);
+  if (lane == 0 && fresh) atomicAdd(&sh.fresh, fresh);
+  __syncthreads();
+  if (threadIdx.x == 0 && sh.fresh && n_unique) atomicAdd(n_unique, (unsigned long long)sh.fresh);
 }
 
 }  // namespace pfg

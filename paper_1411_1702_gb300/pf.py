@@ -34,6 +34,7 @@ ABI_SYMBOLS = [
     "pf_load_observations", "pf_run", "pf_synchronize", "pf_reset", "pf_get_ensemble",
     "pf_set_ensemble", "pf_set_moments", "pf_get_work", "pf_get_history", "pf_set_history",
     "pf_substep_table", "pf_version", "pf_kernel_times", "pf_resample_systematic_noalloc",
+    "pf_systematic_indices",
     "pf_batch_create", "pf_batch_assimilate", "pf_batch_stats", "pf_batch_last_error",
     "pf_batch_destroy", "pf_server_create", "pf_server_open", "pf_server_submit",
     "pf_server_step", "pf_server_drain", "pf_server_close", "pf_server_session",
@@ -134,6 +135,8 @@ def load(path: str = LIB_PATH):
         "pf_kernel_times": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), C.c_int]),
         "pf_resample_systematic_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
                                                      C.c_void_p, C.c_void_p]),
+        "pf_systematic_indices": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
+                                            C.c_void_p]),
         "pf_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
         "pf_batch_assimilate": (C.c_int, [C.c_void_p, _dp, C.POINTER(_dp), C.POINTER(C.c_int)]),
         "pf_batch_stats": (C.c_int, [C.c_void_p, C.POINTER(BatchStats)]),
@@ -185,6 +188,14 @@ def pf_resample_systematic_noalloc(log_g_ptr, N, u, cumulative_ptr, idx_ptr, str
     st = load().pf_resample_systematic_noalloc(C.c_void_p(log_g_ptr), int(N), float(u),
                                                C.c_void_p(cumulative_ptr), C.c_void_p(idx_ptr),
                                                C.c_void_p(stream) if stream else None)
+    _check(st, None)
+
+
+def pf_systematic_indices(cumulative_ptr, N, u, idx_ptr, stream=None):
+    """Step 3b's systematic search alone on caller-owned device buffers (raw
+    device addresses): the filter's own kernel; asynchronous on `stream`."""
+    st = load().pf_systematic_indices(C.c_void_p(cumulative_ptr), int(N), float(u),
+                                      C.c_void_p(idx_ptr), C.c_void_p(stream) if stream else None)
     _check(st, None)
 
 

@@ -74,6 +74,20 @@ def test_invalid_arguments_rejected_before_gpu(pf, bad):
     assert ei.value.status == pf.PF_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("bad", [
+    dict(c=0), dict(idx=0), dict(N=0), dict(N=-3), dict(N=1 << 31), dict(u=1.0), dict(u=-0.5),
+    dict(u=float("nan")),
+])
+def test_systematic_indices_rejects_arguments_before_gpu(pf, bad):
+    # the checks come before any launch, so the (never dereferenced) buffer
+    # addresses may be placeholders
+    a = dict(c=0x1000, N=16, u=0.5, idx=0x2000)
+    a.update(bad)
+    with pytest.raises(pf.PfError) as ei:
+        pf.pf_systematic_indices(a["c"], a["N"], a["u"], a["idx"])
+    assert ei.value.status == pf.PF_ERR_INVALID_ARG
+
+
 def _compare_tables(w, t_prev, t_next, depth, h1, h2, pf):
     cfg = oracle.make_config(w)
     tab, S, dout = oracle.build_substeps(cfg, t_prev, t_next, depth, h1, h2)
