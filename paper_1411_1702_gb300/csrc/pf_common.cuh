@@ -22,9 +22,9 @@ constexpr int kDMax = 64;            // largest state kept in registers (small m
 constexpr int kPMax = 5;
 constexpr int kMMax = PF_MAX_OBS;
 constexpr int kSMax = PF_MAX_SUBSTEPS;
-constexpr int kScanItems = 4;        // elements per thread in the scan
+constexpr int kScanItemsMax = 4;     // elements per thread in the scan, at most
 constexpr int kScanThreads = 256;
-constexpr int kScanTile = kScanItems * kScanThreads;
+constexpr int kScanTargetTiles = 608;  // tiles that fill 4 blocks on each of 152 SMs
 constexpr int kMomentBlocks = 304;   // 2 per SM on a 152-SM GB300
 constexpr int kMomentThreads = 256;
 

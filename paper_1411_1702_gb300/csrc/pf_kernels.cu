@@ -257,73 +257,21 @@ __device__ __forceinline__ void stage1_body(const FilterDev& fd, const EpochPara
 }
 
 // ------------------------------------------------------------------- scan
-// g_k = exp(lg_k - max lg) and its cumulative sums c_k (Step 3a, 3b).  Each
-// thread sums kScanItems consecutive g sequentially, threads are combined by a
-// block scan and tiles by the tile offsets of the last block.  A parallel FP64
-// scan may dip by an ulp where partial sums meet, so two exact prefix-maximum
-// passes (thread level and tile level) make c non-decreasing; the maximum is
-// exact and associative, so c is still a deterministic function of g for a
-// given N.
+// Step 3a/3b's cumulative weights: scan_tile_core and scan_add_core
+// (pf_scan.cuh) on the filter's buffers; the shift M is lg_max.
+__device__ __forceinline__ ScanArgs scan_args(const FilterDev& fd) {
+  Ctrl* ctrl = fd.ctrl;
+  return ScanArgs{fd.lg, fd.N, ctrl->lg_max, fd.c, fd.blk, fd.boff, fd.pmax, fd.ticket + 1,
+                  &ctrl->c_total};
+}
+
 __device__ __forceinline__ void scan_tile_body(const FilterDev& fd, int vb, int vg, double* s_warp,
                                                int* s_flag) {
-  Ctrl* ctrl = fd.ctrl;
-  const double M = ctrl->lg_max;
-  const int64_t N = fd.N;
-  const int64_t base = (int64_t)vb * kScanTile + (int64_t)threadIdx.x * kScanItems;
-  double v[kScanItems];
-  double run = 0.0;
-#pragma unroll
-  for (int j = 0; j < kScanItems; ++j) {
-    const int64_t k = base + j;
-    const double g = (k < N) ? exp(fd.lg[k] - M) : 0.0;
-    run += g;
-    v[j] = run;
-  }
-  double total;
-  const double excl = block_exclusive_scan<SumOp>(run, s_warp, total);
-#pragma unroll
-  for (int j = 0; j < kScanItems; ++j) v[j] = excl + v[j];
-  double tile_last;
-  const double floor_prev = block_exclusive_scan<MaxOp>(v[kScanItems - 1], s_warp, tile_last);
-#pragma unroll
-  for (int j = 0; j < kScanItems; ++j) {
-    const int64_t k = base + j;
-    if (k < N) fd.c[k] = fmax(v[j], floor_prev);
-  }
-  if (threadIdx.x == 0) fd.blk[vb] = tile_last;
-  if (elect_last_block(fd.ticket + 1, s_flag, (unsigned)vg)) {
-    // tile offsets boff_b = sum of earlier tile totals, and the running maximum
-    // pmax_b of the earlier tiles' last values boff_b' + T_b'
-    const int nb = vg;
-    const int chunk = (nb + blockDim.x - 1) / blockDim.x;
-    const int b0 = threadIdx.x * chunk;
-    double acc = 0.0;
-    for (int b = b0; b < b0 + chunk && b < nb; ++b) acc += __ldcg(fd.blk + b);
-    double grand;
-    double off = block_exclusive_scan<SumOp>(acc, s_warp, grand);
-    double lmax = 0.0;
-    for (int b = b0; b < b0 + chunk && b < nb; ++b) {
-      fd.boff[b] = off;
-      const double T = __ldcg(fd.blk + b);
-      lmax = fmax(lmax, off + T);
-      off += T;
-    }
-    double gmax;
-    double pm = block_exclusive_scan<MaxOp>(lmax, s_warp, gmax);
-    for (int b = b0; b < b0 + chunk && b < nb; ++b) {
-      fd.pmax[b] = pm;
-      pm = fmax(pm, fd.boff[b] + __ldcg(fd.blk + b));
-    }
-    if (threadIdx.x == 0) ctrl->c_total = gmax;
-  }
+  scan_tile_core(scan_args(fd), vb, vg, s_warp, s_flag);
 }
 
 __device__ __forceinline__ void scan_add_body(const FilterDev& fd, int vb) {
-  const int64_t k = (int64_t)vb * blockDim.x + threadIdx.x;
-  if (k < fd.N) {
-    const int64_t b = k / kScanTile;
-    fd.c[k] = fmax(fd.boff[b] + fd.c[k], fd.pmax[b]);
-  }
+  scan_add_core(scan_args(fd), (int64_t)vb * blockDim.x + threadIdx.x);
 }
 
 // --------------------------------------------------------------- resample
@@ -431,17 +379,57 @@ struct MomentLayout {
                        kN = kSx + D;
 };
 
-// Sum each of NV per-thread values over the block with one barrier round:
-// warp shuffles, then one row per warp in shared memory summed by NV threads.
-// out[k] (shared or global) receives the totals; s_part needs 8 * NV doubles.
+// Warp sums of a vector of N values by reduce-scatter.  A butterfly per value
+// costs 5 N FP64 adds a lane; here each exchange halves the vector instead (a
+// lane keeps one half and adds the partner's copy of it), so the adds are
+// about N + 5 a lane, which matters where FP64 instructions are scarce.  On
+// the last exchange each lane holds the warp totals of positions [lo, lo + N)
+// of the original vector, of which the first cnt are real (the rest padding);
+// lanes that are copies of a partner (the vector had one value left) write
+// nothing.  The order of additions depends only on the lane layout.
+template <int N, int O>
+struct WarpScatter {
+  __device__ __forceinline__ static void run(const double (&v)[N], int lane, int lo, int cnt, bool dup,
+                                             double* out) {
+    if constexpr (O == 0) {
+      if (!dup) {
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if (k < cnt) out[lo + k] = v[k];
+      }
+    } else if constexpr (N == 1) {
+      const double a[1] = {v[0] + __shfl_xor_sync(0xffffffffu, v[0], O)};
+      WarpScatter<1, O / 2>::run(a, lane, lo, cnt, dup || (lane & O) != 0, out);
+    } else {
+      constexpr int H = (N + 1) / 2;
+      const bool up = (lane & O) != 0;
+      double a[H];
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        const double lv = v[k];
+        const double hv = (H + k < N) ? v[H + k] : 0.0;
+        a[k] = (up ? hv : lv) + __shfl_xor_sync(0xffffffffu, up ? lv : hv, O);
+      }
+      // lower lanes keep positions [0, H), upper lanes [H, 2H)
+      const int ncnt = up ? (cnt > H ? cnt - H : 0) : (cnt < H ? cnt : H);
+      WarpScatter<H, O / 2>::run(a, lane, up ? lo + H : lo, ncnt, dup, out);
+    }
+  }
+};
+
+// shared scratch of the moment kernels: 8 warp rows of NV values, or the
+// group sums of the last block (at most kMomentThreads values)
+template <int NV>
+constexpr int kMomentShared = (kMomentThreads / 32) * NV > kMomentThreads ? (kMomentThreads / 32) * NV
+                                                                         : kMomentThreads;
+
+// Sum each of NV per-thread values over the block: warp reduce-scatter into
+// one row per warp in shared memory, then NV threads add the rows.  out[k]
+// (shared or global) receives the totals; s_part needs 8 * NV doubles.
 template <int NV>
 __device__ __forceinline__ void block_sum_vec(double (&acc)[NV], double* s_part, double* out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    const double v = warp_sum(acc[k]);
-    if (lane == 0) s_part[wid * NV + k] = v;
-  }
+  WarpScatter<NV, 16>::run(acc, lane, 0, NV, false, s_part + wid * NV);
   __syncthreads();
   for (int k = threadIdx.x; k < NV; k += blockDim.x) {
     double t = 0.0;
@@ -494,52 +482,113 @@ __device__ __forceinline__ void moments_body(const FilterDev& fd, int is_init, i
   }
   block_sum_vec<NV>(acc, s_part, fd.part + (int64_t)vb * fd.nrec);
   if (!elect_last_block(fd.ticket + 3, s_flag, (unsigned)vg)) return;
+  // the vg partial records: thread (j, k) adds value k of records j, j + G,
+  // ... (G groups of NV threads; loads issued eight at a time), then NV
+  // threads add the G group sums
+  const int G = (int)blockDim.x / NV;
+  if ((int)threadIdx.x < G * NV) {
+    const int k = threadIdx.x % NV, j = threadIdx.x / NV;
+    double t = 0.0;
+    for (int b0 = j; b0 < vg; b0 += 8 * G) {
+      double x[8];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < vg; b += blockDim.x) {
+      for (int q = 0; q < 8; ++q) {
+        const int b = b0 + q * G;
+        x[q] = b < vg ? __ldcg(fd.part + (int64_t)b * fd.nrec + k) : 0.0;
+      }
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(fd.part + (int64_t)b * fd.nrec + k);
-  }
-  block_sum_vec<NV>(acc, s_part, s_tot);
-  if (threadIdx.x != 0) return;
-  const double S0 = s_tot[Lay::kS0];
-  // moments about the shift c (the previous mean): the first moment of the
-  // differences gives the mean's displacement to full relative precision, so
-  // C = E[(phi - c)(phi - c)^T] - m m^T loses only eps E[|phi - c|^2]
-  double mean[P], m1[P], C[kPMax * kPMax], L[kPMax * kPMax];
-  for (int i = 0; i < kPMax * kPMax; ++i) C[i] = 0.0;
-  bool ok = S0 > 0.0;
-  for (int i = 0; i < P; ++i) {
-    m1[i] = s_tot[Lay::kS1 + i] / S0;
-    mean[i] = c[i] + m1[i];
-    ok = ok && finite_bits(mean[i]);
-  }
-  int q = Lay::kS2;
-  for (int i = 0; i < P; ++i) {
-    for (int j = i; j < P; ++j) {
-      const double v = s_tot[q++] / S0 - m1[i] * m1[j];
-      C[i * kPMax + j] = v;
-      C[j * kPMax + i] = v;
-      ok = ok && finite_bits(v);
+      for (int q = 0; q < 8; ++q) t += x[q];
     }
+    s_part[j * NV + k] = t;
   }
-  if (!ok) {
-    ctrl->status = PF_ERR_NUMERIC;
-    ctrl->failed_epoch = ctrl->epochs_done;
+  __syncthreads();
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    double t = 0.0;
+    for (int j = 0; j < G; ++j) t += s_part[j * NV + k];
+    s_tot[k] = t;
+  }
+  __syncthreads();
+  // The commit.  Moments about the shift c (the previous mean): the first
+  // moment of the differences gives the mean's displacement to full relative
+  // precision, so C = E[(phi - c)(phi - c)^T] - m m^T loses only
+  // eps E[|phi - c|^2].  Warp 0 forms the mean and C a lane per entry and
+  // checks them; then, at once, warp 0 factors C (a lane per row), warp 1
+  // stores the weight statistics and warp 2 the state mean.
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double S0 = s_tot[Lay::kS0];
+  double* s_m1 = s_part;                // P values
+  double* s_C = s_part + kPMax;         // kPMax^2 values
+  double* s_L = s_C + kPMax * kPMax;    // kPMax^2 values
+  constexpr int NC = P * (P + 1) / 2;
+  if (wid == 0) {
+    const double inv = 1.0 / S0;
+    bool bad = !(S0 > 0.0);
+    if (lane < kPMax * kPMax) {
+      s_C[lane] = 0.0;
+      s_L[lane] = 0.0;
+    }
+    if (lane < P) {
+      const double m1 = s_tot[Lay::kS1 + lane] * inv;
+      s_m1[lane] = m1;
+      bad = bad || !finite_bits(ctrl->phibar[lane] + m1);
+    }
+    __syncwarp();
+    if (lane < NC) {
+      int i = 0, r = lane;
+      while (r >= P - i) {
+        r -= P - i;
+        ++i;
+      }
+      const int j = i + r;
+      const double v = s_tot[Lay::kS2 + lane] * inv - s_m1[i] * s_m1[j];
+      s_C[i * kPMax + j] = v;
+      s_C[j * kPMax + i] = v;
+      bad = bad || !finite_bits(v);
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) *s_flag = bad ? 1 : 0;
+  }
+  __syncthreads();
+  if (*s_flag) {
+    if (threadIdx.x == 0) {
+      ctrl->status = PF_ERR_NUMERIC;
+      ctrl->failed_epoch = ctrl->epochs_done;
+    }
     return;
   }
-  cholesky_psd(P, C, L);
-  for (int i = 0; i < P; ++i) ctrl->phibar[i] = mean[i];
-  for (int i = 0; i < kPMax * kPMax; ++i) {
-    ctrl->C[i] = C[i];
-    ctrl->L[i] = L[i];
+  if (wid == 0) {
+    // Cholesky by columns; a pivot that is not positive leaves its column zero
+    for (int j = 0; j < P; ++j) {
+      double dsum = s_C[j * kPMax + j];
+      for (int k = 0; k < j; ++k) dsum -= s_L[j * kPMax + k] * s_L[j * kPMax + k];
+      if (dsum > 0.0) {
+        const double ljj = sqrt(dsum);
+        if (lane == j) s_L[j * kPMax + j] = ljj;
+        if (lane > j && lane < P) {
+          double sv = s_C[lane * kPMax + j];
+          for (int k = 0; k < j; ++k) sv -= s_L[lane * kPMax + k] * s_L[j * kPMax + k];
+          s_L[lane * kPMax + j] = sv / ljj;
+        }
+      }
+      __syncwarp();
+    }
+    if (lane < kPMax * kPMax) {
+      ctrl->C[lane] = s_C[lane];
+      ctrl->L[lane] = s_L[lane];
+    }
+    if (lane < P) ctrl->phibar[lane] += s_m1[lane];
+  } else if (wid == 1) {
+    if (lane == 0) {
+      ctrl->wsum = S0;
+      ctrl->ess = S0 * S0 / s_tot[Lay::kW2];
+      ctrl->logW = M + log(S0);
+      ctrl->cur = 1 - cur;
+      if (!is_init) ctrl->epochs_done += 1;
+    }
+  } else if (wid == 2) {
+    const double inv = 1.0 / S0;
+    for (int i = lane; i < D; i += 32) fd.xbar[i] = s_tot[Lay::kSx + i] * inv;
   }
-  for (int i = 0; i < D; ++i) fd.xbar[i] = s_tot[Lay::kSx + i] / S0;
-  ctrl->wsum = S0;
-  ctrl->ess = S0 * S0 / s_tot[Lay::kW2];
-  ctrl->logW = M + log(S0);
-  ctrl->cur = 1 - cur;
-  if (!is_init) ctrl->epochs_done += 1;
 }
 
 // ========================================================= single filter
@@ -595,7 +644,7 @@ template <int D, int P>
 __global__ void __launch_bounds__(kMomentThreads) k_moments(const __grid_constant__ FilterDev fd,
                                                             int is_init) {
   constexpr int NV = MomentLayout<D, P>::kN;
-  __shared__ double s_part[(kMomentThreads / 32) * NV];
+  __shared__ double s_part[kMomentShared<NV>];
   __shared__ double s_tot[NV];
   __shared__ int s_flag;
   if (fd.ctrl->status != PF_OK) return;
@@ -703,7 +752,7 @@ __global__ void __launch_bounds__(kScanThreads) k_batch_scan_tile(const FilterDe
   const BatchTile t = tiles[blockIdx.x];
   const FilterDev& fd = *(fds + t.f);
   if (fd.ctrl->status != PF_OK) return;
-  scan_tile_body(fd, t.vb, (int)((fd.N + kScanTile - 1) / kScanTile), s_warp, &s_flag);
+  scan_tile_body(fd, t.vb, scan_tile_count(fd.N), s_warp, &s_flag);
 }
 
 __global__ void __launch_bounds__(256) k_batch_scan_add(const FilterDev* __restrict__ fds,
@@ -729,7 +778,7 @@ __global__ void __launch_bounds__(kMomentThreads) k_batch_moments(const FilterDe
                                                                 const BatchTile* __restrict__ tiles,
                                                                 int is_init) {
   constexpr int NV = MomentLayout<D, P>::kN;
-  __shared__ double s_part[(kMomentThreads / 32) * NV];
+  __shared__ double s_part[kMomentShared<NV>];
   __shared__ double s_tot[NV];
   __shared__ int s_flag;
   const BatchTile t = tiles[blockIdx.x];
@@ -759,14 +808,14 @@ int moment_record_size(int ode) {
 
 int max_grid_blocks(int64_t N) {
   const int64_t a = N;  // at least as many as any stage launch (one block per particle for M2)
-  const int64_t b = (N + kScanTile - 1) / kScanTile;
+  const int64_t b = scan_tile_count(N);
   const int64_t c = (2 * N + kRsTile - 1) / kRsTile;
   int64_t m = a > b ? a : b;
   m = m > c ? m : c;
   return (int)(m > kMomentBlocks ? m : kMomentBlocks);
 }
 
-int scan_tiles(int64_t N) { return (int)((N + kScanTile - 1) / kScanTile); }
+int scan_tiles(int64_t N) { return scan_tile_count(N); }
 
 int phase_blocks(int phase, int ode, int64_t N) {
   switch (phase) {

@@ -28,7 +28,11 @@
 namespace pfg {
 
 constexpr int64_t kNaMaxParticles = PF_NOALLOC_MAX_PARTICLES;
-constexpr int kNaMaxTiles = (int)((kNaMaxParticles + kScanTile - 1) / kScanTile);
+// the most scan tiles of any N up to the maximum (scan_tile_count)
+constexpr int kNaMaxTiles =
+    kNaMaxParticles / (kScanThreads * kScanItemsMax) > kScanTargetTiles
+        ? (int)((kNaMaxParticles + kScanThreads * kScanItemsMax - 1) / (kScanThreads * kScanItemsMax))
+        : kScanTargetTiles;
 constexpr int kNaMaxBlocks = 304;  // blocks of the maximum reduction
 constexpr int kNaThreads = 256;
 // byte layout of the scratch array
@@ -60,12 +64,6 @@ static NaScratch carve(unsigned char* base) {
                    reinterpret_cast<double*>(base + kNaPmaxOff)};
 }
 
-// Only -inf and finite log weights are meaningful; anything else counts as a
-// zero weight (for valid inputs this is the identity).
-__device__ __forceinline__ double clean_logw(double v) {
-  return finite_bits(v) ? v : -CUDART_INF;
-}
-
 __global__ void __launch_bounds__(kNaThreads) k_na_max(const double* __restrict__ lg, int64_t N,
                                                      NaScratch sc) {
   __shared__ double s_red[32];
@@ -73,7 +71,7 @@ __global__ void __launch_bounds__(kNaThreads) k_na_max(const double* __restrict_
   double m = -CUDART_INF;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x)
-    m = fmax(m, clean_logw(lg[k]));
+    if (finite_bits(lg[k])) m = fmax(m, lg[k]);
   m = block_max(m, s_red);
   if (threadIdx.x == 0) sc.blockmax[blockIdx.x] = m;
   if (elect_last_block(sc.ticket + 0, &s_flag, gridDim.x)) {
@@ -84,63 +82,21 @@ __global__ void __launch_bounds__(kNaThreads) k_na_max(const double* __restrict_
   }
 }
 
+// the filter's scan (scan_tile_core, scan_add_core) on the caller's buffers
+__device__ __forceinline__ ScanArgs na_scan_args(const double* lg, int64_t N, double* c,
+                                                 const NaScratch& sc) {
+  return ScanArgs{lg, N, __ldcg(sc.head), c, sc.tile, sc.boff, sc.pmax, sc.ticket + 1, nullptr};
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_na_scan_tile(const double* __restrict__ lg,
                                                              int64_t N, double* c, NaScratch sc) {
   __shared__ double s_warp[33];
   __shared__ int s_flag;
-  const double M = __ldcg(sc.head);
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-  double v[kScanItems];
-  double run = 0.0;
-#pragma unroll
-  for (int j = 0; j < kScanItems; ++j) {
-    const int64_t k = base + j;
-    const double g = (k < N) ? exp(clean_logw(lg[k]) - M) : 0.0;
-    run += g;
-    v[j] = run;
-  }
-  double total;
-  const double excl = block_exclusive_scan<SumOp>(run, s_warp, total);
-#pragma unroll
-  for (int j = 0; j < kScanItems; ++j) v[j] = excl + v[j];
-  double tile_last;
-  const double floor_prev = block_exclusive_scan<MaxOp>(v[kScanItems - 1], s_warp, tile_last);
-#pragma unroll
-  for (int j = 0; j < kScanItems; ++j) {
-    const int64_t k = base + j;
-    if (k < N) c[k] = fmax(v[j], floor_prev);
-  }
-  if (threadIdx.x == 0) sc.tile[blockIdx.x] = tile_last;
-  if (elect_last_block(sc.ticket + 1, &s_flag, gridDim.x)) {
-    const int nb = gridDim.x;
-    const int chunk = (nb + blockDim.x - 1) / blockDim.x;
-    const int b0 = threadIdx.x * chunk;
-    double acc = 0.0;
-    for (int b = b0; b < b0 + chunk && b < nb; ++b) acc += __ldcg(sc.tile + b);
-    double grand;
-    double off = block_exclusive_scan<SumOp>(acc, s_warp, grand);
-    double lmax = 0.0;
-    for (int b = b0; b < b0 + chunk && b < nb; ++b) {
-      sc.boff[b] = off;
-      const double T = __ldcg(sc.tile + b);
-      lmax = fmax(lmax, off + T);
-      off += T;
-    }
-    double gmax;
-    double pm = block_exclusive_scan<MaxOp>(lmax, s_warp, gmax);
-    for (int b = b0; b < b0 + chunk && b < nb; ++b) {
-      sc.pmax[b] = pm;
-      pm = fmax(pm, sc.boff[b] + __ldcg(sc.tile + b));
-    }
-  }
+  scan_tile_core(na_scan_args(lg, N, c, sc), blockIdx.x, gridDim.x, s_warp, &s_flag);
 }
 
 __global__ void __launch_bounds__(256) k_na_scan_add(int64_t N, double* c, NaScratch sc) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < N) {
-    const int64_t b = k / kScanTile;
-    c[k] = fmax(__ldcg(sc.boff + b) + c[k], __ldcg(sc.pmax + b));
-  }
+  scan_add_core(na_scan_args(nullptr, N, c, sc), (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // the filter's merge-path search (resample_tile), one block per diagonal tile
@@ -212,7 +168,7 @@ extern "C" pf_status pf_resample_systematic_noalloc(const double* log_g, int64_t
     const int64_t mb = (N + kNaThreads - 1) / kNaThreads;
     const unsigned g_max = (unsigned)(mb < kNaMaxBlocks ? mb : kNaMaxBlocks);
     k_na_max<<<g_max, kNaThreads, 0, st>>>(log_g, N, sc);
-    k_na_scan_tile<<<(unsigned)((N + kScanTile - 1) / kScanTile), kScanThreads, 0, st>>>(
+    k_na_scan_tile<<<(unsigned)scan_tile_count(N), kScanThreads, 0, st>>>(
         log_g, N, cumulative, sc);
     k_na_scan_add<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, cumulative, sc);
     k_na_resample<<<resample_blocks(N), kResampleThreads, 0, st>>>(cumulative, N, u, idx);

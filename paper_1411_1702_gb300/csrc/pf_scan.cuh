@@ -75,6 +75,139 @@ __device__ __forceinline__ int32_t systematic_index(const double* c, int64_t N, 
   return (int32_t)k;
 }
 
+// --------------------------------------------------- cumulative weights
+// g_k = exp(lg_k - M) and their cumulative sums c_k (Algorithm 1, Step 3a).
+// The N values are cut into tiles of kScanThreads * items consecutive values;
+// each thread sums `items` of them sequentially, threads are combined by a
+// block scan and tiles by the tile offsets of the last block.  A parallel FP64
+// scan may dip by an ulp where partial sums meet, so two exact prefix-maximum
+// passes (thread level and tile level) make c non-decreasing; the maximum is
+// exact and associative, so c is a deterministic function of the log weights
+// for a given N.
+//
+// The exponentials are the scan's cost and FP64 issue is scarce, so the tile
+// length follows N: of 1 to kScanItemsMax values a thread, the one whose
+// busiest SM has the least to do -- ceil(tiles / 152) tiles of (items + 0.3)
+// units, the 0.3 standing for a thread's share of the block scan -- among
+// those that keep the tile count at most max(kScanTargetTiles,
+// ceil(N / (kScanThreads * kScanItemsMax))); ties go to more values a thread.
+__host__ __device__ inline int scan_items(int64_t N) {
+  const int64_t cap_long = (N + kScanThreads * kScanItemsMax - 1) / (kScanThreads * kScanItemsMax);
+  const int64_t cap = cap_long > kScanTargetTiles ? cap_long : kScanTargetTiles;
+  int best = kScanItemsMax;
+  int64_t best_cost = -1;
+  for (int it = kScanItemsMax; it >= 1; --it) {
+    const int64_t tiles = (N + (int64_t)kScanThreads * it - 1) / ((int64_t)kScanThreads * it);
+    if (tiles > cap) break;
+    const int64_t cost = (tiles + 151) / 152 * (10 * it + 3);
+    if (best_cost < 0 || cost < best_cost) {
+      best = it;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+__host__ __device__ inline int64_t scan_tile_len(int64_t N) {
+  return (int64_t)kScanThreads * scan_items(N);
+}
+__host__ __device__ inline int scan_tile_count(int64_t N) {
+  const int64_t L = scan_tile_len(N);
+  return (int)((N + L - 1) / L);
+}
+
+// g = exp(lg - M) for a finite log weight, 0 for anything else (-inf, and any
+// other non-finite value, is a zero weight; the filter's own log weights are
+// finite or -inf).  A zero weight stays 0 whatever M is, so all-zero weights
+// give c = 0.
+__device__ __forceinline__ double scan_weight(double lg, double M) {
+  return finite_bits(lg) ? exp(lg - M) : 0.0;
+}
+
+// The maximum of two doubles >= +0 (every partial sum here is): their order is
+// that of their bit patterns as integers, so this runs on the integer units.
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x > y ? x : y);
+}
+struct MaxNonnegOp {
+  __device__ static double apply(double a, double b) { return max_nonneg(a, b); }
+};
+
+struct ScanArgs {
+  const double* lg;  // N log weights
+  int64_t N;
+  double M;          // their maximum (the log-sum-exp shift)
+  double* c;         // N cumulative weights (tile-local after the tile pass)
+  double* tile;      // per-tile totals
+  double* boff;      // per-tile offsets (sum of the earlier tiles)
+  double* pmax;      // per-tile floor (running maximum of the earlier tiles' last values)
+  unsigned* ticket;  // completion counter of the tile pass
+  double* c_total;   // optional: c_{N-1}
+};
+
+// Tile vb of vg: tile-local cumulative sums; the last tile to finish turns the
+// tile totals into offsets and floors.
+__device__ __forceinline__ void scan_tile_core(const ScanArgs& a, int vb, int vg, double* s_warp,
+                                               int* s_flag) {
+  const int items = scan_items(a.N);
+  const int64_t base = (int64_t)vb * kScanThreads * items + (int64_t)threadIdx.x * items;
+  double v[kScanItemsMax];
+  double run = 0.0;
+#pragma unroll
+  for (int j = 0; j < kScanItemsMax; ++j) {
+    if (j < items) {
+      const int64_t k = base + j;
+      run += (k < a.N) ? scan_weight(a.lg[k], a.M) : 0.0;
+    }
+    v[j] = run;
+  }
+  double total;
+  const double excl = block_exclusive_scan<SumOp>(run, s_warp, total);
+#pragma unroll
+  for (int j = 0; j < kScanItemsMax; ++j) v[j] = excl + v[j];
+  double tile_last;
+  const double floor_prev = block_exclusive_scan<MaxNonnegOp>(v[kScanItemsMax - 1], s_warp, tile_last);
+#pragma unroll
+  for (int j = 0; j < kScanItemsMax; ++j) {
+    const int64_t k = base + j;
+    if (j < items && k < a.N) a.c[k] = max_nonneg(v[j], floor_prev);
+  }
+  if (threadIdx.x == 0) a.tile[vb] = tile_last;
+  if (elect_last_block(a.ticket, s_flag, (unsigned)vg)) {
+    // tile offsets boff_b = sum of earlier tile totals, and the running maximum
+    // pmax_b of the earlier tiles' last values boff_b' + T_b'
+    const int nb = vg;
+    const int chunk = (nb + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * chunk;
+    double acc = 0.0;
+    for (int b = b0; b < b0 + chunk && b < nb; ++b) acc += __ldcg(a.tile + b);
+    double grand;
+    double off = block_exclusive_scan<SumOp>(acc, s_warp, grand);
+    double lmax = 0.0;
+    for (int b = b0; b < b0 + chunk && b < nb; ++b) {
+      a.boff[b] = off;
+      const double T = __ldcg(a.tile + b);
+      lmax = max_nonneg(lmax, off + T);
+      off += T;
+    }
+    double gmax;
+    double pm = block_exclusive_scan<MaxNonnegOp>(lmax, s_warp, gmax);
+    for (int b = b0; b < b0 + chunk && b < nb; ++b) {
+      a.pmax[b] = pm;
+      pm = max_nonneg(pm, a.boff[b] + __ldcg(a.tile + b));
+    }
+    if (threadIdx.x == 0 && a.c_total) *a.c_total = gmax;
+  }
+}
+
+// c_k = max(tile offset + tile-local sum, tile floor)
+__device__ __forceinline__ void scan_add_core(const ScanArgs& a, int64_t k) {
+  if (k < a.N) {
+    const int64_t b = k / scan_tile_len(a.N);
+    a.c[k] = max_nonneg(__ldcg(a.boff + b) + a.c[k], __ldcg(a.pmax + b));
+  }
+}
+
 // ------------------------------------------------------ merge-path search
 // Systematic resampling (Step 3b): tau_i = ((i + u)/N) c_{N-1} with one
 // u per epoch; l_i = min{k : c_k > tau_i},

@@ -67,3 +67,25 @@ def test_noalloc_rejects_oversized_and_bad_arguments(env):
     with pytest.raises(pf.PfError) as ei:
         pf.pf_resample_systematic_noalloc(d.data_ptr(), 4, 1.0, d.data_ptr(), i.data_ptr())
     assert ei.value.status == pf.PF_ERR_INVALID_ARG
+
+
+def test_noalloc_zero_and_nonfinite_weights(env):
+    # every weight zero: c is all zero and every index is 0; NaN and +inf
+    # log weights count as zero weights, like -inf
+    pf, torch = env
+    for N in (1, 700, 70000):
+        c, idx = _noalloc(pf, torch, np.full(N, -np.inf), 0.5)
+        assert np.all(c == 0.0) and np.all(idx == 0)
+    rng = np.random.default_rng(11)
+    N = 9000
+    lg = rng.standard_normal(N) * 3.0
+    bad = rng.choice(N, size=N // 10, replace=False)
+    lg[bad] = rng.choice([np.nan, np.inf, -np.inf], size=len(bad))
+    u = 0.3
+    c, idx = _noalloc(pf, torch, lg, u)
+    fin = np.isfinite(lg)
+    g = np.where(fin, np.exp(np.where(fin, lg, 0.0) - np.max(lg[fin])), 0.0)
+    assert np.allclose(c, np.cumsum(g), rtol=1e-12, atol=0.0)
+    assert np.all(np.diff(c) >= 0.0)
+    assert np.array_equal(idx, oracle.resample_systematic(c, u))
+    assert not np.any(np.isin(idx, np.flatnonzero(~fin)))
