@@ -117,7 +117,10 @@ static size_t layout(pf_filter* f, char* base) {
   f->fd.boff = (double*)take(sizeof(double) * scan_tiles(N));
   f->fd.pmax = (double*)take(sizeof(double) * scan_tiles(N));
   f->fd.part = (double*)take(sizeof(double) * kMomentBlocks * f->fd.nrec);
+  // model work arrays: the Brusselator's stage buffers; the 2D system's
+  // committed weights exp(lw - max lw), which the moments store for x-bar
   f->fd.wk = (f->ode == PF_ODE_BRUSSELATOR1D) ? (double*)take(sizeof(double) * bruss_work_doubles(N))
+             : (f->ode == PF_ODE_ADVDIFF2D)   ? (double*)take(sizeof(double) * N)
                                               : nullptr;
   f->fd.x0 = (const double*)take(sizeof(double) * d);
   f->fd.xbar = (double*)take(sizeof(double) * d);

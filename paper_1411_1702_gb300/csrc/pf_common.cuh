@@ -118,7 +118,7 @@ struct FilterDev {
   double* boff;     // per-tile offsets of the scan
   double* pmax;     // per-tile running maximum of the earlier tiles' last c
   double* part;     // moment partial records, kMomentBlocks * nrec
-  double* wk;       // model work arrays (Brusselator: r, predictor, error sums; 3*d*N)
+  double* wk;       // model work arrays (Brusselator: r, predictor, error sums; 2D system: weights)
   unsigned* ticket; // 4 counters for the last-block pattern
   Ctrl* ctrl;
   int nrec;

@@ -457,8 +457,12 @@ __device__ __forceinline__ void moments_body(const FilterDev& fd, int is_init, i
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
   for (int64_t n = (int64_t)vb * blockDim.x + threadIdx.x; n < N; n += (int64_t)vg * blockDim.x) {
     const double lw = nw.lw[n];
-    if (is_neg_inf(lw)) continue;
+    if (is_neg_inf(lw)) {
+      if constexpr (D == 0) fd.wk[n] = 0.0;
+      continue;
+    }
     const double e = exp(lw - M);
+    if constexpr (D == 0) fd.wk[n] = e;  // the weights x-bar needs (k_xbar)
     acc[Lay::kS0] += e;
     acc[Lay::kW2] = fma(e, e, acc[Lay::kW2]);
     double dp[P];
@@ -687,21 +691,22 @@ __global__ void k_set_moments(const __grid_constant__ FilterDev fd) {
 
 // Weighted mean of x for states too large for the per-thread moment records
 // (D = 0 moments): one block per component row of the newly committed
-// ensemble, w_n = exp(lw_n - lw_max) / wsum with the moments' own total.
+// ensemble, w_n = e_n / wsum with the weights e_n = exp(lw_n - lw_max) the
+// moment kernel stored (zero-weight particles, whose state may be
+// non-finite, are skipped by the bit pattern of their 0).
 __global__ void __launch_bounds__(kMomentThreads) k_xbar(const __grid_constant__ FilterDev fd) {
   __shared__ double s_red[32];
   const Ctrl* ctrl = fd.ctrl;
   if (ctrl->status != PF_OK) return;
   const Ensemble E = committed(fd, ctrl->cur);
   const int64_t N = fd.N;
-  const double M = ctrl->lw_max;
+  const double* __restrict__ e = fd.wk;
   for (int i = blockIdx.x; i < fd.d; i += gridDim.x) {
     const double* xi = E.x + (int64_t)i * N;
     double acc = 0.0;
     for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
-      const double lw = E.lw[n];
-      if (is_neg_inf(lw)) continue;
-      acc = fma(exp(lw - M), xi[n], acc);
+      const double en = __ldg(e + n);
+      if (__double_as_longlong(en) != 0) acc = fma(en, xi[n], acc);
     }
     acc = block_sum(acc, s_red);
     if (threadIdx.x == 0) fd.xbar[i] = acc / ctrl->wsum;
