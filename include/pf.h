@@ -384,7 +384,10 @@ typedef struct {
 
 /* budget_bytes: device memory the sessions may occupy (their filters' single
  * allocations); lanes: 1..64, or 0 for one lane per model and size class (6).
- * Errors: INVALID_ARG, OOM, CUDA. */
+ * The sessions' memory comes from a stream-ordered pool owned by the server;
+ * when the budget fits in 90 % of the free device memory, creation maps all of
+ * it into the pool at once (so admissions never wait for the driver), and it
+ * stays reserved until pf_server_destroy.  Errors: INVALID_ARG, OOM, CUDA. */
 pf_status pf_server_create(int64_t budget_bytes, int lanes, pf_server** out);
 /* Queue a session (arguments as pf_create; the options' stream and timing are
  * ignored).  It is admitted by a later pf_server_step when its memory fits.

@@ -653,6 +653,7 @@ struct Session {
 struct pf_server {
   std::vector<pf_batch*> lanes;  // one stream and one epoch in flight each
   cudaMemPool_t pool = nullptr;  // the sessions' device memory
+  int64_t reserved = 0;          // bytes of the budget mapped in the pool at creation
   int64_t budget = 0, in_use = 0;
   int64_t next_id = 1;
   std::map<int64_t, Session> sessions;
@@ -845,6 +846,34 @@ pf_status pf_batch_stats(const pf_batch* b, pf_batch_stats_t* out) {
   return PF_OK;
 }
 
+// Reserve the budget in the pool once, at creation: allocating it and freeing
+// it maps its pages now, and the release threshold keeps them, so admissions
+// only sub-allocate mapped memory.  Growing the pool during admission instead
+// held a pf_server_step for tens of milliseconds (the driver mapping the
+// pages of a large session).  A budget beyond the free device memory is not
+// reserved; the pool then grows as sessions arrive.
+static void reserve_budget(pf_server* s) {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if ((double)s->budget > 0.9 * (double)free_b) return;
+  cudaStream_t rs = nullptr;
+  if (cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  void* p = nullptr;
+  if (cudaMallocFromPoolAsync(&p, (size_t)s->budget, s->pool, rs) == cudaSuccess) {
+    cudaFreeAsync(p, rs);
+    s->reserved = s->budget;
+  }
+  cudaGetLastError();  // a reservation that did not fit is not an error
+  cudaStreamSynchronize(rs);
+  cudaStreamDestroy(rs);
+}
+
 pf_status pf_server_create(int64_t budget_bytes, int lanes, pf_server** out) {
   if (!out) return sfail(nullptr, PF_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -876,6 +905,7 @@ pf_status pf_server_create(int64_t budget_bytes, int lanes, pf_server** out) {
     return sfail(nullptr, PF_ERR_CUDA, std::string("memory pool creation failed: ") +
                                            cudaGetErrorString(e));
   }
+  reserve_budget(s);
   int least = 0, greatest = 0;
   cudaDeviceGetStreamPriorityRange(&least, &greatest);
   for (int i = 0; i < lanes; ++i) {

@@ -28,6 +28,15 @@ constexpr int kScanTargetTiles = 608;  // tiles that fill 4 blocks on each of 15
 constexpr int kMomentBlocks = 304;   // 2 per SM on a 152-SM GB300
 constexpr int kMomentThreads = 256;
 
+// Blocks of the moment kernels for N particles: one per 256 particles up to
+// one block per SM, then one per SM (grid-stride, so no SM holds two blocks
+// while another holds one) until two per SM pay, then two per SM.
+__host__ __device__ inline int moment_blocks(int64_t N) {
+  const int64_t b = (N + kMomentThreads - 1) / kMomentThreads;
+  if (b <= kMomentBlocks / 2) return (int)b;
+  return b < kMomentBlocks ? kMomentBlocks / 2 : kMomentBlocks;
+}
+
 // Random-stream purposes (Philox counter word 2, low byte).
 enum : uint32_t { kRngInit = 1, kRngTheta = 2, kRngInnov = 3, kRngResample = 4 };
 

@@ -42,6 +42,33 @@ __device__ inline void cholesky_psd(int p, const double* C, double* L) {
   }
 }
 
+// Step 4a's factor L of the committed covariance C, by one warp (lane = 0..31)
+// of the filter's first resampling block: only stage 2 uses L, and that warp
+// is idle while two others search the tile corners, so the factorisation is
+// off the epoch's serial tails.  Lane i owns row i; the column order and the
+// operations are those of cholesky_psd, so L is the same to the bit.  s needs
+// kPMax * kPMax doubles of shared memory of the warp's own.
+__device__ __forceinline__ void factor_covariance(const FilterDev& fd, int p, double* s, int lane) {
+  Ctrl* ctrl = fd.ctrl;
+  if (lane < kPMax * kPMax) s[lane] = 0.0;
+  __syncwarp();
+  for (int j = 0; j < p; ++j) {
+    double dsum = ctrl->C[j * kPMax + j];
+    for (int k = 0; k < j; ++k) dsum -= s[j * kPMax + k] * s[j * kPMax + k];
+    if (dsum > 0.0) {
+      const double ljj = sqrt(dsum);
+      if (lane == j) s[j * kPMax + j] = ljj;
+      if (lane > j && lane < p) {
+        double sv = ctrl->C[lane * kPMax + j];
+        for (int k = 0; k < j; ++k) sv -= s[lane * kPMax + k] * s[j * kPMax + k];
+        s[lane * kPMax + j] = sv / ljj;
+      }
+    }
+    __syncwarp();
+  }
+  if (lane < kPMax * kPMax) ctrl->L[lane] = s[lane];
+}
+
 // End of stage 1 (Step 3a): block maximum of the log fitness weights; the
 // last of the filter's vg blocks stores the global maximum (the log-sum-exp
 // shift) and flags a degenerate epoch.  Every thread of the block must call it.

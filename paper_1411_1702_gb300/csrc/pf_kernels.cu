@@ -278,7 +278,9 @@ __device__ __forceinline__ void scan_add_body(const FilterDev& fd, int vb) {
 // Step 3b: the epoch's u is Philox purpose RESAMPLE, slot 0; the search is
 // resample_tile (pf_scan.cuh).
 __device__ __forceinline__ void resample_body(const FilterDev& fd, const EpochParams* __restrict__ ep,
-                                              int vb, RsShared& sh) {
+                                              int vb, RsShared& sh, double* s_chol) {
+  // warp 2 of the first block factors C for stage 2 (warps 0 and 1 search)
+  if (vb == 0 && (threadIdx.x >> 5) == 2) factor_covariance(fd, fd.p, s_chol, threadIdx.x & 31);
   const U4 w = draw_block(fd, kRngResample, 0u, ep->epoch, 0u);
   resample_tile(fd.c, fd.N, uniform53(w.x, w.y), fd.idx,
                 reinterpret_cast<unsigned long long*>(&fd.ctrl->n_unique), vb, sh);
@@ -516,21 +518,17 @@ __device__ __forceinline__ void moments_body(const FilterDev& fd, int is_init, i
   // moment of the differences gives the mean's displacement to full relative
   // precision, so C = E[(phi - c)(phi - c)^T] - m m^T loses only
   // eps E[|phi - c|^2].  Warp 0 forms the mean and C a lane per entry and
-  // checks them; then, at once, warp 0 factors C (a lane per row), warp 1
-  // stores the weight statistics and warp 2 the state mean.
+  // checks them; then, at once, warp 0 stores them, warp 1 the weight
+  // statistics and warp 2 the state mean.
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double S0 = s_tot[Lay::kS0];
   double* s_m1 = s_part;                // P values
   double* s_C = s_part + kPMax;         // kPMax^2 values
-  double* s_L = s_C + kPMax * kPMax;    // kPMax^2 values
   constexpr int NC = P * (P + 1) / 2;
   if (wid == 0) {
     const double inv = 1.0 / S0;
     bool bad = !(S0 > 0.0);
-    if (lane < kPMax * kPMax) {
-      s_C[lane] = 0.0;
-      s_L[lane] = 0.0;
-    }
+    if (lane < kPMax * kPMax) s_C[lane] = 0.0;
     if (lane < P) {
       const double m1 = s_tot[Lay::kS1 + lane] * inv;
       s_m1[lane] = m1;
@@ -561,25 +559,8 @@ __device__ __forceinline__ void moments_body(const FilterDev& fd, int is_init, i
     return;
   }
   if (wid == 0) {
-    // Cholesky by columns; a pivot that is not positive leaves its column zero
-    for (int j = 0; j < P; ++j) {
-      double dsum = s_C[j * kPMax + j];
-      for (int k = 0; k < j; ++k) dsum -= s_L[j * kPMax + k] * s_L[j * kPMax + k];
-      if (dsum > 0.0) {
-        const double ljj = sqrt(dsum);
-        if (lane == j) s_L[j * kPMax + j] = ljj;
-        if (lane > j && lane < P) {
-          double sv = s_C[lane * kPMax + j];
-          for (int k = 0; k < j; ++k) sv -= s_L[lane * kPMax + k] * s_L[j * kPMax + k];
-          s_L[lane * kPMax + j] = sv / ljj;
-        }
-      }
-      __syncwarp();
-    }
-    if (lane < kPMax * kPMax) {
-      ctrl->C[lane] = s_C[lane];
-      ctrl->L[lane] = s_L[lane];
-    }
+    // (L, the factor of C, is formed by the next resampling launch)
+    if (lane < kPMax * kPMax) ctrl->C[lane] = s_C[lane];
     if (lane < P) ctrl->phibar[lane] += s_m1[lane];
   } else if (wid == 1) {
     if (lane == 0) {
@@ -628,8 +609,9 @@ __global__ void __launch_bounds__(256) k_scan_add(const __grid_constant__ Filter
 __global__ void __launch_bounds__(kResampleThreads) k_resample(const __grid_constant__ FilterDev fd,
                                                                const EpochParams* __restrict__ ep) {
   __shared__ RsShared sh;
+  __shared__ double s_chol[kPMax * kPMax];
   if (fd.ctrl->status != PF_OK) return;
-  resample_body(fd, ep, blockIdx.x, sh);
+  resample_body(fd, ep, blockIdx.x, sh, s_chol);
 }
 
 template <class M, int F>
@@ -772,10 +754,11 @@ __global__ void __launch_bounds__(kResampleThreads) k_batch_resample(
     const FilterDev* __restrict__ fds, const EpochParams* const* __restrict__ eps,
     const BatchTile* __restrict__ tiles) {
   __shared__ RsShared sh;
+  __shared__ double s_chol[kPMax * kPMax];
   const BatchTile t = tiles[blockIdx.x];
   const FilterDev& fd = *(fds + t.f);
   if (fd.ctrl->status != PF_OK) return;
-  resample_body(fd, eps[t.f], t.vb, sh);
+  resample_body(fd, eps[t.f], t.vb, sh, s_chol);
 }
 
 template <int D, int P>
@@ -789,8 +772,7 @@ __global__ void __launch_bounds__(kMomentThreads) k_batch_moments(const FilterDe
   const BatchTile t = tiles[blockIdx.x];
   const FilterDev& fd = *(fds + t.f);
   if (fd.ctrl->status != PF_OK) return;
-  const int64_t b = (fd.N + kMomentThreads - 1) / kMomentThreads;
-  const int vg = (int)(b < kMomentBlocks ? b : kMomentBlocks);
+  const int vg = moment_blocks(fd.N);
   moments_body<D, P>(fd, is_init, t.vb, vg, s_part, s_tot, &s_flag);
 }
 
@@ -833,10 +815,7 @@ int phase_blocks(int phase, int ode, int64_t N) {
     case kPhaseScanTile: return scan_tiles(N);
     case kPhaseScanAdd: return (int)((N + 255) / 256);
     case kPhaseResample: return (int)((2 * N + kRsTile - 1) / kRsTile);
-    case kPhaseMoments: {
-      const int64_t b = (N + kMomentThreads - 1) / kMomentThreads;
-      return (int)(b < kMomentBlocks ? b : kMomentBlocks);
-    }
+    case kPhaseMoments: return moment_blocks(N);
   }
   return 0;
 }
