@@ -461,8 +461,8 @@ static pf_status batch_add(pf_batch* b, pf_filter* f, int* slot_out) {
     s = b->cap;
     PF_BCUDA(b, grow(b, b->cap + 1));
   }
-  PF_BCUDA(b, cudaMemcpyAsync(b->fds_dev + s, &f->fd, sizeof(FilterDev), cudaMemcpyHostToDevice,
-                              f->stream));
+  static_assert(sizeof(FilterDev) <= (size_t)kUploadBytes, "FilterDev fits a parameter upload");
+  PF_BCUDA(b, upload_small(b->fds_dev + s, &f->fd, sizeof(FilterDev), f->stream));
   if (f->ready) {
     // the batch's next launch waits, on the device, for the filter's pending
     // work (its initialisation) and the descriptor
@@ -653,6 +653,7 @@ struct Session {
 struct pf_server {
   std::vector<pf_batch*> lanes;  // one stream and one epoch in flight each
   cudaMemPool_t pool = nullptr;  // the sessions' device memory
+  cudaStream_t init_stream = nullptr;  // greatest priority; every session initialises on it
   int64_t reserved = 0;          // bytes of the budget mapped in the pool at creation
   int64_t budget = 0, in_use = 0;
   int64_t next_id = 1;
@@ -697,7 +698,9 @@ static pf_status admit(pf_server* s, Session& ss) {
   pf_options o = ss.opt;
   o.obs_idx = ss.obs.data();
   o.sigma = ss.sigma.data();
-  o.stream = nullptr;
+  // the server's own init stream: creating a stream per session had held an
+  // admission for tens of milliseconds
+  o.stream = s->init_stream;
   o.timing = 0;
   pf_filter* f = nullptr;
   pf_status st = filter_create(ss.ode, ss.d, ss.p, ss.N, ss.lmm, ss.dt, &pr, &o, s->pool, &f);
@@ -908,6 +911,13 @@ pf_status pf_server_create(int64_t budget_bytes, int lanes, pf_server** out) {
   reserve_budget(s);
   int least = 0, greatest = 0;
   cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  e = cudaStreamCreateWithPriority(&s->init_stream, cudaStreamNonBlocking, greatest);
+  if (e != cudaSuccess) {
+    s->init_stream = nullptr;
+    pf_server_destroy(s);
+    return sfail(nullptr, PF_ERR_CUDA, std::string("init stream creation failed: ") +
+                                           cudaGetErrorString(e));
+  }
   for (int i = 0; i < lanes; ++i) {
     int rank = 3;
     for (int cls = 0; cls < 2 * kCostModels; ++cls)
@@ -937,6 +947,7 @@ void pf_server_destroy(pf_server* s) {
     cudaDeviceSynchronize();  // the stream-ordered frees of the sessions
     cudaMemPoolDestroy(s->pool);
   }
+  if (s->init_stream) cudaStreamDestroy(s->init_stream);
   delete s;
 }
 

@@ -197,9 +197,12 @@ static pf_status do_init(pf_filter* f, bool check = true) {
   h->status = PF_OK;
   for (int i = 0; i < f->p; ++i) h->phibar[i] = prior_center_phi(f, i);
   h->lw_max = 0.0;
-  PF_CUDA(f, cudaMemcpyAsync(f->fd.ctrl, h, sizeof(Ctrl), cudaMemcpyHostToDevice, f->stream));
-  PF_CUDA(f, cudaMemcpyAsync(const_cast<double*>(f->fd.x0), f->x0.data(), sizeof(double) * f->d,
-                             cudaMemcpyHostToDevice, f->stream));
+  // small uploads as kernel parameters: a pooled filter's host blocks are
+  // pageable, and a pageable copy may wait for the stream
+  static_assert(sizeof(Ctrl) <= (size_t)kUploadBytes, "Ctrl fits a parameter upload");
+  PF_CUDA(f, upload_small(f->fd.ctrl, h, sizeof(Ctrl), f->stream));
+  PF_CUDA(f, upload_small(const_cast<double*>(f->fd.x0), f->x0.data(), sizeof(double) * f->d,
+                          f->stream));
   PF_CUDA(f, cudaMemsetAsync(f->fd.ticket, 0, sizeof(unsigned) * 8, f->stream));
   PF_CUDA(f, launch_init(f->ode, f->fd, f->stream));
   f->hist = HistoryState{0, 0, f->t0, 0.0, 0.0};
@@ -399,8 +402,9 @@ pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double 
   if (opt->stream) {
     f->stream = (cudaStream_t)opt->stream;
   } else {
-    // a pooled filter's own stream only initialises it: at the greatest
-    // priority, so creation is not queued behind long kernels of other streams
+    // a pooled filter's stream only initialises it: at the greatest priority,
+    // so creation is not queued behind long kernels of other streams (the
+    // server passes its own such stream, shared by all sessions)
     int least = 0, greatest = 0;
     if (pool) cudaDeviceGetStreamPriorityRange(&least, &greatest);
     e = cudaStreamCreateWithPriority(&f->stream, cudaStreamNonBlocking, pool ? greatest : 0);
@@ -447,7 +451,11 @@ extern "C" {
 
 void pf_destroy(pf_filter* f) {
   if (!f) return;
-  if (f->stream) cudaStreamSynchronize(f->stream);
+  // A pooled filter (a server session) initialises on the server's shared init
+  // stream and frees its memory in that stream's order, so it does not wait
+  // for the other sessions' initialisations; its host blocks have no copy in
+  // flight (its uploads travel as kernel parameters, its reads are waited for).
+  if (f->stream && !f->pool) cudaStreamSynchronize(f->stream);
   if (f->series_dev) cudaFree(f->series_dev);
   if (f->pool) {
     if (f->dmem) cudaFreeAsync(f->dmem, f->stream);

@@ -21,6 +21,8 @@
 // never on where its tiles land, so a filter gives bit-identical results alone
 // and in a batch.  Every phase returns at once if an earlier epoch of its
 // filter failed (Ctrl::status), so epochs can be enqueued ahead.
+#include <cstring>
+
 #include "pf_common.cuh"
 #include "pf_epoch.cuh"
 #include "pf_kernels.h"
@@ -1002,6 +1004,23 @@ cudaError_t allow_step_table(const void* k) {
                               (int)(sizeof(StepCoef) * (size_t)kSMax));
 }
 
+struct UploadBlob {
+  unsigned char b[kUploadBytes];
+};
+
+__global__ void k_upload(unsigned char* __restrict__ dst, int n, const __grid_constant__ UploadBlob blob) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = blob.b[i];
+}
+
+cudaError_t upload_small(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes > (size_t)kUploadBytes) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  if (bytes == 0) return cudaSuccess;
+  UploadBlob blob;
+  std::memcpy(blob.b, src, bytes);
+  k_upload<<<1, 128, 0, st>>>(static_cast<unsigned char*>(dst), (int)bytes, blob);
+  return cudaGetLastError();
+}
+
 cudaError_t preload_main_kernels() {
   const void* ks[] = {
       (const void*)k_init<2, 2>, (const void*)k_init<3, 3>, (const void*)k_init<64, 3>,
@@ -1010,7 +1029,7 @@ cudaError_t preload_main_kernels() {
       (const void*)k_scan_tile, (const void*)k_scan_add, (const void*)k_resample,
       (const void*)k_theta_mean<2>, (const void*)k_theta_mean<3>, (const void*)k_theta_mean<5>,
       (const void*)k_set_moments, (const void*)k_init<0, 5>, (const void*)k_moments<0, 5>,
-      (const void*)k_xbar,
+      (const void*)k_xbar, (const void*)k_upload,
       (const void*)k_batch_init, (const void*)k_batch_scan_tile,
       (const void*)k_batch_scan_add, (const void*)k_batch_resample,
       (const void*)k_batch_moments<2, 2>, (const void*)k_batch_moments<3, 3>,

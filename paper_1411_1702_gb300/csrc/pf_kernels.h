@@ -48,6 +48,12 @@ cudaError_t launch_epoch(int ode, const FilterDev& fd, const EpochParams* ep, in
                          cudaEvent_t* marks = nullptr);
 // Recompute the Cholesky factor after the host set phibar and C.
 cudaError_t launch_set_moments(const FilterDev& fd, cudaStream_t st);
+
+// Host-to-device copy of at most kUploadBytes bytes carried as a kernel
+// parameter: never synchronises, whatever memory src is in (a copy from
+// pageable memory may wait for its stream).
+constexpr int kUploadBytes = 2048;
+cudaError_t upload_small(void* dst, const void* src, size_t bytes, cudaStream_t st);
 int moment_record_size(int ode);
 // Weighted theta-space mean of the committed ensemble into Ctrl::theta_mean.
 cudaError_t launch_theta_mean(const FilterDev& fd, cudaStream_t st);
