@@ -495,6 +495,8 @@ static void CUDART_CB mark_done(void* p) { *static_cast<double*>(p) = now_ms(); 
 // Launch one epoch for the slots with y[slot] != NULL (no waiting).  status[s]
 // gets PF_ERR_INVALID_ARG for a rejected observation.
 static pf_status batch_launch(pf_batch* b, const double* t, const double* const* y, int* status) {
+  for (int i = 0; i < b->cap; ++i)
+    if (b->slot[i]) b->slot[i]->est_fresh = false;  // batched epochs change the estimates
   if (b->in_flight) return bfail(b, PF_ERR_STATE, "an epoch is already in flight");
   const int cap = b->cap;
   std::vector<char> active(cap, 0);

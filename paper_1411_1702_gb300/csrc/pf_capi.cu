@@ -430,6 +430,7 @@ pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double 
   } else {
     e = cudaMallocHost(&f->ep_host, sizeof(EpochParams));
     if (e == cudaSuccess) e = cudaMallocHost(&f->ctrl_host, sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaMallocHost(&f->xbar_host, sizeof(double) * f->d);
   }
   if (e == cudaSuccess) e = cudaEventCreate(&f->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&f->ev1);
@@ -465,6 +466,7 @@ void pf_destroy(pf_filter* f) {
     if (f->dmem) cudaFree(f->dmem);
     if (f->ep_host) cudaFreeHost(f->ep_host);
     if (f->ctrl_host) cudaFreeHost(f->ctrl_host);
+    if (f->xbar_host) cudaFreeHost(f->xbar_host);
   }
   free_marks(f);
   if (f->ev0) cudaEventDestroy(f->ev0);
@@ -489,12 +491,20 @@ pf_status pf_assimilate(pf_filter* f, double t_k, const double* y_k) {
   int depth_out = 0;
   const int S = fill_epoch(f, f->hist, t_k, y_k, f->ep_host, &depth_out);
   if (S < 1) return fail(f, PF_ERR_INVALID_ARG, "substep grid of the interval is invalid");
+  f->est_fresh = false;
   const size_t bytes = kEpochHeaderBytes + sizeof(StepCoef) * (size_t)S;
   PF_CUDA(f, cudaMemcpyAsync(f->ep_dev, f->ep_host, bytes, cudaMemcpyHostToDevice, f->stream));
   f->h2d_bytes += (int64_t)bytes;
   PF_CUDA(f, cudaEventRecord(f->ev0, f->stream));
   PF_CUDA(f, launch_epoch(f->ode, f->fd, f->ep_dev, S, f->stream, take_marks(f)));
   PF_CUDA(f, cudaEventRecord(f->ev1, f->stream));
+  // x-bar comes back with the control block in the same wait, so estimates
+  // asked for right after need no second round trip
+  if (f->xbar_host) {
+    PF_CUDA(f, cudaMemcpyAsync(f->xbar_host, f->fd.xbar, sizeof(double) * f->d,
+                               cudaMemcpyDeviceToHost, f->stream));
+    f->d2h_bytes += (int64_t)(sizeof(double) * f->d);
+  }
   pf_status st = read_ctrl(f);
   if (st != PF_OK) return st;
   float ms = 0.0f;
@@ -506,18 +516,25 @@ pf_status pf_assimilate(pf_filter* f, double t_k, const double* y_k) {
     return fail(f, (pf_status)dst, status_text(dst));
   }
   f->hist = advance_history(f->hist, t_k, f->ep_host, depth_out);
+  f->est_fresh = f->xbar_host != nullptr;
   return PF_OK;
 }
 
 pf_status pf_estimates(const pf_filter* cf, double* theta_bar, double* C, double* x_bar) {
   pf_filter* f = const_cast<pf_filter*>(cf);
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
-  PF_CUDA(f, cudaMemcpyAsync(f->ctrl_host, f->fd.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, f->stream));
-  if (x_bar)
-    PF_CUDA(f, cudaMemcpyAsync(x_bar, f->fd.xbar, sizeof(double) * f->d, cudaMemcpyDeviceToHost,
+  if (f->est_fresh) {
+    // right after pf_assimilate: its wait already brought the estimates back
+    if (x_bar) std::memcpy(x_bar, f->xbar_host, sizeof(double) * f->d);
+  } else {
+    PF_CUDA(f, cudaMemcpyAsync(f->ctrl_host, f->fd.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
                                f->stream));
-  PF_CUDA(f, cudaStreamSynchronize(f->stream));
-  f->d2h_bytes += sizeof(Ctrl) + (x_bar ? sizeof(double) * f->d : 0);
+    if (x_bar)
+      PF_CUDA(f, cudaMemcpyAsync(x_bar, f->fd.xbar, sizeof(double) * f->d, cudaMemcpyDeviceToHost,
+                                 f->stream));
+    PF_CUDA(f, cudaStreamSynchronize(f->stream));
+    f->d2h_bytes += sizeof(Ctrl) + (x_bar ? sizeof(double) * f->d : 0);
+  }
   const Ctrl* h = f->ctrl_host;
   if (theta_bar) for (int i = 0; i < f->p; ++i) theta_bar[i] = h->phibar[i];
   if (C)
@@ -615,6 +632,7 @@ pf_status pf_load_observations(pf_filter* f, int T, const double* t, const doubl
 }
 
 pf_status pf_run(pf_filter* f, int k0, int k1) {
+  if (f) f->est_fresh = false;
   const pfg::NvtxRange nvtx_range("pf_run");
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
   if (!f->series_dev) return fail(f, PF_ERR_STATE, "no observation series loaded");
@@ -648,6 +666,7 @@ pf_status pf_synchronize(pf_filter* f) {
 }
 
 pf_status pf_reset(pf_filter* f) {
+  if (f) f->est_fresh = false;
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
   PF_CUDA(f, cudaStreamSynchronize(f->stream));
   pf_status st = do_init(f);
@@ -698,6 +717,7 @@ pf_status pf_get_ensemble(const pf_filter* cf, double* x, double* h1, double* h2
 
 pf_status pf_set_ensemble(pf_filter* f, const double* x, const double* h1, const double* h2,
                           const double* phi, const double* logw) {
+  if (f) f->est_fresh = false;
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
   pf_status st = read_ctrl(f);
   if (st != PF_OK) return st;
@@ -726,6 +746,7 @@ pf_status pf_set_ensemble(pf_filter* f, const double* x, const double* h1, const
 }
 
 pf_status pf_set_moments(pf_filter* f, const double* phibar, const double* C) {
+  if (f) f->est_fresh = false;
   if (!f || !phibar || !C) return fail(f, PF_ERR_INVALID_ARG, "NULL argument");
   pf_status st = read_ctrl(f);
   if (st != PF_OK) return st;
@@ -824,6 +845,7 @@ pf_status pf_save(const pf_filter* cf, void* buf, size_t bytes) {
 }
 
 pf_status pf_load(pf_filter* f, const void* buf, size_t bytes) {
+  if (f) f->est_fresh = false;
   if (!f || !buf) return fail(nullptr, PF_ERR_INVALID_ARG, "NULL argument");
   if (f->in_batch) return fail(f, PF_ERR_STATE, "the filter is a member of a batch");
   CkptHeader h;
@@ -881,6 +903,7 @@ pf_status pf_get_history(const pf_filter* f, int64_t* epochs, int* depth, double
 
 pf_status pf_set_history(pf_filter* f, int64_t epochs, int depth, double t_prev, double hprev1,
                          double hprev2) {
+  if (f) f->est_fresh = false;
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
   if (epochs < 0 || depth < 0 || depth > 2 || !std::isfinite(t_prev))
     return fail(f, PF_ERR_INVALID_ARG, "history out of range");

@@ -52,6 +52,8 @@ struct pf_filter {
   pfg::EpochParams* ep_dev = nullptr;    // online parameter slot
   pfg::EpochParams* ep_host = nullptr;   // staging (pinned; pageable when pooled)
   pfg::Ctrl* ctrl_host = nullptr;        // pinned; pageable when pooled
+  double* xbar_host = nullptr;           // pinned mirror of x-bar (not pooled)
+  bool est_fresh = false;                 // ctrl_host and xbar_host hold the committed estimates
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t ready = nullptr;            // pooled: the work queued on `stream` is done
   // committed history (host view)

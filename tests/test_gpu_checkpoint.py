@@ -108,3 +108,28 @@ def test_fp64_fma_rate_reaches_the_nominal_peak(pf):
     assert 0.5 * 1.259 < r < 1.1 * 1.259, r
     with pytest.raises(pf.PfError):
         pf.pf_fp64_fma_rate(0.0)
+
+
+@pytest.mark.parametrize("name", ["robertson", "brusselator", "advdiff20"])
+def test_estimates_after_assimilate_equal_a_device_read(pf, name):
+    # pf_estimates right after pf_assimilate is served from the values that
+    # pf_assimilate's own wait brought back; after any call that may change the
+    # device state it reads the device again.  Both must give the same bits,
+    # and the mirror must not survive a state change.
+    w = W.get(name, N=600 if name != "advdiff20" else 64)
+    g = pf.Filter.from_workload(w)
+    for k in range(3):
+        g.pf_assimilate(w.t_obs[k], w.y_obs[k])
+        fast = g.pf_estimates()
+        blob = g.pf_save()
+        g.pf_load(blob)  # the same state, and the mirror is dropped
+        slow = g.pf_estimates()
+        for u, v in zip(fast, slow):
+            assert np.array_equal(u, v)
+    # a state change after the mirror was filled is seen
+    before = g.pf_estimates()
+    phibar, Cm, _ = before
+    g.pf_set_moments(phibar + 0.25, Cm)
+    after = g.pf_estimates()
+    assert np.array_equal(after[0], phibar + 0.25)
+    g.close()
