@@ -137,6 +137,24 @@ STAGE2_TRAFFIC = {"robertson": 11552512 + 0,
 # 8 MATLAB workers on an i7-3820), converted to particle-LMM-steps/s at 600
 # steps per particle per run.
 PAPER_BASELINE = {"advdiff20": 3.0e6 / 7.20e3, "advdiff40": 3.0e6 / 3.39e4}
+# The ensemble size each traffic capture was taken at (traffic is reported only
+# for that size).
+TRAFFIC_N = {"robertson": 131072, "brusselator": 65536, "advdiff20": 5000, "advdiff40": 5000,
+             "michaelisBDF2": 50000, "michaelisAM3": 50000, "michaelisAB3": 50000}
+# Algorithmic DRAM bytes per particle of the scan and resampling launches:
+# the tile scan reads log g and writes c, the offset pass reads and writes c,
+# resampling reads c and writes the int32 index.
+SUPPORT_BYTES = {"scan_tile": 16, "scan_add": 16, "resample": 12}
+
+
+def hbm_peak():
+    """The measured copy bandwidth of the GB300s (GB/s), else the
+    profiling recipe's fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s"
 # Particles of the timed CPU-oracle sample, where the workload's own N would
 # take minutes per epoch on the host cores.
 CPU_SAMPLE_N = {"advdiff20": 512, "advdiff40": 48}
@@ -219,6 +237,29 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def epoch_launches(w):
+    """Kernels of one single-filter epoch: stage 1, scan tile, scan add,
+    resampling, stage 2, moments; plus the state mean of the 2D system and the
+    corner pass of a resampling above one wave of merge tiles (the library's
+    rs_two_phase: more than 4 * 152 tiles of 1024 items)."""
+    n = 6 + (1 if w.ode == W_ADVDIFF else 0)
+    return n + (1 if (2 * w.N + 1023) // 1024 > 4 * 152 else 0)
+
+
+def support_roofline(ktimes, N):
+    """Achieved bandwidth of the scan and resampling phases (algorithmic bytes
+    over their mean device time) against the HBM peak."""
+    peak, src = hbm_peak()
+    out = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": src, "kernels": {}}
+    for name, bpp in SUPPORT_BYTES.items():
+        ms, n = ktimes.get(name, (0.0, 0))
+        if n and ms > 0.0:
+            us = ms / n * 1e3
+            gbs = bpp * N / (us * 1e-6) / 1e9
+            out["kernels"][name] = {"us": us, "bytes": bpp * N, "achieved": gbs, "frac": gbs / peak}
+    return out
 
 
 def cpu_oracle_rate(w, seconds=12.0, max_epochs=None, N=None):
@@ -410,16 +451,18 @@ def run_ours(args, w):
                 "d2h_bytes_per_step": int(round(d2h))},
         # per epoch: stage 1, scan tiles, scan offsets, resampling, stage 2,
         # moments (+ the weighted state mean of the 2D system)
-        "gpu_launches": (7 if w.ode == W_ADVDIFF else 6) * args.steps,
+        "gpu_launches": epoch_launches(w) * args.steps,
         "roofline": {"bound": "alu", "kernel": STAGE2_KERNEL[w.name], "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                     "traffic": STAGE2_TRAFFIC.get(w.name),
+                     "traffic": (STAGE2_TRAFFIC.get(w.name)
+                                 if TRAFFIC_N.get(w.name) == w.N else None),
                      "peak_source": "2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz (nominal GB300 FP64)",
                      "fp64_fma_measured": fma_measured,
                      "frac_of_measured_fma": (achieved / fma_measured) if achieved and fma_measured else None},
         "kernel_share": shares,
         "kernel_ms_per_step": {k2: v[0] / max(1, v[1]) for k2, v in ktimes.items()},
+        "support_roofline": support_roofline(ktimes, w.N),
     }
     if not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(w, seconds=args.cpu_seconds,
@@ -740,8 +783,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="robertson",
-                    choices=["robertson", "linear2", "brusselator", "advdiff20", "advdiff40",
-                             "michaelis"] + ["michaelis" + n for n in W_LMM_NAMES] + [
+                    choices=["robertson", "robertson22", "linear2", "brusselator", "advdiff20",
+                             "advdiff40", "michaelis"] + ["michaelis" + n for n in W_LMM_NAMES] + [
                              "batched", "serving"])
     ap.add_argument("--batch-filters", type=int, default=256)
     ap.add_argument("--serve-sessions", type=int, default=64)

@@ -434,7 +434,7 @@ void pf_server_destroy(pf_server* s);
  * every weight is zero, c is all zero and every index is 0.
  *
  * Nothing is allocated or freed.  The scratch (per-tile sums and offsets,
- * completion counters) is one fixed array of about 400 KB in the library's
+ * completion counters, merge-tile corners) is one fixed array of about 530 KB in the library's
  * device image; every GPU that loads the library holds it until the process
  * exits.  The first call on a device looks up that array's device address
  * with the device current; make that first call before any stream capture.
@@ -453,7 +453,9 @@ pf_status pf_resample_systematic_noalloc(const double* log_g, int64_t N, double 
  * k with c_k = c_{N-1}), for given cumulative weights c.  It is the filter's own
  * search (the merge-path kernel pf_assimilate launches), so for the same c and
  * u the indices are bit-identical to the filter's.  Runs on `stream` (NULL =
- * the legacy default stream) without waiting, allocating nothing.
+ * the legacy default stream) without waiting, allocating nothing: each block
+ * finds its own tile corners, so beyond about 300k particles it is slower than
+ * the filter's two-launch form (which keeps its corners in scratch).
  *
  * cumulative: N doubles of device memory, read; must be non-decreasing and
  * >= +0, as a cumulative sum of non-negative weights is (other input gives

@@ -279,13 +279,22 @@ __device__ __forceinline__ void scan_add_body(const FilterDev& fd, int vb) {
 // --------------------------------------------------------------- resample
 // Step 3b: the epoch's u is Philox purpose RESAMPLE, slot 0; the search is
 // resample_tile (pf_scan.cuh).
+__device__ __forceinline__ double resample_u(const FilterDev& fd, const EpochParams* __restrict__ ep) {
+  const U4 w = draw_block(fd, kRngResample, 0u, ep->epoch, 0u);
+  return uniform53(w.x, w.y);
+}
+
+// corners: the filter's corner array (two-phase, in the per-block scratch,
+// which holds nothing else between the scan and stage 2), or null
 __device__ __forceinline__ void resample_body(const FilterDev& fd, const EpochParams* __restrict__ ep,
-                                              int vb, RsShared& sh, double* s_chol) {
+                                              int vb, RsShared& sh, double* s_chol,
+                                              const int32_t* corners) {
   // warp 2 of the first block factors C for stage 2 (warps 0 and 1 search)
   if (vb == 0 && (threadIdx.x >> 5) == 2) factor_covariance(fd, fd.p, s_chol, threadIdx.x & 31);
-  const U4 w = draw_block(fd, kRngResample, 0u, ep->epoch, 0u);
-  resample_tile(fd.c, fd.N, uniform53(w.x, w.y), fd.idx,
-                reinterpret_cast<unsigned long long*>(&fd.ctrl->n_unique), vb, sh);
+  // u is drawn by the two warps that use it (resample_tile)
+  const double u = threadIdx.x < 64 ? resample_u(fd, ep) : 0.0;
+  resample_tile(fd.c, fd.N, u, fd.idx, reinterpret_cast<unsigned long long*>(&fd.ctrl->n_unique), vb,
+                sh, corners);
 }
 
 // ---------------------------------------------------------------- stage 2
@@ -608,12 +617,22 @@ __global__ void __launch_bounds__(256) k_scan_add(const __grid_constant__ Filter
   scan_add_body(fd, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kResampleThreads) k_resample(const __grid_constant__ FilterDev fd,
+// Two-phase resampling of a large ensemble: every tile corner, one warp each,
+// into the per-block scratch.
+__global__ void __launch_bounds__(256) k_rs_corners(const __grid_constant__ FilterDev fd,
+                                                   const EpochParams* __restrict__ ep) {
+  if (fd.ctrl->status != PF_OK) return;
+  rs_corners_core(fd.c, fd.N, resample_u(fd, ep), ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                  reinterpret_cast<int32_t*>(fd.blk));
+}
+
+__global__ void __launch_bounds__(kResampleThreads, 5) k_resample(const __grid_constant__ FilterDev fd,
                                                                const EpochParams* __restrict__ ep) {
   __shared__ RsShared sh;
   __shared__ double s_chol[kPMax * kPMax];
   if (fd.ctrl->status != PF_OK) return;
-  resample_body(fd, ep, blockIdx.x, sh, s_chol);
+  const int32_t* corners = rs_two_phase(fd.N) ? reinterpret_cast<const int32_t*>(fd.blk) : nullptr;
+  resample_body(fd, ep, blockIdx.x, sh, s_chol, corners);
 }
 
 template <class M, int F>
@@ -760,7 +779,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_batch_resample(
   const BatchTile t = tiles[blockIdx.x];
   const FilterDev& fd = *(fds + t.f);
   if (fd.ctrl->status != PF_OK) return;
-  resample_body(fd, eps[t.f], t.vb, sh, s_chol);
+  resample_body(fd, eps[t.f], t.vb, sh, s_chol, nullptr);
 }
 
 template <int D, int P>
@@ -816,7 +835,7 @@ int phase_blocks(int phase, int ode, int64_t N) {
                                          : (int)((N + kSmallThreads - 1) / kSmallThreads);
     case kPhaseScanTile: return scan_tiles(N);
     case kPhaseScanAdd: return (int)((N + 255) / 256);
-    case kPhaseResample: return (int)((2 * N + kRsTile - 1) / kRsTile);
+    case kPhaseResample: return (int)rs_tiles(N);
     case kPhaseMoments: return moment_blocks(N);
   }
   return 0;
@@ -876,6 +895,7 @@ static cudaError_t launch_epoch_t(const FilterDev& fd, const EpochParams* ep, in
   mark(2);
   k_scan_add<<<(unsigned)phase_blocks(kPhaseScanAdd, M::ODE, N), 256, 0, st>>>(fd);
   mark(3);
+  if (rs_two_phase(N)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
   k_resample<<<(unsigned)phase_blocks(kPhaseResample, M::ODE, N), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
   k2<<<g_small, kSmallThreads, smem, st>>>(fd, ep);
@@ -901,6 +921,7 @@ static cudaError_t launch_epoch_bruss(const FilterDev& fd, const EpochParams* ep
   mark(2);
   k_scan_add<<<(unsigned)phase_blocks(kPhaseScanAdd, ode, N), 256, 0, st>>>(fd);
   mark(3);
+  if (rs_two_phase(N)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
   k_resample<<<(unsigned)phase_blocks(kPhaseResample, ode, N), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
   if ((e = launch_bruss_stage(2, fd, ep, S, st)) != cudaSuccess) return e;
@@ -929,6 +950,7 @@ static cudaError_t launch_epoch_ad(const FilterDev& fd, const EpochParams* ep, i
   mark(2);
   k_scan_add<<<(unsigned)phase_blocks(kPhaseScanAdd, ode, N), 256, 0, st>>>(fd);
   mark(3);
+  if (rs_two_phase(N)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
   k_resample<<<(unsigned)phase_blocks(kPhaseResample, ode, N), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
   if ((e = launch_ad_stage(2, fd, ep, S, st)) != cudaSuccess) return e;
@@ -1029,7 +1051,7 @@ cudaError_t preload_main_kernels() {
       (const void*)k_scan_tile, (const void*)k_scan_add, (const void*)k_resample,
       (const void*)k_theta_mean<2>, (const void*)k_theta_mean<3>, (const void*)k_theta_mean<5>,
       (const void*)k_set_moments, (const void*)k_init<0, 5>, (const void*)k_moments<0, 5>,
-      (const void*)k_xbar, (const void*)k_upload,
+      (const void*)k_xbar, (const void*)k_upload, (const void*)k_rs_corners,
       (const void*)k_batch_init, (const void*)k_batch_scan_tile,
       (const void*)k_batch_scan_add, (const void*)k_batch_resample,
       (const void*)k_batch_moments<2, 2>, (const void*)k_batch_moments<3, 3>,

@@ -42,7 +42,9 @@ constexpr size_t kNaBlockMaxOff = 512;                     // kNaMaxBlocks doubl
 constexpr size_t kNaTileOff = kNaBlockMaxOff + 8 * 512;    // tile totals
 constexpr size_t kNaBoffOff = kNaTileOff + 8 * (size_t)kNaMaxTiles;
 constexpr size_t kNaPmaxOff = kNaBoffOff + 8 * (size_t)kNaMaxTiles;
-constexpr size_t kNaBytes = kNaPmaxOff + 8 * (size_t)kNaMaxTiles;
+constexpr size_t kNaCornerOff = kNaPmaxOff + 8 * (size_t)kNaMaxTiles;  // merge-tile corners
+constexpr int64_t kNaMaxCorners = (2 * kNaMaxParticles + kRsTile - 1) / kRsTile + 1;
+constexpr size_t kNaBytes = kNaCornerOff + 4 * (size_t)kNaMaxCorners;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -53,6 +55,7 @@ struct NaScratch {
   double* tile;
   double* boff;
   double* pmax;
+  int32_t* corners;
 };
 
 static NaScratch carve(unsigned char* base) {
@@ -61,7 +64,8 @@ static NaScratch carve(unsigned char* base) {
                    reinterpret_cast<double*>(base + kNaBlockMaxOff),
                    reinterpret_cast<double*>(base + kNaTileOff),
                    reinterpret_cast<double*>(base + kNaBoffOff),
-                   reinterpret_cast<double*>(base + kNaPmaxOff)};
+                   reinterpret_cast<double*>(base + kNaPmaxOff),
+                   reinterpret_cast<int32_t*>(base + kNaCornerOff)};
 }
 
 __global__ void __launch_bounds__(kNaThreads) k_na_max(const double* __restrict__ lg, int64_t N,
@@ -99,12 +103,19 @@ __global__ void __launch_bounds__(256) k_na_scan_add(int64_t N, double* c, NaScr
   scan_add_core(na_scan_args(nullptr, N, c, sc), (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// the filter's merge-path search (resample_tile), one block per diagonal tile
-__global__ void __launch_bounds__(kResampleThreads) k_na_resample(const double* __restrict__ c,
+// the filter's merge-path search (resample_tile), one block per diagonal tile;
+// corners: found first by k_na_corners (two-phase), or null
+__global__ void __launch_bounds__(kResampleThreads, 5) k_na_resample(const double* __restrict__ c,
                                                                   int64_t N, double u,
-                                                                  int32_t* __restrict__ idx) {
+                                                                  int32_t* __restrict__ idx,
+                                                                  const int32_t* __restrict__ corners) {
   __shared__ RsShared sh;
-  resample_tile(c, N, u, idx, nullptr, blockIdx.x, sh);
+  resample_tile(c, N, u, idx, nullptr, blockIdx.x, sh, corners);
+}
+
+__global__ void __launch_bounds__(256) k_na_corners(const double* __restrict__ c, int64_t N, double u,
+                                                   int32_t* __restrict__ corners) {
+  rs_corners_core(c, N, u, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, corners);
 }
 
 static unsigned resample_blocks(int64_t N) { return (unsigned)((2 * N + kRsTile - 1) / kRsTile); }
@@ -171,7 +182,10 @@ extern "C" pf_status pf_resample_systematic_noalloc(const double* log_g, int64_t
     k_na_scan_tile<<<(unsigned)scan_tile_count(N), kScanThreads, 0, st>>>(
         log_g, N, cumulative, sc);
     k_na_scan_add<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, cumulative, sc);
-    k_na_resample<<<resample_blocks(N), kResampleThreads, 0, st>>>(cumulative, N, u, idx);
+    if (rs_two_phase(N))
+      k_na_corners<<<rs_corner_blocks(N), 256, 0, st>>>(cumulative, N, u, sc.corners);
+    k_na_resample<<<resample_blocks(N), kResampleThreads, 0, st>>>(cumulative, N, u, idx,
+                                                                   rs_two_phase(N) ? sc.corners : nullptr);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {
@@ -198,7 +212,7 @@ extern "C" pf_status pf_systematic_indices(const double* cumulative, int64_t N, 
     return PF_ERR_INVALID_ARG;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  k_na_resample<<<resample_blocks(N), kResampleThreads, 0, st>>>(cumulative, N, u, idx);
+  k_na_resample<<<resample_blocks(N), kResampleThreads, 0, st>>>(cumulative, N, u, idx, nullptr);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_thread_error(std::string("pf_systematic_indices: launch failed: ") + cudaGetErrorString(e));

@@ -225,12 +225,13 @@ __device__ __forceinline__ void scan_add_core(const ScanArgs& a, int64_t k) {
 // FP64 instructions are scarce on this chip (two lanes a clock per SM), so
 // the search compares bit patterns: for non-negative doubles their order as
 // integers is their numeric order.  Each test tau_i < c_k is first decided
-// from the estimate (i + u) * (c_{N-1} / N): the estimate and tau_i each lie
-// within two roundings of the real (i + u) c_{N-1} / N, so for a normal
-// estimate they are under 4 ulps apart and their bit patterns at most 10;
-// a c_k more than kRsUlps patterns away lies on the same side of both, and
-// only closer calls (or tiny estimates) compute tau_i itself.  The one FP64
-// operation per output is the estimate's multiply.
+// from the estimate fma(i, s, u s) with s = c_{N-1} / N and u s both rounded:
+// it lies within three roundings of the real (i + u) c_{N-1} / N (the rounding
+// of u s is at most u / (i + u) <= 1 of a rounding of the whole), tau_i within
+// two, so for a normal estimate they are under 3 ulps apart and their bit
+// patterns at most 6; a c_k more than kRsUlps patterns away lies on the same
+// side of both, and only closer calls (or tiny estimates) compute tau_i
+// itself.  The one FP64 operation per output is the estimate's FMA.
 constexpr int kResampleThreads = 256;
 constexpr int kRsItems = 4;
 constexpr int kRsTile = kResampleThreads * kRsItems;
@@ -239,6 +240,7 @@ constexpr long long kRsTiny = 0x0170000000000000LL;  // bit pattern of 2^-1000
 
 struct RsTau {
   double u, total, step;  // step = total / N, rounded
+  double ustep;           // u * step, rounded
   int64_t N;
 };
 
@@ -255,7 +257,7 @@ __device__ __forceinline__ double rs_tau(int64_t i, const RsTau& t) {
 }
 
 __device__ __forceinline__ long long rs_estimate(int64_t i, const RsTau& t) {
-  return __double_as_longlong(__dmul_rn((double)i + t.u, t.step));
+  return __double_as_longlong(__fma_rn((double)i, t.step, t.ustep));
 }
 
 // tau_i < c, exactly, given e = rs_estimate(i); e and c are bit patterns
@@ -289,13 +291,45 @@ __device__ __forceinline__ int64_t rs_corner(const double* c, int64_t dg, const 
   return lo;
 }
 
+// Tiles of the merge of N taus with N cumulative weights.  Above one wave of
+// tiles the corners are found first, by a launch of one thread per tile
+// boundary (rs_corners_core), so that the dependent loads of all the corner
+// searches overlap instead of heading every tile; below it each block finds
+// its own two (rs_corner), which saves the launch.
+constexpr int kRsTwoPhaseTiles = 4 * 152;
+__host__ __device__ inline int64_t rs_tiles(int64_t N) { return (2 * N + kRsTile - 1) / kRsTile; }
+__host__ __device__ inline bool rs_two_phase(int64_t N) { return rs_tiles(N) > kRsTwoPhaseTiles; }
+// blocks of 256 threads (8 warps) for the corner pass: one warp per corner
+__host__ __device__ inline unsigned rs_corner_blocks(int64_t N) {
+  return (unsigned)((rs_tiles(N) + 1 + 7) / 8);
+}
+
+// Corner v (0 <= v <= rs_tiles(N)) of the merge, taus among its first
+// min(v * kRsTile, 2N) items, by one full warp (rs_corner's 32-probe rounds:
+// a handful of dependent loads instead of a binary search's twenty-odd).
+// Every lane of the warp calls it with the same v.
+__device__ __forceinline__ void rs_corners_core(const double* __restrict__ c, int64_t N, double u,
+                                                int64_t v, int32_t* __restrict__ corners) {
+  if (v > rs_tiles(N)) return;
+  RsTau t;
+  t.u = u;
+  t.total = __ldg(c + (N - 1));
+  t.N = N;
+  t.step = t.total / (double)N;
+  t.ustep = u * t.step;
+  const int64_t dg = v * kRsTile < 2 * N ? v * kRsTile : 2 * N;
+  const int64_t a = rs_corner(c, dg, t);
+  if ((threadIdx.x & 31) == 0) corners[v] = (int32_t)a;
+}
+
 // One block's tile of the merge (blockDim.x == kResampleThreads): writes
 // idx over the tile's taus and, if n_unique is not null, adds the number of
 // outputs whose index differs from the previous output's (the distinct
 // parents) to it.
 __device__ __forceinline__ void resample_tile(const double* __restrict__ c, int64_t N, double u,
                                               int32_t* __restrict__ idx,
-                                              unsigned long long* n_unique, int vb, RsShared& sh) {
+                                              unsigned long long* n_unique, int vb, RsShared& sh,
+                                              const int32_t* __restrict__ corners = nullptr) {
   // the block's tile of the merge: items [d0, d1), taus [a0, a1), c [b0, b1)
   const int64_t d0 = (int64_t)vb * kRsTile;
   const int64_t d1 = d0 + kRsTile < 2 * N ? d0 + kRsTile : 2 * N;
@@ -306,7 +340,9 @@ __device__ __forceinline__ void resample_tile(const double* __restrict__ c, int6
     t.total = __ldg(c + (N - 1));
     t.N = N;
     t.step = t.total / (double)N;
-    const int64_t a = rs_corner(c, wid == 0 ? d0 : d1, t);
+    t.ustep = u * t.step;
+    // the corners: given (two-phase), else a warp-wide search each
+    const int64_t a = corners ? (int64_t)__ldg(corners + vb + wid) : rs_corner(c, wid == 0 ? d0 : d1, t);
     if (lane == 0) {
       sh.corner[wid] = a;
       if (wid == 0) {

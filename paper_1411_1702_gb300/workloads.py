@@ -498,6 +498,9 @@ BY_NAME = {"linear2": linear2, "robertson": robertson, "brusselator": brusselato
            "advdiff20": advdiff20, "advdiff40": advdiff40, "michaelis": michaelis}
 for _lname, _lmm in LMM_NAMES.items():
     BY_NAME["michaelis" + _lname] = functools.partial(michaelis, lmm=_lmm)
+# Robertson at 2^22 particles: the scan and resampling kernels at a size where
+# they move enough data for their bandwidth to show
+BY_NAME["robertson22"] = functools.partial(robertson, N=1 << 22)
 
 
 def get(name: str, **kw) -> Workload:

@@ -130,3 +130,41 @@ def test_same_as_filter_on_its_own_weights(env):
         u = oracle.uniform(w.seed, 0, oracle.RNG_RESAMPLE, 0, k, 0)
         np.testing.assert_array_equal(_gpu(pf, torch, work["c"], u), work["idx"])
     g.close()
+
+
+def test_two_phase_paths_equal_oracle(env):
+    # above one wave of merge tiles (N > 4 * 152 * 512) the filter and the
+    # allocation-free call find every tile corner in a launch of their own;
+    # their indices must equal the oracle's and the one-launch form's
+    pf, torch = env
+    rng = np.random.default_rng(23)
+    N = (1 << 20) + 4099
+    lg = -0.5 * (rng.standard_normal(N) * 4.0) ** 2
+    lg[rng.random(N) < 0.3] = -np.inf
+    u = float(rng.random())
+    d_lg = torch.tensor(lg, dtype=torch.float64, device="cuda")
+    d_c = torch.empty(N, dtype=torch.float64, device="cuda")
+    d_idx = torch.full((N,), -7, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    pf.pf_resample_systematic_noalloc(d_lg.data_ptr(), N, u, d_c.data_ptr(), d_idx.data_ptr(),
+                                      stream or None)
+    torch.cuda.synchronize()
+    c = d_c.cpu().numpy()
+    idx = d_idx.cpu().numpy()
+    np.testing.assert_array_equal(idx, oracle.resample_systematic(c, u))
+    np.testing.assert_array_equal(idx, _gpu(pf, torch, c, u))
+
+
+def test_filter_two_phase_resampling_equals_oracle(env):
+    # a Robertson filter large enough for the two-launch resampling
+    pf, torch = env
+    from paper_1411_1702_gb300 import workloads as W
+    w = W.robertson(N=400000, T=2)
+    g = pf.Filter.from_workload(w)
+    for k in range(w.T):
+        g.pf_assimilate(w.t_obs[k], w.y_obs[k])
+        work = g.pf_get_work()
+        u = oracle.uniform(w.seed, 0, oracle.RNG_RESAMPLE, 0, k, 0)
+        np.testing.assert_array_equal(work["idx"], oracle.resample_systematic(work["c"], u))
+        assert g.pf_stats()["unique_parents"] == len(np.unique(work["idx"]))
+    g.close()
