@@ -167,6 +167,21 @@ typedef struct {
 pf_status pf_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
                     const pf_prior* prior, const pf_options* opt, pf_filter** out);
 
+/* Device bytes a filter of this shape lays out: its ensembles (two
+ * ping-pong copies of x, h1, h2, phi, w), work arrays and control block in one
+ * block.  Host-only.  Errors: INVALID_ARG (NULL bytes, unsupported ode, d < 1,
+ * p outside 1..5, N < 1). */
+pf_status pf_device_bytes(pf_ode ode, int d, int p, int64_t N, size_t* bytes);
+/* pf_create in caller-owned device memory: the filter lays all its device
+ * arrays out in device_mem (at least pf_device_bytes(ode, d, p, N) bytes,
+ * 256-byte aligned, on the current device) and never frees it; the caller
+ * keeps it alive and unused elsewhere until pf_destroy returns.  Everything
+ * else is as pf_create.  Errors: as pf_create, and INVALID_ARG for a NULL,
+ * misaligned or too small device_mem (checked before any device work). */
+pf_status pf_create_with_buffers(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
+                                 const pf_prior* prior, const pf_options* opt, void* device_mem,
+                                 size_t device_bytes, pf_filter** out);
+
 /* Assimilate one observation y_k (m host doubles) at time t_k > the previous
  * observation time: Steps 2-6 of Algorithm 1 (shrink, propagate, first-stage
  * weights, systematic resampling, proliferation, repropagation with the

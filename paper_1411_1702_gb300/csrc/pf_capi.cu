@@ -4,6 +4,7 @@
 // arithmetic on particles runs in the kernels of pf_kernels.cu.
 #include <mutex>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -353,18 +354,43 @@ pf_status pf_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
   return filter_create(ode, d, p, N, lmm, dt, prior, opt, nullptr, out);
 }
 
+pf_status pf_device_bytes(pf_ode ode, int d, int p, int64_t N, size_t* bytes) {
+  if (!bytes) return fail(nullptr, PF_ERR_INVALID_ARG, "bytes is NULL");
+  if (!pfg::ode_supported(ode) || d < 1 || p < 1 || p > pfg::kPMax || N < 1)
+    return fail(nullptr, PF_ERR_INVALID_ARG, "need a supported ode, d >= 1, 1 <= p <= 5, N >= 1");
+  *bytes = pfg::filter_device_bytes(ode, d, p, N);
+  return PF_OK;
+}
+
+pf_status pf_create_with_buffers(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
+                                 const pf_prior* prior, const pf_options* opt, void* device_mem,
+                                 size_t device_bytes, pf_filter** out) {
+  const pfg::NvtxRange nvtx_range("pf_create_with_buffers");
+  if (!device_mem) return fail(nullptr, PF_ERR_INVALID_ARG, "device_mem is NULL");
+  return filter_create(ode, d, p, N, lmm, dt, prior, opt, nullptr, out, device_mem, device_bytes);
+}
+
 }  // extern "C"
 
 namespace pfg {
 
 pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
                         const pf_prior* prior, const pf_options* opt, cudaMemPool_t pool,
-                        pf_filter** out) {
+                        pf_filter** out, void* ext_mem, size_t ext_bytes) {
   if (!out) return fail(nullptr, PF_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   {
     const pf_status cs = check_create_args(ode, d, p, N, lmm, dt, prior, opt);
     if (cs != PF_OK) return cs;
+  }
+  if (ext_mem) {
+    if ((reinterpret_cast<uintptr_t>(ext_mem) & 255u) != 0)
+      return fail(nullptr, PF_ERR_INVALID_ARG, "device_mem must be 256-byte aligned");
+    const size_t need = filter_device_bytes(ode, d, p, N);
+    if (ext_bytes < need)
+      return fail(nullptr, PF_ERR_INVALID_ARG,
+                  "device_bytes " + std::to_string(ext_bytes) + " < the " + std::to_string(need) +
+                      " bytes pf_device_bytes reports");
   }
 
   {
@@ -413,8 +439,14 @@ pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double 
   }
   f->dbytes = layout(f, nullptr);
   f->pool = pool;
-  e = pool ? cudaMallocFromPoolAsync(&f->dmem, f->dbytes, pool, f->stream)
-           : cudaMalloc(&f->dmem, f->dbytes);
+  if (ext_mem) {
+    f->dmem = ext_mem;
+    f->ext_mem = true;
+    e = cudaSuccess;
+  } else {
+    e = pool ? cudaMallocFromPoolAsync(&f->dmem, f->dbytes, pool, f->stream)
+             : cudaMalloc(&f->dmem, f->dbytes);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     f->dmem = nullptr;
@@ -463,7 +495,7 @@ void pf_destroy(pf_filter* f) {
     delete f->ep_host;
     delete f->ctrl_host;
   } else {
-    if (f->dmem) cudaFree(f->dmem);
+    if (f->dmem && !f->ext_mem) cudaFree(f->dmem);  // caller memory stays the caller's
     if (f->ep_host) cudaFreeHost(f->ep_host);
     if (f->ctrl_host) cudaFreeHost(f->ctrl_host);
     if (f->xbar_host) cudaFreeHost(f->xbar_host);

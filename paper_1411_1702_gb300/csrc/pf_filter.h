@@ -45,6 +45,7 @@ struct pf_filter {
   // CUDA resources
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  bool ext_mem = false;                    // dmem belongs to the caller (pf_create_with_buffers)
   cudaMemPool_t pool = nullptr;           // dmem is stream-ordered from this pool
   void* dmem = nullptr;
   size_t dbytes = 0;
@@ -88,10 +89,11 @@ pf_status check_create_args(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, dou
 // pf_create with the device allocation taken, stream-ordered, from `pool` and
 // pageable host staging, so that neither creation nor pf_destroy makes an
 // implicitly device-wide synchronising call (the server's sessions).  A NULL
-// pool is pf_create.
+// pool is pf_create.  ext_mem (with ext_bytes) is caller-owned device memory
+// the filter lays itself out in instead (pf_create_with_buffers).
 pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
                         const pf_prior* prior, const pf_options* opt, cudaMemPool_t pool,
-                        pf_filter** out);
+                        pf_filter** out, void* ext_mem = nullptr, size_t ext_bytes = 0);
 // Device bytes of a filter of this shape (its single allocation).
 size_t filter_device_bytes(int ode, int d, int p, int64_t N);
 // History after an epoch with parameter block ep.

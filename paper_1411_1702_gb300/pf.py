@@ -34,7 +34,7 @@ ABI_SYMBOLS = [
     "pf_load_observations", "pf_run", "pf_synchronize", "pf_reset", "pf_get_ensemble",
     "pf_set_ensemble", "pf_set_moments", "pf_get_work", "pf_get_history", "pf_set_history",
     "pf_substep_table", "pf_version", "pf_kernel_times", "pf_resample_systematic_noalloc",
-    "pf_systematic_indices",
+    "pf_systematic_indices", "pf_device_bytes", "pf_create_with_buffers",
     "pf_batch_create", "pf_batch_assimilate", "pf_batch_stats", "pf_batch_last_error",
     "pf_batch_destroy", "pf_server_create", "pf_server_open", "pf_server_submit",
     "pf_server_step", "pf_server_drain", "pf_server_close", "pf_server_session",
@@ -109,6 +109,11 @@ def load(path: str = LIB_PATH):
     sig = {
         "pf_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int, C.c_double,
                                 C.POINTER(Prior), C.POINTER(Options), C.POINTER(C.c_void_p)]),
+        "pf_device_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64,
+                                      C.POINTER(C.c_size_t)]),
+        "pf_create_with_buffers": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int,
+                                             C.c_double, C.POINTER(Prior), C.POINTER(Options),
+                                             C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]),
         "pf_assimilate": (C.c_int, [C.c_void_p, C.c_double, _dp]),
         "pf_estimates": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
         "pf_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
@@ -199,6 +204,13 @@ def pf_systematic_indices(cumulative_ptr, N, u, idx_ptr, stream=None):
     _check(st, None)
 
 
+def pf_device_bytes(ode, d, p, N):
+    """Device bytes a filter of this shape lays out (pf_create_with_buffers)."""
+    out = C.c_size_t()
+    _check(load().pf_device_bytes(int(ode), int(d), int(p), int(N), C.byref(out)), None)
+    return out.value
+
+
 def pf_fp64_fma_rate(ms=200.0, stream=None):
     """Sustained FP64 FMA throughput of the current GPU in TFLOP/s."""
     out = C.c_double()
@@ -224,7 +236,7 @@ class Filter:
 
     def __init__(self, ode, d, p, N, lmm, dt, prior_kind, prior_lo, prior_hi, x0, t0, *,
                  a, newton_iters, spacing, substeps, q0, history, transform, obs_idx, noise,
-                 sigma, kappa, seed, filter_id=0, stream=None, timing=False):
+                 sigma, kappa, seed, filter_id=0, stream=None, timing=False, device_buffer=None):
         L = load()
         self._keep = []
         kind = (C.c_int * len(prior_kind))(*[int(k) for k in prior_kind])
@@ -239,20 +251,33 @@ class Filter:
                      float(kappa), int(seed), int(filter_id), C.c_void_p(stream) if stream else None,
                      1 if timing else 0)
         h = C.c_void_p()
-        st = L.pf_create(int(ode), int(d), int(p), int(N), int(lmm), float(dt), C.byref(pr),
-                         C.byref(op), C.byref(h))
+        if device_buffer is None:
+            st = L.pf_create(int(ode), int(d), int(p), int(N), int(lmm), float(dt), C.byref(pr),
+                             C.byref(op), C.byref(h))
+        else:
+            # caller-owned device memory: (address, bytes), or an object with
+            # data_ptr() and nbytes (a CUDA tensor), kept referenced here
+            if hasattr(device_buffer, "data_ptr"):
+                ptr, nbytes = device_buffer.data_ptr(), device_buffer.nbytes
+            else:
+                ptr, nbytes = device_buffer
+            self._keep.append(device_buffer)
+            st = L.pf_create_with_buffers(int(ode), int(d), int(p), int(N), int(lmm), float(dt),
+                                          C.byref(pr), C.byref(op), C.c_void_p(int(ptr)),
+                                          int(nbytes), C.byref(h))
         _check(st, None)
         self._h = h
         self.ode, self.d, self.p, self.N, self.m = ode, d, p, N, len(obs_idx)
 
     @classmethod
-    def from_workload(cls, w, N=None, stream=None, seed=None, filter_id=0, timing=False):
+    def from_workload(cls, w, N=None, stream=None, seed=None, filter_id=0, timing=False,
+                      device_buffer=None):
         return cls(w.ode, w.d, w.p, int(N if N is not None else w.N), w.lmm, w.dt, w.prior_kind,
                    w.prior_lo, w.prior_hi, w.x0, w.t0, a=w.a, newton_iters=w.newton_iters,
                    spacing=w.spacing, substeps=w.substeps, q0=w.q0, history=w.history,
                    transform=w.transform, obs_idx=w.obs_idx, noise=w.noise, sigma=w.sigma,
                    kappa=w.kappa, seed=w.seed if seed is None else seed, filter_id=filter_id,
-                   stream=stream, timing=timing)
+                   stream=stream, timing=timing, device_buffer=device_buffer)
 
     @classmethod
     def borrowed(cls, handle, ode, d, p, N, m):

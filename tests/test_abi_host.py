@@ -88,6 +88,33 @@ def test_systematic_indices_rejects_arguments_before_gpu(pf, bad):
     assert ei.value.status == pf.PF_ERR_INVALID_ARG
 
 
+def test_device_bytes_cover_the_ensembles(pf):
+    w = W.robertson(N=8, T=2)
+    a = pf.pf_device_bytes(w.ode, w.d, w.p, 1000)
+    b = pf.pf_device_bytes(w.ode, w.d, w.p, 2000)
+    # two ping-pong copies of x, h1, h2 (d each), phi (p) and w, at least
+    assert a >= 8 * 1000 * 2 * (3 * w.d + w.p + 1)
+    assert b > a
+    for bad in (dict(ode=9), dict(d=0), dict(p=0), dict(p=6), dict(N=0)):
+        args = dict(ode=w.ode, d=w.d, p=w.p, N=1000)
+        args.update(bad)
+        with pytest.raises(pf.PfError) as ei:
+            pf.pf_device_bytes(**args)
+        assert ei.value.status == pf.PF_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("case", ["null", "misaligned", "small"])
+def test_create_with_buffers_rejects_memory_before_gpu(pf, case):
+    # the buffer checks come before any device work, so the (never touched)
+    # addresses may be placeholders
+    w = W.robertson(N=64, T=2)
+    need = pf.pf_device_bytes(w.ode, w.d, w.p, 64)
+    buf = {"null": (0, need), "misaligned": (0x100080, need), "small": (0x100000, need - 1)}[case]
+    with pytest.raises(pf.PfError) as ei:
+        pf.Filter.from_workload(w, N=64, device_buffer=buf)
+    assert ei.value.status == pf.PF_ERR_INVALID_ARG
+
+
 def _compare_tables(w, t_prev, t_next, depth, h1, h2, pf):
     cfg = oracle.make_config(w)
     tab, S, dout = oracle.build_substeps(cfg, t_prev, t_next, depth, h1, h2)
