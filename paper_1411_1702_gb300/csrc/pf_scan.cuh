@@ -9,9 +9,6 @@ namespace pfg {
 struct SumOp {
   __device__ static double apply(double a, double b) { return a + b; }
 };
-struct MaxOp {
-  __device__ static double apply(double a, double b) { return fmax(a, b); }
-};
 
 // Exclusive block scan with identity 0 (all inputs are >= 0); total gets the
 // inclusive result of the last thread.  s_warp needs 33 doubles.
