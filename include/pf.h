@@ -206,6 +206,8 @@ typedef struct {
   double last_epoch_ms;  /* device time of the last synchronous epoch      */
   int64_t h2d_bytes;     /* host-to-device bytes copied since creation     */
   int64_t d2h_bytes;     /* device-to-host bytes copied since creation     */
+  double ess_stage1;     /* (sum g)^2 / sum g^2 of the last epoch's first-stage
+                            weights g (Step 3a), 0 before the first epoch   */
 } pf_stats_t;
 pf_status pf_stats(const pf_filter* f, pf_stats_t* out);
 

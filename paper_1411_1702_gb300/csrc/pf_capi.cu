@@ -117,6 +117,7 @@ static size_t layout(pf_filter* f, char* base) {
   f->fd.blk = (double*)take(sizeof(double) * max_grid_blocks(N));
   f->fd.boff = (double*)take(sizeof(double) * scan_tiles(N));
   f->fd.pmax = (double*)take(sizeof(double) * scan_tiles(N));
+  f->fd.tsq = (double*)take(sizeof(double) * scan_tiles(N));
   f->fd.part = (double*)take(sizeof(double) * kMomentBlocks * f->fd.nrec);
   // model work arrays: the Brusselator's stage buffers; the 2D system's
   // committed weights exp(lw - max lw), which the moments store for x-bar
@@ -592,6 +593,7 @@ pf_status pf_stats(const pf_filter* cf, pf_stats_t* out) {
   out->last_epoch_ms = f->last_ms;
   out->h2d_bytes = f->h2d_bytes;
   out->d2h_bytes = f->d2h_bytes;
+  out->ess_stage1 = (h->g_sq > 0.0) ? h->c_total * h->c_total / h->g_sq : 0.0;
   return PF_OK;
 }
 

@@ -264,7 +264,7 @@ __device__ __forceinline__ void stage1_body(const FilterDev& fd, const EpochPara
 __device__ __forceinline__ ScanArgs scan_args(const FilterDev& fd) {
   Ctrl* ctrl = fd.ctrl;
   return ScanArgs{fd.lg, fd.N, ctrl->lg_max, fd.c, fd.blk, fd.boff, fd.pmax, fd.ticket + 1,
-                  &ctrl->c_total};
+                  &ctrl->c_total, fd.tsq, &ctrl->g_sq};
 }
 
 __device__ __forceinline__ void scan_tile_body(const FilterDev& fd, int vb, int vg, double* s_warp,
@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_batch_stage(const FilterDev* 
   else stage2_body<M, F>(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_batch_scan_tile(const FilterDev* __restrict__ fds,
+__global__ void __launch_bounds__(kScanThreads, 4) k_batch_scan_tile(const FilterDev* __restrict__ fds,
                                                                 const BatchTile* __restrict__ tiles) {
   __shared__ double s_warp[33];
   __shared__ int s_flag;

@@ -70,7 +70,7 @@ class Stats(C.Structure):
     _fields_ = [("epochs", C.c_int64), ("ess", C.c_double), ("log_weight_sum", C.c_double),
                 ("unique_parents", C.c_int64), ("nonfinite", C.c_int64),
                 ("theta_mean", C.c_double * 8), ("last_epoch_ms", C.c_double),
-                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("ess_stage1", C.c_double)]
 
 
 class BatchStats(C.Structure):
@@ -320,7 +320,7 @@ class Filter:
         return dict(epochs=s.epochs, ess=s.ess, log_weight_sum=s.log_weight_sum,
                     unique_parents=s.unique_parents, nonfinite=s.nonfinite,
                     theta_mean=np.array(s.theta_mean[:self.p]), last_epoch_ms=s.last_epoch_ms,
-                    h2d_bytes=s.h2d_bytes, d2h_bytes=s.d2h_bytes)
+                    h2d_bytes=s.h2d_bytes, d2h_bytes=s.d2h_bytes, ess_stage1=s.ess_stage1)
 
     def pf_kernel_times(self):
         """Per-kernel device ms and launch counts since the last call."""

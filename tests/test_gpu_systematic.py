@@ -168,3 +168,23 @@ def test_filter_two_phase_resampling_equals_oracle(env):
         np.testing.assert_array_equal(work["idx"], oracle.resample_systematic(work["c"], u))
         assert g.pf_stats()["unique_parents"] == len(np.unique(work["idx"]))
     g.close()
+
+
+def test_first_stage_ess_matches_the_log_weights(env):
+    # pf_stats' ess_stage1 is (sum g)^2 / sum g^2 of the epoch's first-stage
+    # weights g = exp(lg - max lg); here from the filter's own lg
+    pf, torch = env
+    from paper_1411_1702_gb300 import workloads as W
+    for name, N in (("robertson", 5000), ("brusselator", 300)):
+        w = W.get(name, N=N)
+        g = pf.Filter.from_workload(w)
+        assert g.pf_stats()["ess_stage1"] == 0.0
+        for k in range(3):
+            g.pf_assimilate(w.t_obs[k], w.y_obs[k])
+            lg = g.pf_get_work()["lg"]
+            fin = np.isfinite(lg)
+            e = np.exp(lg[fin] - lg[fin].max())
+            want = e.sum() ** 2 / (e * e).sum()
+            assert 1.0 <= want <= N
+            assert g.pf_stats()["ess_stage1"] == pytest.approx(want, rel=1e-12)
+        g.close()
