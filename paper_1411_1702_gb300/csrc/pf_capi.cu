@@ -117,7 +117,7 @@ static size_t layout(pf_filter* f, char* base) {
   f->fd.blk = (double*)take(sizeof(double) * max_grid_blocks(N));
   f->fd.boff = (double*)take(sizeof(double) * scan_tiles(N));
   f->fd.pmax = (double*)take(sizeof(double) * scan_tiles(N));
-  f->fd.tsq = (double*)take(sizeof(double) * scan_tiles(N));
+  f->fd.tsq = (double*)take(sizeof(double) * kMomentBlocks);
   f->fd.part = (double*)take(sizeof(double) * kMomentBlocks * f->fd.nrec);
   // model work arrays: the Brusselator's stage buffers; the 2D system's
   // committed weights exp(lw - max lw), which the moments store for x-bar
@@ -580,6 +580,8 @@ pf_status pf_stats(const pf_filter* cf, pf_stats_t* out) {
   pf_filter* f = const_cast<pf_filter*>(cf);
   if (!f || !out) return fail(f, PF_ERR_INVALID_ARG, "NULL argument");
   PF_CUDA(f, launch_theta_mean(f->fd, f->stream));
+  const bool have_lg = f->hist.epochs > 0;  // the first-stage weights of an epoch exist
+  if (have_lg) PF_CUDA(f, launch_stage1_ess(f->fd, f->stream));
   pf_status st = read_ctrl(f);
   if (st != PF_OK) return st;
   const Ctrl* h = f->ctrl_host;
@@ -593,7 +595,7 @@ pf_status pf_stats(const pf_filter* cf, pf_stats_t* out) {
   out->last_epoch_ms = f->last_ms;
   out->h2d_bytes = f->h2d_bytes;
   out->d2h_bytes = f->d2h_bytes;
-  out->ess_stage1 = (h->g_sq > 0.0) ? h->c_total * h->c_total / h->g_sq : 0.0;
+  out->ess_stage1 = (have_lg && h->g_sq > 0.0) ? h->c_total * h->c_total / h->g_sq : 0.0;
   return PF_OK;
 }
 

@@ -95,7 +95,7 @@ struct Ctrl {
   double lg_max;        // max log fitness weight of the running epoch
   double lw_max;        // max new log weight of the running epoch
   double c_total;       // total of the cumulative fitness weights
-  double g_sq;          // sum of the squared fitness weights g (ESS of Step 3a)
+  double g_sq;          // sum of the squared fitness weights g (pf_stats, on demand)
   int64_t n_unique;
   int64_t n_nonfinite;
 };
@@ -127,7 +127,7 @@ struct FilterDev {
   double* blk;      // per-block scratch (max or sums), >= max grid size
   double* boff;     // per-tile offsets of the scan
   double* pmax;     // per-tile running maximum of the earlier tiles' last c
-  double* tsq;      // per-tile sums of g^2 (first-stage ESS)
+  double* tsq;      // per-block sums of g^2 (first-stage ESS, kMomentBlocks)
   double* part;     // moment partial records, kMomentBlocks * nrec
   double* wk;       // model work arrays (Brusselator: r, predictor, error sums; 2D system: weights)
   unsigned* ticket; // 4 counters for the last-block pattern

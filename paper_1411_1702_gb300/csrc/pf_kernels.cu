@@ -264,7 +264,7 @@ __device__ __forceinline__ void stage1_body(const FilterDev& fd, const EpochPara
 __device__ __forceinline__ ScanArgs scan_args(const FilterDev& fd) {
   Ctrl* ctrl = fd.ctrl;
   return ScanArgs{fd.lg, fd.N, ctrl->lg_max, fd.c, fd.blk, fd.boff, fd.pmax, fd.ticket + 1,
-                  &ctrl->c_total, fd.tsq, &ctrl->g_sq};
+                  &ctrl->c_total};
 }
 
 __device__ __forceinline__ void scan_tile_body(const FilterDev& fd, int vb, int vg, double* s_warp,
@@ -685,6 +685,34 @@ __global__ void __launch_bounds__(kMomentThreads) k_theta_mean(const __grid_cons
   if (threadIdx.x < P) ctrl->theta_mean[threadIdx.x] = s_tot[threadIdx.x];
 }
 
+// The ESS of the last epoch's first-stage weights for pf_stats (on demand,
+// off the epoch): sum g^2 with g = exp(lg - lg_max) formed as the scan forms
+// it, block partials into the per-block scratch, the last block adds them.
+__global__ void __launch_bounds__(kMomentThreads) k_stage1_ess(const __grid_constant__ FilterDev fd) {
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  const double M = fd.ctrl->lg_max;
+  double sq = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < fd.N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double g = scan_weight(fd.lg[k], M);
+    sq = fma(g, g, sq);
+  }
+  sq = block_sum(sq, s_red);
+  if (threadIdx.x == 0) fd.tsq[blockIdx.x] = sq;
+  if (elect_last_block(fd.ticket + 4, &s_flag, gridDim.x)) {
+    double q = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) q += __ldcg(fd.tsq + b);
+    q = block_sum(q, s_red);
+    if (threadIdx.x == 0) fd.ctrl->g_sq = q;
+  }
+}
+
+cudaError_t launch_stage1_ess(const FilterDev& fd, cudaStream_t st) {
+  k_stage1_ess<<<moment_blocks(fd.N), kMomentThreads, 0, st>>>(fd);
+  return cudaGetLastError();
+}
+
 __global__ void k_set_moments(const __grid_constant__ FilterDev fd) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double L[kPMax * kPMax];
@@ -753,7 +781,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_batch_stage(const FilterDev* 
   else stage2_body<M, F>(fd, ep, t.vb, vg, s_sc, s_red, &s_flag);
 }
 
-__global__ void __launch_bounds__(kScanThreads, 4) k_batch_scan_tile(const FilterDev* __restrict__ fds,
+__global__ void __launch_bounds__(kScanThreads) k_batch_scan_tile(const FilterDev* __restrict__ fds,
                                                                 const BatchTile* __restrict__ tiles) {
   __shared__ double s_warp[33];
   __shared__ int s_flag;
@@ -1052,6 +1080,7 @@ cudaError_t preload_main_kernels() {
       (const void*)k_theta_mean<2>, (const void*)k_theta_mean<3>, (const void*)k_theta_mean<5>,
       (const void*)k_set_moments, (const void*)k_init<0, 5>, (const void*)k_moments<0, 5>,
       (const void*)k_xbar, (const void*)k_upload, (const void*)k_rs_corners,
+      (const void*)k_stage1_ess,
       (const void*)k_batch_init, (const void*)k_batch_scan_tile,
       (const void*)k_batch_scan_add, (const void*)k_batch_resample,
       (const void*)k_batch_moments<2, 2>, (const void*)k_batch_moments<3, 3>,

@@ -48,6 +48,8 @@ cudaError_t launch_epoch(int ode, const FilterDev& fd, const EpochParams* ep, in
                          cudaEvent_t* marks = nullptr);
 // Recompute the Cholesky factor after the host set phibar and C.
 cudaError_t launch_set_moments(const FilterDev& fd, cudaStream_t st);
+// sum of the squared first-stage weights of the last epoch into Ctrl::g_sq
+cudaError_t launch_stage1_ess(const FilterDev& fd, cudaStream_t st);
 
 // Host-to-device copy of at most kUploadBytes bytes carried as a kernel
 // parameter: never synchronises, whatever memory src is in (a copy from

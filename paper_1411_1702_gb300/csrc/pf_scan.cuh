@@ -140,8 +140,6 @@ struct ScanArgs {
   double* pmax;      // per-tile floor (running maximum of the earlier tiles' last values)
   unsigned* ticket;  // completion counter of the tile pass
   double* c_total;   // optional: c_{N-1}
-  double* tile_sq;   // optional: per-tile sums of g^2 (with g_sq)
-  double* g_sq;      // optional: sum of g^2 (the first-stage ESS is c_{N-1}^2 / g_sq)
 };
 
 // Tile vb of vg: tile-local cumulative sums; the last tile to finish turns the
@@ -151,14 +149,12 @@ __device__ __forceinline__ void scan_tile_core(const ScanArgs& a, int vb, int vg
   const int items = scan_items(a.N);
   const int64_t base = (int64_t)vb * kScanThreads * items + (int64_t)threadIdx.x * items;
   double v[kScanItemsMax];
-  double run = 0.0, sq = 0.0;
+  double run = 0.0;
 #pragma unroll
   for (int j = 0; j < kScanItemsMax; ++j) {
     if (j < items) {
       const int64_t k = base + j;
-      const double g = (k < a.N) ? scan_weight(a.lg[k], a.M) : 0.0;
-      run += g;
-      sq = fma(g, g, sq);
+      run += (k < a.N) ? scan_weight(a.lg[k], a.M) : 0.0;
     }
     v[j] = run;
   }
@@ -174,10 +170,6 @@ __device__ __forceinline__ void scan_tile_core(const ScanArgs& a, int vb, int vg
     if (j < items && k < a.N) a.c[k] = max_nonneg(v[j], floor_prev);
   }
   if (threadIdx.x == 0) a.tile[vb] = tile_last;
-  if (a.tile_sq) {
-    const double tsq = block_sum(sq, s_warp);
-    if (threadIdx.x == 0) a.tile_sq[vb] = tsq;
-  }
   if (elect_last_block(a.ticket, s_flag, (unsigned)vg)) {
     // tile offsets boff_b = sum of earlier tile totals, and the running maximum
     // pmax_b of the earlier tiles' last values boff_b' + T_b'
@@ -202,12 +194,6 @@ __device__ __forceinline__ void scan_tile_core(const ScanArgs& a, int vb, int vg
       pm = max_nonneg(pm, a.boff[b] + __ldcg(a.tile + b));
     }
     if (threadIdx.x == 0 && a.c_total) *a.c_total = gmax;
-    if (a.tile_sq) {
-      double q = 0.0;
-      for (int b = b0; b < b0 + chunk && b < nb; ++b) q += __ldcg(a.tile_sq + b);
-      q = block_sum(q, s_warp);
-      if (threadIdx.x == 0) *a.g_sq = q;
-    }
   }
 }
 
