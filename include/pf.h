@@ -214,8 +214,11 @@ pf_status pf_stats(const pf_filter* f, pf_stats_t* out);
 /* Per-kernel device time of the epochs run since the last call (requires
  * pf_options.timing).  Slot k of ms[] and launches[] (n entries, n >= 6):
  * 0 stage 1 (shrink, propagate, first-stage weights), 1 scan tiles, 2 scan
- * offsets, 3 systematic resampling, 4 stage 2 (proliferate, repropagate,
- * innovation, reweight), 5 moments and commit.  Waits for the filter's stream,
+ * offsets (0: resampling applies the tile offsets as it reads the cumulative
+ * weights, so this slot has no launch), 3 systematic resampling (with the
+ * corner pass above one wave of merge tiles), 4 stage 2 (proliferate,
+ * repropagate, innovation, reweight), 5 moments and commit (and the 2D
+ * system's state mean).  Waits for the filter's stream,
  * then resets the accumulators.  Errors: INVALID_ARG (n < 6), STATE (timing
  * off), CUDA. */
 #define PF_KERNEL_SLOTS 6

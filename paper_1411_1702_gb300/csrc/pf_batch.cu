@@ -142,7 +142,7 @@ struct pf_batch {
   BatchTile* tiles_pin = nullptr;        // pinned staging of the tile upload (tiles_cap)
   Range stage[2][kStageGroups];
   Range moments[kMomentGroups];
-  Range scan_tile, scan_add, resample;
+  Range scan_tile, resample;
   int* slots_dev = nullptr;              // active slots of the epoch in flight
   int* slots_pin = nullptr;              // pinned staging (cap)
   int64_t* status_dev = nullptr;
@@ -220,7 +220,6 @@ static void build_tiles(pf_batch* b, const std::vector<char>& active, int order_
   };
   for (int g = 0; g < kStageGroups; ++g) b->stage[0][g] = add(kPhaseStage1, g);
   b->scan_tile = add(kPhaseScanTile, -1);
-  b->scan_add = add(kPhaseScanAdd, -1);
   b->resample = add(kPhaseResample, -1);
   for (int g = 0; g < kStageGroups; ++g) b->stage[1][g] = add(kPhaseStage2, g);
   for (int g = 0; g < kMomentGroups; ++g) b->moments[g] = add(kPhaseMoments, g);
@@ -286,7 +285,6 @@ static cudaError_t launch_phases(pf_batch* b, size_t smem, const Shape& shape, b
   };
   per_model(kPhaseStage1, b->stage[0], kStageGroups, kGroupOde, kGroupLmm);
   run(kPhaseScanTile, 0, 0, b->scan_tile, b->stream);
-  run(kPhaseScanAdd, 0, 0, b->scan_add, b->stream);
   run(kPhaseResample, 0, 0, b->resample, b->stream);
   per_model(kPhaseStage2, b->stage[1], kStageGroups, kGroupOde, kGroupLmm);
   if (with_moments) per_model(kPhaseMoments, b->moments, kMomentGroups, kMomentOde, nullptr);

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "pf_filter.h"
+#include "pf_scan.cuh"
 
 using namespace pfg;
 
@@ -606,8 +607,12 @@ pf_status pf_kernel_times(pf_filter* f, double* ms, int64_t* launches, int n) {
   PF_CUDA(f, cudaStreamSynchronize(f->stream));
   for (cudaEvent_t* m : f->mark_pending) {
     for (int i = 0; i < kEpochKernels; ++i) {
+      // the scan_add slot has no launch and no event of its own (an empty
+      // pair of events still costs the device about 2 us): 0, and the
+      // resampling phase runs from the scan's end mark
       float t = 0.0f;
-      PF_CUDA(f, cudaEventElapsedTime(&t, m[i], m[i + 1]));
+      if (i != kPhaseScanAdd)
+        PF_CUDA(f, cudaEventElapsedTime(&t, m[i == kPhaseResample ? kPhaseScanAdd : i], m[i + 1]));
       f->kernel_ms[i] += t;
       f->kernel_launches[i] += 1;
     }
@@ -796,6 +801,14 @@ pf_status pf_set_moments(pf_filter* f, const double* phibar, const double* C) {
   return PF_OK;
 }
 
+// The maximum of two doubles >= +0 by their bit patterns (max_nonneg's rule).
+static double max_nonneg_host(double a, double b) {
+  long long x, y;
+  std::memcpy(&x, &a, sizeof x);
+  std::memcpy(&y, &b, sizeof y);
+  return x > y ? a : b;
+}
+
 pf_status pf_get_work(const pf_filter* cf, double* loglik1, double* log_g, double* cumulative,
                       int32_t* idx) {
   pf_filter* f = const_cast<pf_filter*>(cf);
@@ -804,10 +817,25 @@ pf_status pf_get_work(const pf_filter* cf, double* loglik1, double* log_g, doubl
   const size_t nb = sizeof(double) * f->N;
   if (loglik1) PF_CUDA(f, copy_sync(f, loglik1, f->fd.ll1, nb, cudaMemcpyDeviceToHost));
   if (log_g) PF_CUDA(f, copy_sync(f, log_g, f->fd.lg, nb, cudaMemcpyDeviceToHost));
-  if (cumulative) PF_CUDA(f, copy_sync(f, cumulative, f->fd.c, nb, cudaMemcpyDeviceToHost));
+  size_t tile_bytes = 0;
+  if (cumulative) {
+    // c as the scan leaves it (tile-local sums) with the tile offsets and
+    // floors, combined here exactly as the device reads them (CumTiles)
+    const int nt = scan_tiles(f->N);
+    std::vector<double> boff(nt), pmax(nt);
+    PF_CUDA(f, copy_sync(f, cumulative, f->fd.c, nb, cudaMemcpyDeviceToHost));
+    PF_CUDA(f, copy_sync(f, boff.data(), f->fd.boff, sizeof(double) * nt, cudaMemcpyDeviceToHost));
+    PF_CUDA(f, copy_sync(f, pmax.data(), f->fd.pmax, sizeof(double) * nt, cudaMemcpyDeviceToHost));
+    tile_bytes = 2 * sizeof(double) * (size_t)nt;
+    const int64_t len = scan_tile_len(f->N);
+    for (int64_t k = 0; k < f->N; ++k) {
+      const int64_t t = k / len;
+      cumulative[k] = max_nonneg_host(boff[t] + cumulative[k], pmax[t]);
+    }
+  }
   if (idx) PF_CUDA(f, copy_sync(f, idx, f->fd.idx, sizeof(int32_t) * f->N, cudaMemcpyDeviceToHost));
   f->d2h_bytes += (int64_t)((loglik1 ? nb : 0) + (log_g ? nb : 0) + (cumulative ? nb : 0) +
-                            (idx ? sizeof(int32_t) * f->N : 0));
+                            tile_bytes + (idx ? sizeof(int32_t) * f->N : 0));
   return PF_OK;
 }
 

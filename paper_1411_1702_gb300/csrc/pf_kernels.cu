@@ -1,14 +1,15 @@
 // pf_kernels.cu -- the per-observation epoch of Algorithm 1 (Arnold, Calvetti,
 // Somersalo) as CUDA kernels for sm_103a, for one filter or for a batch.
 //
-// One epoch j -> j+1 is six phases:
+// One epoch j -> j+1 is five phases:
 //   stage1      Steps 2, 3a: shrink phi, propagate by Psi, first-stage log
 //               weights log g = log w + log pi(y | xbar); the filter's last
 //               block takes the maximum (log-sum-exp shift)
 //   scan_tile   Step 3a/3b: g = exp(log g - max), tile-local inclusive scan;
-//               the filter's last block scans the tile totals
-//   scan_add    cumulative weights c_k = tile offset + tile-local sum
-//   resample    Step 3b: systematic resampling, l_i = min{k : c_k > tau_i}
+//               the filter's last block scans the tile totals into offsets
+//   resample    Step 3b: systematic resampling, l_i = min{k : c_k > tau_i},
+//               reading c_k = tile offset + tile-local sum on the fly
+//               (CumTiles: no pass of its own stores the final c)
 //   stage2      Steps 3c, 4, 5: gather by l, proliferate phi, repropagate with
 //               the Milne local-error sums, innovation, new log weights
 //   moments     Steps 5-6: normalisation, weighted mean/covariance of phi,
@@ -259,8 +260,9 @@ __device__ __forceinline__ void stage1_body(const FilterDev& fd, const EpochPara
 }
 
 // ------------------------------------------------------------------- scan
-// Step 3a/3b's cumulative weights: scan_tile_core and scan_add_core
-// (pf_scan.cuh) on the filter's buffers; the shift M is lg_max.
+// Step 3a/3b's cumulative weights: scan_tile_core (pf_scan.cuh) on the
+// filter's buffers; the shift M is lg_max.  c keeps the tile-local sums, and
+// its readers apply the tile offsets and floors (CumTiles).
 __device__ __forceinline__ ScanArgs scan_args(const FilterDev& fd) {
   Ctrl* ctrl = fd.ctrl;
   return ScanArgs{fd.lg, fd.N, ctrl->lg_max, fd.c, fd.blk, fd.boff, fd.pmax, fd.ticket + 1,
@@ -272,13 +274,16 @@ __device__ __forceinline__ void scan_tile_body(const FilterDev& fd, int vb, int 
   scan_tile_core(scan_args(fd), vb, vg, s_warp, s_flag);
 }
 
-__device__ __forceinline__ void scan_add_body(const FilterDev& fd, int vb) {
-  scan_add_core(scan_args(fd), (int64_t)vb * blockDim.x + threadIdx.x);
-}
 
 // --------------------------------------------------------------- resample
 // Step 3b: the epoch's u is Philox purpose RESAMPLE, slot 0; the search is
 // resample_tile (pf_scan.cuh).
+// The filter's cumulative weights as the tile pass leaves them: the offsets
+// and floors are applied on read (no separate offset pass over c).
+__device__ __forceinline__ CumTiles cum_tiles(const FilterDev& fd) {
+  return CumTiles{fd.c, fd.boff, fd.pmax, (uint32_t)scan_tile_len(fd.N)};
+}
+
 __device__ __forceinline__ double resample_u(const FilterDev& fd, const EpochParams* __restrict__ ep) {
   const U4 w = draw_block(fd, kRngResample, 0u, ep->epoch, 0u);
   return uniform53(w.x, w.y);
@@ -293,8 +298,8 @@ __device__ __forceinline__ void resample_body(const FilterDev& fd, const EpochPa
   if (vb == 0 && (threadIdx.x >> 5) == 2) factor_covariance(fd, fd.p, s_chol, threadIdx.x & 31);
   // u is drawn by the two warps that use it (resample_tile)
   const double u = threadIdx.x < 64 ? resample_u(fd, ep) : 0.0;
-  resample_tile(fd.c, fd.N, u, fd.idx, reinterpret_cast<unsigned long long*>(&fd.ctrl->n_unique), vb,
-                sh, corners);
+  resample_tile(cum_tiles(fd), fd.N, u, fd.idx,
+                reinterpret_cast<unsigned long long*>(&fd.ctrl->n_unique), vb, sh, corners);
 }
 
 // ---------------------------------------------------------------- stage 2
@@ -612,21 +617,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tile(const __grid_constan
   scan_tile_body(fd, blockIdx.x, gridDim.x, s_warp, &s_flag);
 }
 
-__global__ void __launch_bounds__(256) k_scan_add(const __grid_constant__ FilterDev fd) {
-  if (fd.ctrl->status != PF_OK) return;
-  scan_add_body(fd, blockIdx.x);
-}
-
 // Two-phase resampling of a large ensemble: every tile corner, one warp each,
 // into the per-block scratch.
 __global__ void __launch_bounds__(256) k_rs_corners(const __grid_constant__ FilterDev fd,
                                                    const EpochParams* __restrict__ ep) {
   if (fd.ctrl->status != PF_OK) return;
-  rs_corners_core(fd.c, fd.N, resample_u(fd, ep), ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                  reinterpret_cast<int32_t*>(fd.blk));
+  rs_corners_core(cum_tiles(fd), fd.N, resample_u(fd, ep),
+                  ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, reinterpret_cast<int32_t*>(fd.blk));
 }
 
-__global__ void __launch_bounds__(kResampleThreads, 5) k_resample(const __grid_constant__ FilterDev fd,
+__global__ void __launch_bounds__(kResampleThreads, 4) k_resample(const __grid_constant__ FilterDev fd,
                                                                const EpochParams* __restrict__ ep) {
   __shared__ RsShared sh;
   __shared__ double s_chol[kPMax * kPMax];
@@ -791,14 +791,6 @@ __global__ void __launch_bounds__(kScanThreads) k_batch_scan_tile(const FilterDe
   scan_tile_body(fd, t.vb, scan_tile_count(fd.N), s_warp, &s_flag);
 }
 
-__global__ void __launch_bounds__(256) k_batch_scan_add(const FilterDev* __restrict__ fds,
-                                                      const BatchTile* __restrict__ tiles) {
-  const BatchTile t = tiles[blockIdx.x];
-  const FilterDev& fd = *(fds + t.f);
-  if (fd.ctrl->status != PF_OK) return;
-  scan_add_body(fd, t.vb);
-}
-
 __global__ void __launch_bounds__(kResampleThreads) k_batch_resample(
     const FilterDev* __restrict__ fds, const EpochParams* const* __restrict__ eps,
     const BatchTile* __restrict__ tiles) {
@@ -862,7 +854,6 @@ int phase_blocks(int phase, int ode, int64_t N) {
       return ode == PF_ODE_BRUSSELATOR1D ? bruss_stage_blocks(N)
                                          : (int)((N + kSmallThreads - 1) / kSmallThreads);
     case kPhaseScanTile: return scan_tiles(N);
-    case kPhaseScanAdd: return (int)((N + 255) / 256);
     case kPhaseResample: return (int)rs_tiles(N);
     case kPhaseMoments: return moment_blocks(N);
   }
@@ -920,9 +911,7 @@ static cudaError_t launch_epoch_t(const FilterDev& fd, const EpochParams* ep, in
   k1<<<g_small, kSmallThreads, smem, st>>>(fd, ep);
   mark(1);
   k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, M::ODE, N), kScanThreads, 0, st>>>(fd);
-  mark(2);
-  k_scan_add<<<(unsigned)phase_blocks(kPhaseScanAdd, M::ODE, N), 256, 0, st>>>(fd);
-  mark(3);
+  mark(2);  // (marks[3] is not recorded: the scan_add slot is empty)
   if (rs_two_phase(N)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
   k_resample<<<(unsigned)phase_blocks(kPhaseResample, M::ODE, N), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
@@ -946,9 +935,7 @@ static cudaError_t launch_epoch_bruss(const FilterDev& fd, const EpochParams* ep
   if ((e = launch_bruss_stage(1, fd, ep, S, st)) != cudaSuccess) return e;
   mark(1);
   k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, ode, N), kScanThreads, 0, st>>>(fd);
-  mark(2);
-  k_scan_add<<<(unsigned)phase_blocks(kPhaseScanAdd, ode, N), 256, 0, st>>>(fd);
-  mark(3);
+  mark(2);  // (marks[3] is not recorded: the scan_add slot is empty)
   if (rs_two_phase(N)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
   k_resample<<<(unsigned)phase_blocks(kPhaseResample, ode, N), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
@@ -975,9 +962,7 @@ static cudaError_t launch_epoch_ad(const FilterDev& fd, const EpochParams* ep, i
   if ((e = launch_ad_stage(1, fd, ep, S, st)) != cudaSuccess) return e;
   mark(1);
   k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, ode, N), kScanThreads, 0, st>>>(fd);
-  mark(2);
-  k_scan_add<<<(unsigned)phase_blocks(kPhaseScanAdd, ode, N), 256, 0, st>>>(fd);
-  mark(3);
+  mark(2);  // (marks[3] is not recorded: the scan_add slot is empty)
   if (rs_two_phase(N)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
   k_resample<<<(unsigned)phase_blocks(kPhaseResample, ode, N), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
@@ -1076,13 +1061,13 @@ cudaError_t preload_main_kernels() {
       (const void*)k_init<2, 2>, (const void*)k_init<3, 3>, (const void*)k_init<64, 3>,
       (const void*)k_init<3, 4>, (const void*)k_moments<3, 4>, (const void*)k_theta_mean<4>,
       (const void*)k_moments<2, 2>, (const void*)k_moments<3, 3>, (const void*)k_moments<64, 3>,
-      (const void*)k_scan_tile, (const void*)k_scan_add, (const void*)k_resample,
+      (const void*)k_scan_tile, (const void*)k_resample,
       (const void*)k_theta_mean<2>, (const void*)k_theta_mean<3>, (const void*)k_theta_mean<5>,
       (const void*)k_set_moments, (const void*)k_init<0, 5>, (const void*)k_moments<0, 5>,
       (const void*)k_xbar, (const void*)k_upload, (const void*)k_rs_corners,
       (const void*)k_stage1_ess,
       (const void*)k_batch_init, (const void*)k_batch_scan_tile,
-      (const void*)k_batch_scan_add, (const void*)k_batch_resample,
+      (const void*)k_batch_resample,
       (const void*)k_batch_moments<2, 2>, (const void*)k_batch_moments<3, 3>,
       (const void*)k_batch_moments<64, 3>, (const void*)k_batch_moments<3, 4>};
   for (const void* k : ks) {
@@ -1142,7 +1127,6 @@ cudaError_t launch_batch_phase(int phase, int ode, int lmm, const FilterDev* fds
       break;
     }
     case kPhaseScanTile: k_batch_scan_tile<<<ntiles, kScanThreads, 0, st>>>(fds, tiles); break;
-    case kPhaseScanAdd: k_batch_scan_add<<<ntiles, 256, 0, st>>>(fds, tiles); break;
     case kPhaseResample: k_batch_resample<<<ntiles, kResampleThreads, 0, st>>>(fds, eps, tiles); break;
     case kPhaseMoments:
       if (ode == PF_ODE_LINEAR2) k_batch_moments<2, 2><<<ntiles, kMomentThreads, 0, st>>>(fds, tiles, is_init);

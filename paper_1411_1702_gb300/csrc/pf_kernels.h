@@ -10,7 +10,7 @@ namespace pfg {
 enum : int {
   kPhaseStage1 = 0,
   kPhaseScanTile = 1,
-  kPhaseScanAdd = 2,
+  kPhaseScanAdd = 2,  // (no launch: folded into the readers of c)
   kPhaseResample = 3,
   kPhaseStage2 = 4,
   kPhaseMoments = 5,
@@ -40,9 +40,11 @@ cudaError_t launch_batch_bruss_stage(int stage, const FilterDev* fds, const Epoc
 // Step 1 of Algorithm 1 into the pending buffer, then the moments and commit.
 cudaError_t launch_init(int ode, const FilterDev& fd, cudaStream_t st);
 // One epoch (Steps 2-6) with the parameter block ep (device) of S substeps.
-// If marks is not NULL, marks[i] is recorded before kernel i and marks[6]
-// after the last kernel (kernel order: stage1, scan_tile, scan_add, resample,
-// stage2, moments).
+// If marks is not NULL, marks[i] is recorded before phase i and marks[6]
+// after the last (phase order: stage1, scan_tile, scan_add, resample, stage2,
+// moments).  scan_add is empty -- the offsets are applied where c is read --
+// and marks[3] is not recorded; the slot stays so that pf_kernel_times keeps
+// its layout.
 constexpr int kEpochKernels = 6;
 cudaError_t launch_epoch(int ode, const FilterDev& fd, const EpochParams* ep, int S, cudaStream_t st,
                          cudaEvent_t* marks = nullptr);

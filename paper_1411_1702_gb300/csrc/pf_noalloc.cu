@@ -105,17 +105,17 @@ __global__ void __launch_bounds__(256) k_na_scan_add(int64_t N, double* c, NaScr
 
 // the filter's merge-path search (resample_tile), one block per diagonal tile;
 // corners: found first by k_na_corners (two-phase), or null
-__global__ void __launch_bounds__(kResampleThreads, 5) k_na_resample(const double* __restrict__ c,
+__global__ void __launch_bounds__(kResampleThreads, 4) k_na_resample(const double* __restrict__ c,
                                                                   int64_t N, double u,
                                                                   int32_t* __restrict__ idx,
                                                                   const int32_t* __restrict__ corners) {
   __shared__ RsShared sh;
-  resample_tile(c, N, u, idx, nullptr, blockIdx.x, sh, corners);
+  resample_tile(CumFinal{c}, N, u, idx, nullptr, blockIdx.x, sh, corners);
 }
 
 __global__ void __launch_bounds__(256) k_na_corners(const double* __restrict__ c, int64_t N, double u,
                                                    int32_t* __restrict__ corners) {
-  rs_corners_core(c, N, u, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, corners);
+  rs_corners_core(CumFinal{c}, N, u, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, corners);
 }
 
 static unsigned resample_blocks(int64_t N) { return (unsigned)((2 * N + kRsTile - 1) / kRsTile); }

@@ -44,27 +44,32 @@ __device__ __forceinline__ double block_exclusive_scan(double v, double* s_warp,
   return Op::apply(s_warp[wid], excl);
 }
 
-__device__ __forceinline__ int64_t upper_bound_bits(const double* c, int64_t N, long long key) {
+// Binary searches and the per-output systematic index over a view c(k) of
+// the cumulative weights (CumFinal, CumTiles below), on bit patterns.
+template <class V>
+__device__ __forceinline__ int64_t upper_bound_bits(const V& c, int64_t N, long long key) {
   int64_t lo = 0, hi = N;
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
-    if (__double_as_longlong(__ldg(c + mid)) > key) hi = mid;
+    if (__double_as_longlong(c(mid)) > key) hi = mid;
     else lo = mid + 1;
   }
   return lo;
 }
 
-__device__ __forceinline__ int64_t lower_bound_bits(const double* c, int64_t N, long long key) {
+template <class V>
+__device__ __forceinline__ int64_t lower_bound_bits(const V& c, int64_t N, long long key) {
   int64_t lo = 0, hi = N;
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
-    if (__double_as_longlong(__ldg(c + mid)) >= key) hi = mid;
+    if (__double_as_longlong(c(mid)) >= key) hi = mid;
     else lo = mid + 1;
   }
   return lo;
 }
 
-__device__ __forceinline__ int32_t systematic_index(const double* c, int64_t N, int64_t i, double u,
+template <class V>
+__device__ __forceinline__ int32_t systematic_index(const V& c, int64_t N, int64_t i, double u,
                                                     double total) {
   const double tau = ((double)i + u) / (double)N * total;
   int64_t k = upper_bound_bits(c, N, __double_as_longlong(tau));
@@ -205,6 +210,27 @@ __device__ __forceinline__ void scan_add_core(const ScanArgs& a, int64_t k) {
   }
 }
 
+// ------------------------------------------------- views of the weights
+// CumFinal: c as stored.  CumTiles: c as the tile pass leaves it (tile-local
+// sums) read through the per-tile offsets and floors, c_k = max(boff_t + cl_k,
+// pmax_t) for the tile t holding k: the offset pass (scan_add_core) folded
+// into the reads, bit for bit the values it would store.
+struct CumFinal {
+  const double* c;
+  __device__ __forceinline__ double operator()(int64_t k) const { return __ldg(c + k); }
+};
+
+struct CumTiles {
+  const double* cl;
+  const double* boff;
+  const double* pmax;
+  uint32_t len;  // tile length, scan_tile_len(N)
+  __device__ __forceinline__ double operator()(int64_t k) const {
+    const uint32_t t = (uint32_t)k / len;
+    return max_nonneg(__ldg(boff + t) + __ldg(cl + k), __ldg(pmax + t));
+  }
+};
+
 // ------------------------------------------------------ merge-path search
 // Systematic resampling (Step 3b): tau_i = ((i + u)/N) c_{N-1} with one
 // u per epoch; l_i = min{k : c_k > tau_i},
@@ -269,7 +295,8 @@ __device__ __forceinline__ bool rs_before(int64_t i, long long e, long long c, c
 // Taus among the first dg items of the merge: the largest a with
 // tau_{a-1} < c_{dg-a} (or dg - a = N).  One full warp; each round spreads 32
 // probes over (lo, hi], and the first failing probe bounds the next range.
-__device__ __forceinline__ int64_t rs_corner(const double* c, int64_t dg, const RsTau& t) {
+template <class V>
+__device__ __forceinline__ int64_t rs_corner(const V& c, int64_t dg, const RsTau& t) {
   const int lane = threadIdx.x & 31;
   const int64_t N = t.N;
   int64_t lo = dg > N ? dg - N : 0, hi = dg < N ? dg : N;
@@ -277,8 +304,7 @@ __device__ __forceinline__ int64_t rs_corner(const double* c, int64_t dg, const 
     const int64_t span = hi - lo;
     const int64_t a = lo + (span * (lane + 1) + 31) / 32;  // in (lo, hi]
     const int64_t b = dg - a;
-    const bool ok = b >= N || rs_before(a - 1, rs_estimate(a - 1, t),
-                                        __double_as_longlong(__ldg(c + b)), t);
+    const bool ok = b >= N || rs_before(a - 1, rs_estimate(a - 1, t), __double_as_longlong(c(b)), t);
     const unsigned fail = __ballot_sync(0xffffffffu, !ok);
     const int k = fail ? __ffs(fail) - 1 : 32;  // probes 0 .. k-1 hold
     const int64_t nlo = lo + (span * k + 31) / 32;
@@ -305,12 +331,13 @@ __host__ __device__ inline unsigned rs_corner_blocks(int64_t N) {
 // min(v * kRsTile, 2N) items, by one full warp (rs_corner's 32-probe rounds:
 // a handful of dependent loads instead of a binary search's twenty-odd).
 // Every lane of the warp calls it with the same v.
-__device__ __forceinline__ void rs_corners_core(const double* __restrict__ c, int64_t N, double u,
-                                                int64_t v, int32_t* __restrict__ corners) {
+template <class V>
+__device__ __forceinline__ void rs_corners_core(const V& c, int64_t N, double u, int64_t v,
+                                                int32_t* __restrict__ corners) {
   if (v > rs_tiles(N)) return;
   RsTau t;
   t.u = u;
-  t.total = __ldg(c + (N - 1));
+  t.total = c(N - 1);
   t.N = N;
   t.step = t.total / (double)N;
   t.ustep = u * t.step;
@@ -323,7 +350,8 @@ __device__ __forceinline__ void rs_corners_core(const double* __restrict__ c, in
 // idx over the tile's taus and, if n_unique is not null, adds the number of
 // outputs whose index differs from the previous output's (the distinct
 // parents) to it.
-__device__ __forceinline__ void resample_tile(const double* __restrict__ c, int64_t N, double u,
+template <class V>
+__device__ __forceinline__ void resample_tile(const V& c, int64_t N, double u,
                                               int32_t* __restrict__ idx,
                                               unsigned long long* n_unique, int vb, RsShared& sh,
                                               const int32_t* __restrict__ corners = nullptr) {
@@ -334,7 +362,7 @@ __device__ __forceinline__ void resample_tile(const double* __restrict__ c, int6
   if (wid < 2) {
     RsTau t;
     t.u = u;
-    t.total = __ldg(c + (N - 1));
+    t.total = c(N - 1);
     t.N = N;
     t.step = t.total / (double)N;
     t.ustep = u * t.step;
@@ -353,7 +381,7 @@ __device__ __forceinline__ void resample_tile(const double* __restrict__ c, int6
   const int64_t a0 = sh.corner[0], a1 = sh.corner[1];
   const int64_t b0 = d0 - a0, b1 = d1 - a1;
   for (int64_t k = b0 + threadIdx.x; k < b1; k += blockDim.x)
-    sh.c[k - b0] = __double_as_longlong(__ldg(c + k));
+    sh.c[k - b0] = __double_as_longlong(c(k));
   for (int64_t k = a0 + threadIdx.x; k < a1; k += blockDim.x) sh.t[k - a0] = rs_estimate(k, t);
   __syncthreads();
   // this thread's corner: a merge-path search in shared memory
@@ -378,7 +406,7 @@ __device__ __forceinline__ void resample_tile(const double* __restrict__ c, int6
       if (b == 0) {
         prev_tau_at_b = true;
       } else {
-        const long long cp = b - 1 >= b0 ? sh.c[b - 1 - b0] : __double_as_longlong(__ldg(c + (b - 1)));
+        const long long cp = b - 1 >= b0 ? sh.c[b - 1 - b0] : __double_as_longlong(c(b - 1));
         const long long tp = a - 1 >= a0 ? sh.t[a - 1 - a0] : rs_estimate(a - 1, t);
         prev_tau_at_b = !rs_before(a - 1, tp, cp, t);
       }
