@@ -486,8 +486,9 @@ def run_ours(args, w):
 def run_profile(args, w, pf, stream):
     """Plain launcher for profilers: Step 1, then warmup + steps epochs of the
     loaded series on one stream, no timing, no CPU work.  Launch order: k_init,
-    k_moments, then per epoch k_stage1, k_scan_tile, k_scan_add, k_resample,
-    k_stage2, k_moments."""
+    k_moments, then per epoch k_stage1, k_scan_tile, (k_rs_corners above one
+    wave of merge tiles,) k_resample, k_stage2, k_moments (and k_xbar for the
+    2D system)."""
     g = pf.Filter.from_workload(w, stream=stream.cuda_stream)
     g.pf_load_observations(w.t_obs, w.y_obs)
     n = min(args.warmup + args.steps, w.T)
