@@ -155,11 +155,13 @@ def test_two_phase_paths_equal_oracle(env):
     np.testing.assert_array_equal(idx, _gpu(pf, torch, c, u))
 
 
-def test_filter_two_phase_resampling_equals_oracle(env):
-    # a Robertson filter large enough for the two-launch resampling
+@pytest.mark.parametrize("N", [311296, 311297, 400000])
+def test_filter_two_phase_resampling_equals_oracle(env, N):
+    # Robertson filters on both sides of the two-launch threshold (2N items in
+    # more than 4 * 152 tiles of 1024: N > 311296) and beyond it
     pf, torch = env
     from paper_1411_1702_gb300 import workloads as W
-    w = W.robertson(N=400000, T=2)
+    w = W.robertson(N=N, T=2)
     g = pf.Filter.from_workload(w)
     for k in range(w.T):
         g.pf_assimilate(w.t_obs[k], w.y_obs[k])
