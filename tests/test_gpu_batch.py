@@ -145,3 +145,21 @@ def test_batched_lmm_families_and_m1_equal_alone(pf):
         for a, m in zip(alone, members):
             assert _same(a, m)
             assert all(np.array_equal(u, v) for u, v in zip(a.pf_estimates(), m.pf_estimates()))
+
+
+def test_large_member_batched_equals_alone(pf):
+    # alone, a filter above one wave of merge tiles resamples in two launches
+    # (corners first); in a batch its tiles find their own corners: the
+    # indices, and so everything after them, must agree bit for bit
+    ws = [W.robertson(N=400000, T=2), W.linear2(N=1000, T=2)]
+    alone = [pf.Filter.from_workload(w) for w in ws]
+    members = [pf.Filter.from_workload(w) for w in ws]
+    batch = pf.Batch(members)
+    for k in range(2):
+        for f, w in zip(alone, ws):
+            f.pf_assimilate(w.t_obs[k], w.y_obs[k])
+        st = batch.pf_batch_assimilate([w.t_obs[k] for w in ws], [w.y_obs[k] for w in ws])
+        assert st == [pf.PF_OK] * len(ws)
+        for a, m in zip(alone, members):
+            assert np.array_equal(a.pf_get_work()["idx"], m.pf_get_work()["idx"])
+            assert _same(a, m)
