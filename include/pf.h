@@ -177,7 +177,8 @@ pf_status pf_device_bytes(pf_ode ode, int d, int p, int64_t N, size_t* bytes);
  * 256-byte aligned, on the current device) and never frees it; the caller
  * keeps it alive and unused elsewhere until pf_destroy returns.  Everything
  * else is as pf_create.  Errors: as pf_create, and INVALID_ARG for a NULL,
- * misaligned or too small device_mem (checked before any device work). */
+ * misaligned or too small device_mem, or one that is not device (or managed)
+ * memory of the current device (checked before any device work). */
 pf_status pf_create_with_buffers(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
                                  const pf_prior* prior, const pf_options* opt, void* device_mem,
                                  size_t device_bytes, pf_filter** out);

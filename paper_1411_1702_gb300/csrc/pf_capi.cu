@@ -393,6 +393,16 @@ pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double 
       return fail(nullptr, PF_ERR_INVALID_ARG,
                   "device_bytes " + std::to_string(ext_bytes) + " < the " + std::to_string(need) +
                       " bytes pf_device_bytes reports");
+    // device (or managed) memory of the current device; anything else would
+    // only show as a fault in the first kernel
+    cudaPointerAttributes pa{};
+    int dev = -1;
+    const bool known = cudaPointerGetAttributes(&pa, ext_mem) == cudaSuccess &&
+                       cudaGetDevice(&dev) == cudaSuccess;
+    if (!known) cudaGetLastError();
+    if (!known || (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) ||
+        pa.device != dev)
+      return fail(nullptr, PF_ERR_INVALID_ARG, "device_mem is not device memory of the current device");
   }
 
   {

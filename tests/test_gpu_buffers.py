@@ -45,3 +45,20 @@ def test_caller_buffer_filter_equals_library_filter(env, name, N):
     buf.fill_(7)
     torch.cuda.synchronize()
     assert int(buf[:64].sum()) == 7 * 64
+
+
+def test_host_memory_is_rejected(env):
+    pf, torch = env
+    w = W.robertson(N=128, T=2)
+    need = pf.pf_device_bytes(w.ode, w.d, w.p, 128)
+    pinned = torch.empty(need + 512, dtype=torch.uint8, pin_memory=True)
+    off = (-pinned.data_ptr()) % 256
+    with pytest.raises(pf.PfError) as ei:
+        pf.Filter.from_workload(w, N=128, device_buffer=(pinned.data_ptr() + off, need))
+    assert ei.value.status == pf.PF_ERR_INVALID_ARG
+    import numpy as np_
+    host = np_.zeros(need + 512, dtype=np_.uint8)
+    off = (-host.ctypes.data) % 256
+    with pytest.raises(pf.PfError) as ei:
+        pf.Filter.from_workload(w, N=128, device_buffer=(host.ctypes.data + off, need))
+    assert ei.value.status == pf.PF_ERR_INVALID_ARG
