@@ -102,9 +102,10 @@ def _michaelis_flops(lmm):
 STAGE2_FLOPS_PER_SUBSTEP = {
     "robertson": lambda K, d: 15 + 9 + 12 + 8 + 42 * K,
     "linear2": lambda K, d: 10 + 6 + 8 + 20 + 14 * K,
-    # 32 grid points x 72 flops per Newton iteration (f, G, 2x2 block, Thomas
-    # forward and backward), predictor 5d, history 3d, Milne 4d, constants
-    "brusselator": lambda K, d: 320 + 192 + 256 + 15 + 2304 * K,
+    # 32 grid points x 67 flops per Newton iteration (residual 16, 2x2 block,
+    # Thomas forward and backward), predictor 5d, history 3d (+ the u rows'
+    # g A, 1 each), Milne 4d, constants
+    "brusselator": lambda K, d: 320 + 224 + 256 + 15 + 2144 * K,
     "advdiff20": _advdiff_flops,
     "advdiff40": _advdiff_flops,
 }
@@ -126,7 +127,7 @@ STAGE2_KERNEL["michaelis"] = "k_stage2<Michaelis, 0>"
 # same command on a GB300 (profiles/ names each capture); None where no capture
 # of the kernel as it stands exists.
 STAGE2_TRAFFIC = {"robertson": 11552512 + 0,
-                  "brusselator": 11202826752 + 10732933888,
+                  "brusselator": 11286390016 + 10732937216,
                   "advdiff20": 3081472 + 670720,
                   "advdiff40": 177671424 + 140111872,
                   "michaelisBDF2": 4353024 + 0,

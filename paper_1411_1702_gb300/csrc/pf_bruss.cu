@@ -64,13 +64,18 @@ __device__ void br_euler_predictor(const double* __restrict__ X, double* __restr
 // G = y - r - g f(y), with M_i the 2x2 diagonal block of point i and e = g D:
 //   forward  W_i = (M_i - e^2 W_{i-1})^{-1},  z_i = W_i (-G_i + e z_{i-1}),
 //   backward dy_i = z_i + e W_i dy_{i+1}  (dy_32 = 0).
+// R holds r with g A already added to the u rows (br_propagate), and the
+// Laplacian's -2u, -2v terms are gathered into the diagonal coefficients, so
+//   G_u = (1 + g(B+1) + 2gD) u - (r_u + gA) - g u^2 v - gD (u_L + u_R),
+//   G_v = (1 + 2gD) v - r_v - gB u + g u^2 v - gD (v_L + v_R):
+// the same residual in 9 FP64 instructions a point instead of 13.
 __device__ void br_newton(double* __restrict__ Y, const double* __restrict__ R, int64_t N, int64_t n,
                           double g, int K, const BrTheta& T, double* __restrict__ Wg,
                           double* __restrict__ Zg) {
   const double gD = g * T.D, e2 = gD * gD, g2 = 2.0 * g, mg = -g;
   const double ca = 1.0 + g * (T.B + 1.0) + 2.0 * gD;  // 1 + g(B+1) + 2gD
   const double cd = 1.0 + 2.0 * gD;
-  const double gA = g * T.A, gB1 = g * (T.B + 1.0), gB = g * T.B;
+  const double gB = g * T.B;
   for (int it = 0; it < K; ++it) {
     double uL = 1.0, vL = 3.0;
     double u = Y[n], v = Y[N + n];
@@ -83,9 +88,8 @@ __device__ void br_newton(double* __restrict__ Y, const double* __restrict__ R, 
       }
       const double ru = R[(int64_t)(2 * i) * N + n], rv = R[(int64_t)(2 * i + 1) * N + n];
       const double uu = u * u, uv = u * v, uuv = uu * v;
-      const double lapu = fma(-2.0, u, uL + uR), lapv = fma(-2.0, v, vL + vR);
-      const double Gu = fma(-gD, lapu, fma(gB1, u, fma(mg, uuv, (u - ru) - gA)));
-      const double Gv = fma(-gD, lapv, fma(-gB, u, fma(g, uuv, v - rv)));
+      const double Gu = fma(ca, u, fma(mg, uuv, fma(-gD, uL + uR, -ru)));
+      const double Gv = fma(cd, v, fma(g, uuv, fma(-gB, u, fma(-gD, vL + vR, -rv))));
       double a = fma(-g2, uv, ca), b = mg * uu, c = fma(g2, uv, -gB), d = fma(g, uu, cd);
       a = fma(-e2, W00, a);
       b = fma(-e2, W01, b);
@@ -139,12 +143,14 @@ __device__ void br_propagate(const FilterDev& fd, int64_t n, const StepCoef* sc,
   double* Zg = Wg + 4 * (int64_t)kBrPts * N;
   for (int s = 0; s < S; ++s) {
     const StepCoef& c = sc[s];
+    // r, with gamma A added to the u rows for br_newton's residual
+    const double gA = c.gamma * T.A;
     if (c.kind == 2) {
       for (int k = 0; k < kBrD; ++k) {
         const int64_t o = (int64_t)k * N + n;
         const double xn = P0[o], x1 = P1[o], x2 = P2[o];
         const double xp = fma(c.pi2, x2, fma(c.pi1, x1, c.pi0 * xn));
-        R[o] = fma(c.rho2, x1, c.rho1 * xn);
+        R[o] = fma(c.rho2, x1, fma(c.rho1, xn, (k & 1) ? 0.0 : gA));
         P2[o] = xp;
         if (ERR) XP[o] = xp;
       }
@@ -153,7 +159,7 @@ __device__ void br_propagate(const FilterDev& fd, int64_t n, const StepCoef* sc,
       for (int k = 0; k < kBrD; ++k) {
         const int64_t o = (int64_t)k * N + n;
         const double xn = P0[o];
-        R[o] = xn;
+        R[o] = (k & 1) ? xn : xn + gA;
         P2[o] = xn;
       }
     }
