@@ -83,25 +83,28 @@ def _advdiff_flops_interval(K, d):
 
 def _michaelis_flops(lmm):
     """M1 (Sec. 2.1), d = 3: one Newton iteration (two flux reciprocals, the
-    lower-triangular substitution with two pivot reciprocals) is 41 flops, one
-    evaluation of f 17.  Per substep, by family: BDF1/BDF2 predictor 15,
-    history 9, input 2, pivot constant 3, Milne 12; BDF3 adds the slope f(t_n,
-    x_n) and its term (70 in all); Adams-Moulton: AB predictor 18, AM
-    history 12, input 2, pivot 3, f(x_{n+1}) 17, Milne 12; Adams-Bashforth:
-    predictor 18, history 12, f 17, Milne against AM 18 (no Newton)."""
+    lower-triangular substitution with two pivot reciprocals; the third row
+    folded onto its pivot) is 39 flops, one evaluation of f 17.  Per substep,
+    by family: BDF1/BDF2 predictor 15, history 9, input 2, pivot and third-row
+    constants 6, Milne 12; BDF3 adds the slope f(t_n, x_n) and its term (73 in
+    all); Adams-Moulton: AB predictor 18, AM history 12, input 2, constants 6,
+    f(x_{n+1}) 17, Milne 12; Adams-Bashforth: predictor 18, history 12, f 17,
+    Milne against AM 18 (no Newton)."""
     fam = lmm // 10
     if fam == 2:
         return lambda K, d: 65
     if fam == 1:
-        return lambda K, d: 64 + 41 * K
+        return lambda K, d: 67 + 39 * K
     if lmm == 3:
-        return lambda K, d: 70 + 41 * K
-    return lambda K, d: 41 + 41 * K
+        return lambda K, d: 73 + 39 * K
+    return lambda K, d: 44 + 39 * K
 
 
 STAGE2_FLOPS_PER_SUBSTEP = {
-    "robertson": lambda K, d: 15 + 9 + 12 + 8 + 42 * K,
-    "linear2": lambda K, d: 10 + 6 + 8 + 20 + 14 * K,
+    # per Newton iteration: Robertson 41 (the first residual row one FMA on
+    # its pivot 1 + g k1), linear2 12 (both rows on their pivots)
+    "robertson": lambda K, d: 15 + 9 + 12 + 8 + 41 * K,
+    "linear2": lambda K, d: 10 + 6 + 8 + 20 + 12 * K,
     # 32 grid points x 67 flops per Newton iteration (residual 16, 2x2 block,
     # Thomas forward and backward), predictor 5d, history 3d (+ the u rows'
     # g A, 1 each), Milne 4d, constants
@@ -126,12 +129,12 @@ STAGE2_KERNEL["michaelis"] = "k_stage2<Michaelis, 0>"
 # DRAM bytes (read + write) of one stage-2 launch from an ncu capture of the
 # same command on a GB300 (profiles/ names each capture); None where no capture
 # of the kernel as it stands exists.
-STAGE2_TRAFFIC = {"robertson": 11552512 + 0,
+STAGE2_TRAFFIC = {"robertson": 11568896 + 0,
                   "brusselator": 11286390016 + 10732937216,
                   "advdiff20": 3081472 + 670720,
                   "advdiff40": 177671424 + 140111872,
-                  "michaelisBDF2": 4353024 + 0,
-                  "michaelisAM3": 4586752 + 0,
+                  "michaelisBDF2": 4367360 + 0,
+                  "michaelisAM3": 4604416 + 0,
                   "michaelisAB3": 4459520 + 0}
 # The paper's own number for the same workload, where it has one: Table 3's
 # 2D advection-diffusion runs (BDF2, h = 0.1, N = 5000, 30 unit intervals,

@@ -36,12 +36,14 @@ struct Linear2 {
   __device__ __forceinline__ static void newton(const Th& T, double g, const double* r, double* y,
                                                 int K) {
     const double gt1 = g * T.t1, gt2 = g * T.t2;
+    const double o1 = 1.0 + gt1, o2 = 1.0 + gt2;
     // two refinement steps: with K = 1 no later iteration absorbs the
     // reciprocal's error
-    const double i1 = rcp_nr2(1.0 + gt1), i2 = rcp_nr2(1.0 + gt2);
+    const double i1 = rcp_nr2(o1), i2 = rcp_nr2(o2);
     for (int it = 0; it < K; ++it) {
-      const double G0 = fma(-gt2, y[1], fma(gt1, y[0], y[0] - r[0]));
-      const double G1 = fma(gt2, y[1], y[1] - r[1]);
+      // G = (I - g A) y - r, each row one FMA chain on the pivots
+      const double G0 = fma(-gt2, y[1], fma(o1, y[0], -r[0]));
+      const double G1 = fma(o2, y[1], -r[1]);
       const double d1 = -G1 * i2;
       const double d0 = fma(gt2, d1, -G0) * i1;
       y[0] += d0;
@@ -82,7 +84,8 @@ struct Robertson {
   __device__ __forceinline__ static void newton(const Th& T, double g, const double* r, double* y,
                                                 int K) {
     const double gk1 = g * T.k1, gk2 = g * T.k2, gk3 = g * T.k3;
-    const double im = rcp_nr(1.0 + gk1);
+    const double opk1 = 1.0 + gk1;
+    const double im = rcp_nr(opk1);
     const double l = gk1 * im;
     for (int it = 0; it < K; ++it) {
       const double q = gk3 * y[1];  // g k3 y2
@@ -90,8 +93,9 @@ struct Robertson {
       const double t = gk2 * y[1];  // g k2 y2
       const double w = t + t;       // 2 g k2 y2
       // G = y - r - gamma f(y), the products g k3 y2 y3 = q y3 and
-      // g k2 y2^2 = t y2 fused into the sums
-      const double G1 = fma(-q, y[2], fma(gk1, y[0], y[0] - r[0]));
+      // g k2 y2^2 = t y2 fused into the sums; the first row's y1 + g k1 y1
+      // is one product with the pivot 1 + g k1
+      const double G1 = fma(-q, y[2], fma(opk1, y[0], -r[0]));
       const double G2 = fma(-gk1, y[0], fma(q, y[2], fma(t, y[1], y[1] - r[1])));
       const double G3 = fma(-t, y[1], y[2] - r[2]);
       const double den = fma(im, fma(q, w, p), 1.0 + w);
@@ -136,7 +140,10 @@ struct Michaelis {
 
   __device__ __forceinline__ static void newton(const Th& T, double g, const double* r, double* y,
                                                 int K) {
-    const double gl = rcp_nr2(fma(g, kLambda, 1.0));
+    const double opl = fma(g, kLambda, 1.0);
+    const double gl = rcp_nr2(opl);
+    // the third row's constant part, r3 + g lambda c0, once per substep
+    const double r2 = fma(g * kLambda, kC0, r[2]);
     for (int it = 0; it < K; ++it) {
       const double q1 = rcp_nr2(y[0] + T.k1), q2 = rcp_nr2(y[1] + T.k2);
       const double u1 = T.v1 * q1, u2 = T.v2 * q2;
@@ -145,7 +152,8 @@ struct Michaelis {
       // G = y - r - gamma f_aut(y)
       const double G0 = fma(g, j1, y[0] - r[0]);
       const double G1 = fma(-g, j1 - j2, y[1] - r[1]);
-      const double G2 = fma(-g, fma(-kLambda, y[2] - kC0, j2), y[2] - r[2]);
+      // (1 + g lambda) y3 - (r3 + g lambda c0) - g j2, the same row folded
+      const double G2 = fma(-g, j2, fma(opl, y[2], -r2));
       const double d0 = -G0 * rcp_nr(1.0 + ga);
       const double d1 = fma(ga, d0, -G1) * rcp_nr(1.0 + gb);
       const double d2 = fma(gb, d1, -G2) * gl;
