@@ -129,12 +129,12 @@ STAGE2_KERNEL["michaelis"] = "k_stage2<Michaelis, 0>"
 # DRAM bytes (read + write) of one stage-2 launch from an ncu capture of the
 # same command on a GB300 (profiles/ names each capture); None where no capture
 # of the kernel as it stands exists.
-STAGE2_TRAFFIC = {"robertson": 11568896 + 0,
-                  "brusselator": 11286390016 + 10732937216,
+STAGE2_TRAFFIC = {"robertson": 11554304 + 0,
+                  "brusselator": 11276960000 + 10731582720,
                   "advdiff20": 3081472 + 670720,
                   "advdiff40": 177671424 + 140111872,
-                  "michaelisBDF2": 4367360 + 0,
-                  "michaelisAM3": 4604416 + 0,
+                  "michaelisBDF2": 4365824 + 0,
+                  "michaelisAM3": 4601344 + 0,
                   "michaelisAB3": 4459520 + 0}
 # The paper's own number for the same workload, where it has one: Table 3's
 # 2D advection-diffusion runs (BDF2, h = 0.1, N = 5000, 30 unit intervals,

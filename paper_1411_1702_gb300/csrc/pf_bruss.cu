@@ -76,7 +76,8 @@ __device__ void br_newton(double* __restrict__ Y, const double* __restrict__ R, 
   const double ca = 1.0 + g * (T.B + 1.0) + 2.0 * gD;  // 1 + g(B+1) + 2gD
   const double cd = 1.0 + 2.0 * gD;
   const double gB = g * T.B;
-  for (int it = 0; it < K; ++it) {
+  // one iteration; the determinants' reciprocals are refined only in the last
+  auto step = [&](const bool last) {
     double uL = 1.0, vL = 3.0;
     double u = Y[n], v = Y[N + n];
     double W00 = 0.0, W01 = 0.0, W10 = 0.0, W11 = 0.0, z0 = 0.0, z1 = 0.0;
@@ -95,7 +96,7 @@ __device__ void br_newton(double* __restrict__ Y, const double* __restrict__ R, 
       b = fma(-e2, W01, b);
       c = fma(-e2, W10, c);
       d = fma(-e2, W11, d);
-      const double rdet = rcp_nr(fma(a, d, -(b * c)));
+      const double rdet = rcp_newton(fma(a, d, -(b * c)), last);
       W00 = d * rdet;
       W01 = -b * rdet;
       W10 = -c * rdet;
@@ -127,7 +128,9 @@ __device__ void br_newton(double* __restrict__ Y, const double* __restrict__ R, 
       Y[(int64_t)(2 * i) * N + n] += du;
       Y[(int64_t)(2 * i + 1) * N + n] += dv;
     }
-  }
+  };
+  for (int it = 0; it + 1 < K; ++it) step(false);
+  if (K > 0) step(true);
 }
 
 // Psi over the S substeps.  P0, P1, P2 hold x_n, x_{n-1}, x_{n-2}; each

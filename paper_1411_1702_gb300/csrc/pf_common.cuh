@@ -191,11 +191,24 @@ __device__ __forceinline__ void normal_pair(const U4& w, double& z0, double& z1)
 // Newton-Raphson step r <- r + r (1 - x r) (the textbook iteration for 1/x,
 // e.g. Markstein 1990), which roughly doubles the correct bits.  Used only
 // inside the Newton solves, whose own iteration absorbs the residual error.
-__device__ __forceinline__ double rcp_nr(double x) {
+__device__ __forceinline__ double rcp_hw(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+
+__device__ __forceinline__ double rcp_nr(double x) {
+  const double r = rcp_hw(x);
   const double e = fma(-x, r, 1.0);
   return fma(r, e, r);
+}
+
+// The reciprocal of a Newton correction's pivot: the hardware approximation
+// alone in every iteration but the last, whose successor's residual is exact
+// and so corrects the step's error (an inexact Newton step); refined in the
+// last, whose correction is the final one.
+__device__ __forceinline__ double rcp_newton(double x, bool last) {
+  return last ? rcp_nr(x) : rcp_hw(x);
 }
 
 __device__ __forceinline__ double rcp_nr2(double x) {

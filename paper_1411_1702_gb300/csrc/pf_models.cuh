@@ -87,7 +87,8 @@ struct Robertson {
     const double opk1 = 1.0 + gk1;
     const double im = rcp_nr(opk1);
     const double l = gk1 * im;
-    for (int it = 0; it < K; ++it) {
+    // one iteration; the pivot's reciprocal is refined only in the last
+    auto step = [&](const bool last) {
       const double q = gk3 * y[1];  // g k3 y2
       const double p = gk3 * y[2];  // g k3 y3
       const double t = gk2 * y[1];  // g k2 y2
@@ -100,13 +101,15 @@ struct Robertson {
       const double G3 = fma(-t, y[1], y[2] - r[2]);
       const double den = fma(im, fma(q, w, p), 1.0 + w);
       const double num = fma(q * im, G3, -fma(l, G1, G2));
-      const double d2 = num * rcp_nr(den);
+      const double d2 = num * rcp_newton(den, last);
       const double d3 = fma(w, d2, -G3);
       const double d1 = im * fma(q, d3, fma(p, d2, -G1));
       y[0] += d1;
       y[1] += d2;
       y[2] += d3;
-    }
+    };
+    for (int it = 0; it + 1 < K; ++it) step(false);
+    if (K > 0) step(true);
   }
 };
 
@@ -144,7 +147,8 @@ struct Michaelis {
     const double gl = rcp_nr2(opl);
     // the third row's constant part, r3 + g lambda c0, once per substep
     const double r2 = fma(g * kLambda, kC0, r[2]);
-    for (int it = 0; it < K; ++it) {
+    // one iteration; the pivots' reciprocals are refined only in the last
+    auto step = [&](const bool last) {
       const double q1 = rcp_nr2(y[0] + T.k1), q2 = rcp_nr2(y[1] + T.k2);
       const double u1 = T.v1 * q1, u2 = T.v2 * q2;
       const double j1 = u1 * y[0], j2 = u2 * y[1];
@@ -154,13 +158,15 @@ struct Michaelis {
       const double G1 = fma(-g, j1 - j2, y[1] - r[1]);
       // (1 + g lambda) y3 - (r3 + g lambda c0) - g j2, the same row folded
       const double G2 = fma(-g, j2, fma(opl, y[2], -r2));
-      const double d0 = -G0 * rcp_nr(1.0 + ga);
-      const double d1 = fma(ga, d0, -G1) * rcp_nr(1.0 + gb);
+      const double d0 = -G0 * rcp_newton(1.0 + ga, last);
+      const double d1 = fma(ga, d0, -G1) * rcp_newton(1.0 + gb, last);
       const double d2 = fma(gb, d1, -G2) * gl;
       y[0] += d0;
       y[1] += d1;
       y[2] += d2;
-    }
+    };
+    for (int it = 0; it + 1 < K; ++it) step(false);
+    if (K > 0) step(true);
   }
 };
 
