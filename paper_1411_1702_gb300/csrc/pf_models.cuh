@@ -147,9 +147,13 @@ struct Michaelis {
     const double gl = rcp_nr2(opl);
     // the third row's constant part, r3 + g lambda c0, once per substep
     const double r2 = fma(g * kLambda, kC0, r[2]);
-    // one iteration; the pivots' reciprocals are refined only in the last
+    // one iteration; the pivots' reciprocals are refined only in the last.
+    // The flux reciprocals enter the residual: the last iteration refines
+    // them twice (its residual is the final one), the earlier ones once,
+    // since the next iteration's exact residual corrects their step
     auto step = [&](const bool last) {
-      const double q1 = rcp_nr2(y[0] + T.k1), q2 = rcp_nr2(y[1] + T.k2);
+      const double s1 = y[0] + T.k1, s2 = y[1] + T.k2;
+      const double q1 = last ? rcp_nr2(s1) : rcp_nr(s1), q2 = last ? rcp_nr2(s2) : rcp_nr(s2);
       const double u1 = T.v1 * q1, u2 = T.v2 * q2;
       const double j1 = u1 * y[0], j2 = u2 * y[1];
       const double ga = g * (u1 * T.k1 * q1), gb = g * (u2 * T.k2 * q2);
