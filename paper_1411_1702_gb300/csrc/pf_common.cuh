@@ -203,10 +203,10 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return fma(r, e, r);
 }
 
-// The reciprocal of a Newton correction's pivot: the hardware approximation
-// alone in every iteration but the last, whose successor's residual is exact
-// and so corrects the step's error (an inexact Newton step); refined in the
-// last, whose correction is the final one.
+// The reciprocal of a Newton correction's pivot.  Before the last iteration
+// it is the hardware approximation alone: the following iteration evaluates
+// the exact residual and so corrects that step's error (an inexact Newton
+// step).  In the last iteration, whose correction is final, it is refined.
 __device__ __forceinline__ double rcp_newton(double x, bool last) {
   return last ? rcp_nr(x) : rcp_hw(x);
 }
