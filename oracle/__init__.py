@@ -271,6 +271,13 @@ def propagate(ode, K, theta, tab, S, x, h1, h2, with_error=False):
     return x, h1, h2, E
 
 
+def loglik(cfg: Config, y, x):
+    """Step 3a / Step 5 log-likelihood log pi(y | x) of one state (or_loglik)."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return lib().or_loglik(C.byref(cfg), _d(y), _d(x))
+
+
 def resample_systematic(c, u):
     c = np.ascontiguousarray(c, dtype=np.float64)
     idx = np.zeros(len(c), dtype=np.int32)
