@@ -3,8 +3,10 @@ isolated failures, graph reuse."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1411_1702_gb300 import build as B
 from paper_1411_1702_gb300 import workloads as W
+from parity_util import begin_epoch, finish_epoch
 
 pytestmark = pytest.mark.gpu
 
@@ -12,6 +14,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def pf():
     B.build()
+    oracle.build()
     from paper_1411_1702_gb300 import pf as _pf
     _pf.load()
     return _pf
@@ -163,3 +166,37 @@ def test_large_member_batched_equals_alone(pf):
         for a, m in zip(alone, members):
             assert np.array_equal(a.pf_get_work()["idx"], m.pf_get_work()["idx"])
             assert _same(a, m)
+
+
+def _every_problem_and_family(T=4):
+    """One member of each (problem, LMM family) the batched kernels serve."""
+    return [W.linear2(N=1000, T=T, seed=31),
+            W.linear2(N=513, T=T, seed=32).with_(lmm=W.LMM_AM2),
+            W.linear2(N=700, T=T, seed=33).with_(lmm=W.LMM_AB3),
+            W.linear2(N=257, T=T, seed=34).with_(lmm=W.LMM_BDF3),
+            W.robertson(N=3001, T=T, seed=35),
+            W.brusselator(N=70, T=T, seed=36),
+            W.michaelis(N=1500, T=T, seed=37, lmm=W.LMM_BDF3),
+            W.michaelis(N=2049, T=T, seed=38, lmm=W.LMM_AM3),
+            W.michaelis(N=700, T=T, seed=39, lmm=W.LMM_AB2),
+            W.michaelis(N=257, T=T, seed=40, lmm=W.LMM_BDF2)]
+
+
+def test_batched_members_match_oracle(pf):
+    """Every member of a mixed batch, epoch by epoch, against the oracle run
+    from that member's committed state: every stage output per particle
+    (states to 1e-10, indices bit-exact given the member's cumulative
+    weights, weights and moments within the derived bounds)."""
+    ws = _every_problem_and_family()
+    members = [pf.Filter.from_workload(w) for w in ws]
+    orcs = [oracle.Filter(w) for w in ws]
+    for o in orcs:
+        o.init()
+    batch = pf.Batch(members)
+    for k in range(4):
+        pres = [begin_epoch(m, o) for m, o in zip(members, orcs)]
+        st = batch.pf_batch_assimilate([w.t_obs[k] for w in ws], [w.y_obs[k] for w in ws])
+        assert st == [pf.PF_OK] * len(ws)
+        for m, o, w, pre in zip(members, orcs, ws, pres):
+            errs = finish_epoch(m, o, w.t_obs[k], w.y_obs[k], pre, exempt_dead=True)
+            assert errs["x"] <= 1e-10, (w.name, w.lmm, k, errs["x"])

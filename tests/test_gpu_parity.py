@@ -5,7 +5,7 @@ import pytest
 import oracle
 from paper_1411_1702_gb300 import build as B
 from paper_1411_1702_gb300 import workloads as W
-from parity_util import check_epoch, rel_state_err, sync_oracle_from_gpu
+from parity_util import assert_within_three_mc_se, check_epoch, rel_state_err, sync_oracle_from_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -85,22 +85,8 @@ def test_independent_runs_agree(pf):
 
 
 def test_posterior_within_three_mc_standard_errors(pf):
-    """Across seeds, the GPU and oracle posterior means agree within 3 Monte
-    Carlo standard errors."""
     w0 = W.linear2()
-    R = 6
-    gm, om = [], []
-    for seed in range(R):
-        w = w0.with_(seed=seed)
-        g, o = _pair(pf, w)
-        for k in range(w.T):
-            g.pf_assimilate(w.t_obs[k], w.y_obs[k])
-            assert o.epoch(w.t_obs[k], w.y_obs[k]) == oracle.OK
-        gm.append(g.pf_estimates()[0])
-        om.append(o.moments()["phibar"])
-    gm, om = np.array(gm), np.array(om)
-    se = np.sqrt(gm.var(axis=0, ddof=1) / R + om.var(axis=0, ddof=1) / R) + 1e-15
-    assert np.all(np.abs(gm.mean(axis=0) - om.mean(axis=0)) <= 3 * se)
+    assert_within_three_mc_se(pf, lambda s: w0.with_(seed=s))
 
 
 def test_deterministic_reruns(pf):

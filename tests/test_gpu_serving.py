@@ -3,8 +3,10 @@ results identical to each filter alone, latency accounting."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1411_1702_gb300 import build as B
 from paper_1411_1702_gb300 import workloads as W
+from parity_util import begin_epoch, finish_epoch
 
 pytestmark = pytest.mark.gpu
 
@@ -12,6 +14,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def pf():
     B.build()
+    oracle.build()
     from paper_1411_1702_gb300 import pf as _pf
     _pf.load()
     return _pf
@@ -116,3 +119,31 @@ def test_session_larger_than_budget_is_rejected(pf):
         srv.pf_server_open(W.robertson(N=100000, T=1))
     assert ei.value.status == pf.PF_ERR_BUDGET
     assert srv.pf_server_stats()["rejected"] == 1
+
+
+def test_served_sessions_match_oracle(pf):
+    """Sessions of every problem and LMM family served together: after each
+    round of observations (one per session, then a drain) every session is
+    compared with the oracle run from its committed state, stage by stage.
+    The session's random streams are those of its filter id."""
+    ws = [w.with_(stream=i) for i, w in enumerate(_sessions() + _sessions_lmm())]
+    srv = pf.Server(budget_bytes=8 << 30)
+    sids = [srv.pf_server_open(w, filter_id=i) for i, w in enumerate(ws)]
+    srv.pf_server_step()
+    orcs = [oracle.Filter(w) for w in ws]
+    for o in orcs:
+        o.init()
+    for k in range(4):
+        views = [srv.pf_server_session(s)[0] for s in sids]
+        assert all(v is not None for v in views)
+        pres = [begin_epoch(v, o) for v, o in zip(views, orcs)]
+        order = np.random.default_rng(k).permutation(len(ws))
+        for i in order:
+            srv.pf_server_submit(sids[i], ws[i].t_obs[k], ws[i].y_obs[k])
+            srv.pf_server_step()
+        srv.pf_server_drain()
+        for i, (s, o, w, pre) in enumerate(zip(sids, orcs, ws, pres)):
+            f, done, last = srv.pf_server_session(s)
+            assert done == k + 1 and last == pf.PF_OK
+            errs = finish_epoch(f, o, w.t_obs[k], w.y_obs[k], pre, exempt_dead=True, stats=False)
+            assert errs["x"] <= 1e-10, (w.name, k, errs["x"])
