@@ -296,15 +296,6 @@ pf_status pf_get_history(const pf_filter* f, int64_t* epochs, int* depth, double
 pf_status pf_set_history(pf_filter* f, int64_t epochs, int depth, double t_prev, double hprev1,
                          double hprev2);
 
-/* ---- diagnostics ----------------------------------------------------------
- * The FP64 FMA throughput this GPU sustains, in TFLOP/s (an FMA counts 2):
- * independent FMA chains over every SM for about ms milliseconds (best of
- * three launches after a calibration) on `stream` (cudaStream_t, NULL = the
- * legacy default stream).  The propagation kernels are bound by FP64 issue;
- * this is the roofline denominator they are compared with.  Synchronous.
- * Errors: INVALID_ARG (tflops NULL, ms <= 0), CUDA. */
-pf_status pf_fp64_fma_rate(void* stream, double ms, double* tflops);
-
 /* ---- host-only helper (no GPU needed) -----------------------------------
  * Substep table of one interval (t_prev, t_next] for the given history state,
  * as the filter builds it.  Per substep i, row i of coef (PF_SUBSTEP_ROW = 11
@@ -421,7 +412,9 @@ pf_status pf_server_submit(pf_server* s, int64_t session, double t_k, const doub
  * the epochs it launched. */
 pf_status pf_server_step(pf_server* s, int* launched);
 /* Step (waiting for the device between steps) until every admitted session's
- * queue is empty and nothing is in flight. */
+ * queue is empty and nothing is in flight.  Errors: STATE if observations stay
+ * queued while no epoch is in flight and a step launches none (no wait could
+ * end), or any error of pf_server_step. */
 pf_status pf_server_drain(pf_server* s);
 /* Close a session: it leaves once its queue is done; its memory returns to
  * the budget. */
@@ -457,8 +450,10 @@ void pf_server_destroy(pf_server* s);
  * Nothing is allocated or freed.  The scratch (per-tile sums and offsets,
  * completion counters, merge-tile corners) is one fixed array of about 530 KB in the library's
  * device image; every GPU that loads the library holds it until the process
- * exits.  The first call on a device looks up that array's device address
- * with the device current; make that first call before any stream capture.
+ * exits.  Every call looks up that array's device address on the current
+ * device (so a device reset leaves no stale address behind); the first call on
+ * a device may also load the library's device code, so make it before any
+ * stream capture.
  * All calls share the array and it keeps the last call's contents, so calls
  * whose GPU work overlaps (unordered streams, several host threads) race and
  * corrupt each other's results: order them on one stream or synchronise in

@@ -1100,7 +1100,13 @@ pf_status pf_server_drain(pf_server* s) {
     // sessions still waiting for admission cannot make progress here
     if (!server_pending(s)) return PF_OK;
     if (launched == 0) {
-      // wait until some lane's epoch finishes
+      // wait until some lane's epoch finishes; with nothing in flight no wait
+      // can end (observations are queued that no step launches), so report
+      // that instead of spinning
+      bool flying = false;
+      for (const pf_batch* b : s->lanes) flying = flying || b->in_flight;
+      if (!flying)
+        return sfail(s, PF_ERR_STATE, "drain: observations are queued but no epoch can launch");
       bool any = false;
       while (!any) {
         for (pf_batch* b : s->lanes)

@@ -10,9 +10,9 @@
 // fixed-size scratch array that is part of the library's device image.
 //
 // The scratch array lives at file scope below.  Host code may not use its name
-// as an address (in host code the name is only a host-side stand-in), so the
-// first call on each device looks up its device address with
-// cudaGetSymbolAddress while that device is current, and caches it.
+// as an address (in host code the name is only a host-side stand-in), so every
+// call looks up its device address with cudaGetSymbolAddress on the current
+// device.
 //
 // The kernels repeat the filter's cumulative-weight scan (same tiles, same
 // order of additions, same exact prefix-maximum fix-ups) and run its
@@ -20,8 +20,6 @@
 // bit-identical to the cumulative weights and indices of pf_assimilate.
 // pf_systematic_indices runs that search alone on given cumulative weights;
 // it needs no scratch at all.
-#include <mutex>
-
 #include "pf_filter.h"
 #include "pf_scan.cuh"
 
@@ -120,26 +118,24 @@ __global__ void __launch_bounds__(256) k_na_corners(const double* __restrict__ c
 
 static unsigned resample_blocks(int64_t N) { return (unsigned)((2 * N + kRsTile - 1) / kRsTile); }
 
-// device address of the scratch array, looked up once per device
-constexpr int kMaxDevices = 64;
-static std::mutex g_na_mutex;
-static unsigned char* g_na_ptr[kMaxDevices];
-
+// Device address of the scratch array on the current device.  It is looked up
+// on every call (a table lookup once the module is loaded) rather than cached,
+// so a device reset or a re-created primary context, after which the module is
+// reloaded and the array may move, never leaves a stale address behind.
 static cudaError_t scratch_address(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_na_ptr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_na_ptr[dev];
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
 }
+
+// The scratch layout holds every size up to the maximum: the scan's tile
+// count is at most max(kScanTargetTiles, ceil(N / (kScanThreads *
+// kScanItemsMax))) and the merge has rs_tiles(N) + 1 corners, both largest at
+// the maximum N.
+static_assert(scan_tile_count(kNaMaxParticles) <= kNaMaxTiles, "scan tiles exceed the scratch");
+static_assert(rs_tiles(kNaMaxParticles) + 1 <= kNaMaxCorners, "merge corners exceed the scratch");
 
 }  // namespace pfg
 
@@ -163,6 +159,12 @@ extern "C" pf_status pf_resample_systematic_noalloc(const double* log_g, int64_t
   if (!(u >= 0.0 && u < 1.0)) {
     set_thread_error("pf_resample_systematic_noalloc: need 0 <= u < 1");
     return PF_ERR_INVALID_ARG;
+  }
+  // a second line of defence behind the static_asserts: the layout must hold
+  // this N's tiles and corners
+  if (scan_tile_count(N) > kNaMaxTiles || rs_tiles(N) + 1 > kNaMaxCorners) {
+    set_thread_error("pf_resample_systematic_noalloc: scratch layout too small for this N");
+    return PF_ERR_BUDGET;
   }
   unsigned char* base = nullptr;
   cudaError_t e = scratch_address(&base);

@@ -93,7 +93,7 @@ __device__ __forceinline__ int32_t systematic_index(const V& c, int64_t N, int64
 // units, the 0.3 standing for a thread's share of the block scan -- among
 // those that keep the tile count at most max(kScanTargetTiles,
 // ceil(N / (kScanThreads * kScanItemsMax))); ties go to more values a thread.
-__host__ __device__ inline int scan_items(int64_t N) {
+__host__ __device__ constexpr int scan_items(int64_t N) {
   const int64_t cap_long = (N + kScanThreads * kScanItemsMax - 1) / (kScanThreads * kScanItemsMax);
   const int64_t cap = cap_long > kScanTargetTiles ? cap_long : kScanTargetTiles;
   int best = kScanItemsMax;
@@ -109,10 +109,10 @@ __host__ __device__ inline int scan_items(int64_t N) {
   }
   return best;
 }
-__host__ __device__ inline int64_t scan_tile_len(int64_t N) {
+__host__ __device__ constexpr int64_t scan_tile_len(int64_t N) {
   return (int64_t)kScanThreads * scan_items(N);
 }
-__host__ __device__ inline int scan_tile_count(int64_t N) {
+__host__ __device__ constexpr int scan_tile_count(int64_t N) {
   const int64_t L = scan_tile_len(N);
   return (int)((N + L - 1) / L);
 }
@@ -320,7 +320,7 @@ __device__ __forceinline__ int64_t rs_corner(const V& c, int64_t dg, const RsTau
 // searches overlap instead of heading every tile; below it each block finds
 // its own two (rs_corner), which saves the launch.
 constexpr int kRsTwoPhaseTiles = 4 * 152;
-__host__ __device__ inline int64_t rs_tiles(int64_t N) { return (2 * N + kRsTile - 1) / kRsTile; }
+__host__ __device__ constexpr int64_t rs_tiles(int64_t N) { return (2 * N + kRsTile - 1) / kRsTile; }
 __host__ __device__ inline bool rs_two_phase(int64_t N) { return rs_tiles(N) > kRsTwoPhaseTiles; }
 // blocks of 256 threads (8 warps) for the corner pass: one warp per corner
 __host__ __device__ inline unsigned rs_corner_blocks(int64_t N) {
