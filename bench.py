@@ -243,6 +243,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def fp64_fma_rate(ms, stream):
+    """TFLOP/s of the benchmark's FP64 FMA probe (libpf_fp64_probe.so, built
+    beside the library; not part of its C ABI), or None if it fails."""
+    import ctypes as C
+    from paper_1411_1702_gb300 import build as B
+    lib = C.CDLL(B.PROBE_LIB)
+    lib.fp64_fma_rate.restype = C.c_int
+    lib.fp64_fma_rate.argtypes = [C.c_void_p, C.c_double, C.POINTER(C.c_double)]
+    out = C.c_double()
+    rc = lib.fp64_fma_rate(C.c_void_p(stream) if stream else None, float(ms), C.byref(out))
+    return out.value if rc == 0 else None
+
+
 def epoch_launches(w):
     """Kernels of one single-filter epoch: stage 1, scan tile, resampling
     (which applies the tile offsets as it reads c), stage 2, moments; plus the
@@ -303,7 +316,7 @@ def run_reference(args, w):
         return 0
     import oracle
     oracle.build()
-    n_ref = min(w.N, args.ref_particles, CPU_SAMPLE_N.get(w.name, w.N))
+    n_ref = min(w.N, args.ref_particles or w.N, CPU_SAMPLE_N.get(w.name, w.N))
     o = oracle.Filter(w, N=n_ref)
     o.init()
     k = 0
@@ -323,12 +336,13 @@ def run_reference(args, w):
         steps += 2 * w.substeps_per_interval(k) * n_ref
         k += 1
     value = steps / total
-    sample = f"one epoch per step at N={n_ref} of the N={w.N} workload"
+    sample = (f"one epoch per step of the workload at its N={n_ref}" if n_ref == w.N else
+              f"one epoch per step at N={n_ref} (the workload's N={w.N} would take minutes)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_of(w),
+        "data": "synthetic", "config": config_of(w.with_(N=n_ref)),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -429,7 +443,7 @@ def run_ours(args, w):
     wall_max, e2e_all = reduce_times(dist, wall * 1e3, e2e_done, device="cuda")
     # the FP64 FMA rate this GPU sustains (after the timed regions): checks
     # that the nominal FP64 peak used as the roofline denominator is reached
-    fma_measured = pf.pf_fp64_fma_rate(200.0, stream.cuda_stream)
+    fma_measured = fp64_fma_rate(200.0, stream.cuda_stream)
     e2e_value = e2e_all / (wall_max * 1e-3)
     # only the data of the steps themselves (the resets in between are not steps)
     h2d = (st1["h2d_bytes"] - st0["h2d_bytes"]) / e2e_steps
@@ -483,6 +497,20 @@ def run_ours(args, w):
         oracle.set_threads(cores)
         line["cpu_baseline"]["single_thread"] = {"value": rate1, "sample": sample1}
     g.close()
+    if world == 1 and args.patterns and args.workload == "robertson":
+        # the metric's other halves on the same GPU: the batched workload
+        # against per-filter launches, and serving latency
+        b = batched_result(args)
+        line["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "steps", "config",
+                                             "clocks", "e2e", "per_filter_sync",
+                                             "per_filter_streams", "speedup_vs_per_filter_sync",
+                                             "speedup_vs_per_filter_streams", "autotune")}
+        sv = serving_result(args)
+        line["serving"] = {k: sv[k] for k in ("value", "unit", "config", "clocks", "server",
+                                              "server_one_lane", "serial_per_filter",
+                                              "throughput_vs_serial", "p99_vs_serial")}
+        if "load_sweep" in sv:
+            line["serving"]["load_sweep"] = sv["load_sweep"]
     print(json.dumps(line), flush=True)
     return 0
 
@@ -518,6 +546,13 @@ def shard_by_work(work, world):
 
 
 def run_batched(args):
+    line = batched_result(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def batched_result(args):
     """Batched pattern: 256 independent filters of uneven N (2^10..2^17) and
     mixed problems advanced round by round (a round = every filter that still
     has an observation assimilates its next one).  The same rounds run three
@@ -628,7 +663,7 @@ def run_batched(args):
     wall_async, _ = reduce_times(dist, wall_async * 1e3, 0, device="cuda")
     wall, wall_sync, wall_async = wall * 1e-3, wall_sync * 1e-3, wall_async * 1e-3
     if rank != 0:
-        return 0
+        return None
     value = total_steps / (dev_ms * 1e-3)
     line = {
         "metric": METRIC, "mode": "batched", "value": value, "unit": UNIT, "n_gpus": world,
@@ -655,11 +690,15 @@ def run_batched(args):
                      "candidate_ms": bstats["tune_ms"]},
         "graph_captures": bstats["graph_captures"],
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_serving(args):
+    print(json.dumps(serving_result(args)), flush=True)
+    return 0
+
+
+def serving_result(args):
     """Serving pattern: a trace of filter sessions arriving as a Poisson
     process, each with observations arriving at exponential intervals, served
     in real time three ways: the server (memory-budget admission, continuous
@@ -674,72 +713,6 @@ def run_serving(args):
     from paper_1411_1702_gb300 import build as B
     B.build()
     from paper_1411_1702_gb300 import pf
-    events = []
-    for s, ss in enumerate(trace):
-        events.append((ss.open_s, 0, s, -1))
-        for k, ta in enumerate(ss.obs_s):
-            events.append((float(ta), 1, s, k))
-    events.sort()
-    n_obs = sum(len(ss.obs_s) for ss in trace)
-    total_steps = sum(ss.w.particle_steps(k) for ss in trace for k in range(len(ss.obs_s)))
-
-    def wait_until(t_start, te):
-        while True:
-            dt = te - (time.perf_counter() - t_start)
-            if dt <= 0:
-                return
-            if dt > 2e-3:
-                time.sleep(dt - 1e-3)
-
-    def serve(lanes):
-        srv = pf.Server(budget_bytes=int(args.serve_budget_gb * (1 << 30)), lanes=lanes)
-        sid = {}
-        lags = []
-        t_start = time.perf_counter()
-        i = 0
-        while i < len(events):
-            now = time.perf_counter() - t_start
-            while i < len(events) and events[i][0] <= now:
-                te, kind, s, k = events[i]
-                ss = trace[s]
-                if kind == 0:
-                    sid[s] = srv.pf_server_open(ss.w, filter_id=s)
-                else:
-                    srv.pf_server_submit(sid[s], ss.w.t_obs[k], ss.w.y_obs[k])
-                    lags.append(time.perf_counter() - t_start - te)
-                    if k == len(ss.obs_s) - 1:
-                        srv.pf_server_close(sid[s])
-                i += 1
-            srv.pf_server_step()
-        srv.pf_server_drain()
-        st = srv.pf_server_stats()
-        srv.close()
-        assert st["assimilations"] == n_obs, st
-        st["submit_lag_p99_ms"] = 1e3 * sorted(lags)[int(0.99 * (len(lags) - 1))]
-        return st
-
-    def serial():
-        fil = {}
-        lat = []
-        t_start = time.perf_counter()
-        first = last = None
-        for te, kind, s, k in events:
-            wait_until(t_start, te)
-            ss = trace[s]
-            if kind == 0:
-                fil[s] = pf.Filter.from_workload(ss.w, filter_id=s)
-                continue
-            fil[s].pf_assimilate(ss.w.t_obs[k], ss.w.y_obs[k])
-            done = time.perf_counter() - t_start
-            lat.append(1e3 * (done - te))
-            first = te if first is None else first
-            last = done
-            if k == len(ss.obs_s) - 1:
-                fil[s].close()
-        lat.sort()
-        pct = lambda q: lat[min(len(lat) - 1, max(0, int(math.ceil(q * len(lat))) - 1))]
-        return {"particle_steps_per_s": total_steps / (last - first), "p50_ms": pct(0.5),
-                "p99_ms": pct(0.99), "mean_ms": sum(lat) / len(lat), "max_ms": lat[-1]}
 
     # warm-up: a short trace through both paths (kernels loaded, pools primed)
     warm = W.serving(n_sessions=6, obs_per_session=3, seed=99)
@@ -751,21 +724,27 @@ def run_serving(args):
     srv.pf_server_drain()
     srv.close()
     torch.cuda.synchronize()
+    budget = int(args.serve_budget_gb * (1 << 30))
     with ClockSampler(0) as clocks:
-        ours = serve(0)
-    one_lane = serve(1)
-    base = serial()
+        ours = serve_trace(pf, trace, 0, budget)
+    one_lane = serve_trace(pf, trace, 1, budget)
+    base = serial_trace(pf, trace)
+    n_obs = sum(len(ss.obs_s) for ss in trace)
+    span = trace_span(trace)
+    capacity = ours["particle_steps_per_s"]   # the server saturated: the GPU's rate on this mix
     line = {
         "metric": METRIC, "mode": "serving", "value": ours["particle_steps_per_s"], "unit": UNIT,
         "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"serving: {len(trace)} sessions, Poisson {200.0:g}/s, "
                                f"N = 2^U{{12..18}}, linear2/robertson/brusselator 1/3 each, "
-                               f"{args.serve_obs} observations per session at Exp(5 ms) gaps, "
-                               f"{args.serve_budget_gb:g} GB budget",
+                               + (f"{args.serve_obs} observations per session"
+                                  if args.serve_obs else "the problem's T observations per session")
+                               + f" at Exp(5 ms) gaps, {args.serve_budget_gb:g} GB budget",
                    "sessions": len(trace), "observations": n_obs,
                    "particles": sum(ss.w.N for ss in trace),
-                   "brusselator_sessions": sum(ss.w.ode == W.BRUSSELATOR for ss in trace)},
+                   "brusselator_sessions": sum(ss.w.ode == W.BRUSSELATOR for ss in trace),
+                   "offered_load": trace_steps(trace) / span / capacity},
         "clocks": clocks.summary(),
         "server": {k: ours[k] for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "epochs",
                                         "mean_sessions_per_epoch", "admitted", "rejected",
@@ -779,8 +758,149 @@ def run_serving(args):
         "throughput_vs_serial": ours["particle_steps_per_s"] / base["particle_steps_per_s"],
         "p99_vs_serial": ours["p99_ms"] / base["p99_ms"],
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    if args.serve_sweep:
+        line["load_sweep"] = serving_sweep(args, pf, capacity, budget)
+    return line
+
+
+def trace_span(trace):
+    """Seconds from the first session's arrival to the last observation's."""
+    return max(float(ss.obs_s[-1]) for ss in trace) - min(ss.open_s for ss in trace)
+
+
+def trace_steps(trace):
+    return sum(ss.w.particle_steps(k) for ss in trace for k in range(len(ss.obs_s)))
+
+
+def _events(trace):
+    events = []
+    for s, ss in enumerate(trace):
+        events.append((ss.open_s, 0, s, -1))
+        for k, ta in enumerate(ss.obs_s):
+            events.append((float(ta), 1, s, k))
+    events.sort()
+    return events
+
+
+def _pct(lat, q):
+    lat = sorted(lat)
+    return lat[min(len(lat) - 1, max(0, int(math.ceil(q * len(lat))) - 1))]
+
+
+def serve_trace(pf, trace, lanes, budget):
+    """Replay the trace in real time through a server (admission by budget,
+    continuous batching over `lanes` lanes, 0 = one per class)."""
+    events = _events(trace)
+    n_obs = sum(len(ss.obs_s) for ss in trace)
+    srv = pf.Server(budget_bytes=budget, lanes=lanes)
+    sid = {}
+    lags = []
+    t_start = time.perf_counter()
+    i = 0
+    while i < len(events):
+        now = time.perf_counter() - t_start
+        while i < len(events) and events[i][0] <= now:
+            te, kind, s, k = events[i]
+            ss = trace[s]
+            if kind == 0:
+                sid[s] = srv.pf_server_open(ss.w, filter_id=s)
+            else:
+                srv.pf_server_submit(sid[s], ss.w.t_obs[k], ss.w.y_obs[k])
+                lags.append(time.perf_counter() - t_start - te)
+                if k == len(ss.obs_s) - 1:
+                    srv.pf_server_close(sid[s])
+            i += 1
+        srv.pf_server_step()
+    srv.pf_server_drain()
+    st = srv.pf_server_stats()
+    srv.close()
+    assert st["assimilations"] == n_obs, st
+    st["submit_lag_p99_ms"] = 1e3 * _pct(lags, 0.99)
+    return st
+
+
+def serial_trace(pf, trace):
+    """Replay the trace in real time with serial per-filter calls: each
+    observation assimilated by pf_assimilate in arrival order, the filter
+    created when its session opens."""
+    def wait_until(t_start, te):
+        while True:
+            dt = te - (time.perf_counter() - t_start)
+            if dt <= 0:
+                return
+            if dt > 2e-3:
+                time.sleep(dt - 1e-3)
+
+    fil = {}
+    lat = []
+    t_start = time.perf_counter()
+    first = last = None
+    for te, kind, s, k in _events(trace):
+        wait_until(t_start, te)
+        ss = trace[s]
+        if kind == 0:
+            fil[s] = pf.Filter.from_workload(ss.w, filter_id=s)
+            continue
+        fil[s].pf_assimilate(ss.w.t_obs[k], ss.w.y_obs[k])
+        done = time.perf_counter() - t_start
+        lat.append(1e3 * (done - te))
+        first = te if first is None else first
+        last = done
+        if k == len(ss.obs_s) - 1:
+            fil[s].close()
+    return {"particle_steps_per_s": trace_steps(trace) / (last - first), "p50_ms": _pct(lat, 0.5),
+            "p99_ms": _pct(lat, 0.99), "mean_ms": sum(lat) / len(lat), "max_ms": max(lat)}
+
+
+def epoch_seconds(pf, w):
+    """Wall time of one synchronous epoch of workload w alone (its second
+    epoch, after a warm one)."""
+    f = pf.Filter.from_workload(w)
+    f.pf_assimilate(w.t_obs[0], w.y_obs[0])
+    t0 = time.perf_counter()
+    f.pf_assimilate(w.t_obs[1], w.y_obs[1])
+    dt = time.perf_counter() - t0
+    f.close()
+    return dt
+
+
+def serving_sweep(args, pf, capacity, budget):
+    """The same kind of trace at loads below the GPU's capacity, so that the
+    latency measures assimilation rather than queueing: a smaller trace
+    (args.sweep_sessions sessions of args.sweep_obs observations) with every
+    arrival time dilated by D, i.e. sessions at 200/D per second and
+    observation gaps of mean 5 D ms.  A session's observations are
+    assimilated one after another, so D is set per target load rho from the
+    slowest session: its epoch time alone (measured here) over its mean gap
+    is rho.  offered_load is the whole trace's work over its span against
+    the capacity the saturated server measured on the full trace."""
+    from paper_1411_1702_gb300 import workloads as W
+    base = W.serving(n_sessions=args.sweep_sessions, obs_per_session=args.sweep_obs, seed=1)
+    span0, work = trace_span(base), trace_steps(base)
+    slowest = {}
+    for ss in base:
+        key = (ss.w.ode, ss.w.N)
+        if key not in slowest:
+            slowest[key] = epoch_seconds(pf, ss.w)
+    t_epoch = max(slowest.values())
+    out = []
+    for rho in args.sweep_loads:
+        D = max(1.0, t_epoch / (5e-3 * rho))
+        trace = W.serving(n_sessions=args.sweep_sessions, obs_per_session=args.sweep_obs, seed=1,
+                          rate_hz=200.0 / D, mean_gap_ms=5.0 * D)
+        ours = serve_trace(pf, trace, 0, budget)
+        ser = serial_trace(pf, trace)
+        out.append({"session_load": rho, "slowest_epoch_ms": 1e3 * t_epoch,
+                    "offered_load": work / (capacity * trace_span(trace)),
+                    "session_rate_per_s": 200.0 / D, "mean_obs_gap_ms": 5.0 * D,
+                    "sessions": len(trace), "observations": sum(len(ss.obs_s) for ss in trace),
+                    "server": {k: ours[k] for k in ("particle_steps_per_s", "p50_ms", "p99_ms",
+                                                    "mean_ms", "max_ms", "epochs",
+                                                    "mean_sessions_per_epoch")},
+                    "serial_per_filter": ser,
+                    "p50_vs_serial": ours["p50_ms"] / ser["p50_ms"],
+                    "p99_vs_serial": ours["p99_ms"] / ser["p99_ms"]})
+    return out
 
 
 def main(argv=None):
@@ -795,11 +915,20 @@ def main(argv=None):
                              "batched", "serving"])
     ap.add_argument("--batch-filters", type=int, default=256)
     ap.add_argument("--serve-sessions", type=int, default=64)
-    ap.add_argument("--serve-obs", type=int, default=10)
+    ap.add_argument("--serve-obs", type=int, default=0,
+                    help="observations per session (0: the problem's T)")
+    ap.add_argument("--serve-sweep", type=int, default=1,
+                    help="also serve a smaller trace at loads below capacity")
+    ap.add_argument("--sweep-sessions", type=int, default=16)
+    ap.add_argument("--sweep-obs", type=int, default=10)
+    ap.add_argument("--sweep-loads", type=float, nargs="+", default=[0.5, 0.25])
+    ap.add_argument("--patterns", type=int, default=1,
+                    help="default run: add the batched and serving objects (one GPU)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--e2e-steps", type=int, default=80)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--ref-particles", type=int, default=16384)
+    ap.add_argument("--ref-particles", type=int, default=0,
+                    help="particles of the reference arm's oracle (0: the workload's N)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="only launch the epochs (for ncu); prints no measurement")

@@ -15,6 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpf_gb300.so")
+# the benchmark's FP64 FMA probe: a library of its own, outside the C ABI
+PROBE_SRC = os.path.join(CSRC, "probe", "fp64_fma_probe.cu")
+PROBE_LIB = os.path.join(HERE, "libpf_fp64_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--threads", "1"]
@@ -38,10 +41,13 @@ def _deps():
 
 
 def stale() -> bool:
-    if not os.path.exists(LIB):
-        return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(p) > t for p in sources() + _deps() + [__file__])
+    for lib, deps in ((LIB, sources() + _deps()), (PROBE_LIB, [PROBE_SRC])):
+        if not os.path.exists(lib):
+            return True
+        t = os.path.getmtime(lib)
+        if any(os.path.getmtime(p) > t for p in deps + [__file__]):
+            return True
+    return False
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -49,6 +55,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    probe_tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    probe = subprocess.Popen([nvcc, *ARCH, *FLAGS, "-shared", PROBE_SRC, "-o", probe_tmp],
+                             stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     procs = []
     objs = []
     for src in sources():
@@ -65,8 +74,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(out.decode(errors="replace"))
         if p.returncode != 0:
             failed.append(src)
+    out, _ = probe.communicate()
+    if verbose or probe.returncode != 0:
+        sys.stderr.write(out.decode(errors="replace"))
+    if probe.returncode != 0:
+        failed.append(PROBE_SRC)
     if failed:
         raise RuntimeError("nvcc failed on: " + ", ".join(failed))
+    os.replace(probe_tmp, PROBE_LIB)
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)

@@ -1,6 +1,8 @@
-// pf_diag.cu -- the FP64 FMA throughput this GPU sustains: the denominator of
-// the roofline of the propagation kernels (one particle per thread, bound by
-// FP64 issue), measured rather than taken from a datasheet.
+// fp64_fma_probe.cu -- a measurement probe for the benchmark, built as its own
+// library (libpf_fp64_probe.so), not part of the sampler's C ABI: the FP64 FMA
+// throughput this GPU sustains, beside the nominal FP64 rate that the roofline
+// of the propagation kernels (one particle per thread, bound by FP64 issue)
+// divides by.
 //
 // Every thread runs kChains independent FMA recurrences acc <- acc * a + b
 // (a < 1, so each converges to b / (1 - a) and never over- or underflows),
@@ -10,11 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <string>
 
-#include "pf_filter.h"
-
-namespace pfg {
 namespace {
 
 constexpr int kChains = 8;
@@ -36,14 +34,13 @@ __global__ void __launch_bounds__(kDiagThreads) k_fp64_fma(int iters, double a, 
 }
 
 }  // namespace
-}  // namespace pfg
 
-extern "C" pf_status pf_fp64_fma_rate(void* stream, double ms, double* tflops) {
-  using namespace pfg;
-  if (!tflops || !(ms > 0.0) || !std::isfinite(ms)) {
-    set_thread_error("pf_fp64_fma_rate: need tflops != NULL and ms > 0");
-    return PF_ERR_INVALID_ARG;
-  }
+// TFLOP/s (an FMA counts 2) of independent FMA chains over every SM for about
+// ms milliseconds (best of three launches after a calibration) on `stream`
+// (a cudaStream_t, NULL = the legacy default stream).  Synchronous.  Returns 0,
+// -1 for bad arguments (tflops NULL, ms <= 0), or the CUDA error code.
+extern "C" int fp64_fma_rate(void* stream, double ms, double* tflops) {
+  if (!tflops || !(ms > 0.0) || !std::isfinite(ms)) return -1;
   *tflops = 0.0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int dev = 0, sms = 0;
@@ -94,10 +91,7 @@ extern "C" pf_status pf_fp64_fma_rate(void* stream, double ms, double* tflops) {
   if (sink) cudaFree(sink);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
-  if (e != cudaSuccess) {
-    set_thread_error(std::string("pf_fp64_fma_rate: ") + cudaGetErrorString(e));
-    return PF_ERR_CUDA;
-  }
+  if (e != cudaSuccess) return (int)e;
   *tflops = best;
-  return PF_OK;
+  return 0;
 }

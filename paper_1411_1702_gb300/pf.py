@@ -39,7 +39,7 @@ ABI_SYMBOLS = [
     "pf_batch_destroy", "pf_server_create", "pf_server_open", "pf_server_submit",
     "pf_server_step", "pf_server_drain", "pf_server_close", "pf_server_session",
     "pf_server_stats", "pf_server_last_error", "pf_server_destroy", "pf_checkpoint_size",
-    "pf_save", "pf_load", "pf_fp64_fma_rate",
+    "pf_save", "pf_load",
 ]
 NOALLOC_MAX_PARTICLES = 1 << 24
 KERNEL_SLOTS = ["stage1", "scan_tile", "scan_add", "resample", "stage2", "moments"]
@@ -130,7 +130,6 @@ def load(path: str = LIB_PATH):
         "pf_get_history": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int), _dp, _dp, _dp]),
         "pf_set_history": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_double]),
         "pf_checkpoint_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
-        "pf_fp64_fma_rate": (C.c_int, [C.c_void_p, C.c_double, _dp]),
         "pf_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
         "pf_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
         "pf_substep_table": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
@@ -208,14 +207,6 @@ def pf_device_bytes(ode, d, p, N):
     """Device bytes a filter of this shape lays out (pf_create_with_buffers)."""
     out = C.c_size_t()
     _check(load().pf_device_bytes(int(ode), int(d), int(p), int(N), C.byref(out)), None)
-    return out.value
-
-
-def pf_fp64_fma_rate(ms=200.0, stream=None):
-    """Sustained FP64 FMA throughput of the current GPU in TFLOP/s."""
-    out = C.c_double()
-    _check(load().pf_fp64_fma_rate(C.c_void_p(stream) if stream else None, float(ms), C.byref(out)),
-           None)
     return out.value
 
 

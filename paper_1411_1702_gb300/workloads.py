@@ -464,14 +464,16 @@ class Session:
     obs_s: np.ndarray
 
 
-def serving(n_sessions: int = 64, rate_hz: float = 200.0, obs_per_session: int = 10,
+def serving(n_sessions: int = 64, rate_hz: float = 200.0, obs_per_session: int = 0,
             mean_gap_ms: float = 5.0, seed: int = 0, n_log2=(12, 18)) -> list:
     """Serving trace: sessions arrive as a Poisson process (rate_hz); each is
     linear2, robertson or brusselator with probability 1/3, N = 2^k with k
     uniform on n_log2 (4096 ... 262144), its true parameter drawn from that
     problem's prior (the Brusselator keeps its reference parameter), and its
     observations arrive at exponential intervals of mean mean_gap_ms, the
-    first one a gap after the session opens."""
+    first one a gap after the session opens.  A session has obs_per_session
+    observations, or its problem's T (linear2 50, robertson 40, brusselator
+    30) when that is 0."""
     rng = np.random.default_rng([seed, 0x5E55])
     out = []
     t = 0.0
@@ -479,17 +481,17 @@ def serving(n_sessions: int = 64, rate_hz: float = 200.0, obs_per_session: int =
         t += rng.exponential(1.0 / rate_hz)
         N = 2 ** int(rng.integers(n_log2[0], n_log2[1] + 1))
         kind = int(rng.integers(3))
+        T = obs_per_session or (50, 40, 30)[kind]
         if kind == 0:
             lo, hi = np.array([0.1, 100.0]), np.array([10.0, 1e4])
-            w = linear2(N=N, T=obs_per_session, seed=s,
-                        theta=np.exp(rng.uniform(np.log(lo), np.log(hi))))
+            w = linear2(N=N, T=T, seed=s, theta=np.exp(rng.uniform(np.log(lo), np.log(hi))))
         elif kind == 1:
             star = np.array([0.04, 3e7, 1e4])
-            w = robertson(N=N, T=obs_per_session, seed=s, rtol=1e-8,
+            w = robertson(N=N, T=T, seed=s, rtol=1e-8,
                           theta=np.exp(rng.uniform(np.log(star / 10.0), np.log(star * 10.0))))
         else:
-            w = brusselator(N=N, T=obs_per_session, seed=s)
-        gaps = rng.exponential(mean_gap_ms * 1e-3, size=obs_per_session)
+            w = brusselator(N=N, T=T, seed=s)
+        gaps = rng.exponential(mean_gap_ms * 1e-3, size=T)
         out.append(Session(w=w.with_(stream=s), open_s=t, obs_s=t + np.cumsum(gaps)))
     return out
 

@@ -40,3 +40,41 @@ def test_support_roofline_arithmetic():
     assert out["kernels"]["scan_tile"]["achieved"] == pytest.approx(16e6 / 250e-6 / 1e9)
     assert "scan_add" not in out["kernels"]          # no pass of its own
     assert out["bound"] == "hbm" and out["unit"] == "GB/s"
+
+
+def test_serving_trace_lengths_and_dilation():
+    # sessions carry their problem's T observations by default
+    tr = W.serving(n_sessions=12, seed=5)
+    for ss in tr:
+        assert len(ss.obs_s) == {W.LINEAR2: 50, W.ROBERTSON: 40, W.BRUSSELATOR: 30}[ss.w.ode]
+        assert ss.w.T == len(ss.obs_s)
+    # the load sweep dilates time: the same sessions, every arrival scaled by D
+    a = W.serving(n_sessions=6, obs_per_session=4, seed=1)
+    D = 7.5
+    b = W.serving(n_sessions=6, obs_per_session=4, seed=1, rate_hz=200.0 / D, mean_gap_ms=5.0 * D)
+    for sa, sb in zip(a, b):
+        assert (sa.w.ode, sa.w.N) == (sb.w.ode, sb.w.N)
+        assert sb.open_s == pytest.approx(D * sa.open_s, rel=1e-12)
+        assert sb.obs_s == pytest.approx(D * sa.obs_s, rel=1e-12)
+    assert bench.trace_span(b) == pytest.approx(D * bench.trace_span(a), rel=1e-12)
+    assert bench.trace_steps(a) == bench.trace_steps(b) == sum(
+        ss.w.particle_steps(k) for ss in a for k in range(4))
+
+
+def test_percentile_rule():
+    lat = list(range(1, 101))
+    assert bench._pct(lat, 0.5) == 50 and bench._pct(lat, 0.99) == 99
+    assert bench._pct([3.0], 0.99) == 3.0
+
+
+@pytest.mark.gpu
+def test_fp64_fma_probe_reaches_the_nominal_peak():
+    """The benchmark's FMA probe (its own library, outside the sampler's C
+    ABI) sustains close to the FP64 rate the roofline divides by (2 FMA lanes
+    per clock per SM at the maximum clock, 1.259 TFLOP/s on a 152-SM GB300):
+    between half and 110 % of it."""
+    from paper_1411_1702_gb300 import build as B
+    B.build()
+    r = bench.fp64_fma_rate(50.0, None)
+    assert r is not None and 0.5 * 1.259 < r < 1.1 * 1.259, r
+    assert bench.fp64_fma_rate(0.0, None) is None

@@ -100,16 +100,6 @@ def test_checkpoint_rejects_a_different_filter(pf):
     _same(_snapshot(b), _snapshot(c))
 
 
-def test_fp64_fma_rate_reaches_the_nominal_peak(pf):
-    """The diagnostic FMA kernel sustains close to the FP64 rate the roofline
-    divides by (2 FMA lanes per clock per SM at the maximum clock, 1.259
-    TFLOP/s on a 152-SM GB300): between half and 110 % of it."""
-    r = pf.pf_fp64_fma_rate(50.0)
-    assert 0.5 * 1.259 < r < 1.1 * 1.259, r
-    with pytest.raises(pf.PfError):
-        pf.pf_fp64_fma_rate(0.0)
-
-
 @pytest.mark.parametrize("name", ["robertson", "brusselator", "advdiff20"])
 def test_estimates_after_assimilate_equal_a_device_read(pf, name):
     # pf_estimates right after pf_assimilate is served from the values that
