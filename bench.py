@@ -903,6 +903,99 @@ def serving_sweep(args, pf, capacity, budget):
     return out
 
 
+def run_sharded(args):
+    """One filter of the workload's N particles split into shards
+    (paper_1411_1702_gb300/shard.py): one shard per rank under torchrun,
+    exchanging over NCCL, or --shards G shards driven by threads on one GPU.
+    A step is one epoch of the whole filter; value = its particle-LMM-steps
+    over the slowest rank's time."""
+    import torch
+    from paper_1411_1702_gb300 import workloads as W
+    from paper_1411_1702_gb300 import shard as SH
+    dist, rank, world = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_1411_1702_gb300 import build as B
+    B.build()
+    from paper_1411_1702_gb300 import pf
+    w = W.get(args.workload)
+    G = world if dist is not None else max(1, args.shards)
+    tile = pf.pf_shard_tile(w.N)
+    bounds = SH.shard_bounds(w.N, G, tile)
+    mine = [rank] if dist is not None else list(range(G))
+    engines = {q: SH.LibraryShard(pf, w, w.N, bounds[q], bounds[q + 1] - bounds[q]) for q in mine}
+    torch.cuda.synchronize()
+    if dist is not None:
+        comms = {rank: SH.TorchComm(device=torch.device("cuda", local))}
+    else:
+        hub = SH.ThreadComm(G, timeout=600.0)
+        comms = {q: hub.view(q) for q in mine}
+    filters = {}
+
+    def each(fn):
+        """fn(q) for every shard of this process, side by side."""
+        if len(mine) == 1:
+            fn(mine[0])
+            return
+        errs = []
+
+        def body(q):
+            try:
+                fn(q)
+            except BaseException as ex:   # noqa: BLE001 - re-raised below
+                errs.append(ex)
+                hub.abort()
+        th = [threading.Thread(target=body, args=(q,)) for q in mine]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        if errs:
+            raise errs[0]
+
+    each(lambda q: filters.__setitem__(q, SH.ShardedFilter(engines[q], comms[q], bounds, tile)))
+    k = 0
+
+    def step():
+        nonlocal k
+        kk = k
+        each(lambda q: filters[q].assimilate(w.t_obs[kk], w.y_obs[kk]))
+        k += 1
+        return kk
+
+    for _ in range(args.warmup):
+        step()
+    K = min(args.steps, w.T - args.warmup)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    steps_done = 0
+    with ClockSampler(local) as clocks:
+        t0 = time.perf_counter()
+        for _ in range(K):
+            steps_done += w.particle_steps(step())
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    total_ms, _ = reduce_times(dist, wall * 1e3, 0, device="cuda")
+    for e in engines.values():
+        e.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "mode": "sharded", "value": steps_done / (total_ms * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": total_ms / K,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": dict(config_of(w), parallelism=(f"{G} shards over {world} ranks (NCCL)" if dist
+                                                  else f"{G} shards on one GPU (threads)"),
+                       shards=G, shard_tile=tile, bounds=bounds[:3] + ["..."] if G > 3 else bounds),
+        "clocks": clocks.summary(),
+        "timing": "wall time of whole epochs, all exchanges included",
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -930,6 +1023,9 @@ def main(argv=None):
     ap.add_argument("--ref-particles", type=int, default=0,
                     help="particles of the reference arm's oracle (0: the workload's N)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sharded", action="store_true",
+                    help="one filter split into shards: one per rank, or --shards on one GPU")
+    ap.add_argument("--shards", type=int, default=1)
     ap.add_argument("--profile", action="store_true",
                     help="only launch the epochs (for ncu); prints no measurement")
     args = ap.parse_args(argv)
@@ -940,6 +1036,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.sharded and args.impl != "reference":
+        return run_sharded(args)
     w = W.get(args.workload)
     if args.impl == "reference":
         return run_reference(args, w)

@@ -481,6 +481,112 @@ pf_status pf_resample_systematic_noalloc(const double* log_g, int64_t N, double 
 pf_status pf_systematic_indices(const double* cumulative, int64_t N, double u, int32_t* idx,
                                 void* stream);
 
+/* ---- a particle-sharded filter -------------------------------------------
+ * Algorithm 1's loops over particles are independent of one another (the
+ * paper's particle-parallel layout, Sec. 3.1), so one filter of N particles
+ * can be split into G contiguous shards, one per GPU, each a pf_filter over
+ * the global slots [first, first + n).  Per epoch the shards share only:
+ *  - Step 3a: the maximum of the log fitness weights (an exact max-reduce) and
+ *    the tile totals of the cumulative weights (a gather, in slot order);
+ *  - Step 3b/3c: the parent of every resampled slot, which may live on another
+ *    shard: each shard resamples the outputs whose parent it holds and sends
+ *    each parent's record to the shard of the output's slot (an all-to-all);
+ *  - Steps 5-6: the maximum of the new log weights and the moment sums (a
+ *    max-reduce and a gather, added in shard order).
+ * The calls below run one phase each on `opt->stream` and return what the
+ * other shards need; the caller does the exchange (over NCCL, gloo or host
+ * memory) and must call them in this order, on every shard, each epoch:
+ *   pf_shard_stage1 -> (max of lg_max) -> pf_shard_scan -> (gather the tiles)
+ *   -> pf_shard_offsets -> (plan the output ranges) -> pf_shard_resample ->
+ *   (all-to-all of the records) -> pf_shard_stage2 -> (max of lw_max) ->
+ *   pf_shard_moments -> (add the sums) -> pf_shard_commit.
+ * After pf_shard_create the order starts at pf_shard_moments (Step 1's
+ * moments, lw_max = 0) and pf_shard_commit.  A call out of order returns
+ * PF_ERR_STATE; if the global maximum of a stage is -inf (every weight zero)
+ * the epoch is degenerate: call pf_shard_abort on every shard, which leaves
+ * the committed state as it was.
+ *
+ * Random numbers are keyed by the global slot, and a shard starts on a tile
+ * of the whole ensemble's scan (first a multiple of pf_shard_tile(N)), so the
+ * cumulative weights, the resampled parents and every propagated state are
+ * bit-identical to those of one filter of all N particles given the same
+ * committed state; the moments, added in shard order, equal its to rounding.
+ * The whole-filter calls pf_assimilate, pf_run, pf_load_observations,
+ * pf_reset, pf_save and pf_load return PF_ERR_STATE on a shard, and a shard
+ * cannot join a batch; pf_estimates, pf_get_ensemble (the shard's slots, log
+ * weights normalised over the whole ensemble), pf_set_ensemble, pf_set_moments,
+ * pf_get_history, pf_set_history, pf_stats and pf_get_work serve it. */
+
+/* Tile length of the cumulative-weight scan of an ensemble of N particles:
+ * shard boundaries must be multiples of it.  0 if N < 1. */
+int64_t pf_shard_tile(int64_t N);
+
+/* Create the shard holding the global slots [first, first + n) of a filter of
+ * N particles (other arguments as pf_create; the ODE may not be
+ * PF_ODE_ADVDIFF2D).  first must be a multiple of pf_shard_tile(N), and n too
+ * unless first + n = N.  Step 1 is drawn for its slots; its moments are
+ * committed by pf_shard_moments + pf_shard_commit.  Errors as pf_create. */
+pf_status pf_shard_create(pf_ode ode, int d, int p, int64_t N, int64_t first, int64_t n, pf_lmm lmm,
+                          double dt, const pf_prior* prior, const pf_options* opt, pf_filter** out);
+
+/* The shard's shape: the whole ensemble's N, its first slot, its number of
+ * scan tiles, the whole ensemble's number of tiles, and the doubles of one
+ * parent record (3d + p + 2).  Any pointer may be NULL. */
+pf_status pf_shard_info(const pf_filter* f, int64_t* total, int64_t* first, int* tiles,
+                        int* tiles_all, int* record);
+
+/* Steps 2 and 3a on the shard for the observation y_k (m doubles, host) at
+ * t_k; *lg_max (host) gets the shard's largest log fitness weight (-inf if
+ * every one of its weights is zero). */
+pf_status pf_shard_stage1(pf_filter* f, double t_k, const double* y_k, double* lg_max);
+
+/* Step 3a's tile pass with the global maximum lg_max (finite): tiles (host,
+ * pf_shard_info's `tiles` doubles) gets this shard's tile totals, *cl_last
+ * (host) the tile-local cumulative weight of its last slot. */
+pf_status pf_shard_scan(pf_filter* f, double lg_max, double* tiles, double* cl_last);
+
+/* The global cumulative weights from every shard's tile totals (tiles_all:
+ * host, `tiles_all` doubles in slot order; cl_last: the last shard's): into
+ * tile_end (host, tiles_all doubles) the cumulative weight at the last slot of
+ * every tile, into *total the last one c_{N-1}, into *u the epoch's
+ * resampling uniform (the same on every shard). */
+pf_status pf_shard_offsets(pf_filter* f, const double* tiles_all, double cl_last, double* tile_end,
+                           double* total, double* u);
+
+/* Step 3b for the outputs i in [i_lo, i_hi) whose parent this shard holds:
+ * l_i = min{k : c_k > ((i + u)/N) c_{N-1}}, or, for i >= i_fb (where that
+ * threshold reaches c_{N-1}), the first k with c_k = c_{N-1}.  The parent's
+ * record (x, h1, h2: d each; phi: p; ll1; the global parent slot) of output i
+ * goes to send + (i - i_lo) * (3d + p + 2) (device memory the caller owns).
+ * Errors: INVALID_ARG (range outside [0, N], u outside [0, 1), total <= 0,
+ * NULL send with outputs), STATE, CUDA. */
+pf_status pf_shard_resample(pf_filter* f, int64_t i_lo, int64_t i_hi, int64_t i_fb, double u,
+                            double total, double* send);
+
+/* Steps 3c-5 for this shard's slots from the parent records of its slots in
+ * slot order (recv: device memory the caller owns, n records); *lw_max (host)
+ * gets the shard's largest new log weight. */
+pf_status pf_shard_stage2(pf_filter* f, const double* recv, double* lw_max);
+
+/* Step 6's weighted sums of the shard's new ensemble with the global maximum
+ * lw_max (finite; 0 for Step 1): into sums (host, *nv doubles: sum of
+ * weights, of their squares, of the weighted parameters about the committed
+ * mean, of their products, of the weighted states). */
+pf_status pf_shard_moments(pf_filter* f, double lw_max, double* sums, int* nv);
+
+/* Commit with the global sums (every shard's, added in shard order; host, nv
+ * doubles): the new mean, C, its factor, x-bar, ESS and the normalisation,
+ * identical on every shard.  Errors: NUMERIC (non-finite moments; nothing is
+ * committed and the epoch may be redone), INVALID_ARG, STATE, CUDA. */
+pf_status pf_shard_commit(pf_filter* f, const double* sums, int nv);
+
+/* Drop the epoch in progress (a degenerate one): the committed state stays. */
+pf_status pf_shard_abort(pf_filter* f);
+
+/* The global parent slot of each of the shard's n slots in the last epoch
+ * (host, n int32). */
+pf_status pf_shard_parents(const pf_filter* f, int32_t* parents);
+
 /* Library version string. */
 const char* pf_version(void);
 

@@ -62,6 +62,7 @@ class Config(C.Structure):
         ("a", C.c_double), ("kappa", C.c_double), ("seed", C.c_uint64), ("stream", C.c_uint32),
         ("prior_kind", C.c_int * PMAX), ("prior_lo", C.c_double * PMAX),
         ("prior_hi", C.c_double * PMAX), ("x0", C.c_double * DMAX), ("t0", C.c_double),
+        ("slot0", C.c_uint32),
     ]
 
 
@@ -122,6 +123,12 @@ def lib():
             "or_get_work": (None, [C.c_void_p, _dp, _dp, _dp, _ip]),
             "or_get_history": (None, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp, _dp, _dp]),
             "or_set_history": (None, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double]),
+            "or_shard_init": (C.c_int, [C.c_void_p]),
+            "or_get_pending_lw": (None, [C.c_void_p, _dp]),
+            "or_set_ll1": (None, [C.c_void_p, _dp]),
+            "or_shard_nsums": (C.c_int, [C.c_void_p]),
+            "or_shard_sums": (None, [C.c_void_p, C.c_int, C.c_double, _dp]),
+            "or_shard_commit": (C.c_int, [C.c_void_p, C.c_int, C.c_double, _dp, C.c_double]),
             "or_threads": (C.c_int, []),
             "or_set_threads": (None, [C.c_int]),
         }
@@ -335,11 +342,12 @@ def make_config(w) -> Config:
 class Filter:
     """Algorithm 1 on the CPU, one epoch per observation."""
 
-    def __init__(self, workload, N=None):
+    def __init__(self, workload, N=None, slot0=0):
         w = workload
         self.cfg = make_config(w)
         if N is not None:
             self.cfg.N = int(N)
+        self.cfg.slot0 = int(slot0)
         self.N, self.d, self.p, self.m = self.cfg.N, w.d, w.p, len(w.obs_idx)
         self._h = lib().or_create(C.byref(self.cfg))
         if not self._h:
@@ -414,6 +422,27 @@ class Filter:
         idx = np.zeros(N, dtype=np.int32)
         lib().or_get_work(self._h, _d(ll1), _d(lg), _d(c), _i(idx))
         return dict(ll1=ll1, lg=lg, c=c, idx=idx)
+
+    # a shard of a particle-sharded filter (cfg.slot0 = its first global slot)
+    def shard_init(self):
+        return lib().or_shard_init(self._h)
+
+    def pending_lw(self):
+        out = np.zeros(self.N)
+        lib().or_get_pending_lw(self._h, _d(out))
+        return out
+
+    def set_ll1(self, ll1):
+        lib().or_set_ll1(self._h, _d(np.ascontiguousarray(ll1, dtype=np.float64)))
+
+    def shard_sums(self, pending, M):
+        out = np.zeros(lib().or_shard_nsums(self._h))
+        lib().or_shard_sums(self._h, int(pending), float(M), _d(out))
+        return out
+
+    def shard_commit(self, pending, M, sums, t_next=0.0):
+        sums = np.ascontiguousarray(sums, dtype=np.float64)
+        return lib().or_shard_commit(self._h, int(pending), float(M), _d(sums), float(t_next))
 
     def history(self):
         e, dp = C.c_int(), C.c_int()

@@ -968,7 +968,7 @@ int or_init(or_filter* f) {
   int p = f->p, d = f->d;
   for (int64_t n = 0; n < f->N; ++n) {
     for (int i = 0; i < p; ++i) {
-      double u = or_uniform(cfg->seed, cfg->stream, OR_RNG_INIT, (uint32_t)n, 0u, i);
+      double u = or_uniform(cfg->seed, cfg->stream, OR_RNG_INIT, (uint32_t)n + cfg->slot0, 0u, i);
       double th;
       if (cfg->prior_kind[i] == OR_LOGUNIFORM) {
         double lo = log(cfg->prior_lo[i]), hi = log(cfg->prior_hi[i]);
@@ -1072,7 +1072,8 @@ int or_stage2(or_filter* f, const or_substep* tab, int S, const double* y, const
     int64_t l = idx[n];
     double ph[OR_PMAX], th[OR_PMAX], z[OR_PMAX], x[OR_DMAX], h1[OR_DMAX], h2[OR_DMAX];
     double E[OR_DMAX];
-    for (int i = 0; i < p; ++i) z[i] = or_normal(cfg->seed, cfg->stream, OR_RNG_THETA, (uint32_t)n, epoch, i);
+    const uint32_t slot = (uint32_t)n + cfg->slot0;
+    for (int i = 0; i < p; ++i) z[i] = or_normal(cfg->seed, cfg->stream, OR_RNG_THETA, slot, epoch, i);
     double shrunk[OR_PMAX];
     or_liu_west_shrink(p, a, &f->phi[l * p], f->phibar, shrunk);
     for (int i = 0; i < p; ++i) {
@@ -1087,7 +1088,7 @@ int or_stage2(or_filter* f, const or_substep* tab, int S, const double* y, const
     for (int i = 0; i < d; ++i) E[i] = 0.0;
     int bad = or_propagate(cfg->ode, d, cfg->newton_iters, th, tab, S, x, h1, h2, E);
     for (int i = 0; i < d; ++i) {
-      double zi = or_normal(cfg->seed, cfg->stream, OR_RNG_INNOV, (uint32_t)n, epoch, i);
+      double zi = or_normal(cfg->seed, cfg->stream, OR_RNG_INNOV, slot, epoch, i);
       double v = sqrt(cfg->kappa * E[i]) * zi;
       x[i] += v;
       h1[i] += v;
@@ -1196,6 +1197,90 @@ void or_get_history(const or_filter* f, int* epoch, int* depth, double* t_prev, 
 void or_set_history(or_filter* f, int epoch, int depth, double t_prev, double hprev1, double hprev2) {
   f->epoch = epoch; f->depth = depth; f->t_prev = t_prev;
   f->hprev1 = hprev1; f->hprev2 = hprev2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* A shard of a particle-sharded filter                                     */
+/* ------------------------------------------------------------------------ */
+int or_shard_init(or_filter* f) {
+  int st = or_init(f);
+  for (int64_t n = 0; n < f->N; ++n) f->lw[n] = 0.0;
+  /* the sums of every shard are taken about one common shift: zero for
+   * Step 1 (the committed mean afterwards) */
+  for (int i = 0; i < f->p; ++i) f->phibar[i] = 0.0;
+  for (int i = 0; i < f->p * f->p; ++i) f->C[i] = 0.0;
+  return st;
+}
+
+void or_get_pending_lw(const or_filter* f, double* lw) { memcpy(lw, f->nlw, sizeof(double) * f->N); }
+
+void or_set_ll1(or_filter* f, const double* ll1) { memcpy(f->ll1, ll1, sizeof(double) * f->N); }
+
+int or_shard_nsums(const or_filter* f) { return 2 + f->p + f->p * (f->p + 1) / 2 + f->d; }
+
+/* Step 6's weighted sums of one shard, about the committed mean phibar */
+void or_shard_sums(const or_filter* f, int pending, double M, double* sums) {
+  const int p = f->p, d = f->d;
+  const double* lw = pending ? f->nlw : f->lw;
+  const double* phi = pending ? f->nphi : f->phi;
+  const double* x = pending ? f->nx : f->x;
+  const int ns = or_shard_nsums(f);
+  for (int k = 0; k < ns; ++k) sums[k] = 0.0;
+  double* S1 = sums + 2;
+  double* S2 = S1 + p;
+  double* Sx = S2 + p * (p + 1) / 2;
+  for (int64_t n = 0; n < f->N; ++n) {
+    double e = exp(lw[n] - M);
+    if (e == 0.0) continue; /* a zero-weight particle contributes nothing */
+    sums[0] += e;
+    sums[1] += e * e;
+    double dp[OR_PMAX];
+    for (int i = 0; i < p; ++i) {
+      dp[i] = phi[n * p + i] - f->phibar[i];
+      S1[i] += e * dp[i];
+    }
+    int q = 0;
+    for (int i = 0; i < p; ++i)
+      for (int j = i; j < p; ++j) S2[q++] += e * dp[i] * dp[j];
+    for (int i = 0; i < d; ++i) Sx[i] += e * x[n * d + i];
+  }
+}
+
+int or_shard_commit(or_filter* f, int pending, double M, const double* sums, double t_next) {
+  const int p = f->p, d = f->d;
+  const double S0 = sums[0];
+  if (!(S0 > 0.0)) return OR_ERR_DEGENERATE;
+  const double* S1 = sums + 2;
+  const double* S2 = S1 + p;
+  const double* Sx = S2 + p * (p + 1) / 2;
+  double m[OR_PMAX];
+  for (int i = 0; i < p; ++i) m[i] = S1[i] / S0;
+  int q = 0;
+  for (int i = 0; i < p; ++i)
+    for (int j = i; j < p; ++j) {
+      double v = S2[q++] / S0 - m[i] * m[j];
+      f->C[i * p + j] = v;
+      f->C[j * p + i] = v;
+    }
+  for (int i = 0; i < p; ++i) f->phibar[i] += m[i];
+  for (int i = 0; i < d; ++i) f->xbar[i] = Sx[i] / S0;
+  f->ess = S0 * S0 / sums[1];
+  const double lse = M + log(S0);
+  if (pending) {
+    double* t;
+    t = f->x; f->x = f->nx; f->nx = t;
+    t = f->h1; f->h1 = f->nh1; f->nh1 = t;
+    t = f->h2; f->h2 = f->nh2; f->nh2 = t;
+    t = f->phi; f->phi = f->nphi; f->nphi = t;
+    t = f->lw; f->lw = f->nlw; f->nlw = t;
+    f->depth = f->pend_depth;
+    f->hprev1 = f->pend_h1;
+    f->hprev2 = f->pend_h2;
+    f->t_prev = t_next;
+    f->epoch += 1;
+  }
+  for (int64_t n = 0; n < f->N; ++n) f->lw[n] = f->lw[n] - lse;
+  return OR_OK;
 }
 
 int or_threads(void) {

@@ -70,6 +70,8 @@ typedef struct {
   double prior_lo[OR_PMAX], prior_hi[OR_PMAX];
   double x0[OR_DMAX];
   double t0;        /* time of the initial state                            */
+  uint32_t slot0;   /* first global slot of a shard (its random streams are
+                       keyed by the global slot); 0 for a whole filter       */
 } or_config;
 
 /* One substep of the LMM on the shared grid.
@@ -154,6 +156,28 @@ void or_get_history(const or_filter* f, int* epoch, int* depth, double* t_prev,
                     double* hprev1, double* hprev2);
 void or_set_history(or_filter* f, int epoch, int depth, double t_prev, double hprev1,
                     double hprev2);
+/* --- a shard of a particle-sharded filter (Sec. 3.1's particle loops split
+ * over processes): Step 5's normalisation and Step 6's moments taken from
+ * sums over every shard.  Test infrastructure for the sharded protocol. */
+/* Step 1's draws for the shard's slots; raw log weight 0; the moments are
+ * zero (the common shift of Step 1's sums) until or_shard_commit */
+int or_shard_init(or_filter* f);
+/* raw log weights of the last or_stage2 (before any normalisation) */
+void or_get_pending_lw(const or_filter* f, double* lw);
+/* first-stage log-likelihoods (as received with the parents) */
+void or_set_ll1(or_filter* f, const double* ll1);
+/* number of Step 6 sums: 2 + p + p(p+1)/2 + d */
+int or_shard_nsums(const or_filter* f);
+/* Step 6's sums over the shard's new ensemble (pending = 1) or its committed
+ * one (pending = 0, Step 1), with weights e_n = exp(lw_n - M): sum e, sum e^2,
+ * sum e (phi - phibar), sum e (phi_i - phibar_i)(phi_j - phibar_j) (i <= j),
+ * sum e x, phibar the committed mean */
+void or_shard_sums(const or_filter* f, int pending, double M, double* sums);
+/* commit with the sums over every shard: phibar += S1 / S0,
+ * C = S2 / S0 - (S1 / S0)(S1 / S0)^T, xbar = Sx / S0, ess = S0^2 / W2, and the
+ * log weights normalised by M + log S0; pending = 1 takes the new ensemble
+ * and advances the history (or_commit's bookkeeping) */
+int or_shard_commit(or_filter* f, int pending, double M, const double* sums, double t_next);
 int or_threads(void);
 void or_set_threads(int n);
 #endif

@@ -778,6 +778,7 @@ pf_status pf_batch_create(pf_filter* const* filters, int n, void* stream, pf_bat
   for (int i = 0; i < n; ++i) {
     if (!filters[i]) return bfail(nullptr, PF_ERR_INVALID_ARG, "NULL filter");
     if (filters[i]->in_batch) return bfail(nullptr, PF_ERR_INVALID_ARG, "filter already in a batch");
+    if (filters[i]->shard_total > 0) return bfail(nullptr, PF_ERR_INVALID_ARG, "a shard cannot join a batch");
     for (int j = 0; j < i; ++j)
       if (filters[j] == filters[i]) return bfail(nullptr, PF_ERR_INVALID_ARG, "filter listed twice");
   }

@@ -116,8 +116,29 @@ static size_t layout(pf_filter* f, char* base) {
   f->fd.c = (double*)take(sizeof(double) * N);
   f->fd.idx = (int32_t*)take(sizeof(int32_t) * N);
   f->fd.blk = (double*)take(sizeof(double) * max_grid_blocks(N));
-  f->fd.boff = (double*)take(sizeof(double) * scan_tiles(N));
-  f->fd.pmax = (double*)take(sizeof(double) * scan_tiles(N));
+  if (f->shard_total > 0) {
+    // a shard keeps the whole ensemble's tile offsets; its own tiles are the
+    // slice from its first tile on
+    const int nb = f->shard_tiles_all;
+    const int64_t t0 = f->shard_first / scan_tile_len(f->shard_total);
+    f->sh_boff = (double*)take(sizeof(double) * nb);
+    f->sh_pmax = (double*)take(sizeof(double) * nb);
+    f->sh_tiles = (double*)take(sizeof(double) * nb);
+    f->sh_out = (double*)take(sizeof(double) * (nb + 2));
+    f->sh_sums = (double*)take(sizeof(double) * f->fd.nrec);
+    f->fd.boff = f->sh_boff ? f->sh_boff + t0 : nullptr;
+    f->fd.pmax = f->sh_pmax ? f->sh_pmax + t0 : nullptr;
+    f->sh_parent.x = (double*)take(sizeof(double) * N * d);
+    f->sh_parent.h1 = (double*)take(sizeof(double) * N * d);
+    f->sh_parent.h2 = (double*)take(sizeof(double) * N * d);
+    f->sh_parent.phi = (double*)take(sizeof(double) * N * p);
+    f->sh_parent.lw = nullptr;
+    f->sh_parent_ll1 = (double*)take(sizeof(double) * N);
+    f->sh_gparent = (int32_t*)take(sizeof(int32_t) * N);
+  } else {
+    f->fd.boff = (double*)take(sizeof(double) * scan_tiles(N));
+    f->fd.pmax = (double*)take(sizeof(double) * scan_tiles(N));
+  }
   f->fd.tsq = (double*)take(sizeof(double) * kMomentBlocks);
   f->fd.part = (double*)take(sizeof(double) * kMomentBlocks * f->fd.nrec);
   // model work arrays: the Brusselator's stage buffers; the 2D system's
@@ -171,6 +192,11 @@ static pf_status read_ctrl(pf_filter* f) {
 }
 
 namespace pfg {
+pf_status record_error(pf_filter* f, pf_status st, const std::string& msg) { return fail(f, st, msg); }
+pf_status read_control(pf_filter* f) { return read_ctrl(f); }
+}  // namespace pfg
+
+namespace pfg {
 
 cudaError_t preload_kernels() {
   static std::mutex mu;
@@ -194,6 +220,7 @@ cudaError_t preload_kernels() {
 // filters) nothing waits; a non-finite start shows up as the sticky status of
 // the filter's first epoch.
 static pf_status do_init(pf_filter* f, bool check = true) {
+  const bool shard = f->shard_total > 0;
   Ctrl* h = f->ctrl_host;
   std::memset(h, 0, sizeof(Ctrl));
   h->cur = 0;
@@ -207,8 +234,13 @@ static pf_status do_init(pf_filter* f, bool check = true) {
   PF_CUDA(f, upload_small(const_cast<double*>(f->fd.x0), f->x0.data(), sizeof(double) * f->d,
                           f->stream));
   PF_CUDA(f, cudaMemsetAsync(f->fd.ticket, 0, sizeof(unsigned) * 8, f->stream));
-  PF_CUDA(f, launch_init(f->ode, f->fd, f->stream));
+  // a shard draws its particles; the moments wait for every shard's sums
+  PF_CUDA(f, shard ? launch_init_draws(f->ode, f->fd, f->stream) : launch_init(f->ode, f->fd, f->stream));
   f->hist = HistoryState{0, 0, f->t0, 0.0, 0.0};
+  if (shard) {
+    f->sh_stage = kShardInitDrawn;  // its moments wait for pf_shard_moments + pf_shard_commit
+    return PF_OK;
+  }
   if (!check) return PF_OK;
   pf_status st = read_ctrl(f);
   if (st != PF_OK) return st;
@@ -378,7 +410,8 @@ namespace pfg {
 
 pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
                         const pf_prior* prior, const pf_options* opt, cudaMemPool_t pool,
-                        pf_filter** out, void* ext_mem, size_t ext_bytes) {
+                        pf_filter** out, void* ext_mem, size_t ext_bytes, int64_t shard_total,
+                        int64_t shard_first) {
   if (!out) return fail(nullptr, PF_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   {
@@ -429,6 +462,12 @@ pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double 
   fd.a = f->a; fd.s = std::sqrt(1.0 - f->a * f->a); fd.kappa = f->kappa;
   fd.seed = f->seed; fd.stream_id = f->filter_id;
   fd.nrec = moment_record_size(ode);
+  fd.slot0 = (uint32_t)shard_first;
+  fd.Ntile = shard_total > 0 ? shard_total : N;
+  fd.shard_sums = nullptr;
+  f->shard_total = shard_total;
+  f->shard_first = shard_first;
+  f->shard_tiles_all = shard_total > 0 ? scan_tile_count(shard_total) : 0;
   for (int i = 0; i < kPMax; ++i) {
     fd.prior_kind[i] = i < p ? f->prior_kind[i] : 0;
     fd.prior_lo[i] = i < p ? f->prior_lo[i] : 0.0;
@@ -526,6 +565,7 @@ const char* pf_last_error(const pf_filter* f) {
 
 pf_status pf_assimilate(pf_filter* f, double t_k, const double* y_k) {
   const pfg::NvtxRange nvtx_range("pf_assimilate");
+  if (f && f->shard_total > 0) return fail(f, PF_ERR_STATE, "a shard's epochs run through the pf_shard_* calls");
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
   if (!y_k) return fail(f, PF_ERR_INVALID_ARG, "y_k is NULL");
   for (int i = 0; i < f->m; ++i)
@@ -641,6 +681,7 @@ pf_status pf_kernel_times(pf_filter* f, double* ms, int64_t* launches, int n) {
 }
 
 pf_status pf_load_observations(pf_filter* f, int T, const double* t, const double* y) {
+  if (f && f->shard_total > 0) return fail(f, PF_ERR_STATE, "a shard's epochs run through the pf_shard_* calls");
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
   if (T < 1 || !t || !y) return fail(f, PF_ERR_INVALID_ARG, "need T >= 1 observations");
   PF_CUDA(f, cudaStreamSynchronize(f->stream));
@@ -683,6 +724,7 @@ pf_status pf_load_observations(pf_filter* f, int T, const double* t, const doubl
 }
 
 pf_status pf_run(pf_filter* f, int k0, int k1) {
+  if (f && f->shard_total > 0) return fail(f, PF_ERR_STATE, "a shard's epochs run through the pf_shard_* calls");
   if (f) f->est_fresh = false;
   const pfg::NvtxRange nvtx_range("pf_run");
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
@@ -717,6 +759,7 @@ pf_status pf_synchronize(pf_filter* f) {
 }
 
 pf_status pf_reset(pf_filter* f) {
+  if (f && f->shard_total > 0) return fail(f, PF_ERR_STATE, "a shard's epochs run through the pf_shard_* calls");
   if (f) f->est_fresh = false;
   if (!f) return fail(nullptr, PF_ERR_INVALID_ARG, "filter is NULL");
   PF_CUDA(f, cudaStreamSynchronize(f->stream));
@@ -831,13 +874,14 @@ pf_status pf_get_work(const pf_filter* cf, double* loglik1, double* log_g, doubl
   if (cumulative) {
     // c as the scan leaves it (tile-local sums) with the tile offsets and
     // floors, combined here exactly as the device reads them (CumTiles)
-    const int nt = scan_tiles(f->N);
+    // (a shard: its own tiles of the whole ensemble's tiling)
+    const int64_t len = scan_tile_len(f->fd.Ntile);
+    const int nt = (int)((f->N + len - 1) / len);
     std::vector<double> boff(nt), pmax(nt);
     PF_CUDA(f, copy_sync(f, cumulative, f->fd.c, nb, cudaMemcpyDeviceToHost));
     PF_CUDA(f, copy_sync(f, boff.data(), f->fd.boff, sizeof(double) * nt, cudaMemcpyDeviceToHost));
     PF_CUDA(f, copy_sync(f, pmax.data(), f->fd.pmax, sizeof(double) * nt, cudaMemcpyDeviceToHost));
     tile_bytes = 2 * sizeof(double) * (size_t)nt;
-    const int64_t len = scan_tile_len(f->N);
     for (int64_t k = 0; k < f->N; ++k) {
       const int64_t t = k / len;
       cumulative[k] = max_nonneg_host(boff[t] + cumulative[k], pmax[t]);
@@ -883,6 +927,7 @@ pf_status pf_checkpoint_size(const pf_filter* f, size_t* bytes) {
 }
 
 pf_status pf_save(const pf_filter* cf, void* buf, size_t bytes) {
+  if (cf && cf->shard_total > 0) return fail(const_cast<pf_filter*>(cf), PF_ERR_STATE, "a shard's epochs run through the pf_shard_* calls");
   pf_filter* f = const_cast<pf_filter*>(cf);
   if (!f || !buf) return fail(nullptr, PF_ERR_INVALID_ARG, "NULL argument");
   const size_t need = ckpt_bytes(f);
@@ -919,6 +964,7 @@ pf_status pf_save(const pf_filter* cf, void* buf, size_t bytes) {
 }
 
 pf_status pf_load(pf_filter* f, const void* buf, size_t bytes) {
+  if (f && f->shard_total > 0) return fail(f, PF_ERR_STATE, "a shard's epochs run through the pf_shard_* calls");
   if (f) f->est_fresh = false;
   if (!f || !buf) return fail(nullptr, PF_ERR_INVALID_ARG, "NULL argument");
   if (f->in_batch) return fail(f, PF_ERR_STATE, "the filter is a member of a batch");

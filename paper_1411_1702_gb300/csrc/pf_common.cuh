@@ -137,6 +137,15 @@ struct FilterDev {
   double prior_lo[kPMax], prior_hi[kPMax];
   const double* x0; // fixed initial state (d)
   double* xbar;     // committed weighted mean of x (d)
+  // A shard of a particle-sharded filter holds the global slots
+  // [slot0, slot0 + N) of an ensemble of Ntile particles: its random streams
+  // are keyed by the global slot, and its cumulative weights use the tiling of
+  // the global ensemble.  A filter of its own has slot0 = 0 and Ntile = N.
+  uint32_t slot0;
+  int64_t Ntile;
+  // if set, the moments kernel stores its weighted sums here instead of
+  // committing (a shard's part of the global sums)
+  double* shard_sums;
 };
 
 // ---------------------------------------------------------------- Philox
@@ -163,9 +172,12 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// n is the particle's slot in its filter (a shard adds its first global
+// slot); the epoch's resampling uniform is keyed by slot 0 of the whole filter.
 __device__ __forceinline__ U4 draw_block(const FilterDev& fd, uint32_t purpose, uint32_t n,
                                          uint32_t epoch, uint32_t block) {
-  return philox4x32_10(U4{n, epoch, purpose | (block << 8), fd.stream_id},
+  const uint32_t slot = purpose == kRngResample ? n : n + fd.slot0;
+  return philox4x32_10(U4{slot, epoch, purpose | (block << 8), fd.stream_id},
                        (uint32_t)(fd.seed & 0xffffffffu), (uint32_t)(fd.seed >> 32));
 }
 

@@ -19,6 +19,11 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// The first phases of a shard's epoch (pf_shard.cu): committed and idle, or
+// Step 1 drawn with its moments still to be committed.
+constexpr int kShardIdle = 0;
+constexpr int kShardInitDrawn = 1;
+
 struct HistoryState {
   int64_t epochs;
   int depth;
@@ -76,6 +81,22 @@ struct pf_filter {
   double last_ms = 0.0;
   int64_t h2d_bytes = 0, d2h_bytes = 0;
   bool in_batch = false;                  // epochs are driven by a pf_batch
+  // a shard of a particle-sharded filter (pf_shard_create): the global slots
+  // [shard_first, shard_first + N) of an ensemble of shard_total particles
+  int64_t shard_total = 0;                // 0: a filter of its own
+  int64_t shard_first = 0;
+  int shard_tiles_all = 0;                // scan tiles of the whole ensemble
+  pfg::Ensemble sh_parent{};              // received parents by slot (SoA)
+  double* sh_parent_ll1 = nullptr;
+  int32_t* sh_gparent = nullptr;          // global parent slot of each slot
+  double* sh_tiles = nullptr;             // every shard's tile totals (upload)
+  double* sh_boff = nullptr;              // the whole ensemble's tile offsets
+  double* sh_pmax = nullptr;              // and floors
+  double* sh_out = nullptr;               // tile ends, c_{N-1}, u
+  double* sh_sums = nullptr;              // moment sums (this shard's, then the global ones)
+  int sh_stage = 0;                       // last stage call of the epoch in progress
+  int sh_depth_out = 0;                   // history after the epoch in progress
+  double sh_t = 0.0;
   std::string err;
 };
 
@@ -91,9 +112,17 @@ pf_status check_create_args(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, dou
 // implicitly device-wide synchronising call (the server's sessions).  A NULL
 // pool is pf_create.  ext_mem (with ext_bytes) is caller-owned device memory
 // the filter lays itself out in instead (pf_create_with_buffers).
+// shard_total > 0 makes a shard of that many particles holding the global
+// slots [shard_first, shard_first + N): Step 1 draws its particles but leaves
+// the commit to pf_shard_commit with the global moment sums.
 pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double dt,
                         const pf_prior* prior, const pf_options* opt, cudaMemPool_t pool,
-                        pf_filter** out, void* ext_mem = nullptr, size_t ext_bytes = 0);
+                        pf_filter** out, void* ext_mem = nullptr, size_t ext_bytes = 0,
+                        int64_t shard_total = 0, int64_t shard_first = 0);
+// a fail() for other translation units: records msg on f (or the thread)
+pf_status record_error(pf_filter* f, pf_status st, const std::string& msg);
+// The control block into f->ctrl_host (waits for the stream).
+pf_status read_control(pf_filter* f);
 // Device bytes of a filter of this shape (its single allocation).
 size_t filter_device_bytes(int ode, int d, int p, int64_t N);
 // History after an epoch with parameter block ep.

@@ -265,7 +265,7 @@ __device__ __forceinline__ void stage1_body(const FilterDev& fd, const EpochPara
 // its readers apply the tile offsets and floors (CumTiles).
 __device__ __forceinline__ ScanArgs scan_args(const FilterDev& fd) {
   Ctrl* ctrl = fd.ctrl;
-  return ScanArgs{fd.lg, fd.N, ctrl->lg_max, fd.c, fd.blk, fd.boff, fd.pmax, fd.ticket + 1,
+  return ScanArgs{fd.lg, fd.N, fd.Ntile, ctrl->lg_max, fd.c, fd.blk, fd.boff, fd.pmax, fd.ticket + 1,
                   &ctrl->c_total};
 }
 
@@ -281,7 +281,7 @@ __device__ __forceinline__ void scan_tile_body(const FilterDev& fd, int vb, int 
 // The filter's cumulative weights as the tile pass leaves them: the offsets
 // and floors are applied on read (no separate offset pass over c).
 __device__ __forceinline__ CumTiles cum_tiles(const FilterDev& fd) {
-  return CumTiles{fd.c, fd.boff, fd.pmax, (uint32_t)scan_tile_len(fd.N)};
+  return CumTiles{fd.c, fd.boff, fd.pmax, (uint32_t)scan_tile_len(fd.Ntile)};
 }
 
 __device__ __forceinline__ double resample_u(const FilterDev& fd, const EpochParams* __restrict__ ep) {
@@ -458,6 +458,10 @@ __device__ __forceinline__ void block_sum_vec(double (&acc)[NV], double* s_part,
 }
 
 template <int D, int P>
+__device__ __forceinline__ void moments_commit(const FilterDev& fd, int is_init, const double* s_tot,
+                                               double* s_part, int* s_flag);
+
+template <int D, int P>
 __device__ __forceinline__ void moments_body(const FilterDev& fd, int is_init, int vb, int vg,
                                              double* s_part, double* s_tot, int* s_flag) {
   using Lay = MomentLayout<D, P>;
@@ -530,6 +534,24 @@ __device__ __forceinline__ void moments_body(const FilterDev& fd, int is_init, i
     s_tot[k] = t;
   }
   __syncthreads();
+  if (fd.shard_sums) {
+    // a shard: its sums are one part of the global ones, which the commit
+    // takes (moments_commit, after the caller has added every shard's)
+    for (int k = threadIdx.x; k < NV; k += blockDim.x) fd.shard_sums[k] = s_tot[k];
+    return;
+  }
+  moments_commit<D, P>(fd, is_init, s_tot, s_part, s_flag);
+}
+
+// The commit of Step 6 from the weighted sums s_tot (shared memory) of the
+// pending buffer: every thread of one block calls it.
+template <int D, int P>
+__device__ __forceinline__ void moments_commit(const FilterDev& fd, int is_init, const double* s_tot,
+                                               double* s_part, int* s_flag) {
+  using Lay = MomentLayout<D, P>;
+  Ctrl* ctrl = fd.ctrl;
+  const int cur = ctrl->cur;
+  const double M = ctrl->lw_max;
   // The commit.  Moments about the shift c (the previous mean): the first
   // moment of the differences gives the mean's displacement to full relative
   // precision, so C = E[(phi - c)(phi - c)^T] - m m^T loses only
@@ -1091,6 +1113,205 @@ cudaError_t preload_main_kernels() {
     }
   }
   return cudaSuccess;
+}
+
+// ================================================ shard of a sharded filter
+// Algorithm 1 over a global ensemble split into contiguous shards, one per GPU
+// (the particle-parallel layout of Sec. 3.1): each shard runs the phases above
+// on its own particles, and the host exchanges what couples them -- the
+// log-sum-exp shift, the tile totals of the cumulative weights, the parents
+// of the resampled slots and the moment sums.  A shard starts on a tile
+// boundary of the global scan tiling, so its tile totals are those of a
+// filter of the whole ensemble, and so are the offsets below.
+
+// The global tile offsets and floors from every tile's total (all shards',
+// in slot order): the block of scan_offsets_core a filter of the whole
+// ensemble runs, so they are bit-identical to its.  out[t] = c at the last
+// slot of tile t (a full tile: boff + T), out[nb] = c_{N-1} from the last
+// tile's last tile-local value cl_last, out[nb + 1] = the epoch's resampling
+// uniform.
+__global__ void __launch_bounds__(kScanThreads) k_shard_offsets(const __grid_constant__ FilterDev fd,
+                                                              const EpochParams* __restrict__ ep,
+                                                              const double* __restrict__ tiles, int nb,
+                                                              double cl_last, double* boff_all,
+                                                              double* pmax_all, double* out) {
+  __shared__ double s_warp[33];
+  scan_offsets_core(tiles, nb, boff_all, pmax_all, s_warp, nullptr);
+  __syncthreads();
+  for (int t = threadIdx.x; t < nb; t += blockDim.x)
+    out[t] = max_nonneg(boff_all[t] + tiles[t], pmax_all[t]);
+  if (threadIdx.x == 0) {
+    const double total = max_nonneg(boff_all[nb - 1] + cl_last, pmax_all[nb - 1]);
+    out[nb] = total;
+    out[nb + 1] = resample_u(fd, ep);
+    fd.ctrl->c_total = total;
+  }
+}
+
+// Step 3b for the outputs i in [i_lo, i_lo + cnt) whose parent lies in this
+// shard: l_i = min{k : c_k > tau_i} over the shard's cumulative weights (the
+// first k with c_k = c_{N-1} for i >= i_fb, where tau_i reaches the total),
+// tau_i = ((i + u)/N) c_{N-1} over the whole ensemble.  Each output's parent
+// record -- x, h1, h2 (d each), phi (p), ll1, the global parent slot -- goes to
+// send[j * R], j = i - i_lo, R = 3d + p + 2.
+__global__ void __launch_bounds__(256) k_shard_resample(const __grid_constant__ FilterDev fd, int64_t i_lo,
+                                                       int64_t cnt, int64_t i_fb, double u, double total,
+                                                       int64_t n_all, double* __restrict__ send) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= cnt) return;
+  const int64_t i = i_lo + j;
+  const CumTiles c = cum_tiles(fd);
+  const int64_t N = fd.N;
+  int64_t l;
+  if (i >= i_fb) {
+    l = lower_bound_bits(c, N, __double_as_longlong(total));
+  } else {
+    const double tau = ((double)i + u) / (double)n_all * total;
+    l = upper_bound_bits(c, N, __double_as_longlong(tau));
+  }
+  // the host plans only outputs whose parent lies here, so l < N; the clamp
+  // keeps a wrong plan from reading past the shard
+  if (l >= N) l = N - 1;
+  const Ensemble E = committed(fd, fd.ctrl->cur);
+  const int d = fd.d, p = fd.p;
+  double* r = send + j * (int64_t)(3 * d + p + 2);
+  for (int k = 0; k < d; ++k) {
+    r[k] = E.x[k * N + l];
+    r[d + k] = E.h1[k * N + l];
+    r[2 * d + k] = E.h2[k * N + l];
+  }
+  for (int k = 0; k < p; ++k) r[3 * d + k] = E.phi[k * N + l];
+  r[3 * d + p] = fd.ll1[l];
+  r[3 * d + p + 1] = (double)(l + (int64_t)fd.slot0);
+}
+
+// The received parent records of this shard's slots (in slot order) into the
+// parent buffers stage 2 gathers from (x, h1, h2, phi: SoA; ll1), the slot's
+// own index as its gather index, and the global parent slot.
+__global__ void __launch_bounds__(256) k_shard_unpack(const __grid_constant__ FilterDev fd,
+                                                     const double* __restrict__ recv, Ensemble par,
+                                                     double* __restrict__ par_ll1,
+                                                     int32_t* __restrict__ gparent) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t N = fd.N;
+  if (n >= N) return;
+  const int d = fd.d, p = fd.p;
+  const double* r = recv + n * (int64_t)(3 * d + p + 2);
+  for (int k = 0; k < d; ++k) {
+    par.x[k * N + n] = r[k];
+    par.h1[k * N + n] = r[d + k];
+    par.h2[k * N + n] = r[2 * d + k];
+  }
+  for (int k = 0; k < p; ++k) par.phi[k * N + n] = r[3 * d + k];
+  par_ll1[n] = r[3 * d + p];
+  gparent[n] = (int32_t)r[3 * d + p + 1];
+  fd.idx[n] = (int32_t)n;
+}
+
+// Step 6's commit from the global moment sums (every shard's, added in shard
+// order by the host), then the factor L of the new C for the next epoch's
+// Step 4a (cholesky_psd, as the resampling launch of a filter forms it).
+template <int D, int P>
+__global__ void __launch_bounds__(kMomentThreads) k_shard_commit(const __grid_constant__ FilterDev fd,
+                                                               const double* __restrict__ sums,
+                                                               int is_init) {
+  constexpr int NV = MomentLayout<D, P>::kN;
+  __shared__ double s_part[kMomentShared<NV>];
+  __shared__ double s_tot[NV];
+  __shared__ int s_flag;
+  if (fd.ctrl->status != PF_OK) return;
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) s_tot[k] = sums[k];
+  __syncthreads();
+  moments_commit<D, P>(fd, is_init, s_tot, s_part, &s_flag);
+  __syncthreads();
+  if (threadIdx.x == 0 && fd.ctrl->status == PF_OK) {
+    double L[kPMax * kPMax];
+    cholesky_psd(fd.p, fd.ctrl->C, L);
+    for (int i = 0; i < kPMax * kPMax; ++i) fd.ctrl->L[i] = L[i];
+  }
+}
+
+// Step 1's draws alone (a shard's moments are committed from the global sums)
+cudaError_t launch_init_draws(int ode, const FilterDev& fd, cudaStream_t st) {
+  const unsigned g = (unsigned)phase_blocks(kPhaseInit, ode, fd.N);
+  switch (ode) {
+    case PF_ODE_LINEAR2: k_init<2, 2><<<g, kInitThreads, 0, st>>>(fd); break;
+    case PF_ODE_ROBERTSON: k_init<3, 3><<<g, kInitThreads, 0, st>>>(fd); break;
+    case PF_ODE_MICHAELIS3: k_init<3, 4><<<g, kInitThreads, 0, st>>>(fd); break;
+    case PF_ODE_BRUSSELATOR1D: k_init<64, 3><<<g, kInitThreads, 0, st>>>(fd); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Stage 1 or 2 of one epoch of a filter whose moments and ensemble are set
+// (a shard: for stage 2 the caller passes the descriptor whose committed
+// buffers are the received parents)
+cudaError_t launch_stage(int stage, const FilterDev& fd, const EpochParams* ep, int S,
+                         cudaStream_t st) {
+  if (fd.ode == PF_ODE_BRUSSELATOR1D) return launch_bruss_stage(stage, fd, ep, S, st);
+  StageKernel k1, k2;
+  switch (fd.ode) {
+    case PF_ODE_LINEAR2: stage_kernels<Linear2>(fd.lmm, k1, k2); break;
+    case PF_ODE_ROBERTSON: stage_kernels<Robertson>(fd.lmm, k1, k2); break;
+    case PF_ODE_MICHAELIS3: stage_kernels<Michaelis>(fd.lmm, k1, k2); break;
+    default: return cudaErrorInvalidValue;
+  }
+  const unsigned g = (unsigned)phase_blocks(kPhaseStage1, fd.ode, fd.N);
+  (stage == 1 ? k1 : k2)<<<g, kSmallThreads, (size_t)S * sizeof(StepCoef), st>>>(fd, ep);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_tiles(const FilterDev& fd, int ntiles, cudaStream_t st) {
+  k_scan_tile<<<(unsigned)ntiles, kScanThreads, 0, st>>>(fd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shard_offsets(const FilterDev& fd, const EpochParams* ep, const double* tiles,
+                                 int nb, double cl_last, double* boff_all, double* pmax_all,
+                                 double* out, cudaStream_t st) {
+  k_shard_offsets<<<1, kScanThreads, 0, st>>>(fd, ep, tiles, nb, cl_last, boff_all, pmax_all, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shard_resample(const FilterDev& fd, int64_t i_lo, int64_t cnt, int64_t i_fb,
+                                  double u, double total, int64_t n_all, double* send,
+                                  cudaStream_t st) {
+  if (cnt <= 0) return cudaSuccess;
+  k_shard_resample<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(fd, i_lo, cnt, i_fb, u, total,
+                                                                   n_all, send);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shard_unpack(const FilterDev& fd, const double* recv, const Ensemble& par,
+                                double* par_ll1, int32_t* gparent, cudaStream_t st) {
+  k_shard_unpack<<<(unsigned)((fd.N + 255) / 256), 256, 0, st>>>(fd, recv, par, par_ll1, gparent);
+  return cudaGetLastError();
+}
+
+// The moment sums of the pending buffer (fd.shard_sums set) with the shift
+// lw_max already in the control block.
+cudaError_t launch_shard_moments(const FilterDev& fd, cudaStream_t st) {
+  const unsigned g = (unsigned)phase_blocks(kPhaseMoments, fd.ode, fd.N);
+  switch (fd.ode) {
+    case PF_ODE_LINEAR2: k_moments<2, 2><<<g, kMomentThreads, 0, st>>>(fd, 0); break;
+    case PF_ODE_ROBERTSON: k_moments<3, 3><<<g, kMomentThreads, 0, st>>>(fd, 0); break;
+    case PF_ODE_MICHAELIS3: k_moments<3, 4><<<g, kMomentThreads, 0, st>>>(fd, 0); break;
+    case PF_ODE_BRUSSELATOR1D: k_moments<64, 3><<<g, kMomentThreads, 0, st>>>(fd, 0); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shard_commit(const FilterDev& fd, const double* sums, int is_init, cudaStream_t st) {
+  switch (fd.ode) {
+    case PF_ODE_LINEAR2: k_shard_commit<2, 2><<<1, kMomentThreads, 0, st>>>(fd, sums, is_init); break;
+    case PF_ODE_ROBERTSON: k_shard_commit<3, 3><<<1, kMomentThreads, 0, st>>>(fd, sums, is_init); break;
+    case PF_ODE_MICHAELIS3: k_shard_commit<3, 4><<<1, kMomentThreads, 0, st>>>(fd, sums, is_init); break;
+    case PF_ODE_BRUSSELATOR1D: k_shard_commit<64, 3><<<1, kMomentThreads, 0, st>>>(fd, sums, is_init); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 bool ode_supported(int ode) {

@@ -85,6 +85,22 @@ int scan_tiles(int64_t N);
 int kernels_per_epoch(int ode);
 bool ode_supported(int ode);
 
+// A shard of a particle-sharded filter (pf_shard.cu drives these).
+cudaError_t launch_init_draws(int ode, const FilterDev& fd, cudaStream_t st);
+cudaError_t launch_stage(int stage, const FilterDev& fd, const EpochParams* ep, int S,
+                         cudaStream_t st);
+cudaError_t launch_scan_tiles(const FilterDev& fd, int ntiles, cudaStream_t st);
+cudaError_t launch_shard_offsets(const FilterDev& fd, const EpochParams* ep, const double* tiles,
+                                 int nb, double cl_last, double* boff_all, double* pmax_all,
+                                 double* out, cudaStream_t st);
+cudaError_t launch_shard_resample(const FilterDev& fd, int64_t i_lo, int64_t cnt, int64_t i_fb,
+                                  double u, double total, int64_t n_all, double* send,
+                                  cudaStream_t st);
+cudaError_t launch_shard_unpack(const FilterDev& fd, const double* recv, const Ensemble& par,
+                                double* par_ll1, int32_t* gparent, cudaStream_t st);
+cudaError_t launch_shard_moments(const FilterDev& fd, cudaStream_t st);
+cudaError_t launch_shard_commit(const FilterDev& fd, const double* sums, int is_init, cudaStream_t st);
+
 // Substep table of one observation interval (host code, pf_grid.cu).
 int build_substeps(int lmm, int spacing, double dt, int substeps, double q0, double t_prev,
                    double t_next, int depth, double hprev1, double hprev2, StepCoef* tab,

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kNaThreads) k_na_max(const double* __restrict_
 // the filter's scan (scan_tile_core, scan_add_core) on the caller's buffers
 __device__ __forceinline__ ScanArgs na_scan_args(const double* lg, int64_t N, double* c,
                                                  const NaScratch& sc) {
-  return ScanArgs{lg, N, __ldcg(sc.head), c, sc.tile, sc.boff, sc.pmax, sc.ticket + 1, nullptr};
+  return ScanArgs{lg, N, N, __ldcg(sc.head), c, sc.tile, sc.boff, sc.pmax, sc.ticket + 1, nullptr};
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_na_scan_tile(const double* __restrict__ lg,

@@ -138,6 +138,8 @@ struct MaxNonnegOp {
 struct ScanArgs {
   const double* lg;  // N log weights
   int64_t N;
+  int64_t Ntile;     // the ensemble size whose tile length applies (N, or the
+                     // whole ensemble's size for a shard of it)
   double M;          // their maximum (the log-sum-exp shift)
   double* c;         // N cumulative weights (tile-local after the tile pass)
   double* tile;      // per-tile totals
@@ -147,11 +149,39 @@ struct ScanArgs {
   double* c_total;   // optional: c_{N-1}
 };
 
+// Tile offsets boff_b = sum of the earlier tile totals, and the running
+// maximum pmax_b of the earlier tiles' last values boff_b' + T_b', from the nb
+// tile totals, by one block; c_total (if set) gets the largest last value,
+// c_{N-1}.  The order of additions depends only on nb and the block size.
+__device__ __forceinline__ void scan_offsets_core(const double* tile, int nb, double* boff,
+                                                  double* pmax, double* s_warp, double* c_total) {
+  const int chunk = (nb + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * chunk;
+  double acc = 0.0;
+  for (int b = b0; b < b0 + chunk && b < nb; ++b) acc += __ldcg(tile + b);
+  double grand;
+  double off = block_exclusive_scan<SumOp>(acc, s_warp, grand);
+  double lmax = 0.0;
+  for (int b = b0; b < b0 + chunk && b < nb; ++b) {
+    boff[b] = off;
+    const double T = __ldcg(tile + b);
+    lmax = max_nonneg(lmax, off + T);
+    off += T;
+  }
+  double gmax;
+  double pm = block_exclusive_scan<MaxNonnegOp>(lmax, s_warp, gmax);
+  for (int b = b0; b < b0 + chunk && b < nb; ++b) {
+    pmax[b] = pm;
+    pm = max_nonneg(pm, boff[b] + __ldcg(tile + b));
+  }
+  if (threadIdx.x == 0 && c_total) *c_total = gmax;
+}
+
 // Tile vb of vg: tile-local cumulative sums; the last tile to finish turns the
 // tile totals into offsets and floors.
 __device__ __forceinline__ void scan_tile_core(const ScanArgs& a, int vb, int vg, double* s_warp,
                                                int* s_flag) {
-  const int items = scan_items(a.N);
+  const int items = scan_items(a.Ntile);
   const int64_t base = (int64_t)vb * kScanThreads * items + (int64_t)threadIdx.x * items;
   double v[kScanItemsMax];
   double run = 0.0;
@@ -175,37 +205,14 @@ __device__ __forceinline__ void scan_tile_core(const ScanArgs& a, int vb, int vg
     if (j < items && k < a.N) a.c[k] = max_nonneg(v[j], floor_prev);
   }
   if (threadIdx.x == 0) a.tile[vb] = tile_last;
-  if (elect_last_block(a.ticket, s_flag, (unsigned)vg)) {
-    // tile offsets boff_b = sum of earlier tile totals, and the running maximum
-    // pmax_b of the earlier tiles' last values boff_b' + T_b'
-    const int nb = vg;
-    const int chunk = (nb + blockDim.x - 1) / blockDim.x;
-    const int b0 = threadIdx.x * chunk;
-    double acc = 0.0;
-    for (int b = b0; b < b0 + chunk && b < nb; ++b) acc += __ldcg(a.tile + b);
-    double grand;
-    double off = block_exclusive_scan<SumOp>(acc, s_warp, grand);
-    double lmax = 0.0;
-    for (int b = b0; b < b0 + chunk && b < nb; ++b) {
-      a.boff[b] = off;
-      const double T = __ldcg(a.tile + b);
-      lmax = max_nonneg(lmax, off + T);
-      off += T;
-    }
-    double gmax;
-    double pm = block_exclusive_scan<MaxNonnegOp>(lmax, s_warp, gmax);
-    for (int b = b0; b < b0 + chunk && b < nb; ++b) {
-      a.pmax[b] = pm;
-      pm = max_nonneg(pm, a.boff[b] + __ldcg(a.tile + b));
-    }
-    if (threadIdx.x == 0 && a.c_total) *a.c_total = gmax;
-  }
+  if (elect_last_block(a.ticket, s_flag, (unsigned)vg))
+    scan_offsets_core(a.tile, vg, a.boff, a.pmax, s_warp, a.c_total);
 }
 
 // c_k = max(tile offset + tile-local sum, tile floor)
 __device__ __forceinline__ void scan_add_core(const ScanArgs& a, int64_t k) {
   if (k < a.N) {
-    const int64_t b = k / scan_tile_len(a.N);
+    const int64_t b = k / scan_tile_len(a.Ntile);
     a.c[k] = max_nonneg(__ldcg(a.boff + b) + a.c[k], __ldcg(a.pmax + b));
   }
 }

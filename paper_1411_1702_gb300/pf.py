@@ -39,7 +39,9 @@ ABI_SYMBOLS = [
     "pf_batch_destroy", "pf_server_create", "pf_server_open", "pf_server_submit",
     "pf_server_step", "pf_server_drain", "pf_server_close", "pf_server_session",
     "pf_server_stats", "pf_server_last_error", "pf_server_destroy", "pf_checkpoint_size",
-    "pf_save", "pf_load",
+    "pf_save", "pf_load", "pf_shard_tile", "pf_shard_create", "pf_shard_info", "pf_shard_stage1",
+    "pf_shard_scan", "pf_shard_offsets", "pf_shard_resample", "pf_shard_stage2", "pf_shard_moments",
+    "pf_shard_commit", "pf_shard_abort", "pf_shard_parents",
 ]
 NOALLOC_MAX_PARTICLES = 1 << 24
 KERNEL_SLOTS = ["stage1", "scan_tile", "scan_add", "resample", "stage2", "moments"]
@@ -159,6 +161,22 @@ def load(path: str = LIB_PATH):
         "pf_server_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
         "pf_server_last_error": (C.c_char_p, [C.c_void_p]),
         "pf_server_destroy": (None, [C.c_void_p]),
+        "pf_shard_tile": (C.c_int64, [C.c_int64]),
+        "pf_shard_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64,
+                                      C.c_int, C.c_double, C.POINTER(Prior), C.POINTER(Options),
+                                      C.POINTER(C.c_void_p)]),
+        "pf_shard_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "pf_shard_stage1": (C.c_int, [C.c_void_p, C.c_double, _dp, _dp]),
+        "pf_shard_scan": (C.c_int, [C.c_void_p, C.c_double, _dp, _dp]),
+        "pf_shard_offsets": (C.c_int, [C.c_void_p, _dp, C.c_double, _dp, _dp, _dp]),
+        "pf_shard_resample": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_double,
+                                        C.c_double, C.c_void_p]),
+        "pf_shard_stage2": (C.c_int, [C.c_void_p, C.c_void_p, _dp]),
+        "pf_shard_moments": (C.c_int, [C.c_void_p, C.c_double, _dp, C.POINTER(C.c_int)]),
+        "pf_shard_commit": (C.c_int, [C.c_void_p, _dp, C.c_int]),
+        "pf_shard_abort": (C.c_int, [C.c_void_p]),
+        "pf_shard_parents": (C.c_int, [C.c_void_p, _ip]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -227,7 +245,8 @@ class Filter:
 
     def __init__(self, ode, d, p, N, lmm, dt, prior_kind, prior_lo, prior_hi, x0, t0, *,
                  a, newton_iters, spacing, substeps, q0, history, transform, obs_idx, noise,
-                 sigma, kappa, seed, filter_id=0, stream=None, timing=False, device_buffer=None):
+                 sigma, kappa, seed, filter_id=0, stream=None, timing=False, device_buffer=None,
+                 shard=None):
         L = load()
         self._keep = []
         kind = (C.c_int * len(prior_kind))(*[int(k) for k in prior_kind])
@@ -242,7 +261,12 @@ class Filter:
                      float(kappa), int(seed), int(filter_id), C.c_void_p(stream) if stream else None,
                      1 if timing else 0)
         h = C.c_void_p()
-        if device_buffer is None:
+        if shard is not None:
+            # the slots [first, first + N) of a sharded filter of n_all particles
+            n_all, first = shard
+            st = L.pf_shard_create(int(ode), int(d), int(p), int(n_all), int(first), int(N),
+                                   int(lmm), float(dt), C.byref(pr), C.byref(op), C.byref(h))
+        elif device_buffer is None:
             st = L.pf_create(int(ode), int(d), int(p), int(N), int(lmm), float(dt), C.byref(pr),
                              C.byref(op), C.byref(h))
         else:
@@ -262,13 +286,13 @@ class Filter:
 
     @classmethod
     def from_workload(cls, w, N=None, stream=None, seed=None, filter_id=0, timing=False,
-                      device_buffer=None):
+                      device_buffer=None, shard=None):
         return cls(w.ode, w.d, w.p, int(N if N is not None else w.N), w.lmm, w.dt, w.prior_kind,
                    w.prior_lo, w.prior_hi, w.x0, w.t0, a=w.a, newton_iters=w.newton_iters,
                    spacing=w.spacing, substeps=w.substeps, q0=w.q0, history=w.history,
                    transform=w.transform, obs_idx=w.obs_idx, noise=w.noise, sigma=w.sigma,
                    kappa=w.kappa, seed=w.seed if seed is None else seed, filter_id=filter_id,
-                   stream=stream, timing=timing, device_buffer=device_buffer)
+                   stream=stream, timing=timing, device_buffer=device_buffer, shard=shard)
 
     @classmethod
     def borrowed(cls, handle, ode, d, p, N, m):
@@ -378,6 +402,68 @@ class Filter:
     def pf_load(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))
         _check(load().pf_load(self._h, buf, len(blob)), self._h)
+
+
+    # ---- a shard of a particle-sharded filter (pf_shard_* in include/pf.h);
+    # device buffers are addresses (int), host arrays NumPy
+    def pf_shard_info(self):
+        tot, first = C.c_int64(), C.c_int64()
+        nt, nta, rec = C.c_int(), C.c_int(), C.c_int()
+        _check(load().pf_shard_info(self._h, C.byref(tot), C.byref(first), C.byref(nt),
+                                    C.byref(nta), C.byref(rec)), self._h)
+        return dict(total=tot.value, first=first.value, tiles=nt.value, tiles_all=nta.value,
+                    record=rec.value)
+
+    def pf_shard_stage1(self, t, y):
+        m = C.c_double()
+        _check(load().pf_shard_stage1(self._h, float(t), _d(_f64(y)), C.byref(m)), self._h)
+        return m.value
+
+    def pf_shard_scan(self, lg_max, n_tiles):
+        tiles = np.zeros(n_tiles)
+        cl = C.c_double()
+        _check(load().pf_shard_scan(self._h, float(lg_max), _d(tiles), C.byref(cl)), self._h)
+        return tiles, cl.value
+
+    def pf_shard_offsets(self, tiles_all, cl_last):
+        ta = _f64(tiles_all)
+        ends = np.zeros(len(ta))
+        tot, u = C.c_double(), C.c_double()
+        _check(load().pf_shard_offsets(self._h, _d(ta), float(cl_last), _d(ends), C.byref(tot),
+                                       C.byref(u)), self._h)
+        return ends, tot.value, u.value
+
+    def pf_shard_resample(self, i_lo, i_hi, i_fb, u, total, send_ptr):
+        _check(load().pf_shard_resample(self._h, int(i_lo), int(i_hi), int(i_fb), float(u),
+                                        float(total), C.c_void_p(int(send_ptr)) if send_ptr else None),
+               self._h)
+
+    def pf_shard_stage2(self, recv_ptr):
+        m = C.c_double()
+        _check(load().pf_shard_stage2(self._h, C.c_void_p(int(recv_ptr)), C.byref(m)), self._h)
+        return m.value
+
+    def pf_shard_moments(self, lw_max):
+        sums = np.zeros(128)
+        nv = C.c_int()
+        _check(load().pf_shard_moments(self._h, float(lw_max), _d(sums), C.byref(nv)), self._h)
+        return sums[:nv.value].copy()
+
+    def pf_shard_commit(self, sums):
+        sm = _f64(sums)
+        _check(load().pf_shard_commit(self._h, _d(sm), len(sm)), self._h)
+
+    def pf_shard_abort(self):
+        _check(load().pf_shard_abort(self._h), self._h)
+
+    def pf_shard_parents(self):
+        out = np.zeros(self.N, dtype=np.int32)
+        _check(load().pf_shard_parents(self._h, out.ctypes.data_as(_ip)), self._h)
+        return out
+
+
+def pf_shard_tile(N):
+    return int(load().pf_shard_tile(int(N)))
 
 
 class Batch:
