@@ -20,6 +20,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pf_oracle.c")
 _HDR = os.path.join(_HERE, "pf_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_OPC_SRC = os.path.join(_HERE, "opcount.cpp")
+_OPC_LIB = os.path.join(_HERE, "libopcount.so")
+_opc = None
 _lock = threading.Lock()
 _lib = None
 
@@ -48,6 +51,15 @@ def build(force: bool = False) -> str:
                    "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, _LIB)
+        # the op-counting build of the same source (opcount.cpp)
+        stale = (not os.path.exists(_OPC_LIB)) or any(
+            os.path.getmtime(s) > os.path.getmtime(_OPC_LIB) for s in (_SRC, _HDR, _OPC_SRC))
+        if force or stale:
+            tmp = _OPC_LIB + f".tmp{os.getpid()}"
+            cmd = ["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                   "-shared", "-o", tmp, _OPC_SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, _OPC_LIB)
     return _LIB
 
 
@@ -276,6 +288,29 @@ def propagate(ode, K, theta, tab, S, x, h1, h2, with_error=False):
     if rc != 0:
         raise np.linalg.LinAlgError("singular Newton matrix")
     return x, h1, h2, E
+
+
+def count_propagate(ode, K, theta, tab, S, x, h1, h2, with_error=False):
+    """Exact operation counts of or_propagate over the S substeps of tab for
+    one particle (opcount.cpp): additions/subtractions, multiplications,
+    divisions, square roots, elementary functions, and the propagated state."""
+    global _opc
+    if _opc is None:
+        build()
+        L = C.CDLL(_OPC_LIB)
+        L.or_count_propagate.restype = C.c_int
+        L.or_count_propagate.argtypes = [C.c_int, C.c_int, C.c_int, _dp, C.POINTER(Substep), C.c_int,
+                                         _dp, _dp, _dp, C.c_int, C.POINTER(C.c_longlong), _dp]
+        _opc = L
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    x, h1, h2 = (np.ascontiguousarray(v, dtype=np.float64) for v in (x, h1, h2))
+    out = (C.c_longlong * 5)()
+    xo = np.zeros(len(x))
+    rc = _opc.or_count_propagate(ode, len(x), K, _d(th), tab, S, _d(x), _d(h1), _d(h2),
+                                 1 if with_error else 0, out, _d(xo))
+    if rc != 0:
+        raise np.linalg.LinAlgError("singular Newton matrix")
+    return dict(add=out[0], mul=out[1], div=out[2], sqrt=out[3], elem=out[4], x=xo)
 
 
 def loglik(cfg: Config, y, x):
