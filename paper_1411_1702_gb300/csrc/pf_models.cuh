@@ -147,6 +147,10 @@ struct Michaelis {
     const double gl = rcp_nr2(opl);
     // the third row's constant part, r3 + g lambda c0, once per substep
     const double r2 = fma(g * kLambda, kC0, r[2]);
+    // the fluxes' constant factors, once per substep: with q = 1/(x + k),
+    // g j = (g V) (q x) and g a = (g V k) q^2
+    const double gv1 = g * T.v1, gv2 = g * T.v2;
+    const double gv1k1 = gv1 * T.k1, gv2k2 = gv2 * T.k2;
     // one iteration; the pivots' reciprocals are refined only in the last.
     // The flux reciprocals enter the residual: the last iteration refines
     // them twice (its residual is the final one), the earlier ones once,
@@ -154,14 +158,13 @@ struct Michaelis {
     auto step = [&](const bool last) {
       const double s1 = y[0] + T.k1, s2 = y[1] + T.k2;
       const double q1 = last ? rcp_nr2(s1) : rcp_nr(s1), q2 = last ? rcp_nr2(s2) : rcp_nr(s2);
-      const double u1 = T.v1 * q1, u2 = T.v2 * q2;
-      const double j1 = u1 * y[0], j2 = u2 * y[1];
-      const double ga = g * (u1 * T.k1 * q1), gb = g * (u2 * T.k2 * q2);
+      const double w1 = q1 * y[0], w2 = q2 * y[1];      // j / V
+      const double ga = gv1k1 * (q1 * q1), gb = gv2k2 * (q2 * q2);
       // G = y - r - gamma f_aut(y)
-      const double G0 = fma(g, j1, y[0] - r[0]);
-      const double G1 = fma(-g, j1 - j2, y[1] - r[1]);
+      const double G0 = fma(gv1, w1, y[0] - r[0]);
+      const double G1 = fma(-gv1, w1, fma(gv2, w2, y[1] - r[1]));
       // (1 + g lambda) y3 - (r3 + g lambda c0) - g j2, the same row folded
-      const double G2 = fma(-g, j2, fma(opl, y[2], -r2));
+      const double G2 = fma(-gv2, w2, fma(opl, y[2], -r2));
       const double d0 = -G0 * rcp_newton(1.0 + ga, last);
       const double d1 = fma(ga, d0, -G1) * rcp_newton(1.0 + gb, last);
       const double d2 = fma(gb, d1, -G2) * gl;
