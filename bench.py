@@ -633,6 +633,13 @@ def batched_result(args):
     # 1. the batch
     fb = [pf.Filter.from_workload(w, stream=stream.cuda_stream, filter_id=i) for i, w in zip(ids, ws)]
     batch = pf.Batch(fb, stream=stream.cuda_stream)
+    if args.profile:
+        # plain launcher for profilers: warmup + steps rounds, no timing
+        for r in range(min(args.warmup + args.steps, R)):
+            batch.pf_batch_assimilate(*inputs(r))
+        torch.cuda.synchronize()
+        batch.close()
+        return None
     for r in range(args.warmup):
         batch.pf_batch_assimilate(*inputs(r))
     dev_ms, wall = 0.0, 0.0

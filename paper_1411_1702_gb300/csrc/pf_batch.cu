@@ -999,13 +999,13 @@ pf_status pf_server_submit(pf_server* s, int64_t session, double t_k, const doub
   return PF_OK;
 }
 
-static pf_status server_step(pf_server* s, int* launched);
+static pf_status server_step(pf_server* s, int* launched, int* consumed);
 
 pf_status pf_server_step(pf_server* s, int* launched) {
   const pfg::NvtxRange nvtx_range("pf_server_step");
   if (!s) return sfail(nullptr, PF_ERR_INVALID_ARG, "server is NULL");
   const double t0 = now_ms();
-  const pf_status st = server_step(s, launched);
+  const pf_status st = server_step(s, launched, nullptr);
   const double dt = now_ms() - t0;
   ++s->step_calls;
   s->step_ms_total += dt;
@@ -1013,8 +1013,11 @@ pf_status pf_server_step(pf_server* s, int* launched) {
   return st;
 }
 
-static pf_status server_step(pf_server* s, int* launched) {
+// consumed (if set): observations taken off the queues, launched or rejected
+static pf_status server_step(pf_server* s, int* launched, int* consumed) {
   if (launched) *launched = 0;
+  if (consumed) *consumed = 0;
+  int taken = 0;
   const int L = (int)s->lanes.size();
   // 1. collect the lanes whose epoch has finished (no waiting)
   for (int li = 0; li < L; ++li)
@@ -1081,6 +1084,7 @@ static pf_status server_step(pf_server* s, int* launched) {
         ++n;
       }
       ss->queue.pop_front();
+      ++taken;
     }
     if (n > 0) {
       ++s->epochs;
@@ -1089,18 +1093,25 @@ static pf_status server_step(pf_server* s, int* launched) {
     total += n;
   }
   if (launched) *launched = total;
+  if (consumed) *consumed = taken;
   return PF_OK;
 }
 
 pf_status pf_server_drain(pf_server* s) {
   if (!s) return sfail(nullptr, PF_ERR_INVALID_ARG, "server is NULL");
   for (;;) {
-    int launched = 0;
-    pf_status st = pf_server_step(s, &launched);
+    int launched = 0, consumed = 0;
+    const double t0 = now_ms();
+    pf_status st = server_step(s, &launched, &consumed);
+    const double dt = now_ms() - t0;
+    ++s->step_calls;
+    s->step_ms_total += dt;
+    s->step_ms_max = std::max(s->step_ms_max, dt);
     if (st != PF_OK) return st;
     // sessions still waiting for admission cannot make progress here
     if (!server_pending(s)) return PF_OK;
-    if (launched == 0) {
+    // rejected observations leave their queues without an epoch: step again
+    if (launched == 0 && consumed == 0) {
       // wait until some lane's epoch finishes; with nothing in flight no wait
       // can end (observations are queued that no step launches), so report
       // that instead of spinning

@@ -147,3 +147,31 @@ def test_served_sessions_match_oracle(pf):
             assert done == k + 1 and last == pf.PF_OK
             errs = finish_epoch(f, o, w.t_obs[k], w.y_obs[k], pre, exempt_dead=True, stats=False)
             assert errs["x"] <= 1e-10, (w.name, k, errs["x"])
+
+
+def test_drain_passes_rejected_observations(pf):
+    """Observations the epoch rejects (not finite) leave their queues without
+    an epoch; draining steps on past them instead of waiting for a launch
+    that never comes, and the valid observations of the other sessions are
+    assimilated as usual."""
+    ws = [W.linear2(N=512, T=4, seed=41), W.robertson(N=1000, T=4, seed=42)]
+    srv = pf.Server(budget_bytes=2 << 30)
+    sids = [srv.pf_server_open(w, filter_id=i) for i, w in enumerate(ws)]
+    bad = np.full_like(ws[0].y_obs[0], np.nan)
+    for k in range(3):
+        srv.pf_server_submit(sids[0], ws[0].t_obs[k], bad)
+    for k in range(2):
+        srv.pf_server_submit(sids[1], ws[1].t_obs[k], ws[1].y_obs[k])
+    srv.pf_server_drain()
+    f0, done0, last0 = srv.pf_server_session(sids[0])
+    f1, done1, last1 = srv.pf_server_session(sids[1])
+    assert done0 == 0 and last0 == pf.PF_ERR_INVALID_ARG
+    assert done1 == 2 and last1 == pf.PF_OK
+    alone = pf.Filter.from_workload(ws[1], filter_id=1)
+    for k in range(2):
+        alone.pf_assimilate(ws[1].t_obs[k], ws[1].y_obs[k])
+    assert _same(alone, f1)
+    # the rejected session still takes valid observations afterwards
+    srv.pf_server_submit(sids[0], ws[0].t_obs[0], ws[0].y_obs[0])
+    srv.pf_server_drain()
+    assert srv.pf_server_session(sids[0])[1] == 1

@@ -89,3 +89,22 @@ def test_noalloc_zero_and_nonfinite_weights(env):
     assert np.all(np.diff(c) >= 0.0)
     assert np.array_equal(idx, oracle.resample_systematic(c, u))
     assert not np.any(np.isin(idx, np.flatnonzero(~fin)))
+
+
+def test_noalloc_at_its_maximum_size(env):
+    """N = PF_NOALLOC_MAX_PARTICLES (2^24): the scratch layout's largest
+    case, two calls in a row, indices against the oracle's systematic search
+    on the call's own cumulative weights."""
+    pf, torch = env
+    N = pf.NOALLOC_MAX_PARTICLES
+    rng = np.random.default_rng(24)
+    lg = rng.standard_normal(N) * 2.0
+    lg[rng.random(N) < 0.05] = -np.inf
+    for u in (0.37, 0.0):
+        c, idx = _noalloc(pf, torch, lg, u)
+        assert np.all(np.diff(c) >= 0.0)
+        assert np.array_equal(idx, oracle.resample_systematic(c, u))
+        fin = np.isfinite(lg)
+        g = np.where(fin, np.exp(np.where(fin, lg, 0.0) - np.max(lg[fin])), 0.0)
+        ref = np.cumsum(g)
+        assert np.allclose(c, ref, rtol=1e-11, atol=1e-11 * ref[-1])
