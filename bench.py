@@ -152,13 +152,13 @@ STAGE2_KERNEL["michaelis"] = "k_stage2<Michaelis, 0>"
 # DRAM bytes (read + write) of one stage-2 launch from an ncu capture of the
 # same command on a GB300 (profiles/ names each capture); None where no capture
 # of the kernel as it stands exists.
-STAGE2_TRAFFIC = {"robertson": 11554304 + 0,
-                  "brusselator": 11276960000 + 10731582720,
-                  "advdiff20": 3081472 + 670720,
-                  "advdiff40": 177671424 + 140111872,
-                  "michaelisBDF2": None,
-                  "michaelisAM3": None,
-                  "michaelisAB3": 4459520 + 0}
+STAGE2_TRAFFIC = {"robertson": 11552256 + 0,
+                  "brusselator": 11264311808 + 10727972352,
+                  "advdiff20": 3246336 + 519680,
+                  "advdiff40": 177949952 + 138333184,
+                  "michaelisBDF2": 4360704 + 0,
+                  "michaelisAM3": 4608000 + 0,
+                  "michaelisAB3": 4472832 + 0}
 # The paper's own number for the same workload, where it has one: Table 3's
 # 2D advection-diffusion runs (BDF2, h = 0.1, N = 5000, 30 unit intervals,
 # 8 MATLAB workers on an i7-3820), converted to particle-LMM-steps/s at 600
@@ -279,14 +279,26 @@ def fp64_fma_rate(ms, stream):
     return out.value if rc == 0 else None
 
 
-def epoch_launches(w):
+def device_sms():
+    """SM count of GPU 0 (152 on a GB300), or 152 without a GPU."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(0).multi_processor_count)
+    except Exception:  # noqa: BLE001 - no device: the GB300's count
+        pass
+    return 152
+
+
+def epoch_launches(w, sms=None):
     """Kernels of one single-filter epoch: stage 1, scan tile, resampling
     (which applies the tile offsets as it reads c), stage 2, moments; plus the
     state mean of the 2D system and the corner pass of a resampling above one
-    wave of merge tiles (the library's rs_two_phase: more than 4 * 152 tiles of
-    1024 items)."""
+    wave of merge tiles (the library's rs_two_phase: more than 4 tiles of 1024
+    items for each of the device's SMs)."""
+    sms = device_sms() if sms is None else sms
     n = 5 + (1 if w.ode == W_ADVDIFF else 0)
-    return n + (1 if (2 * w.N + 1023) // 1024 > 4 * 152 else 0)
+    return n + (1 if (2 * w.N + 1023) // 1024 > 4 * sms else 0)
 
 
 def support_roofline(ktimes, N):

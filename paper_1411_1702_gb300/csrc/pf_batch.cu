@@ -202,17 +202,18 @@ static void build_tiles(pf_batch* b, const std::vector<char>& active, int order_
       for (int f : order) {
         const pf_filter* F = b->slot[f];
         if (!member(F, phase, model)) continue;
-        const int nb = phase_blocks(phase, F->ode, F->N);
+        const int nb = phase_blocks(phase, F->ode, F->N, F->fd.sms);
         for (int v = 0; v < nb; ++v) b->tiles_host.push_back(BatchTile{f, v});
       }
     } else {
       int most = 0;
-      for (int f : order) most = std::max(most, phase_blocks(phase, b->slot[f]->ode, b->slot[f]->N));
+      for (int f : order)
+        most = std::max(most, phase_blocks(phase, b->slot[f]->ode, b->slot[f]->N, b->slot[f]->fd.sms));
       for (int v = 0; v < most; ++v)
         for (int f : order) {
           const pf_filter* F = b->slot[f];
           if (!member(F, phase, model)) continue;
-          if (v < phase_blocks(phase, F->ode, F->N)) b->tiles_host.push_back(BatchTile{f, v});
+          if (v < phase_blocks(phase, F->ode, F->N, F->fd.sms)) b->tiles_host.push_back(BatchTile{f, v});
         }
     }
     r.cnt = (int)b->tiles_host.size() - r.off;

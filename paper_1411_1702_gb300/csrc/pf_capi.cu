@@ -115,12 +115,13 @@ static size_t layout(pf_filter* f, char* base) {
   f->fd.lg = (double*)take(sizeof(double) * N);
   f->fd.c = (double*)take(sizeof(double) * N);
   f->fd.idx = (int32_t*)take(sizeof(int32_t) * N);
-  f->fd.blk = (double*)take(sizeof(double) * max_grid_blocks(N));
+  const int sms = f->fd.sms;
+  f->fd.blk = (double*)take(sizeof(double) * max_grid_blocks(N, sms));
   if (f->shard_total > 0) {
     // a shard keeps the whole ensemble's tile offsets; its own tiles are the
     // slice from its first tile on
     const int nb = f->shard_tiles_all;
-    const int64_t t0 = f->shard_first / scan_tile_len(f->shard_total);
+    const int64_t t0 = f->shard_first / scan_tile_len(f->shard_total, sms);
     f->sh_boff = (double*)take(sizeof(double) * nb);
     f->sh_pmax = (double*)take(sizeof(double) * nb);
     f->sh_tiles = (double*)take(sizeof(double) * nb);
@@ -136,11 +137,11 @@ static size_t layout(pf_filter* f, char* base) {
     f->sh_parent_ll1 = (double*)take(sizeof(double) * N);
     f->sh_gparent = (int32_t*)take(sizeof(int32_t) * N);
   } else {
-    f->fd.boff = (double*)take(sizeof(double) * scan_tiles(N));
-    f->fd.pmax = (double*)take(sizeof(double) * scan_tiles(N));
+    f->fd.boff = (double*)take(sizeof(double) * scan_tiles(N, sms));
+    f->fd.pmax = (double*)take(sizeof(double) * scan_tiles(N, sms));
   }
-  f->fd.tsq = (double*)take(sizeof(double) * kMomentBlocks);
-  f->fd.part = (double*)take(sizeof(double) * kMomentBlocks * f->fd.nrec);
+  f->fd.tsq = (double*)take(sizeof(double) * moment_blocks_max(sms));
+  f->fd.part = (double*)take(sizeof(double) * moment_blocks_max(sms) * f->fd.nrec);
   // model work arrays: the Brusselator's stage buffers; the 2D system's
   // committed weights exp(lw - max lw), which the moments store for x-bar
   f->fd.wk = (f->ode == PF_ODE_BRUSSELATOR1D) ? (double*)take(sizeof(double) * bruss_work_doubles(N))
@@ -162,6 +163,7 @@ size_t filter_device_bytes(int ode, int d, int p, int64_t N) {
   probe.p = p;
   probe.N = N;
   probe.fd.nrec = moment_record_size(ode);
+  probe.fd.sms = device_sms();
   return layout(&probe, nullptr);
 }
 }  // namespace pfg
@@ -193,6 +195,16 @@ static pf_status read_ctrl(pf_filter* f) {
 
 namespace pfg {
 pf_status record_error(pf_filter* f, pf_status st, const std::string& msg) { return fail(f, st, msg); }
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    return kMaxSms;
+  }
+  return sms < kMaxSms ? sms : kMaxSms;
+}
 pf_status read_control(pf_filter* f) { return read_ctrl(f); }
 }  // namespace pfg
 
@@ -465,9 +477,10 @@ pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double 
   fd.slot0 = (uint32_t)shard_first;
   fd.Ntile = shard_total > 0 ? shard_total : N;
   fd.shard_sums = nullptr;
+  fd.sms = device_sms();
   f->shard_total = shard_total;
   f->shard_first = shard_first;
-  f->shard_tiles_all = shard_total > 0 ? scan_tile_count(shard_total) : 0;
+  f->shard_tiles_all = shard_total > 0 ? scan_tile_count(shard_total, fd.sms) : 0;
   for (int i = 0; i < kPMax; ++i) {
     fd.prior_kind[i] = i < p ? f->prior_kind[i] : 0;
     fd.prior_lo[i] = i < p ? f->prior_lo[i] : 0.0;
@@ -875,7 +888,7 @@ pf_status pf_get_work(const pf_filter* cf, double* loglik1, double* log_g, doubl
     // c as the scan leaves it (tile-local sums) with the tile offsets and
     // floors, combined here exactly as the device reads them (CumTiles)
     // (a shard: its own tiles of the whole ensemble's tiling)
-    const int64_t len = scan_tile_len(f->fd.Ntile);
+    const int64_t len = scan_tile_len(f->fd.Ntile, f->fd.sms);
     const int nt = (int)((f->N + len - 1) / len);
     std::vector<double> boff(nt), pmax(nt);
     PF_CUDA(f, copy_sync(f, cumulative, f->fd.c, nb, cudaMemcpyDeviceToHost));

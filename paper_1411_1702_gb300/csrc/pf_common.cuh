@@ -24,18 +24,22 @@ constexpr int kMMax = PF_MAX_OBS;
 constexpr int kSMax = PF_MAX_SUBSTEPS;
 constexpr int kScanItemsMax = 4;     // elements per thread in the scan, at most
 constexpr int kScanThreads = 256;
-constexpr int kScanTargetTiles = 608;  // tiles that fill 4 blocks on each of 152 SMs
-constexpr int kMomentBlocks = 304;   // 2 per SM on a 152-SM GB300
+constexpr int kScanTilesPerSm = 4;    // scan tiles that fill one wave: 4 blocks on each SM
+constexpr int kMomentBlocksPerSm = 2;
 constexpr int kMomentThreads = 256;
+// the most SMs a device may have for the fixed-size scratch of the no-alloc call
+constexpr int kMaxSms = 1024;
 
-// Blocks of the moment kernels for N particles: one per 256 particles up to
-// one block per SM, then one per SM (grid-stride, so no SM holds two blocks
-// while another holds one) until two per SM pay, then two per SM.
-__host__ __device__ inline int moment_blocks(int64_t N) {
+// Blocks of the moment kernels for N particles on a device of sms SMs: one
+// per 256 particles up to one block per SM, then one per SM (grid-stride, so
+// no SM holds two blocks while another holds one) until two per SM pay, then
+// two per SM.
+__host__ __device__ inline int moment_blocks(int64_t N, int sms) {
   const int64_t b = (N + kMomentThreads - 1) / kMomentThreads;
-  if (b <= kMomentBlocks / 2) return (int)b;
-  return b < kMomentBlocks ? kMomentBlocks / 2 : kMomentBlocks;
+  if (b <= sms) return (int)b;
+  return b < (int64_t)kMomentBlocksPerSm * sms ? sms : kMomentBlocksPerSm * sms;
 }
+__host__ __device__ inline int moment_blocks_max(int sms) { return kMomentBlocksPerSm * sms; }
 
 // Random-stream purposes (Philox counter word 2, low byte).
 enum : uint32_t { kRngInit = 1, kRngTheta = 2, kRngInnov = 3, kRngResample = 4 };
@@ -127,8 +131,8 @@ struct FilterDev {
   double* blk;      // per-block scratch (max or sums), >= max grid size
   double* boff;     // per-tile offsets of the scan
   double* pmax;     // per-tile running maximum of the earlier tiles' last c
-  double* tsq;      // per-block sums of g^2 (first-stage ESS, kMomentBlocks)
-  double* part;     // moment partial records, kMomentBlocks * nrec
+  double* tsq;      // per-block sums of g^2 (first-stage ESS, moment_blocks_max(sms))
+  double* part;     // moment partial records, moment_blocks_max(sms) * nrec
   double* wk;       // model work arrays (Brusselator: r, predictor, error sums; 2D system: weights)
   unsigned* ticket; // 4 counters for the last-block pattern
   Ctrl* ctrl;
@@ -143,6 +147,7 @@ struct FilterDev {
   // the global ensemble.  A filter of its own has slot0 = 0 and Ntile = N.
   uint32_t slot0;
   int64_t Ntile;
+  int sms;          // SMs of the device the filter lives on (grid shapes)
   // if set, the moments kernel stores its weighted sums here instead of
   // committing (a shard's part of the global sums)
   double* shard_sums;

@@ -265,8 +265,8 @@ __device__ __forceinline__ void stage1_body(const FilterDev& fd, const EpochPara
 // its readers apply the tile offsets and floors (CumTiles).
 __device__ __forceinline__ ScanArgs scan_args(const FilterDev& fd) {
   Ctrl* ctrl = fd.ctrl;
-  return ScanArgs{fd.lg, fd.N, fd.Ntile, ctrl->lg_max, fd.c, fd.blk, fd.boff, fd.pmax, fd.ticket + 1,
-                  &ctrl->c_total};
+  return ScanArgs{fd.lg, fd.N, fd.Ntile, fd.sms, ctrl->lg_max, fd.c, fd.blk, fd.boff, fd.pmax,
+                  fd.ticket + 1, &ctrl->c_total};
 }
 
 __device__ __forceinline__ void scan_tile_body(const FilterDev& fd, int vb, int vg, double* s_warp,
@@ -281,7 +281,7 @@ __device__ __forceinline__ void scan_tile_body(const FilterDev& fd, int vb, int 
 // The filter's cumulative weights as the tile pass leaves them: the offsets
 // and floors are applied on read (no separate offset pass over c).
 __device__ __forceinline__ CumTiles cum_tiles(const FilterDev& fd) {
-  return CumTiles{fd.c, fd.boff, fd.pmax, (uint32_t)scan_tile_len(fd.Ntile)};
+  return CumTiles{fd.c, fd.boff, fd.pmax, (uint32_t)scan_tile_len(fd.Ntile, fd.sms)};
 }
 
 __device__ __forceinline__ double resample_u(const FilterDev& fd, const EpochParams* __restrict__ ep) {
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(kResampleThreads, 4) k_resample(const __grid_c
   __shared__ RsShared sh;
   __shared__ double s_chol[kPMax * kPMax];
   if (fd.ctrl->status != PF_OK) return;
-  const int32_t* corners = rs_two_phase(fd.N) ? reinterpret_cast<const int32_t*>(fd.blk) : nullptr;
+  const int32_t* corners = rs_two_phase(fd.N, fd.sms) ? reinterpret_cast<const int32_t*>(fd.blk) : nullptr;
   resample_body(fd, ep, blockIdx.x, sh, s_chol, corners);
 }
 
@@ -731,7 +731,7 @@ __global__ void __launch_bounds__(kMomentThreads) k_stage1_ess(const __grid_cons
 }
 
 cudaError_t launch_stage1_ess(const FilterDev& fd, cudaStream_t st) {
-  k_stage1_ess<<<moment_blocks(fd.N), kMomentThreads, 0, st>>>(fd);
+  k_stage1_ess<<<moment_blocks(fd.N, fd.sms), kMomentThreads, 0, st>>>(fd);
   return cudaGetLastError();
 }
 
@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(kScanThreads) k_batch_scan_tile(const FilterDe
   const BatchTile t = tiles[blockIdx.x];
   const FilterDev& fd = *(fds + t.f);
   if (fd.ctrl->status != PF_OK) return;
-  scan_tile_body(fd, t.vb, scan_tile_count(fd.N), s_warp, &s_flag);
+  scan_tile_body(fd, t.vb, scan_tile_count(fd.N, fd.sms), s_warp, &s_flag);
 }
 
 __global__ void __launch_bounds__(kResampleThreads) k_batch_resample(
@@ -835,7 +835,7 @@ __global__ void __launch_bounds__(kMomentThreads) k_batch_moments(const FilterDe
   const BatchTile t = tiles[blockIdx.x];
   const FilterDev& fd = *(fds + t.f);
   if (fd.ctrl->status != PF_OK) return;
-  const int vg = moment_blocks(fd.N);
+  const int vg = moment_blocks(fd.N, fd.sms);
   moments_body<D, P>(fd, is_init, t.vb, vg, s_part, s_tot, &s_flag);
 }
 
@@ -856,18 +856,19 @@ int moment_record_size(int ode) {
   return -1;
 }
 
-int max_grid_blocks(int64_t N) {
+int max_grid_blocks(int64_t N, int sms) {
   const int64_t a = N;  // at least as many as any stage launch (one block per particle for M2)
-  const int64_t b = scan_tile_count(N);
+  const int64_t b = scan_tile_count(N, sms);
   const int64_t c = (2 * N + kRsTile - 1) / kRsTile;
   int64_t m = a > b ? a : b;
   m = m > c ? m : c;
-  return (int)(m > kMomentBlocks ? m : kMomentBlocks);
+  const int mb = moment_blocks_max(sms);
+  return (int)(m > mb ? m : mb);
 }
 
-int scan_tiles(int64_t N) { return scan_tile_count(N); }
+int scan_tiles(int64_t N, int sms) { return scan_tile_count(N, sms); }
 
-int phase_blocks(int phase, int ode, int64_t N) {
+int phase_blocks(int phase, int ode, int64_t N, int sms) {
   switch (phase) {
     case kPhaseInit: return (int)((N + kInitThreads - 1) / kInitThreads);
     case kPhaseStage1:
@@ -875,9 +876,9 @@ int phase_blocks(int phase, int ode, int64_t N) {
       if (ode == PF_ODE_ADVDIFF2D) return (int)N;
       return ode == PF_ODE_BRUSSELATOR1D ? bruss_stage_blocks(N)
                                          : (int)((N + kSmallThreads - 1) / kSmallThreads);
-    case kPhaseScanTile: return scan_tiles(N);
+    case kPhaseScanTile: return scan_tiles(N, sms);
     case kPhaseResample: return (int)rs_tiles(N);
-    case kPhaseMoments: return moment_blocks(N);
+    case kPhaseMoments: return moment_blocks(N, sms);
   }
   return 0;
 }
@@ -885,8 +886,8 @@ int phase_blocks(int phase, int ode, int64_t N) {
 template <class M>
 static cudaError_t launch_init_t(const FilterDev& fd, cudaStream_t st) {
   const int64_t N = fd.N;
-  k_init<M::D, M::P><<<phase_blocks(kPhaseInit, M::ODE, N), kInitThreads, 0, st>>>(fd);
-  k_moments<M::D, M::P><<<phase_blocks(kPhaseMoments, M::ODE, N), kMomentThreads, 0, st>>>(fd, 1);
+  k_init<M::D, M::P><<<phase_blocks(kPhaseInit, M::ODE, N, fd.sms), kInitThreads, 0, st>>>(fd);
+  k_moments<M::D, M::P><<<phase_blocks(kPhaseMoments, M::ODE, N, fd.sms), kMomentThreads, 0, st>>>(fd, 1);
   return cudaGetLastError();
 }
 
@@ -925,21 +926,21 @@ static cudaError_t launch_epoch_t(const FilterDev& fd, const EpochParams* ep, in
   const size_t smem = (size_t)S * sizeof(StepCoef);
   StageKernel k1, k2;
   stage_kernels<M>(fd.lmm, k1, k2);
-  const unsigned g_small = (unsigned)phase_blocks(kPhaseStage1, M::ODE, N);
+  const unsigned g_small = (unsigned)phase_blocks(kPhaseStage1, M::ODE, N, fd.sms);
   auto mark = [&](int i) {
     if (marks) cudaEventRecord(marks[i], st);
   };
   mark(0);
   k1<<<g_small, kSmallThreads, smem, st>>>(fd, ep);
   mark(1);
-  k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, M::ODE, N), kScanThreads, 0, st>>>(fd);
+  k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, M::ODE, N, fd.sms), kScanThreads, 0, st>>>(fd);
   mark(2);  // (marks[3] is not recorded: the scan_add slot is empty)
-  if (rs_two_phase(N)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
-  k_resample<<<(unsigned)phase_blocks(kPhaseResample, M::ODE, N), kResampleThreads, 0, st>>>(fd, ep);
+  if (rs_two_phase(N, fd.sms)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
+  k_resample<<<(unsigned)phase_blocks(kPhaseResample, M::ODE, N, fd.sms), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
   k2<<<g_small, kSmallThreads, smem, st>>>(fd, ep);
   mark(5);
-  k_moments<M::D, M::P><<<phase_blocks(kPhaseMoments, M::ODE, N), kMomentThreads, 0, st>>>(fd, 0);
+  k_moments<M::D, M::P><<<phase_blocks(kPhaseMoments, M::ODE, N, fd.sms), kMomentThreads, 0, st>>>(fd, 0);
   mark(6);
   return cudaGetLastError();
 }
@@ -956,14 +957,14 @@ static cudaError_t launch_epoch_bruss(const FilterDev& fd, const EpochParams* ep
   mark(0);
   if ((e = launch_bruss_stage(1, fd, ep, S, st)) != cudaSuccess) return e;
   mark(1);
-  k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, ode, N), kScanThreads, 0, st>>>(fd);
+  k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, ode, N, fd.sms), kScanThreads, 0, st>>>(fd);
   mark(2);  // (marks[3] is not recorded: the scan_add slot is empty)
-  if (rs_two_phase(N)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
-  k_resample<<<(unsigned)phase_blocks(kPhaseResample, ode, N), kResampleThreads, 0, st>>>(fd, ep);
+  if (rs_two_phase(N, fd.sms)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
+  k_resample<<<(unsigned)phase_blocks(kPhaseResample, ode, N, fd.sms), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
   if ((e = launch_bruss_stage(2, fd, ep, S, st)) != cudaSuccess) return e;
   mark(5);
-  k_moments<64, 3><<<phase_blocks(kPhaseMoments, ode, N), kMomentThreads, 0, st>>>(fd, 0);
+  k_moments<64, 3><<<phase_blocks(kPhaseMoments, ode, N, fd.sms), kMomentThreads, 0, st>>>(fd, 0);
   mark(6);
   return cudaGetLastError();
 }
@@ -983,14 +984,14 @@ static cudaError_t launch_epoch_ad(const FilterDev& fd, const EpochParams* ep, i
   mark(0);
   if ((e = launch_ad_stage(1, fd, ep, S, st)) != cudaSuccess) return e;
   mark(1);
-  k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, ode, N), kScanThreads, 0, st>>>(fd);
+  k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, ode, N, fd.sms), kScanThreads, 0, st>>>(fd);
   mark(2);  // (marks[3] is not recorded: the scan_add slot is empty)
-  if (rs_two_phase(N)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
-  k_resample<<<(unsigned)phase_blocks(kPhaseResample, ode, N), kResampleThreads, 0, st>>>(fd, ep);
+  if (rs_two_phase(N, fd.sms)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
+  k_resample<<<(unsigned)phase_blocks(kPhaseResample, ode, N, fd.sms), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
   if ((e = launch_ad_stage(2, fd, ep, S, st)) != cudaSuccess) return e;
   mark(5);
-  k_moments<0, 5><<<phase_blocks(kPhaseMoments, ode, N), kMomentThreads, 0, st>>>(fd, 0);
+  k_moments<0, 5><<<phase_blocks(kPhaseMoments, ode, N, fd.sms), kMomentThreads, 0, st>>>(fd, 0);
   k_xbar<<<xbar_blocks(fd), kMomentThreads, 0, st>>>(fd);
   mark(6);
   return cudaGetLastError();
@@ -1000,8 +1001,8 @@ cudaError_t launch_init(int ode, const FilterDev& fd, cudaStream_t st) {
   switch (ode) {
     case PF_ODE_ADVDIFF2D: {
       const int64_t N = fd.N;
-      k_init<0, 5><<<phase_blocks(kPhaseInit, ode, N), kInitThreads, 0, st>>>(fd);
-      k_moments<0, 5><<<phase_blocks(kPhaseMoments, ode, N), kMomentThreads, 0, st>>>(fd, 1);
+      k_init<0, 5><<<phase_blocks(kPhaseInit, ode, N, fd.sms), kInitThreads, 0, st>>>(fd);
+      k_moments<0, 5><<<phase_blocks(kPhaseMoments, ode, N, fd.sms), kMomentThreads, 0, st>>>(fd, 1);
       k_xbar<<<xbar_blocks(fd), kMomentThreads, 0, st>>>(fd);
       return cudaGetLastError();
     }
@@ -1010,8 +1011,8 @@ cudaError_t launch_init(int ode, const FilterDev& fd, cudaStream_t st) {
     case PF_ODE_MICHAELIS3: return launch_init_t<Michaelis>(fd, st);
     case PF_ODE_BRUSSELATOR1D: {
       const int64_t N = fd.N;
-      k_init<64, 3><<<phase_blocks(kPhaseInit, ode, N), kInitThreads, 0, st>>>(fd);
-      k_moments<64, 3><<<phase_blocks(kPhaseMoments, ode, N), kMomentThreads, 0, st>>>(fd, 1);
+      k_init<64, 3><<<phase_blocks(kPhaseInit, ode, N, fd.sms), kInitThreads, 0, st>>>(fd);
+      k_moments<64, 3><<<phase_blocks(kPhaseMoments, ode, N, fd.sms), kMomentThreads, 0, st>>>(fd, 1);
       return cudaGetLastError();
     }
   }
@@ -1233,7 +1234,7 @@ __global__ void __launch_bounds__(kMomentThreads) k_shard_commit(const __grid_co
 
 // Step 1's draws alone (a shard's moments are committed from the global sums)
 cudaError_t launch_init_draws(int ode, const FilterDev& fd, cudaStream_t st) {
-  const unsigned g = (unsigned)phase_blocks(kPhaseInit, ode, fd.N);
+  const unsigned g = (unsigned)phase_blocks(kPhaseInit, ode, fd.N, fd.sms);
   switch (ode) {
     case PF_ODE_LINEAR2: k_init<2, 2><<<g, kInitThreads, 0, st>>>(fd); break;
     case PF_ODE_ROBERTSON: k_init<3, 3><<<g, kInitThreads, 0, st>>>(fd); break;
@@ -1257,7 +1258,7 @@ cudaError_t launch_stage(int stage, const FilterDev& fd, const EpochParams* ep, 
     case PF_ODE_MICHAELIS3: stage_kernels<Michaelis>(fd.lmm, k1, k2); break;
     default: return cudaErrorInvalidValue;
   }
-  const unsigned g = (unsigned)phase_blocks(kPhaseStage1, fd.ode, fd.N);
+  const unsigned g = (unsigned)phase_blocks(kPhaseStage1, fd.ode, fd.N, fd.sms);
   (stage == 1 ? k1 : k2)<<<g, kSmallThreads, (size_t)S * sizeof(StepCoef), st>>>(fd, ep);
   return cudaGetLastError();
 }
@@ -1292,7 +1293,7 @@ cudaError_t launch_shard_unpack(const FilterDev& fd, const double* recv, const E
 // The moment sums of the pending buffer (fd.shard_sums set) with the shift
 // lw_max already in the control block.
 cudaError_t launch_shard_moments(const FilterDev& fd, cudaStream_t st) {
-  const unsigned g = (unsigned)phase_blocks(kPhaseMoments, fd.ode, fd.N);
+  const unsigned g = (unsigned)phase_blocks(kPhaseMoments, fd.ode, fd.N, fd.sms);
   switch (fd.ode) {
     case PF_ODE_LINEAR2: k_moments<2, 2><<<g, kMomentThreads, 0, st>>>(fd, 0); break;
     case PF_ODE_ROBERTSON: k_moments<3, 3><<<g, kMomentThreads, 0, st>>>(fd, 0); break;

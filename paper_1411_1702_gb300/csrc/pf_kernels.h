@@ -24,7 +24,8 @@ struct BatchTile {
 };
 
 // blocks one filter of N particles needs in a phase
-int phase_blocks(int phase, int ode, int64_t N);
+// on a device of sms SMs
+int phase_blocks(int phase, int ode, int64_t N, int sms);
 int bruss_stage_blocks(int64_t N);
 // One batched phase over a device tile table (see pf_kernels.cu); stage
 // phases take the tiles of one model (ode) and LMM family (that of lmm), the
@@ -80,8 +81,11 @@ cudaError_t launch_ad_stage(int stage, const FilterDev& fd, const EpochParams* e
 size_t ad_stage_smem(int d, int S, int stage);
 int ad_threads(int nt);
 cudaError_t preload_ad_kernels();
-int max_grid_blocks(int64_t N);
-int scan_tiles(int64_t N);
+int max_grid_blocks(int64_t N, int sms);
+int scan_tiles(int64_t N, int sms);
+// SM count of the current device (1024 when there is none, the most the
+// fixed-size scratch of the no-alloc call is laid out for)
+int device_sms();
 int kernels_per_epoch(int ode);
 bool ode_supported(int ode);
 

@@ -26,11 +26,13 @@
 namespace pfg {
 
 constexpr int64_t kNaMaxParticles = PF_NOALLOC_MAX_PARTICLES;
-// the most scan tiles of any N up to the maximum (scan_tile_count)
-constexpr int kNaMaxTiles =
-    kNaMaxParticles / (kScanThreads * kScanItemsMax) > kScanTargetTiles
-        ? (int)((kNaMaxParticles + kScanThreads * kScanItemsMax - 1) / (kScanThreads * kScanItemsMax))
-        : kScanTargetTiles;
+// the most scan tiles of any N up to the maximum on a device of up to kMaxSms
+// SMs (scan_tile_count)
+constexpr int64_t kNaLongTiles = (kNaMaxParticles + kScanThreads * kScanItemsMax - 1) /
+                                 (kScanThreads * kScanItemsMax);
+constexpr int kNaMaxTiles = (int)(kNaLongTiles > (int64_t)kScanTilesPerSm * kMaxSms
+                                      ? kNaLongTiles
+                                      : (int64_t)kScanTilesPerSm * kMaxSms);
 constexpr int kNaMaxBlocks = 304;  // blocks of the maximum reduction
 constexpr int kNaThreads = 256;
 // byte layout of the scratch array
@@ -85,20 +87,21 @@ __global__ void __launch_bounds__(kNaThreads) k_na_max(const double* __restrict_
 }
 
 // the filter's scan (scan_tile_core, scan_add_core) on the caller's buffers
-__device__ __forceinline__ ScanArgs na_scan_args(const double* lg, int64_t N, double* c,
+__device__ __forceinline__ ScanArgs na_scan_args(const double* lg, int64_t N, int sms, double* c,
                                                  const NaScratch& sc) {
-  return ScanArgs{lg, N, N, __ldcg(sc.head), c, sc.tile, sc.boff, sc.pmax, sc.ticket + 1, nullptr};
+  return ScanArgs{lg, N, N, sms, __ldcg(sc.head), c, sc.tile, sc.boff, sc.pmax, sc.ticket + 1, nullptr};
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_na_scan_tile(const double* __restrict__ lg,
-                                                             int64_t N, double* c, NaScratch sc) {
+                                                             int64_t N, int sms, double* c,
+                                                             NaScratch sc) {
   __shared__ double s_warp[33];
   __shared__ int s_flag;
-  scan_tile_core(na_scan_args(lg, N, c, sc), blockIdx.x, gridDim.x, s_warp, &s_flag);
+  scan_tile_core(na_scan_args(lg, N, sms, c, sc), blockIdx.x, gridDim.x, s_warp, &s_flag);
 }
 
-__global__ void __launch_bounds__(256) k_na_scan_add(int64_t N, double* c, NaScratch sc) {
-  scan_add_core(na_scan_args(nullptr, N, c, sc), (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void __launch_bounds__(256) k_na_scan_add(int64_t N, int sms, double* c, NaScratch sc) {
+  scan_add_core(na_scan_args(nullptr, N, sms, c, sc), (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // the filter's merge-path search (resample_tile), one block per diagonal tile;
@@ -131,10 +134,12 @@ static cudaError_t scratch_address(unsigned char** out) {
 }
 
 // The scratch layout holds every size up to the maximum: the scan's tile
-// count is at most max(kScanTargetTiles, ceil(N / (kScanThreads *
+// count is at most max(kScanTilesPerSm * sms, ceil(N / (kScanThreads *
 // kScanItemsMax))) and the merge has rs_tiles(N) + 1 corners, both largest at
-// the maximum N.
-static_assert(scan_tile_count(kNaMaxParticles) <= kNaMaxTiles, "scan tiles exceed the scratch");
+// the maximum N and SM count.
+static_assert(scan_tile_count(kNaMaxParticles, kMaxSms) <= kNaMaxTiles, "scan tiles exceed the scratch");
+static_assert(scan_tile_count(kScanThreads * kScanTilesPerSm * kMaxSms, kMaxSms) <= kNaMaxTiles,
+              "scan tiles exceed the scratch");
 static_assert(rs_tiles(kNaMaxParticles) + 1 <= kNaMaxCorners, "merge corners exceed the scratch");
 
 }  // namespace pfg
@@ -161,8 +166,9 @@ extern "C" pf_status pf_resample_systematic_noalloc(const double* log_g, int64_t
     return PF_ERR_INVALID_ARG;
   }
   // a second line of defence behind the static_asserts: the layout must hold
-  // this N's tiles and corners
-  if (scan_tile_count(N) > kNaMaxTiles || rs_tiles(N) + 1 > kNaMaxCorners) {
+  // this N's tiles and corners on this device
+  const int sms = device_sms();
+  if (scan_tile_count(N, sms) > kNaMaxTiles || rs_tiles(N) + 1 > kNaMaxCorners) {
     set_thread_error("pf_resample_systematic_noalloc: scratch layout too small for this N");
     return PF_ERR_BUDGET;
   }
@@ -181,13 +187,13 @@ extern "C" pf_status pf_resample_systematic_noalloc(const double* log_g, int64_t
     const int64_t mb = (N + kNaThreads - 1) / kNaThreads;
     const unsigned g_max = (unsigned)(mb < kNaMaxBlocks ? mb : kNaMaxBlocks);
     k_na_max<<<g_max, kNaThreads, 0, st>>>(log_g, N, sc);
-    k_na_scan_tile<<<(unsigned)scan_tile_count(N), kScanThreads, 0, st>>>(
-        log_g, N, cumulative, sc);
-    k_na_scan_add<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, cumulative, sc);
-    if (rs_two_phase(N))
-      k_na_corners<<<rs_corner_blocks(N), 256, 0, st>>>(cumulative, N, u, sc.corners);
+    k_na_scan_tile<<<(unsigned)scan_tile_count(N, sms), kScanThreads, 0, st>>>(
+        log_g, N, sms, cumulative, sc);
+    k_na_scan_add<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, sms, cumulative, sc);
+    const bool two = rs_two_phase(N, sms);
+    if (two) k_na_corners<<<rs_corner_blocks(N), 256, 0, st>>>(cumulative, N, u, sc.corners);
     k_na_resample<<<resample_blocks(N), kResampleThreads, 0, st>>>(cumulative, N, u, idx,
-                                                                   rs_two_phase(N) ? sc.corners : nullptr);
+                                                                   two ? sc.corners : nullptr);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

@@ -88,20 +88,22 @@ __device__ __forceinline__ int32_t systematic_index(const V& c, int64_t N, int64
 // for a given N.
 //
 // The exponentials are the scan's cost and FP64 issue is scarce, so the tile
-// length follows N: of 1 to kScanItemsMax values a thread, the one whose
-// busiest SM has the least to do -- ceil(tiles / 152) tiles of (items + 0.3)
-// units, the 0.3 standing for a thread's share of the block scan -- among
-// those that keep the tile count at most max(kScanTargetTiles,
-// ceil(N / (kScanThreads * kScanItemsMax))); ties go to more values a thread.
-__host__ __device__ constexpr int scan_items(int64_t N) {
+// length follows N and the device's SM count: of 1 to kScanItemsMax values a
+// thread, the one whose busiest SM has the least to do -- ceil(tiles / sms)
+// tiles of (items + 0.3) units, the 0.3 standing for a thread's share of the
+// block scan -- among those that keep the tile count at most
+// max(kScanTilesPerSm * sms, ceil(N / (kScanThreads * kScanItemsMax))); ties
+// go to more values a thread.
+__host__ __device__ constexpr int scan_items(int64_t N, int sms) {
   const int64_t cap_long = (N + kScanThreads * kScanItemsMax - 1) / (kScanThreads * kScanItemsMax);
-  const int64_t cap = cap_long > kScanTargetTiles ? cap_long : kScanTargetTiles;
+  const int64_t target = (int64_t)kScanTilesPerSm * sms;
+  const int64_t cap = cap_long > target ? cap_long : target;
   int best = kScanItemsMax;
   int64_t best_cost = -1;
   for (int it = kScanItemsMax; it >= 1; --it) {
     const int64_t tiles = (N + (int64_t)kScanThreads * it - 1) / ((int64_t)kScanThreads * it);
     if (tiles > cap) break;
-    const int64_t cost = (tiles + 151) / 152 * (10 * it + 3);
+    const int64_t cost = (tiles + sms - 1) / sms * (10 * it + 3);
     if (best_cost < 0 || cost < best_cost) {
       best = it;
       best_cost = cost;
@@ -109,11 +111,11 @@ __host__ __device__ constexpr int scan_items(int64_t N) {
   }
   return best;
 }
-__host__ __device__ constexpr int64_t scan_tile_len(int64_t N) {
-  return (int64_t)kScanThreads * scan_items(N);
+__host__ __device__ constexpr int64_t scan_tile_len(int64_t N, int sms) {
+  return (int64_t)kScanThreads * scan_items(N, sms);
 }
-__host__ __device__ constexpr int scan_tile_count(int64_t N) {
-  const int64_t L = scan_tile_len(N);
+__host__ __device__ constexpr int scan_tile_count(int64_t N, int sms) {
+  const int64_t L = scan_tile_len(N, sms);
   return (int)((N + L - 1) / L);
 }
 
@@ -140,6 +142,7 @@ struct ScanArgs {
   int64_t N;
   int64_t Ntile;     // the ensemble size whose tile length applies (N, or the
                      // whole ensemble's size for a shard of it)
+  int sms;           // the device's SM count (the tile length depends on it)
   double M;          // their maximum (the log-sum-exp shift)
   double* c;         // N cumulative weights (tile-local after the tile pass)
   double* tile;      // per-tile totals
@@ -181,7 +184,7 @@ __device__ __forceinline__ void scan_offsets_core(const double* tile, int nb, do
 // tile totals into offsets and floors.
 __device__ __forceinline__ void scan_tile_core(const ScanArgs& a, int vb, int vg, double* s_warp,
                                                int* s_flag) {
-  const int items = scan_items(a.Ntile);
+  const int items = scan_items(a.Ntile, a.sms);
   const int64_t base = (int64_t)vb * kScanThreads * items + (int64_t)threadIdx.x * items;
   double v[kScanItemsMax];
   double run = 0.0;
@@ -212,7 +215,7 @@ __device__ __forceinline__ void scan_tile_core(const ScanArgs& a, int vb, int vg
 // c_k = max(tile offset + tile-local sum, tile floor)
 __device__ __forceinline__ void scan_add_core(const ScanArgs& a, int64_t k) {
   if (k < a.N) {
-    const int64_t b = k / scan_tile_len(a.Ntile);
+    const int64_t b = k / scan_tile_len(a.Ntile, a.sms);
     a.c[k] = max_nonneg(__ldcg(a.boff + b) + a.c[k], __ldcg(a.pmax + b));
   }
 }
@@ -231,7 +234,7 @@ struct CumTiles {
   const double* cl;
   const double* boff;
   const double* pmax;
-  uint32_t len;  // tile length, scan_tile_len(N)
+  uint32_t len;  // tile length, scan_tile_len(N, sms)
   __device__ __forceinline__ double operator()(int64_t k) const {
     const uint32_t t = (uint32_t)k / len;
     return max_nonneg(__ldg(boff + t) + __ldg(cl + k), __ldg(pmax + t));
@@ -322,13 +325,16 @@ __device__ __forceinline__ int64_t rs_corner(const V& c, int64_t dg, const RsTau
 }
 
 // Tiles of the merge of N taus with N cumulative weights.  Above one wave of
-// tiles the corners are found first, by a launch of one thread per tile
-// boundary (rs_corners_core), so that the dependent loads of all the corner
-// searches overlap instead of heading every tile; below it each block finds
-// its own two (rs_corner), which saves the launch.
-constexpr int kRsTwoPhaseTiles = 4 * 152;
+// tiles (kRsTwoPhaseTilesPerSm on each SM) the corners are found first, by a
+// launch of one thread per tile boundary (rs_corners_core), so that the
+// dependent loads of all the corner searches overlap instead of heading every
+// tile; below it each block finds its own two (rs_corner), which saves the
+// launch.
+constexpr int kRsTwoPhaseTilesPerSm = 4;
 __host__ __device__ constexpr int64_t rs_tiles(int64_t N) { return (2 * N + kRsTile - 1) / kRsTile; }
-__host__ __device__ inline bool rs_two_phase(int64_t N) { return rs_tiles(N) > kRsTwoPhaseTiles; }
+__host__ __device__ inline bool rs_two_phase(int64_t N, int sms) {
+  return rs_tiles(N) > (int64_t)kRsTwoPhaseTilesPerSm * sms;
+}
 // blocks of 256 threads (8 warps) for the corner pass: one warp per corner
 __host__ __device__ inline unsigned rs_corner_blocks(int64_t N) {
   return (unsigned)((rs_tiles(N) + 1 + 7) / 8);

@@ -57,7 +57,7 @@ pf_status sfail(pf_filter* f, pf_status st, const std::string& msg) { return rec
 int record_doubles(const pf_filter* f) { return 3 * f->d + f->p + 2; }
 
 int64_t local_tiles(const pf_filter* f) {
-  const int64_t L = scan_tile_len(f->shard_total);
+  const int64_t L = scan_tile_len(f->shard_total, f->fd.sms);
   return (f->N + L - 1) / L;
 }
 
@@ -93,7 +93,7 @@ pf_status set_ctrl_double(pf_filter* f, double* dev_field, double v) {
 
 extern "C" {
 
-int64_t pf_shard_tile(int64_t N) { return N >= 1 ? scan_tile_len(N) : 0; }
+int64_t pf_shard_tile(int64_t N) { return N >= 1 ? scan_tile_len(N, device_sms()) : 0; }
 
 pf_status pf_shard_create(pf_ode ode, int d, int p, int64_t N, int64_t first, int64_t n, pf_lmm lmm,
                           double dt, const pf_prior* prior, const pf_options* opt, pf_filter** out) {
@@ -108,7 +108,7 @@ pf_status pf_shard_create(pf_ode ode, int d, int p, int64_t N, int64_t first, in
     set_thread_error("pf_shard_create: need 1 <= n and 0 <= first, first + n <= N <= PF_MAX_PARTICLES");
     return PF_ERR_INVALID_ARG;
   }
-  const int64_t L = scan_tile_len(N);
+  const int64_t L = scan_tile_len(N, device_sms());
   if (first % L != 0 || (first + n != N && n % L != 0)) {
     set_thread_error("pf_shard_create: a shard must start on a multiple of pf_shard_tile(N) and, "
                      "unless it is the last, hold a multiple of it");

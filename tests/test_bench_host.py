@@ -18,15 +18,16 @@ def _cuh_int(name):
 
 
 def test_launch_count_follows_the_two_phase_threshold():
-    # the library switches to a separate corner launch above 4 * 152 merge
-    # tiles of kResampleThreads * kRsItems = 1024 items
-    assert _cuh_int("kRsTwoPhaseTiles").replace(" ", "") == "4*152"
+    # the library switches to a separate corner launch above 4 merge tiles of
+    # kResampleThreads * kRsItems = 1024 items for each SM (608 on a GB300)
+    assert _cuh_int("kRsTwoPhaseTilesPerSm") == "4"
     assert _cuh_int("kResampleThreads") == "256" and _cuh_int("kRsItems") == "4"
     w = W.robertson(N=8, T=2)
-    edge = 4 * 152 * 1024 // 2           # 2N items fill exactly 608 tiles
-    assert bench.epoch_launches(w.with_(N=edge)) == 5
-    assert bench.epoch_launches(w.with_(N=edge + 1)) == 6
-    assert bench.epoch_launches(W.advdiff20(N=16, T=2)) == 6   # + the state mean
+    for sms in (152, 148, 160):
+        edge = 4 * sms * 1024 // 2           # 2N items fill exactly 4 tiles an SM
+        assert bench.epoch_launches(w.with_(N=edge), sms) == 5
+        assert bench.epoch_launches(w.with_(N=edge + 1), sms) == 6
+    assert bench.epoch_launches(W.advdiff20(N=16, T=2), 152) == 6   # + the state mean
 
 
 def test_support_roofline_arithmetic():
