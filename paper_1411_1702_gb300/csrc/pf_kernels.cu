@@ -868,6 +868,24 @@ int max_grid_blocks(int64_t N, int sms) {
 
 int scan_tiles(int64_t N, int sms) { return scan_tile_count(N, sms); }
 
+// Threads per block of a filter's own stage launches (a batch's tiles are
+// always kSmallThreads): 128, halved (down to one warp) while the filter has
+// fewer than 6 such blocks an SM.  The stage kernels are FP64-issue bound and
+// their particles all cost the same, so a launch ends with the SMs that hold
+// one block more than the others: 2.6 blocks of 128 an SM (M1, N = 50000) lose
+// 1.7 % of the epoch against 10.3 blocks of 32.  The blocks only reduce a
+// maximum and a count, so the results do not depend on the block size.
+static int stage_threads(int64_t N, int sms) {
+  int t = kSmallThreads;
+  while (t > 32 && N < (int64_t)6 * t * sms) t >>= 1;
+  return t;
+}
+
+static unsigned stage_grid(int64_t N, int sms) {
+  const int t = stage_threads(N, sms);
+  return (unsigned)((N + t - 1) / t);
+}
+
 int phase_blocks(int phase, int ode, int64_t N, int sms) {
   switch (phase) {
     case kPhaseInit: return (int)((N + kInitThreads - 1) / kInitThreads);
@@ -926,19 +944,20 @@ static cudaError_t launch_epoch_t(const FilterDev& fd, const EpochParams* ep, in
   const size_t smem = (size_t)S * sizeof(StepCoef);
   StageKernel k1, k2;
   stage_kernels<M>(fd.lmm, k1, k2);
-  const unsigned g_small = (unsigned)phase_blocks(kPhaseStage1, M::ODE, N, fd.sms);
+  const unsigned g_small = stage_grid(N, fd.sms);
+  const int t_small = stage_threads(N, fd.sms);
   auto mark = [&](int i) {
     if (marks) cudaEventRecord(marks[i], st);
   };
   mark(0);
-  k1<<<g_small, kSmallThreads, smem, st>>>(fd, ep);
+  k1<<<g_small, t_small, smem, st>>>(fd, ep);
   mark(1);
   k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, M::ODE, N, fd.sms), kScanThreads, 0, st>>>(fd);
   mark(2);  // (marks[3] is not recorded: the scan_add slot is empty)
   if (rs_two_phase(N, fd.sms)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
   k_resample<<<(unsigned)phase_blocks(kPhaseResample, M::ODE, N, fd.sms), kResampleThreads, 0, st>>>(fd, ep);
   mark(4);
-  k2<<<g_small, kSmallThreads, smem, st>>>(fd, ep);
+  k2<<<g_small, t_small, smem, st>>>(fd, ep);
   mark(5);
   k_moments<M::D, M::P><<<phase_blocks(kPhaseMoments, M::ODE, N, fd.sms), kMomentThreads, 0, st>>>(fd, 0);
   mark(6);
@@ -1258,8 +1277,8 @@ cudaError_t launch_stage(int stage, const FilterDev& fd, const EpochParams* ep, 
     case PF_ODE_MICHAELIS3: stage_kernels<Michaelis>(fd.lmm, k1, k2); break;
     default: return cudaErrorInvalidValue;
   }
-  const unsigned g = (unsigned)phase_blocks(kPhaseStage1, fd.ode, fd.N, fd.sms);
-  (stage == 1 ? k1 : k2)<<<g, kSmallThreads, (size_t)S * sizeof(StepCoef), st>>>(fd, ep);
+  const unsigned g = stage_grid(fd.N, fd.sms);
+  (stage == 1 ? k1 : k2)<<<g, stage_threads(fd.N, fd.sms), (size_t)S * sizeof(StepCoef), st>>>(fd, ep);
   return cudaGetLastError();
 }
 

@@ -52,9 +52,9 @@ def test_linear2_epoch_parity(pf, lmm):
         check_epoch(g, o, w.t_obs[k], w.y_obs[k], exempt_dead=True)
 
 
-@pytest.mark.parametrize("lmm", [W.LMM_BDF3, W.LMM_AM3, W.LMM_AB2])
+@pytest.mark.parametrize("lmm", [W.LMM_BDF1, W.LMM_BDF2] + NEW_LMMS)
 def test_robertson_uniform_epoch_parity(pf, lmm):
-    """Robertson on a uniform grid (2e-6 steps) with the new families."""
+    """Robertson on a uniform grid (2e-6 steps) with each of the nine methods."""
     w = W.robertson(N=300, T=3)
     w = w.with_(lmm=lmm, spacing=W.SPACING_UNIFORM, dt=2e-6,
                 t_obs=np.array([1e-4, 2e-4, 3e-4]), y_obs=w.y_obs[:3], x_true=w.x_true[:3])
