@@ -478,6 +478,12 @@ class Batch:
                                C.byref(h))
         _check(st, None)
         self._h = h
+        # one row of observations per member, reused by every call: the
+        # pointer array is the rows' addresses (0 for idle members)
+        self._m = [f.m for f in self.filters]
+        self._ybuf = np.zeros((len(self.filters), max(self._m + [1])), dtype=np.float64)
+        self._rows = (self._ybuf.ctypes.data
+                      + self._ybuf.strides[0] * np.arange(len(self.filters), dtype=np.uint64))
 
     def close(self):
         h = getattr(self, "_h", None)
@@ -492,15 +498,21 @@ class Batch:
         """t: n times; ys: list of n observation arrays or None (idle).
         Returns the per-filter status codes."""
         n = len(self.filters)
+        if len(t) != n or len(ys) != n:
+            raise ValueError(f"need {n} times and {n} observations (None for idle)")
         tt = _f64(t)
-        keep = [None if y is None else _f64(y) for y in ys]
-        ptrs = (_dp * n)(*[(_d(y) if y is not None else _dp()) for y in keep])
-        status = (C.c_int * n)()
-        st = load().pf_batch_assimilate(self._h, _d(tt), ptrs, status)
+        addr = np.zeros(n, dtype=np.uint64)
+        for i, y in enumerate(ys):
+            if y is not None:
+                self._ybuf[i, :self._m[i]] = y
+                addr[i] = self._rows[i]
+        status = np.zeros(n, dtype=np.int32)
+        st = load().pf_batch_assimilate(self._h, _d(tt), C.cast(addr.ctypes.data, C.POINTER(_dp)),
+                                        status.ctypes.data_as(C.POINTER(C.c_int)))
         if st != PF_OK:
             msg = load().pf_batch_last_error(self._h)
             raise PfError(st, msg.decode() if msg else "")
-        return [int(s) for s in status]
+        return status.tolist()
 
     def pf_batch_stats(self):
         s = BatchStats()
