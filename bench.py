@@ -157,8 +157,8 @@ STAGE2_TRAFFIC = {"robertson": 11552256 + 0,
                   "advdiff20": 3246336 + 519680,
                   "advdiff40": 177949952 + 138333184,
                   "michaelisBDF2": 4376576 + 0,
-                  "michaelisAM3": 4608000 + 0,
-                  "michaelisAB3": 4472832 + 0}
+                  "michaelisAM3": 4603648 + 0,
+                  "michaelisAB3": 4457472 + 0}
 # The paper's own number for the same workload, where it has one: Table 3's
 # 2D advection-diffusion runs (BDF2, h = 0.1, N = 5000, 30 unit intervals,
 # 8 MATLAB workers on an i7-3820), converted to particle-LMM-steps/s at 600
