@@ -152,13 +152,13 @@ STAGE2_KERNEL["michaelis"] = "k_stage2<Michaelis, 0>"
 # DRAM bytes (read + write) of one stage-2 launch from an ncu capture of the
 # same command on a GB300 (profiles/ names each capture); None where no capture
 # of the kernel as it stands exists.
-STAGE2_TRAFFIC = {"robertson": 11552256 + 0,
-                  "brusselator": 11264311808 + 10727972352,
-                  "advdiff20": 3246336 + 519680,
-                  "advdiff40": 177949952 + 138333184,
-                  "michaelisBDF2": 4376576 + 0,
-                  "michaelisAM3": 4603648 + 0,
-                  "michaelisAB3": 4457472 + 0}
+STAGE2_TRAFFIC = {"robertson": 11549440 + 0,
+                  "brusselator": None,
+                  "advdiff20": None,
+                  "advdiff40": None,
+                  "michaelisBDF2": None,
+                  "michaelisAM3": None,
+                  "michaelisAB3": None}
 # The paper's own number for the same workload, where it has one: Table 3's
 # 2D advection-diffusion runs (BDF2, h = 0.1, N = 5000, 30 unit intervals,
 # 8 MATLAB workers on an i7-3820), converted to particle-LMM-steps/s at 600

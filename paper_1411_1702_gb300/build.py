@@ -15,8 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpf_gb300.so")
-# the benchmark's FP64 FMA probe: a library of its own, outside the C ABI
-PROBE_SRC = os.path.join(CSRC, "probe", "fp64_fma_probe.cu")
+# probes outside the C ABI, in a library of their own: the benchmark's FP64 FMA
+# probe and the device side of the test of the table-driven math routines
+PROBE_SRCS = [os.path.join(CSRC, "probe", f) for f in ("fp64_fma_probe.cu", "math_probe.cu")]
 PROBE_LIB = os.path.join(HERE, "libpf_fp64_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -41,7 +42,7 @@ def _deps():
 
 
 def stale() -> bool:
-    for lib, deps in ((LIB, sources() + _deps()), (PROBE_LIB, [PROBE_SRC])):
+    for lib, deps in ((LIB, sources() + _deps()), (PROBE_LIB, PROBE_SRCS + _deps())):
         if not os.path.exists(lib):
             return True
         t = os.path.getmtime(lib)
@@ -56,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     probe_tmp = PROBE_LIB + f".tmp{os.getpid()}"
-    probe = subprocess.Popen([nvcc, *ARCH, *FLAGS, "-shared", PROBE_SRC, "-o", probe_tmp],
+    probe = subprocess.Popen([nvcc, *ARCH, *FLAGS, "-shared", *PROBE_SRCS, "-o", probe_tmp],
                              stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     procs = []
     objs = []
@@ -78,7 +79,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose or probe.returncode != 0:
         sys.stderr.write(out.decode(errors="replace"))
     if probe.returncode != 0:
-        failed.append(PROBE_SRC)
+        failed.append(" ".join(PROBE_SRCS))
     if failed:
         raise RuntimeError("nvcc failed on: " + ", ".join(failed))
     os.replace(probe_tmp, PROBE_LIB)

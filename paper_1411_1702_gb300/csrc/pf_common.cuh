@@ -15,6 +15,7 @@
 #include <math_constants.h>
 
 #include "../../include/pf.h"
+#include "pf_math.cuh"
 
 namespace pfg {
 
@@ -192,13 +193,19 @@ __device__ __forceinline__ double uniform53(uint32_t a, uint32_t b) {
   return (double)bits * 0x1.0p-53;
 }
 
-// Two standard normals from one Philox block by Box-Muller (Box & Muller 1958).
+// Two standard normals from one Philox block by Box-Muller (Box & Muller
+// 1958): r = sqrt(-2 log(1 - u1)), (z0, z1) = r (cos 2 pi u2, sin 2 pi u2)
+// for the 53-bit uniforms u1 = k1 2^-53, u2 = k2 2^-53 of uniform53.  1 - u1
+// = (2^53 - k1) 2^-53 is exact; the logarithm and the angle's sine and cosine
+// are the table-driven ones of pf_math.cuh (about 28 FP64 instructions fewer
+// a pair than the library routines).
 __device__ __forceinline__ void normal_pair(const U4& w, double& z0, double& z1) {
-  const double u1 = uniform53(w.x, w.y);
-  const double u2 = uniform53(w.z, w.w);
-  const double r = sqrt(-2.0 * log(1.0 - u1));
+  const uint64_t k1 = ((uint64_t)(w.x >> 5) << 26) | (uint64_t)(w.y >> 6);
+  const uint64_t k2 = ((uint64_t)(w.z >> 5) << 26) | (uint64_t)(w.w >> 6);
+  const double v = (double)((1ULL << 53) - k1) * 0x1.0p-53;
+  const double r = sqrt(-2.0 * pfm::log_pos(v));
   double sn, cs;
-  sincospi(2.0 * u2, &sn, &cs);
+  pfm::sincospi_k52(k2, sn, cs);
   z0 = r * cs;
   z1 = r * sn;
 }
