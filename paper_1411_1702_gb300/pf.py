@@ -116,8 +116,10 @@ def load(path: str = LIB_PATH):
         "pf_create_with_buffers": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int,
                                              C.c_double, C.POINTER(Prior), C.POINTER(Options),
                                              C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]),
-        "pf_assimilate": (C.c_int, [C.c_void_p, C.c_double, _dp]),
-        "pf_estimates": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
+        # the per-epoch calls take plain addresses: building ctypes pointer
+        # objects cost about as much host time as the calls themselves
+        "pf_assimilate": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p]),
+        "pf_estimates": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         "pf_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
         "pf_last_error": (C.c_char_p, [C.c_void_p]),
         "pf_destroy": (None, [C.c_void_p]),
@@ -322,12 +324,18 @@ class Filter:
     # ---- the calls of include/pf.h ---------------------------------------
     def pf_assimilate(self, t, y):
         y = _f64(y)
-        _check(load().pf_assimilate(self._h, float(t), _d(y)), self._h)
+        if y.size < self.m:
+            raise ValueError(f"need {self.m} observed values, got {y.size}")
+        _check(load().pf_assimilate(self._h, float(t), y.ctypes.data), self._h)
 
     def pf_estimates(self):
-        tb, Cm, xb = np.zeros(self.p), np.zeros((self.p, self.p)), np.zeros(self.d)
-        _check(load().pf_estimates(self._h, _d(tb), _d(Cm), _d(xb)), self._h)
-        return tb, Cm, xb
+        # one buffer, every entry written by the call, returned as three
+        # disjoint views (theta-bar, C, x-bar)
+        p, d = self.p, self.d
+        buf = np.empty(p + p * p + d)
+        a = buf.ctypes.data
+        _check(load().pf_estimates(self._h, a, a + 8 * p, a + 8 * (p + p * p)), self._h)
+        return buf[:p], buf[p:p + p * p].reshape(p, p), buf[p + p * p:]
 
     def pf_stats(self):
         s = Stats()
