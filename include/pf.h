@@ -152,8 +152,11 @@ typedef struct {
   uint32_t filter_id; /* fourth Philox counter word                       */
   void* stream;       /* cudaStream_t to run on; NULL = a stream the filter
                          creates and owns                                  */
-  int timing;         /* nonzero: record CUDA events around every kernel of
-                         every epoch (read them with pf_kernel_times)      */
+  int timing;         /* 0: no timing events; 1: CUDA events around every
+                         kernel of every epoch; 2: around stage 2 only, the
+                         dominant kernel (the other kernels keep their
+                         programmatic launch overlap).  Read them with
+                         pf_kernel_times.  Other values: INVALID_ARG.      */
 } pf_options;
 
 /* Create a filter and run Step 1 of Algorithm 1 (prior draws, w = 1/N,
@@ -219,9 +222,9 @@ pf_status pf_stats(const pf_filter* f, pf_stats_t* out);
  * weights, so this slot has no launch), 3 systematic resampling (with the
  * corner pass above one wave of merge tiles), 4 stage 2 (proliferate,
  * repropagate, innovation, reweight), 5 moments and commit (and the 2D
- * system's state mean).  Waits for the filter's stream,
- * then resets the accumulators.  Errors: INVALID_ARG (n < 6), STATE (timing
- * off), CUDA. */
+ * system's state mean).  With timing 2 only slot 4 is measured (the others
+ * read 0 with 0 launches).  Waits for the filter's stream, then resets the
+ * accumulators.  Errors: INVALID_ARG (n < 6), STATE (timing off), CUDA. */
 #define PF_KERNEL_SLOTS 6
 pf_status pf_kernel_times(pf_filter* f, double* ms, int64_t* launches, int n);
 

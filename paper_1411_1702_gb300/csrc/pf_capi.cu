@@ -33,10 +33,14 @@ static cudaEvent_t* take_marks(pf_filter* f) {
     f->mark_pending.push_back(m);
     return m;
   }
+  // timing 2: only the events around stage 2 (slot kPhaseStage2, marks 4 and 5)
   cudaEvent_t* m = new cudaEvent_t[kEpochKernels + 1];
   for (int i = 0; i <= kEpochKernels; ++i) {
+    m[i] = nullptr;
+    if (f->timing == 2 && i != kPhaseStage2 && i != kPhaseStage2 + 1) continue;
     if (cudaEventCreate(&m[i]) != cudaSuccess) {
-      for (int j = 0; j < i; ++j) cudaEventDestroy(m[j]);
+      for (int j = 0; j < i; ++j)
+        if (m[j]) cudaEventDestroy(m[j]);
       delete[] m;
       return nullptr;
     }
@@ -48,7 +52,8 @@ static cudaEvent_t* take_marks(pf_filter* f) {
 static void free_marks(pf_filter* f) {
   for (auto* v : {&f->mark_free, &f->mark_pending}) {
     for (cudaEvent_t* m : *v) {
-      for (int i = 0; i <= kEpochKernels; ++i) cudaEventDestroy(m[i]);
+      for (int i = 0; i <= kEpochKernels; ++i)
+        if (m[i]) cudaEventDestroy(m[i]);
       delete[] m;
     }
     v->clear();
@@ -386,6 +391,7 @@ pf_status check_create_args(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, dou
     return fail(nullptr, PF_ERR_INVALID_ARG, "unknown noise model");
   if (!(opt->kappa >= 0.0) || !std::isfinite(opt->kappa))
     return fail(nullptr, PF_ERR_INVALID_ARG, "kappa must be >= 0");
+  if (opt->timing < 0 || opt->timing > 2) return fail(nullptr, PF_ERR_INVALID_ARG, "timing must be 0, 1 or 2");
   return PF_OK;
 }
 }  // namespace pfg
@@ -461,7 +467,7 @@ pf_status filter_create(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm, double 
   f->transform = opt->transform; f->noise = opt->noise;
   f->dt = dt; f->q0 = opt->q0; f->a = opt->a; f->kappa = opt->kappa;
   f->seed = opt->seed; f->filter_id = opt->filter_id; f->N = N; f->t0 = prior->t0;
-  f->timing = opt->timing != 0;
+  f->timing = opt->timing;
   for (int i = 0; i < opt->m; ++i) { f->obs[i] = opt->obs_idx[i]; f->sigma[i] = opt->sigma[i]; }
   for (int i = 0; i < p; ++i) {
     f->prior_kind[i] = prior->kind[i]; f->prior_lo[i] = prior->lo[i]; f->prior_hi[i] = prior->hi[i];
@@ -673,9 +679,10 @@ pf_status pf_kernel_times(pf_filter* f, double* ms, int64_t* launches, int n) {
       // the scan_add slot has no launch and no event of its own (an empty
       // pair of events still costs the device about 2 us): 0, and the
       // resampling phase runs from the scan's end mark
+      const cudaEvent_t a = m[i == kPhaseResample ? kPhaseScanAdd : i], b = m[i + 1];
+      if (i == kPhaseScanAdd || !a || !b) continue;
       float t = 0.0f;
-      if (i != kPhaseScanAdd)
-        PF_CUDA(f, cudaEventElapsedTime(&t, m[i == kPhaseResample ? kPhaseScanAdd : i], m[i + 1]));
+      PF_CUDA(f, cudaEventElapsedTime(&t, a, b));
       f->kernel_ms[i] += t;
       f->kernel_launches[i] += 1;
     }

@@ -241,6 +241,18 @@ __device__ __forceinline__ double rcp_nr2(double x) {
   return fma(r, e, r);
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// the programmatic-stream-serialization attribute may be scheduled while the
+// stream's previous kernel is still running.  pdl_wait() returns once that
+// kernel has completed and its memory operations are visible (at once when
+// the launch had no such dependency), so every access of the epoch's state
+// comes after it.  pdl_trigger() lets the next such kernel be scheduled once
+// every block of this one has called it or exited; it orders nothing.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Finite test on the bit pattern (integer pipe, no FP64 compare).
 __device__ __forceinline__ bool finite_bits(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);

@@ -72,7 +72,7 @@ struct pf_filter {
   std::vector<pfg::HistoryState> series_after;  // history after epoch k of the series
   pfg::HistoryState series_start{};
   // per-kernel timing (pf_options.timing)
-  bool timing = false;
+  int timing = 0;  // pf_options.timing: 0 off, 1 every kernel, 2 stage 2 only
   std::vector<cudaEvent_t*> mark_free;     // sets of kEpochKernels + 1 events
   std::vector<cudaEvent_t*> mark_pending;  // recorded, not yet read
   double kernel_ms[pfg::kEpochKernels] = {0};

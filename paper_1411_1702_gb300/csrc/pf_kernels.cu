@@ -256,6 +256,7 @@ __device__ __forceinline__ void stage1_body(const FilterDev& fd, const EpochPara
     if (!finite_bits(lg)) lg = -CUDART_INF;
     fd.lg[n] = lg;
   }
+  pdl_trigger();
   stage1_tail(fd, ep->epoch, lg, vb, vg, s_red, s_flag);
 }
 
@@ -382,6 +383,7 @@ __device__ __forceinline__ void stage2_body(const FilterDev& fd, const EpochPara
     for (int i = 0; i < P; ++i) dst.phi[i * N + n] = ph[i];
     dst.lw[n] = lwn;
   }
+  pdl_trigger();
   stage2_tail(fd, epoch, lwn, bad, vb, vg, s_red, s_flag);
 }
 
@@ -507,6 +509,7 @@ __device__ __forceinline__ void moments_body(const FilterDev& fd, int is_init, i
     for (int i = 0; i < D; ++i) acc[Lay::kSx + i] = fma(e, nw.x[i * N + n], acc[Lay::kSx + i]);
   }
   block_sum_vec<NV>(acc, s_part, fd.part + (int64_t)vb * fd.nrec);
+  pdl_trigger();
   if (!elect_last_block(fd.ticket + 3, s_flag, (unsigned)vg)) return;
   // the vg partial records: thread (j, k) adds value k of records j, j + G,
   // ... (G groups of NV threads; loads issued eight at a time), then NV
@@ -626,15 +629,19 @@ __global__ void __launch_bounds__(kSmallThreads) k_stage1(const __grid_constant_
   extern __shared__ double s_dyn[];
   __shared__ double s_red[32];
   __shared__ int s_flag;
-  if (fd.ctrl->status != PF_OK) return;
+  // the parameter block is written only by copies before the epoch's first
+  // launch, so its substep table is staged before the wait
   StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
   load_steps(s_sc, ep, ep->S);
+  pdl_wait();
+  if (fd.ctrl->status != PF_OK) return;
   stage1_body<M, F>(fd, ep, blockIdx.x, gridDim.x, s_sc, s_red, &s_flag);
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_tile(const __grid_constant__ FilterDev fd) {
   __shared__ double s_warp[33];
   __shared__ int s_flag;
+  pdl_wait();
   if (fd.ctrl->status != PF_OK) return;
   scan_tile_body(fd, blockIdx.x, gridDim.x, s_warp, &s_flag);
 }
@@ -643,6 +650,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tile(const __grid_constan
 // into the per-block scratch.
 __global__ void __launch_bounds__(256) k_rs_corners(const __grid_constant__ FilterDev fd,
                                                    const EpochParams* __restrict__ ep) {
+  pdl_wait();
   if (fd.ctrl->status != PF_OK) return;
   rs_corners_core(cum_tiles(fd), fd.N, resample_u(fd, ep),
                   ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, reinterpret_cast<int32_t*>(fd.blk));
@@ -652,6 +660,7 @@ __global__ void __launch_bounds__(kResampleThreads, 4) k_resample(const __grid_c
                                                                const EpochParams* __restrict__ ep) {
   __shared__ RsShared sh;
   __shared__ double s_chol[kPMax * kPMax];
+  pdl_wait();
   if (fd.ctrl->status != PF_OK) return;
   const int32_t* corners = rs_two_phase(fd.N, fd.sms) ? reinterpret_cast<const int32_t*>(fd.blk) : nullptr;
   resample_body(fd, ep, blockIdx.x, sh, s_chol, corners);
@@ -663,9 +672,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_stage2(const __grid_constant_
   extern __shared__ double s_dyn[];
   __shared__ double s_red[32];
   __shared__ int s_flag;
-  if (fd.ctrl->status != PF_OK) return;
   StepCoef* s_sc = reinterpret_cast<StepCoef*>(s_dyn);
   load_steps(s_sc, ep, ep->S);
+  pdl_wait();
+  if (fd.ctrl->status != PF_OK) return;
   stage2_body<M, F>(fd, ep, blockIdx.x, gridDim.x, s_sc, s_red, &s_flag);
 }
 
@@ -676,6 +686,7 @@ __global__ void __launch_bounds__(kMomentThreads) k_moments(const __grid_constan
   __shared__ double s_part[kMomentShared<NV>];
   __shared__ double s_tot[NV];
   __shared__ int s_flag;
+  pdl_wait();
   if (fd.ctrl->status != PF_OK) return;
   moments_body<D, P>(fd, is_init, blockIdx.x, gridDim.x, s_part, s_tot, &s_flag);
 }
@@ -937,6 +948,25 @@ static void batch_stage_kernels(int lmm, BatchStageKernel& k1, BatchStageKernel&
   k2 = k_batch_stage<M, 2, kFamBdf12>;
 }
 
+// Launch kernel k on st with programmatic stream serialization: its blocks may
+// be scheduled while the stream's previous kernel drains, and the kernel's
+// pdl_wait() orders its accesses after that kernel's.
+template <typename... P, typename... A>
+static cudaError_t launch_pdl(void (*k)(P...), unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t st, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <class M>
 static cudaError_t launch_epoch_t(const FilterDev& fd, const EpochParams* ep, int S,
                                   cudaStream_t st, cudaEvent_t* marks) {
@@ -947,20 +977,28 @@ static cudaError_t launch_epoch_t(const FilterDev& fd, const EpochParams* ep, in
   const unsigned g_small = stage_grid(N, fd.sms);
   const int t_small = stage_threads(N, fd.sms);
   auto mark = [&](int i) {
-    if (marks) cudaEventRecord(marks[i], st);
+    if (marks && marks[i]) cudaEventRecord(marks[i], st);
+  };
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
   };
   mark(0);
-  k1<<<g_small, t_small, smem, st>>>(fd, ep);
+  ok(launch_pdl(k1, g_small, t_small, smem, st, fd, ep));
   mark(1);
-  k_scan_tile<<<(unsigned)phase_blocks(kPhaseScanTile, M::ODE, N, fd.sms), kScanThreads, 0, st>>>(fd);
+  ok(launch_pdl(k_scan_tile, (unsigned)phase_blocks(kPhaseScanTile, M::ODE, N, fd.sms), kScanThreads, 0,
+                st, fd));
   mark(2);  // (marks[3] is not recorded: the scan_add slot is empty)
-  if (rs_two_phase(N, fd.sms)) k_rs_corners<<<rs_corner_blocks(N), 256, 0, st>>>(fd, ep);
-  k_resample<<<(unsigned)phase_blocks(kPhaseResample, M::ODE, N, fd.sms), kResampleThreads, 0, st>>>(fd, ep);
+  if (rs_two_phase(N, fd.sms)) ok(launch_pdl(k_rs_corners, (unsigned)rs_corner_blocks(N), 256, 0, st, fd, ep));
+  ok(launch_pdl(k_resample, (unsigned)phase_blocks(kPhaseResample, M::ODE, N, fd.sms), kResampleThreads, 0,
+                st, fd, ep));
   mark(4);
-  k2<<<g_small, t_small, smem, st>>>(fd, ep);
+  ok(launch_pdl(k2, g_small, t_small, smem, st, fd, ep));
   mark(5);
-  k_moments<M::D, M::P><<<phase_blocks(kPhaseMoments, M::ODE, N, fd.sms), kMomentThreads, 0, st>>>(fd, 0);
+  ok(launch_pdl(k_moments<M::D, M::P>, (unsigned)phase_blocks(kPhaseMoments, M::ODE, N, fd.sms),
+                kMomentThreads, 0, st, fd, 0));
   mark(6);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -970,7 +1008,7 @@ static cudaError_t launch_epoch_bruss(const FilterDev& fd, const EpochParams* ep
   const int64_t N = fd.N;
   const int ode = PF_ODE_BRUSSELATOR1D;
   auto mark = [&](int i) {
-    if (marks) cudaEventRecord(marks[i], st);
+    if (marks && marks[i]) cudaEventRecord(marks[i], st);
   };
   cudaError_t e;
   mark(0);
@@ -997,7 +1035,7 @@ static cudaError_t launch_epoch_ad(const FilterDev& fd, const EpochParams* ep, i
   const int64_t N = fd.N;
   const int ode = PF_ODE_ADVDIFF2D;
   auto mark = [&](int i) {
-    if (marks) cudaEventRecord(marks[i], st);
+    if (marks && marks[i]) cudaEventRecord(marks[i], st);
   };
   cudaError_t e;
   mark(0);

@@ -208,6 +208,7 @@ __device__ __forceinline__ void scan_tile_core(const ScanArgs& a, int vb, int vg
     if (j < items && k < a.N) a.c[k] = max_nonneg(v[j], floor_prev);
   }
   if (threadIdx.x == 0) a.tile[vb] = tile_last;
+  pdl_trigger();
   if (elect_last_block(a.ticket, s_flag, (unsigned)vg))
     scan_offsets_core(a.tile, vg, a.boff, a.pmax, s_warp, a.c_total);
 }

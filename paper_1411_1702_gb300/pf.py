@@ -261,7 +261,7 @@ class Filter:
         op = Options(float(a), int(newton_iters), int(spacing), int(substeps), float(q0),
                      int(history), int(transform), len(obs_idx), obs, int(noise), _d(sig),
                      float(kappa), int(seed), int(filter_id), C.c_void_p(stream) if stream else None,
-                     1 if timing else 0)
+                     int(timing))  # False/0 off, True/1 every kernel, 2 stage 2 only
         h = C.c_void_p()
         if shard is not None:
             # the slots [first, first + N) of a sharded filter of n_all particles
