@@ -152,13 +152,13 @@ STAGE2_KERNEL["michaelis"] = "k_stage2<Michaelis, 0>"
 # DRAM bytes (read + write) of one stage-2 launch from an ncu capture of the
 # same command on a GB300 (profiles/ names each capture); None where no capture
 # of the kernel as it stands exists.
-STAGE2_TRAFFIC = {"robertson": 11549440 + 0,
+STAGE2_TRAFFIC = {"robertson": 11549184 + 0,
                   "brusselator": 11237054976 + 10729370624,
                   "advdiff20": 3076608 + 756736,
                   "advdiff40": 177258240 + 138143744,
                   "michaelisBDF2": 4356864 + 0,
-                  "michaelisAM3": 4591104 + 0,
-                  "michaelisAB3": 4452096 + 0}
+                  "michaelisAM3": 4591616 + 0,
+                  "michaelisAB3": 4453888 + 0}
 # The paper's own number for the same workload, where it has one: Table 3's
 # 2D advection-diffusion runs (BDF2, h = 0.1, N = 5000, 30 unit intervals,
 # 8 MATLAB workers on an i7-3820), converted to particle-LMM-steps/s at 600
