@@ -67,6 +67,7 @@ def _create(pf, **over):
     dict(lmm=12), dict(a=0.0), dict(a=1.5),
     dict(newton_iters=0), dict(obs_idx=[5]), dict(sigma=[0.0, 0.01]), dict(substeps=0),
     dict(substeps=100000), dict(prior_lo=[-1.0, 1.0, 1.0]), dict(kappa=-1.0), dict(spacing=7),
+    dict(timing=3), dict(timing=-1),
 ])
 def test_invalid_arguments_rejected_before_gpu(pf, bad):
     with pytest.raises(pf.PfError) as ei:
