@@ -207,7 +207,10 @@ typedef struct {
   int64_t unique_parents;/* distinct indices of the last resampling        */
   int64_t nonfinite;     /* particles given zero weight in the last epoch  */
   double theta_mean[8];  /* weighted mean of theta (model space)           */
-  double last_epoch_ms;  /* device time of the last synchronous epoch      */
+  double last_epoch_ms;  /* device time of the last synchronous epoch (of
+                            pf_assimilate: with its parameter upload and
+                            read-back when timing is off and the epoch runs
+                            as one graph)                                   */
   int64_t h2d_bytes;     /* host-to-device bytes copied since creation     */
   int64_t d2h_bytes;     /* device-to-host bytes copied since creation     */
   double ess_stage1;     /* (sum g)^2 / sum g^2 of the last epoch's first-stage

@@ -571,6 +571,8 @@ void pf_destroy(pf_filter* f) {
     if (f->xbar_host) cudaFreeHost(f->xbar_host);
   }
   free_marks(f);
+  for (cudaGraphExec_t x : f->epoch_exec)
+    if (x) cudaGraphExecDestroy(x);
   if (f->ev0) cudaEventDestroy(f->ev0);
   if (f->ev1) cudaEventDestroy(f->ev1);
   if (f->ready) cudaEventDestroy(f->ready);
@@ -580,6 +582,54 @@ void pf_destroy(pf_filter* f) {
 
 const char* pf_last_error(const pf_filter* f) {
   return f ? f->err.c_str() : g_thread_error.c_str();
+}
+
+static cudaError_t capture_epoch(pf_filter* f, int S, size_t bytes, cudaGraphExec_t* out);
+
+// Returns the graph for S (captured into the next slot if none has it) or
+// NULL when the stream cannot be captured.
+static cudaGraphExec_t epoch_graph(pf_filter* f, int S, size_t bytes) {
+  for (int i = 0; i < pf_filter::kEpochGraphs; ++i)
+    if (f->epoch_exec[i] && f->epoch_exec_S[i] == S) return f->epoch_exec[i];
+  const int slot = f->epoch_exec_next;
+  f->epoch_exec_next = (slot + 1) % pf_filter::kEpochGraphs;
+  if (f->epoch_exec[slot]) {
+    cudaGraphExecDestroy(f->epoch_exec[slot]);
+    f->epoch_exec[slot] = nullptr;
+    f->epoch_exec_S[slot] = 0;
+  }
+  cudaGraphExec_t x = nullptr;
+  if (capture_epoch(f, S, bytes, &x) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  f->epoch_exec[slot] = x;
+  f->epoch_exec_S[slot] = S;
+  return x;
+}
+
+// pf_assimilate's epoch as one graph: upload of the parameter block (bytes),
+// the epoch's kernels, and the read-back of x-bar and the control block.  One
+// graph launch replaces seven stream calls; the epoch's timing events are
+// recorded around it, on the stream.
+static cudaError_t capture_epoch(pf_filter* f, int S, size_t bytes, cudaGraphExec_t* out) {
+  cudaError_t e = cudaStreamBeginCapture(f->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t le = cudaMemcpyAsync(f->ep_dev, f->ep_host, bytes, cudaMemcpyHostToDevice, f->stream);
+  if (le == cudaSuccess) le = launch_epoch(f->ode, f->fd, f->ep_dev, S, f->stream, nullptr);
+  if (le == cudaSuccess)
+    le = cudaMemcpyAsync(f->xbar_host, f->fd.xbar, sizeof(double) * f->d, cudaMemcpyDeviceToHost,
+                         f->stream);
+  if (le == cudaSuccess)
+    le = cudaMemcpyAsync(f->ctrl_host, f->fd.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, f->stream);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(f->stream, &g);
+  if (le == cudaSuccess) le = e;
+  *out = nullptr;
+  if (le == cudaSuccess) le = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (le != cudaSuccess) *out = nullptr;
+  return le;
 }
 
 pf_status pf_assimilate(pf_filter* f, double t_k, const double* y_k) {
@@ -596,22 +646,40 @@ pf_status pf_assimilate(pf_filter* f, double t_k, const double* y_k) {
   if (S < 1) return fail(f, PF_ERR_INVALID_ARG, "substep grid of the interval is invalid");
   f->est_fresh = false;
   const size_t bytes = kEpochHeaderBytes + sizeof(StepCoef) * (size_t)S;
-  PF_CUDA(f, cudaMemcpyAsync(f->ep_dev, f->ep_host, bytes, cudaMemcpyHostToDevice, f->stream));
-  f->h2d_bytes += (int64_t)bytes;
-  PF_CUDA(f, cudaEventRecord(f->ev0, f->stream));
-  PF_CUDA(f, launch_epoch(f->ode, f->fd, f->ep_dev, S, f->stream, take_marks(f)));
-  PF_CUDA(f, cudaEventRecord(f->ev1, f->stream));
-  // x-bar comes back with the control block in the same wait, so estimates
-  // asked for right after need no second round trip
-  if (f->xbar_host) {
-    PF_CUDA(f, cudaMemcpyAsync(f->xbar_host, f->fd.xbar, sizeof(double) * f->d,
-                               cudaMemcpyDeviceToHost, f->stream));
-    f->d2h_bytes += (int64_t)(sizeof(double) * f->d);
+  // the whole epoch as one graph launch where the host blocks are pinned and
+  // no per-kernel events are wanted; a stream that cannot be captured (the
+  // legacy default stream) takes the calls one by one
+  bool graphed = false;
+  if (!f->timing && f->xbar_host && !f->pool && f->stream) {
+    const cudaGraphExec_t x = epoch_graph(f, S, bytes);
+    if (x) {
+      PF_CUDA(f, cudaEventRecord(f->ev0, f->stream));
+      PF_CUDA(f, cudaGraphLaunch(x, f->stream));
+      PF_CUDA(f, cudaEventRecord(f->ev1, f->stream));
+      PF_CUDA(f, cudaStreamSynchronize(f->stream));
+      graphed = true;
+    }
   }
-  pf_status st = read_ctrl(f);
-  if (st != PF_OK) return st;
+  f->h2d_bytes += (int64_t)bytes;
+  if (f->xbar_host) f->d2h_bytes += (int64_t)(sizeof(double) * f->d);
+  if (graphed) {
+    f->d2h_bytes += sizeof(Ctrl);
+  } else {
+    PF_CUDA(f, cudaMemcpyAsync(f->ep_dev, f->ep_host, bytes, cudaMemcpyHostToDevice, f->stream));
+    PF_CUDA(f, cudaEventRecord(f->ev0, f->stream));
+    PF_CUDA(f, launch_epoch(f->ode, f->fd, f->ep_dev, S, f->stream, take_marks(f)));
+    PF_CUDA(f, cudaEventRecord(f->ev1, f->stream));
+    // x-bar comes back with the control block in the same wait, so estimates
+    // asked for right after need no second round trip
+    if (f->xbar_host)
+      PF_CUDA(f, cudaMemcpyAsync(f->xbar_host, f->fd.xbar, sizeof(double) * f->d,
+                                 cudaMemcpyDeviceToHost, f->stream));
+    pf_status st = read_ctrl(f);
+    if (st != PF_OK) return st;
+  }
   float ms = 0.0f;
   if (cudaEventElapsedTime(&ms, f->ev0, f->ev1) == cudaSuccess) f->last_ms = ms;
+  else cudaGetLastError();  // a diagnostic only: leave no error behind
   const int dst = f->ctrl_host->status;
   if (dst != PF_OK) {
     pf_status cs = clear_device_status(f);

@@ -61,6 +61,13 @@ struct pf_filter {
   double* xbar_host = nullptr;           // pinned mirror of x-bar (not pooled)
   bool est_fresh = false;                 // ctrl_host and xbar_host hold the committed estimates
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // pf_assimilate's epoch as one CUDA graph (pinned host blocks, timing off):
+  // the parameter upload, the kernels and the two read-backs, captured for a
+  // substep count S and launched whenever an epoch has that S (a few S kept)
+  static constexpr int kEpochGraphs = 4;
+  cudaGraphExec_t epoch_exec[kEpochGraphs] = {};
+  int epoch_exec_S[kEpochGraphs] = {};
+  int epoch_exec_next = 0;
   cudaEvent_t ready = nullptr;            // pooled: the work queued on `stream` is done
   // committed history (host view)
   pfg::HistoryState hist{};

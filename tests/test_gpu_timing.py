@@ -61,3 +61,29 @@ def test_timing_level_out_of_range_is_rejected(pf):
         with pytest.raises(pf.PfError) as ei:
             pf.Filter.from_workload(w, timing=bad)
         assert ei.value.status == pf.PF_ERR_INVALID_ARG
+
+
+def test_assimilate_graph_equals_direct_launches(pf):
+    """pf_assimilate runs its epoch as one captured graph when timing is off
+    (a few substep counts kept) and as separate calls with timing on: the
+    same bits either way, across intervals of seven different lengths (more
+    substep counts than the graphs kept, so some are captured again)."""
+    w = W.get("linear2", N=3000, T=12)
+    gaps = [0.05, 0.1, 0.02, 0.15, 0.05, 0.03, 0.2, 0.1, 0.04, 0.02, 0.05, 0.1]
+    w = w.with_(t_obs=np.cumsum(gaps))
+    fg, fd = pf.Filter.from_workload(w, timing=0), pf.Filter.from_workload(w, timing=1)
+    for k in range(w.T):
+        for f in (fg, fd):
+            f.pf_assimilate(w.t_obs[k], w.y_obs[k])
+        eg, ed = fg.pf_estimates(), fd.pf_estimates()
+        for a, b in zip(eg, ed):
+            assert np.array_equal(a, b), k
+        sg, sd = fg.pf_stats(), fd.pf_stats()
+        assert sg["epochs"] == sd["epochs"] == k + 1
+        assert sg["h2d_bytes"] == sd["h2d_bytes"] and sg["d2h_bytes"] == sd["d2h_bytes"]
+        assert sg["last_epoch_ms"] > 0.0
+    e0, e1 = fg.pf_get_ensemble(), fd.pf_get_ensemble()
+    for key in e0:
+        assert np.array_equal(e0[key], e1[key]), key
+    fg.close()
+    fd.close()
