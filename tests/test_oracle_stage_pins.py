@@ -20,7 +20,7 @@ log-likelihood dropped, |x| in place of |y| in the relative noise) fails:
   log w = log pi(y | x) - ll1[l];
 * Step 5 normalisation and Step 6 moments with unequal weights: against
   np.average and np.cov(aweights=w, bias=True);
-* Step 4a as a whole (the survey's proliferation pin): after shrinkage and
+* Step 4a as a whole (the proliferation pin): after shrinkage and
   the kernel draw the ensemble covariance is a^2 C + s^2 C = C, within Monte
   Carlo standard errors.
 """
