@@ -190,9 +190,11 @@ pf_status pf_create_with_buffers(pf_ode ode, int d, int p, int64_t N, pf_lmm lmm
  * observation time: Steps 2-6 of Algorithm 1 (shrink, propagate, first-stage
  * weights, systematic resampling, proliferation, repropagation with the
  * local-error innovation, reweighting, moments).  Synchronous: returns after
- * the epoch is committed.  Errors: INVALID_ARG (non-finite y, bad t_k, substep
- * count out of range), DEGENERATE (all first- or second-stage weights zero;
- * nothing committed), CUDA. */
+ * the epoch is committed.  With timing off, the upload, the epoch's kernels and
+ * the read-back run as one CUDA graph launch on the filter's stream (a graph is
+ * captured the first time a substep count is seen; a few are kept).  Errors:
+ * INVALID_ARG (non-finite y, bad t_k, substep count out of range), DEGENERATE
+ * (all first- or second-stage weights zero; nothing committed), CUDA. */
 pf_status pf_assimilate(pf_filter* f, double t_k, const double* y_k);
 
 /* Weighted estimates of the committed ensemble (Step 6): theta_bar (p, in phi

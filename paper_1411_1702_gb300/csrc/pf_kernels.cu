@@ -21,7 +21,9 @@
 // of filters of any size.  A filter's reduction trees depend only on its N,
 // never on where its tiles land, so a filter gives bit-identical results alone
 // and in a batch.  Every phase returns at once if an earlier epoch of its
-// filter failed (Ctrl::status), so epochs can be enqueued ahead.
+// filter failed (Ctrl::status), so epochs can be enqueued ahead.  A filter's
+// own epoch (linear2, Robertson, M1) launches its kernels with programmatic
+// dependent launch: each waits (pdl_wait) before touching the epoch's state.
 #include <cstring>
 
 #include "pf_common.cuh"
