@@ -9,12 +9,16 @@ K = 2 Newton iterations, FP64.  One particle-LMM-step is one implicit substep
 
 value     device-resident inputs (the whole observation series uploaded once),
           CUDA-event time of each step on the filter's stream, L2 flushed
-          (256 MiB write) before every step, summed over K steps.
+          (256 MiB write) before every step, summed over K steps; the filter
+          records its own events around stage 2 only.
 e2e       the same metric through the C ABI with host buffers: pf_assimilate
           (host y_k, parameter upload) + pf_estimates (host read-back), wall
           time per step.
 roofline  the dominant kernel (stage 2) against the FP64 ALU peak.
 cpu_baseline / --impl reference: the CPU oracle on the host cores.
+The default run adds the batched workload (256 filters of 2^10..2^17
+particles, and 256 of 2^10..2^11) against per-filter launches, and the
+serving trace's latency with a sweep of loads below capacity.
 
 Multi-GPU (torchrun): independent replicas (one filter per rank, different
 seeds); value = all ranks' particle-steps / the slowest rank's time.
@@ -168,6 +172,8 @@ PAPER_BASELINE = {"advdiff20": 3.0e6 / 7.20e3, "advdiff40": 3.0e6 / 3.39e4}
 # for that size).
 TRAFFIC_N = {"robertson": 131072, "brusselator": 65536, "advdiff20": 5000, "advdiff40": 5000,
              "michaelisBDF2": 50000, "michaelisAM3": 50000, "michaelisAB3": 50000}
+# the N range of the default run's second batched comparison (small filters)
+SMALL_BATCH_LOG2N = (10.0, 11.0)
 # epochs of the per-kernel breakdown pass that follows the timed region
 BREAKDOWN_EPOCHS = 60
 # Algorithmic DRAM bytes per particle of the scan and resampling launches:
@@ -572,10 +578,15 @@ def run_ours(args, w):
         # the metric's other halves on the same GPU: the batched workload
         # against per-filter launches, and serving latency
         b = batched_result(args)
-        line["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "steps", "config",
-                                             "clocks", "e2e", "per_filter_sync",
-                                             "per_filter_streams", "speedup_vs_per_filter_sync",
-                                             "speedup_vs_per_filter_streams", "autotune")}
+        keys = ("value", "unit", "ms_per_step", "steps", "config", "clocks", "e2e",
+                "per_filter_sync", "per_filter_streams", "speedup_vs_per_filter_sync",
+                "speedup_vs_per_filter_streams", "autotune")
+        line["batched"] = {k: b[k] for k in keys}
+        # the same comparison where one filter's launches underfill the GPU:
+        # 256 filters of 2^10 to 2^11 particles
+        small = argparse.Namespace(**dict(vars(args), batch_log2n=list(SMALL_BATCH_LOG2N)))
+        bs = batched_result(small)
+        line["batched_small_filters"] = {k: bs[k] for k in keys}
         sv = serving_result(args)
         line["serving"] = {k: sv[k] for k in ("value", "unit", "config", "clocks", "server",
                                               "server_one_lane", "serial_per_filter",
@@ -634,7 +645,8 @@ def batched_result(args):
     from paper_1411_1702_gb300 import workloads as W
     dist, rank, world = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    ws_all = W.batched(args.batch_filters)
+    lo2, hi2 = args.batch_log2n
+    ws_all = W.batched(args.batch_filters, n_min_log2=lo2, n_max_log2=hi2)
     # with several ranks, the filters are sharded (no collective on the data
     # path); each keeps its global filter id, so its results do not change
     # (work: the stage-2 flops of the whole series, as the roofline counts them)
@@ -747,7 +759,7 @@ def batched_result(args):
         "metric": METRIC, "mode": "batched", "value": value, "unit": UNIT, "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": dev_ms / K, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"batched: {n} filters, N = round(2^U[10,17]) "
+        "config": {"workload": f"batched: {n} filters, N = round(2^U[{lo2:g},{hi2:g}]) "
                                f"(total {sum(w.N for w in ws_all)}), linear2/robertson 50/50, "
                                "one round per step", "filters": n,
                    "robertson_filters": sum(w.ode == W.ROBERTSON for w in ws_all),
@@ -1085,6 +1097,8 @@ def main(argv=None):
                              "advdiff40", "michaelis"] + ["michaelis" + n for n in W_LMM_NAMES] + [
                              "batched", "serving"])
     ap.add_argument("--batch-filters", type=int, default=256)
+    ap.add_argument("--batch-log2n", type=float, nargs=2, default=[10.0, 17.0],
+                    help="the batched filters' N = round(2^U[lo, hi])")
     ap.add_argument("--serve-sessions", type=int, default=64)
     ap.add_argument("--serve-obs", type=int, default=0,
                     help="observations per session (0: the problem's T)")
