@@ -87,21 +87,22 @@ def _advdiff_flops_interval(K, d):
 
 def _michaelis_flops(lmm):
     """M1 (Sec. 2.1), d = 3: one Newton iteration (two flux reciprocals, the
-    lower-triangular substitution with two pivot reciprocals; the third row
-    folded onto its pivot) is 39 flops, one evaluation of f 17.  Per substep,
-    by family: BDF1/BDF2 predictor 15, history 9, input 2, pivot and third-row
-    constants 6, Milne 12; BDF3 adds the slope f(t_n, x_n) and its term (73 in
-    all); Adams-Moulton: AB predictor 18, AM history 12, input 2, constants 6,
-    f(x_{n+1}) 17, Milne 12; Adams-Bashforth: predictor 18, history 12, f 17,
-    Milne against AM 18 (no Newton)."""
+    fluxes as g V - (g V k) q, the residual by additions, the lower-triangular
+    substitution with two pivot reciprocals) is 30 flops, one evaluation of f
+    17.  Per substep, by family: BDF1/BDF2 predictor 15, history 9, input 2,
+    pivot, flux and residual constants 14, Milne 12; BDF3 adds the slope
+    f(t_n, x_n) and its term (81 in all); Adams-Moulton: AB predictor 18, AM
+    history 12, input 2, constants 14, f(x_{n+1}) 17, Milne 12;
+    Adams-Bashforth: predictor 18, history 12, f 17, Milne against AM 18 (no
+    Newton)."""
     fam = lmm // 10
     if fam == 2:
         return lambda K, d: 65
     if fam == 1:
-        return lambda K, d: 67 + 39 * K
+        return lambda K, d: 75 + 30 * K
     if lmm == 3:
-        return lambda K, d: 73 + 39 * K
-    return lambda K, d: 44 + 39 * K
+        return lambda K, d: 81 + 30 * K
+    return lambda K, d: 52 + 30 * K
 
 
 # Exact FP64 operations of one steady-state particle-substep of the oracle's

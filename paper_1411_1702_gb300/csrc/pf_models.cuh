@@ -145,12 +145,17 @@ struct Michaelis {
                                                 int K) {
     const double opl = fma(g, kLambda, 1.0);
     const double gl = rcp_nr2(opl);
-    // the third row's constant part, r3 + g lambda c0, once per substep
-    const double r2 = fma(g * kLambda, kC0, r[2]);
-    // the fluxes' constant factors, once per substep: with q = 1/(x + k),
-    // g j = (g V) (q x) and g a = (g V k) q^2
+    // the fluxes with q = 1/(x + k): g j = g V x q = g V - u, u = (g V k) q,
+    // and g a = (g V k) q^2 = u q.  The residual's constant parts, once per
+    // substep:
+    //   G0 = (y[0] + [g V1 - r[0]]) - u1
+    //   G1 = ((y[1] + [g V2 - g V1 - r[1]]) + u1) - u2
+    //   G2 = (1 + g lambda) y[2] - [r[2] + g lambda c0 + g V2] + u2
     const double gv1 = g * T.v1, gv2 = g * T.v2;
     const double gv1k1 = gv1 * T.k1, gv2k2 = gv2 * T.k2;
+    const double c0 = gv1 - r[0];
+    const double c1 = (gv2 - gv1) - r[1];
+    const double c2 = -(fma(g * kLambda, kC0, r[2]) + gv2);
     // one iteration; the pivots' reciprocals are refined only in the last.
     // The flux reciprocals enter the residual: the last iteration refines
     // them twice (its residual is the final one), the earlier ones once,
@@ -158,13 +163,12 @@ struct Michaelis {
     auto step = [&](const bool last) {
       const double s1 = y[0] + T.k1, s2 = y[1] + T.k2;
       const double q1 = last ? rcp_nr2(s1) : rcp_nr(s1), q2 = last ? rcp_nr2(s2) : rcp_nr(s2);
-      const double w1 = q1 * y[0], w2 = q2 * y[1];      // j / V
-      const double ga = gv1k1 * (q1 * q1), gb = gv2k2 * (q2 * q2);
+      const double u1 = gv1k1 * q1, u2 = gv2k2 * q2;
+      const double ga = u1 * q1, gb = u2 * q2;
       // G = y - r - gamma f_aut(y)
-      const double G0 = fma(gv1, w1, y[0] - r[0]);
-      const double G1 = fma(-gv1, w1, fma(gv2, w2, y[1] - r[1]));
-      // (1 + g lambda) y3 - (r3 + g lambda c0) - g j2, the same row folded
-      const double G2 = fma(-gv2, w2, fma(opl, y[2], -r2));
+      const double G0 = (y[0] + c0) - u1;
+      const double G1 = ((y[1] + c1) + u1) - u2;
+      const double G2 = fma(opl, y[2], c2) + u2;
       const double d0 = -G0 * rcp_newton(1.0 + ga, last);
       const double d1 = fma(ga, d0, -G1) * rcp_newton(1.0 + gb, last);
       const double d2 = fma(gb, d1, -G2) * gl;
