@@ -161,9 +161,9 @@ STAGE2_TRAFFIC = {"robertson": 11549184 + 0,
                   "brusselator": 11237054976 + 10729370624,
                   "advdiff20": 3076608 + 756736,
                   "advdiff40": 177258240 + 138143744,
-                  "michaelisBDF2": 4356864 + 0,
-                  "michaelisAM3": 4591616 + 0,
-                  "michaelisAB3": 4453888 + 0}
+                  "michaelisBDF2": 4355584 + 0,
+                  "michaelisAM3": 4590336 + 0,
+                  "michaelisAB3": 4454144 + 0}
 # The paper's own number for the same workload, where it has one: Table 3's
 # 2D advection-diffusion runs (BDF2, h = 0.1, N = 5000, 30 unit intervals,
 # 8 MATLAB workers on an i7-3820), converted to particle-LMM-steps/s at 600
