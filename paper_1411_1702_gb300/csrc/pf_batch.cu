@@ -38,9 +38,13 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <thread>
 
@@ -122,6 +126,81 @@ double now_ms() {
 
 }  // namespace
 
+namespace {
+
+// A few host threads that build the members' parameter blocks of an epoch in
+// parallel (a block is a substep table of tens of entries: about a
+// microsecond each, which adds up for hundreds of members).  run() splits
+// [0, count) into one range per worker and one for the caller and returns
+// once all are done; it is called by one thread at a time.
+class FillPool {
+ public:
+  explicit FillPool(int workers) {
+    try {
+      for (int w = 0; w < workers; ++w) th_.emplace_back([this, w] { loop(w + 1); });
+    } catch (...) {
+      stop_all();  // the threads that did start
+      throw;
+    }
+  }
+  ~FillPool() { stop_all(); }
+  void run(int count, const std::function<void(int, int)>& fn) {
+    {
+      std::lock_guard<std::mutex> g(m_);
+      fn_ = &fn;
+      count_ = count;
+      left_ = (int)th_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    fn(lo(0), lo(1));
+    std::unique_lock<std::mutex> lk(m_);
+    done_.wait(lk, [this] { return left_ == 0; });
+    fn_ = nullptr;
+  }
+
+ private:
+  void stop_all() {
+    {
+      std::lock_guard<std::mutex> g(m_);
+      stop_ = true;
+      ++gen_;
+    }
+    cv_.notify_all();
+    for (std::thread& t : th_) t.join();
+    th_.clear();
+  }
+  int lo(int part) const { return (int)((int64_t)count_ * part / ((int)th_.size() + 1)); }
+  void loop(int part) {
+    int seen = 0;
+    std::unique_lock<std::mutex> lk(m_);
+    for (;;) {
+      cv_.wait(lk, [&] { return gen_ != seen; });
+      seen = gen_;
+      if (stop_) return;
+      const std::function<void(int, int)>* fn = fn_;
+      const int a = lo(part), b = lo(part + 1);
+      lk.unlock();
+      (*fn)(a, b);
+      lk.lock();
+      if (--left_ == 0) done_.notify_one();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex m_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int, int)>* fn_ = nullptr;
+  int count_ = 0, left_ = 0, gen_ = 0;
+  bool stop_ = false;
+};
+
+// members with an observation from which the parameter blocks are built in
+// parallel, and the pool's worker threads
+constexpr int kParallelFill = 128;
+constexpr int kFillWorkers = 3;
+
+}  // namespace
+
 struct pf_batch {
   int cap = 0;                           // slots
   std::vector<pf_filter*> slot;          // nullptr = free slot
@@ -162,6 +241,8 @@ struct pf_batch {
   std::vector<int> fl_slots, fl_depth;
   std::vector<double> fl_t;
   double fl_done_ms = 0.0;               // host time the device finished (callback)
+  std::vector<int> fl_S;                 // per slot: its epoch's S, -1 invalid, -2 idle
+  std::unique_ptr<FillPool> fill_pool;   // created at the first epoch with many members
   std::string err;
 };
 
@@ -503,13 +584,33 @@ static pf_status batch_launch(pf_batch* b, const double* t, const double* const*
   b->fl_depth.assign(cap, 0);
   b->fl_t.assign(cap, 0.0);
   int S_max = 0;
+  // each member's parameter block (slots are independent: own block, own
+  // depth), in parallel when many members have an observation
+  b->fl_S.assign(cap, -2);
+  const std::function<void(int, int)> fill = [&](int lo, int hi) {
+    for (int s = lo; s < hi; ++s) {
+      const pf_filter* F = b->slot[s];
+      if (!F || !y[s]) continue;
+      bool ok = std::isfinite(t[s]) && t[s] > F->hist.t_prev;
+      for (int i = 0; ok && i < F->m; ++i) ok = std::isfinite(y[s][i]);
+      b->fl_S[s] = ok ? fill_epoch(F, F->hist, t[s], y[s], b->params_host + s, &b->fl_depth[s]) : -1;
+    }
+  };
+  int n_obs = 0;
+  for (int s = 0; s < cap; ++s) n_obs += (b->slot[s] && y[s]) ? 1 : 0;
+  if (n_obs >= kParallelFill && !b->fill_pool && std::thread::hardware_concurrency() > kFillWorkers) {
+    try {
+      b->fill_pool.reset(new FillPool(kFillWorkers));
+    } catch (...) {
+      b->fill_pool.reset();  // no threads to be had: the blocks are built serially
+    }
+  }
+  if (n_obs >= kParallelFill && b->fill_pool) b->fill_pool->run(cap, fill);
+  else fill(0, cap);
   for (int s = 0; s < cap; ++s) {
     if (status) status[s] = PF_OK;
-    pf_filter* F = b->slot[s];
-    if (!F || !y[s]) continue;
-    bool ok = std::isfinite(t[s]) && t[s] > F->hist.t_prev;
-    for (int i = 0; ok && i < F->m; ++i) ok = std::isfinite(y[s][i]);
-    const int S = ok ? fill_epoch(F, F->hist, t[s], y[s], b->params_host + s, &b->fl_depth[s]) : -1;
+    const int S = b->fl_S[s];
+    if (S == -2) continue;
     if (S < 1) {
       if (status) status[s] = PF_ERR_INVALID_ARG;
       continue;
