@@ -200,3 +200,40 @@ def test_batched_members_match_oracle(pf):
         for m, o, w, pre in zip(members, orcs, ws, pres):
             errs = finish_epoch(m, o, w.t_obs[k], w.y_obs[k], pre, exempt_dead=True)
             assert errs["x"] <= 1e-10, (w.name, w.lmm, k, errs["x"])
+
+
+def test_many_members_parameter_blocks_built_in_parallel(pf):
+    """With 128 or more members holding an observation the batch builds their
+    parameter blocks on worker threads: 150 members (linear and Robertson,
+    ragged N, uneven observation times, one member idle every other epoch and
+    one invalid observation) are bit-identical to the same filters alone."""
+    ws = []
+    for i in range(150):
+        name = "linear2" if i % 2 else "robertson"
+        ws.append(W.get(name, N=64 + 37 * (i % 9), T=4, seed=100 + i))
+    alone = [pf.Filter.from_workload(w) for w in ws]
+    members = [pf.Filter.from_workload(w) for w in ws]
+    batch = pf.Batch(members)
+    for k in range(4):
+        ts = [w.t_obs[k] for w in ws]
+        ys = [w.y_obs[k] for w in ws]
+        idle = 7 if k % 2 else None
+        if idle is not None:
+            ys[idle] = None
+        bad = 11 if k == 2 else None
+        if bad is not None:
+            ys[bad] = np.full_like(ws[bad].y_obs[k], np.nan)
+        st = batch.pf_batch_assimilate(ts, ys)
+        for i, (a, w) in enumerate(zip(alone, ws)):
+            if i == idle:
+                assert st[i] == pf.PF_OK
+                continue
+            if i == bad:
+                assert st[i] == pf.PF_ERR_INVALID_ARG
+                continue
+            assert st[i] == pf.PF_OK, (i, st[i])
+            a.pf_assimilate(w.t_obs[k], w.y_obs[k])
+        for a, m in zip(alone, members):
+            assert _same(a, m)
+            assert a.pf_get_history() == m.pf_get_history()
+    batch.close()
